@@ -1,0 +1,179 @@
+/*
+ * ns.h -- C ABI of libns: GB300 (sm_103a) sketch-and-solve approximate null
+ * space, after Park & Nakatsukasa, "A Fast Randomized Algorithm for Computing
+ * an Approximate Null Space".
+ *
+ * The problem (Problem 2.1): given A (m x n, m >= n) and k, find W (n x k)
+ * minimising ||A W||_F over W^T W = I_k.  Algorithm 1 solves it approximately:
+ * draw a sketch S (s x m), form SA, take the SVD of SA and return its k
+ * trailing right singular vectors.  Here the SVD of SA is a Householder QR
+ * SA = QR followed by a one-sided Jacobi SVD of R (SA and R share singular
+ * values and right singular vectors, proof of Theorem 3.2).
+ *
+ * Conventions for every call:
+ *  - Matrices are column-major.  A has leading dimension lda >= m.  Sketch
+ *    outputs SA are s x n with leading dimension s.
+ *  - Every pointer argument named A, SA, Vk, sigk, save, dA, dVk, ws,
+ *    dev_status, problems or any output array is a DEVICE pointer on the
+ *    current CUDA device; sketch descriptors are HOST pointers.
+ *  - The caller owns all memory.  The library never allocates, frees or
+ *    synchronises; it enqueues kernels on `stream` (a cudaStream_t, 0 = the
+ *    legacy default stream) and returns.  Scratch space comes from the
+ *    caller's workspace `ws` of `ws_bytes` bytes (>= the size reported by the
+ *    matching *_workspace_size call, 256-byte aligned).
+ *  - Argument errors are detected on the host before any launch and returned
+ *    (NS_ERR_INVALID_ARG, NS_ERR_WORKSPACE); nothing is enqueued then.  A
+ *    failed launch returns NS_ERR_CUDA.  Numerical conditions found by the
+ *    kernels (non-finite input, Jacobi not converged, TLS without solution,
+ *    a bounded device wait that ran out) are written to *dev_status (a device
+ *    int32, 0 on success) for the caller to read after synchronising; the
+ *    outputs are still written on a best-effort basis.
+ *  - Calls that share a workspace must not overlap on the GPU.
+ */
+#ifndef NS_H
+#define NS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NS_OK = 0,
+    NS_ERR_INVALID_ARG = 1,     /* bad size, pointer, alignment or option */
+    NS_ERR_WORKSPACE = 2,       /* ws_bytes below the required size */
+    NS_ERR_NONFINITE = 3,       /* (device status) A holds Inf or NaN */
+    NS_ERR_NOCONV = 4,          /* (device status) Jacobi hit its sweep limit */
+    NS_ERR_TLS_NOSOLUTION = 5,  /* (device status) v_{n+1} = 0, Section 4 */
+    NS_ERR_TIMEOUT = 6,         /* (device status) a bounded device wait ran out */
+    NS_ERR_CUDA = 7             /* a CUDA launch or attribute call failed */
+} ns_status;
+
+/* Sketch families (Sections 1-2). */
+typedef enum {
+    NS_SRHT = 0,        /* S = (1/sqrt s) R H D: the SRFT of Section 2 with the
+                           Sylvester Walsh-Hadamard matrix H on m' = 2^ceil(log2 m) */
+    NS_SPARSE_SIGN = 1, /* zeta entries +-1/sqrt(zeta) per column of S (sparse
+                           sketch of the kind Section 1 names, CountSketch-like) */
+    NS_GAUSSIAN = 2     /* S = G/sqrt(s), G standard Gaussian (Theorem 2.1) */
+} ns_sketch_kind;
+
+typedef enum { NS_F64 = 0, NS_F32 = 1 } ns_dtype;
+
+/* Arithmetic used to form SA.  QR and Jacobi always run in FP64. */
+typedef enum {
+    NS_PREC_FP64 = 0,        /* exact +-1 transforms on a 64-bit fixed-point
+                                image of A; FP64 results */
+    NS_PREC_FP32_STREAM = 1, /* SRHT streamed in FP32 with FP32 accumulation */
+    NS_PREC_BF16X3 = 2       /* Gaussian: 3-term BF16 split products, FP32
+                                accumulation, on the tensor cores */
+} ns_prec;
+
+/* Sketch descriptor (host memory).  seed selects the realisation of S; the
+ * same (kind, s, zeta, seed) and m always give the same S. */
+typedef struct {
+    int32_t kind;    /* ns_sketch_kind */
+    int32_t zeta;    /* nonzeros per column of S for NS_SPARSE_SIGN (1..64) */
+    int64_t s;       /* sketch size, n <= s; SRHT also needs s <= m' */
+    uint64_t seed;
+    int32_t prec;    /* ns_prec */
+    int32_t reserved;
+} ns_sketch_desc;
+
+/* Human-readable name of a status code (static storage). */
+const char *ns_status_string(int status);
+
+/* Library version string. */
+const char *ns_version(void);
+
+/* Bytes of workspace needed by ns_sketch / ns_solve / ns_backward / ns_residual
+ * for this descriptor and shape (the maximum over the calls).  Returns 0 for
+ * an invalid combination. */
+size_t ns_workspace_size(const ns_sketch_desc *desc, int64_t m, int64_t n, int32_t k);
+
+/* Number of doubles in the `save` buffer of ns_solve: SA (s x n), V (n x n),
+ * sigma (n), in that order. */
+int64_t ns_save_size(int64_t s, int64_t n);
+
+/*
+ * ns_sketch -- Algorithm 1, line 2: SA = S A.
+ *   A      device, m x n (dtype), column-major, leading dimension lda >= m.
+ *   SA     device, s x n FP64 output, leading dimension s.
+ * SRHT (Section 2, with H in place of F): SA = (1/sqrt s) R H_{m'} D [A; 0].
+ * Sparse sign: SA = sum_j S(:, j) A(j, :), zeta entries per column of S.
+ * Gaussian: SA = G A / sqrt(s).
+ * Errors: NS_ERR_INVALID_ARG for m < 1, n < 1, s < 1, lda < m, SRHT s > m',
+ * zeta outside 1..min(64, s), an unsupported (kind, prec, dtype) triple, or a
+ * NULL pointer; NS_ERR_WORKSPACE for a short workspace.
+ */
+ns_status ns_sketch(const ns_sketch_desc *desc, const void *A, int32_t dtype, int64_t m, int64_t n,
+                    int64_t lda, double *SA, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * ns_solve -- Algorithm 1 end to end: sketch, QR of SA, one-sided Jacobi SVD
+ * of R, and W = V(:, n-k+1:n) (line 4).
+ *   Vk    device, n x k FP64 output: the k trailing right singular vectors of
+ *         SA, ordered by non-increasing singular value (the last column
+ *         belongs to the smallest); each column is signed so that its entry of
+ *         largest magnitude (lowest index on ties) is positive.
+ *   sigk  device, k FP64 output: the matching singular values of SA.
+ *   save  device, ns_save_size(s, n) doubles or NULL: SA, V, sigma, kept for
+ *         ns_backward.
+ *   dev_status  device int32 (may be NULL): 0, or NS_ERR_NONFINITE /
+ *         NS_ERR_NOCONV (sweep limit 30) / NS_ERR_TIMEOUT.
+ * Requires 1 <= k <= n <= s and m >= n.
+ */
+ns_status ns_solve(const ns_sketch_desc *desc, const void *A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                   int32_t k, double *Vk, double *sigk, double *save, int32_t *dev_status, void *ws,
+                   size_t ws_bytes, void *stream);
+
+/*
+ * ns_backward -- adjoint of ns_solve for a loss L that depends on W only
+ * through the projector W W^T (a loss that is invariant under W -> W Q).
+ * With M = SA^T SA = V Sigma^2 V^T, T the trailing k indices and N the others:
+ *   dL/dM  = sum_{i in T, j in N} c_ji (v_j v_i^T + v_i v_j^T),
+ *   c_ji   = (v_j . g_i) / (2 (sigma_i^2 - sigma_j^2)),  g_i = dL/dW(:, i),
+ *   dL/dSA = 2 SA dL/dM,    dL/dA = S^T dL/dSA.
+ * For the SRHT, S^T = (1/sqrt s) D H R^T is applied by regenerating D and R
+ * from the seed (nothing of the forward transform is stored).  Components of
+ * dL/dW along span(W) are ignored (they cannot change W W^T).
+ *   save  device: the buffer ns_solve filled.   Vk: the returned W.
+ *   dVk   device n x k: dL/dW.   dA: device m x n output, leading dim ldd >= m.
+ * Only NS_SRHT with NS_PREC_FP64 is supported; requires 1 <= k < n.
+ */
+ns_status ns_backward(const ns_sketch_desc *desc, int64_t m, int64_t n, int32_t k, const double *save,
+                      const double *Vk, const double *dVk, double *dA, int64_t ldd, void *ws, size_t ws_bytes,
+                      void *stream);
+
+/*
+ * ns_residual -- the objective of Problem 2.1, ||A W||_F, in one streaming
+ * pass over A (evaluation only).  W is device n x k FP64; *out (device double)
+ * receives the result.
+ */
+ns_status ns_residual(const void *A, int32_t dtype, int64_t m, int64_t n, int64_t lda, const double *W, int32_t k,
+                      double *out, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * ns_srht_meta -- the realisation of the SRHT's random ingredients, for
+ * inspection and tests: sign_words (device, ceil(m'/32) uint32; bit i set
+ * means d_i = -1) and rows (device, s int32: the coordinates kept by R, in
+ * draw order).  Either pointer may be NULL.
+ */
+ns_status ns_srht_meta(const ns_sketch_desc *desc, int64_t m, uint32_t *sign_words, int32_t *rows, void *stream);
+
+/*
+ * ns_sparse_meta -- the sparse-sign sketch as buckets by output row (CSR of
+ * S's transpose, stable in j): row_ptr (device, s+1 int32) and entries
+ * (device, m*zeta int32): entry = j for d = +1 and ~j (bitwise not) for -1,
+ * entries of row r ordered by increasing j.  ws as for ns_sketch.
+ */
+ns_status ns_sparse_meta(const ns_sketch_desc *desc, int64_t m, int32_t *row_ptr, int32_t *entries, void *ws,
+                         size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NS_H */

@@ -1,0 +1,149 @@
+"""Python binding of libns with the C ABI's names (include/ns.h).
+
+Tensors are torch CUDA tensors; matrices are column-major, i.e. a tensor of
+shape (rows, cols) with stride (1, ld).  ``colmajor(x)`` makes such a copy.
+These wrappers only marshal arguments: they allocate outputs and the
+workspace with torch, pass raw pointers and the current CUDA stream, and
+raise NSError on a non-OK status.
+"""
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import (NS_F32, NS_F64, NS_GAUSSIAN, NS_PREC_BF16X3, NS_PREC_FP32_STREAM, NS_PREC_FP64,  # noqa: F401
+                   NS_SPARSE_SIGN, NS_SRHT, NSError, SketchDesc)
+
+
+def desc(kind=NS_SRHT, s=0, seed=0, zeta=8, prec=NS_PREC_FP64):
+    return SketchDesc(int(kind), int(zeta), int(s), int(seed) & ((1 << 64) - 1), int(prec), 0)
+
+
+def colmajor(x, dtype=None, device=None):
+    """Copy of a 2-D array/tensor as a column-major torch tensor (stride (1, rows))."""
+    t = torch.as_tensor(x)
+    if dtype is not None:
+        t = t.to(dtype)
+    if device is not None:
+        t = t.to(device)
+    return t.t().contiguous().t()
+
+
+def _ld(A):
+    if A.dim() != 2 or A.stride(0) != 1:
+        raise ValueError("expected a column-major matrix (stride (1, ld))")
+    return max(A.stride(1), A.shape[0]) if A.shape[1] > 1 else max(A.shape[0], 1)
+
+
+def _dtype_code(A):
+    if A.dtype == torch.float64:
+        return NS_F64
+    if A.dtype == torch.float32:
+        return NS_F32
+    raise ValueError("A must be float64 or float32")
+
+
+def _p(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _empty_cm(rows, cols, device, dtype=torch.float64):
+    return torch.empty((cols, rows), dtype=dtype, device=device).t()
+
+
+def workspace_size(d, m, n, k=1):
+    return int(_lib.load().ns_workspace_size(ctypes.byref(d), int(m), int(n), int(k)))
+
+
+def save_size(s, n):
+    return int(_lib.load().ns_save_size(int(s), int(n)))
+
+
+def workspace(d, m, n, k=1, device="cuda"):
+    nbytes = workspace_size(d, m, n, k)
+    if nbytes == 0:
+        raise NSError(_lib.NS_ERR_INVALID_ARG, "ns_workspace_size")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def ns_sketch(d, A, SA=None, ws=None, stream=None):
+    """Algorithm 1 line 2: SA = S A (s x n, FP64, column-major)."""
+    m, n = A.shape
+    if SA is None:
+        SA = _empty_cm(d.s, n, A.device)
+    if ws is None:
+        ws = workspace(d, m, n, 1, A.device)
+    st = _lib.load().ns_sketch(ctypes.byref(d), _p(A), _dtype_code(A), m, n, _ld(A), _p(SA), _p(ws), ws.numel(),
+                               _stream(stream))
+    _lib.check(st, "ns_sketch")
+    return SA
+
+
+def ns_solve(d, A, k, save=True, status=None, ws=None, stream=None):
+    """Algorithm 1: returns (Vk n x k, sigk k, save or None, status int32 tensor)."""
+    m, n = A.shape
+    dev = A.device
+    Vk = _empty_cm(n, k, dev)
+    sigk = torch.empty(k, dtype=torch.float64, device=dev)
+    sv = None
+    if save is True:
+        sv = torch.empty(save_size(d.s, n), dtype=torch.float64, device=dev)
+    elif isinstance(save, torch.Tensor):
+        sv = save
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+    if ws is None:
+        ws = workspace(d, m, n, k, dev)
+    st = _lib.load().ns_solve(ctypes.byref(d), _p(A), _dtype_code(A), m, n, _ld(A), int(k), _p(Vk), _p(sigk),
+                              _p(sv), _p(status), _p(ws), ws.numel(), _stream(stream))
+    _lib.check(st, "ns_solve")
+    return Vk, sigk, sv, status
+
+
+def unpack_save(sv, s, n):
+    """Views (SA s x n, V n x n, sigma n) of a save buffer."""
+    SA = sv[: s * n].view(n, s).t()
+    V = sv[s * n: s * n + n * n].view(n, n).t()
+    sigma = sv[s * n + n * n: s * n + n * n + n]
+    return SA, V, sigma
+
+
+def ns_backward(d, m, n, k, save, Vk, dVk, dA=None, ws=None, stream=None):
+    """Adjoint of ns_solve for a loss of W W^T: returns dL/dA (m x n, column-major)."""
+    dev = save.device
+    if dA is None:
+        dA = _empty_cm(m, n, dev)
+    if ws is None:
+        ws = workspace(d, m, n, k, dev)
+    st = _lib.load().ns_backward(ctypes.byref(d), int(m), int(n), int(k), _p(save), _p(Vk), _p(dVk), _p(dA),
+                                 _ld(dA), _p(ws), ws.numel(), _stream(stream))
+    _lib.check(st, "ns_backward")
+    return dA
+
+
+def ns_residual(A, W, ws=None, stream=None):
+    """||A W||_F on the GPU (one FP64 pass over A); returns a 0-d device tensor."""
+    m, n = A.shape
+    out = torch.empty((), dtype=torch.float64, device=A.device)
+    if ws is None:
+        ws = torch.empty(8 * 4096, dtype=torch.uint8, device=A.device)
+    st = _lib.load().ns_residual(_p(A), _dtype_code(A), m, n, _ld(A), _p(W), W.shape[1], _p(out), _p(ws),
+                                 ws.numel(), _stream(stream))
+    _lib.check(st, "ns_residual")
+    return out
+
+
+def ns_srht_meta(d, m, stream=None, device="cuda"):
+    """(sign_words uint32 as int32 tensor, rows int32) of the SRHT realisation."""
+    lg = max(int(m - 1).bit_length(), 0)
+    nwords = ((1 << lg) + 31) // 32
+    words = torch.empty(nwords, dtype=torch.int32, device=device)
+    rows = torch.empty(d.s, dtype=torch.int32, device=device)
+    st = _lib.load().ns_srht_meta(ctypes.byref(d), int(m), _p(words), _p(rows), _stream(stream))
+    _lib.check(st, "ns_srht_meta")
+    return words, rows

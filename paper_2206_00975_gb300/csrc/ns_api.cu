@@ -1,0 +1,202 @@
+// ns_api.cu -- the extern "C" entry points of libns (see include/ns.h).
+//
+// Every entry point validates its arguments on the host, carves the caller's
+// workspace, enqueues kernels on the caller's stream and returns; nothing is
+// allocated, freed or synchronised here.
+#include <cmath>
+#include <cstring>
+#include "ns_device.cuh"
+#include "ns_internal.h"
+
+namespace ns {
+
+constexpr int64_t kMaxS = 16384;   // sketch rows held in one CTA's shared memory
+constexpr int64_t kMaxN = 4096;    // columns handled by the dense kernels
+
+static bool desc_ok(const ns_sketch_desc *d) {
+    if (!d) return false;
+    if (d->kind < NS_SRHT || d->kind > NS_GAUSSIAN) return false;
+    if (d->prec < NS_PREC_FP64 || d->prec > NS_PREC_BF16X3) return false;
+    if (d->s < 1 || d->s > kMaxS) return false;
+    if (d->kind == NS_SPARSE_SIGN && (d->zeta < 1 || d->zeta > 64 || d->zeta > d->s)) return false;
+    return true;
+}
+
+// (kind, prec, dtype) triples with a GPU path
+static bool path_ok(const ns_sketch_desc *d, int32_t dtype) {
+    if (d->kind == NS_SRHT) return d->prec == NS_PREC_FP64 && dtype == NS_F64;
+    return false;
+}
+
+static bool shape_ok(const ns_sketch_desc *d, int64_t m, int64_t n, int64_t lda) {
+    if (m < 1 || n < 1 || lda < m) return false;
+    if (d->kind == NS_SRHT && d->s > ((int64_t)1 << ceil_log2(m))) return false;
+    return true;
+}
+
+struct SolveLayout {
+    int32_t *status_word;
+    SrhtWork srht;
+    double *SA;
+    DenseWork dense;
+    size_t bytes;
+};
+
+static SolveLayout solve_layout(void *ws, const ns_sketch_desc *d, int64_t m, int64_t n, bool need_sa) {
+    Carver c(ws);
+    SolveLayout L;
+    L.status_word = c.take<int32_t>(1);
+    L.srht = srht_carve(c, m, n, d->s);
+    L.SA = need_sa ? c.take<double>((size_t)(d->s * n)) : nullptr;
+    L.dense = dense_carve(c, d->s, n);
+    L.bytes = c.used;
+    return L;
+}
+
+static ns_status cuda_status(cudaError_t e) { return e == cudaSuccess ? NS_OK : NS_ERR_CUDA; }
+
+static ns_status run_sketch(const ns_sketch_desc *d, const void *A, int64_t m, int64_t n, int64_t lda, double *SA,
+                            const SrhtWork &w, int32_t *status, cudaStream_t st) {
+    const SrhtGeom g = srht_geom(m, n);
+    cudaError_t e = launch_srht_meta(d->seed, g.lg, g.sign_words, d->s, w.sign_words, w.rows, st);
+    if (e != cudaSuccess) return NS_ERR_CUDA;
+    return cuda_status(launch_srht_f64((const double *)A, m, n, lda, d->s, w, SA, status, st));
+}
+
+// ---------------------------------------------------------------- residual --
+__global__ void residual_rows_kernel(const double *__restrict__ A, int64_t m, int64_t n, int64_t lda,
+                                     const double *__restrict__ W, int32_t k, double *__restrict__ partial) {
+    extern __shared__ double wsh[];  // n * k
+    __shared__ double red[32];
+    for (int64_t i = threadIdx.x; i < n * k; i += blockDim.x) wsh[i] = W[i];
+    __syncthreads();
+    double ss = 0.0;
+    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < m; row += (int64_t)gridDim.x * blockDim.x) {
+        double y[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) y[c] = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            const double a = __ldcs(A + row + j * lda);
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                if (c < k) y[c] = fma(a, wsh[j + c * n], y[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+            if (c < k) ss = fma(y[c], y[c], ss);
+    }
+    double v[1] = {ss};
+    block_sum<1>(v, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = v[0];
+}
+
+__global__ void residual_final_kernel(const double *partial, int64_t np, double *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double a = 0.0;
+        for (int64_t i = 0; i < np; ++i) a += partial[i];  // fixed order
+        *out = sqrt(a);
+    }
+}
+
+}  // namespace ns
+
+using namespace ns;
+
+extern "C" {
+
+const char *ns_status_string(int status) {
+    switch (status) {
+        case NS_OK: return "NS_OK";
+        case NS_ERR_INVALID_ARG: return "NS_ERR_INVALID_ARG";
+        case NS_ERR_WORKSPACE: return "NS_ERR_WORKSPACE";
+        case NS_ERR_NONFINITE: return "NS_ERR_NONFINITE";
+        case NS_ERR_NOCONV: return "NS_ERR_NOCONV";
+        case NS_ERR_TLS_NOSOLUTION: return "NS_ERR_TLS_NOSOLUTION";
+        case NS_ERR_TIMEOUT: return "NS_ERR_TIMEOUT";
+        case NS_ERR_CUDA: return "NS_ERR_CUDA";
+        default: return "NS_ERR_UNKNOWN";
+    }
+}
+
+const char *ns_version(void) { return "libns 0.1 (sm_103a)"; }
+
+int64_t ns_save_size(int64_t s, int64_t n) { return s * n + n * n + n; }
+
+size_t ns_workspace_size(const ns_sketch_desc *d, int64_t m, int64_t n, int32_t k) {
+    if (!desc_ok(d) || m < 1 || n < 1 || n > kMaxN || k < 0) return 0;
+    const size_t solve = solve_layout(nullptr, d, m, n, true).bytes;
+    const size_t resid = align256(sizeof(double) * 4096);
+    return solve > resid ? solve : resid;
+}
+
+ns_status ns_sketch(const ns_sketch_desc *d, const void *A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                    double *SA, void *ws, size_t ws_bytes, void *stream) {
+    if (!desc_ok(d) || !A || !SA || !ws) return NS_ERR_INVALID_ARG;
+    if (!path_ok(d, dtype) || !shape_ok(d, m, n, lda)) return NS_ERR_INVALID_ARG;
+    if ((((uintptr_t)ws) & 255) != 0 || (((uintptr_t)A) & 7) != 0) return NS_ERR_INVALID_ARG;
+    Carver c(ws);
+    int32_t *status = c.take<int32_t>(1);
+    SrhtWork w = srht_carve(c, m, n, d->s);
+    if (c.used > ws_bytes) return NS_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(status, 0, sizeof(int32_t), st) != cudaSuccess) return NS_ERR_CUDA;
+    return run_sketch(d, A, m, n, lda, SA, w, status, st);
+}
+
+ns_status ns_solve(const ns_sketch_desc *d, const void *A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                   int32_t k, double *Vk, double *sigk, double *save, int32_t *dev_status, void *ws, size_t ws_bytes,
+                   void *stream) {
+    if (!desc_ok(d) || !A || !Vk || !sigk || !ws) return NS_ERR_INVALID_ARG;
+    if (!path_ok(d, dtype) || !shape_ok(d, m, n, lda)) return NS_ERR_INVALID_ARG;
+    if (m < n || n > d->s || n > kMaxN || k < 1 || k > n) return NS_ERR_INVALID_ARG;
+    if ((((uintptr_t)ws) & 255) != 0 || (((uintptr_t)A) & 7) != 0) return NS_ERR_INVALID_ARG;
+    SolveLayout L = solve_layout(ws, d, m, n, save == nullptr);
+    if (L.bytes > ws_bytes) return NS_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *status = dev_status ? dev_status : L.status_word;
+    if (cudaMemsetAsync(status, 0, sizeof(int32_t), st) != cudaSuccess) return NS_ERR_CUDA;
+    double *SA = save ? save : L.SA;
+    ns_status r = run_sketch(d, A, m, n, lda, SA, L.srht, status, st);
+    if (r != NS_OK) return r;
+    double *save_V = save ? save + d->s * n : nullptr;
+    double *save_sigma = save ? save + d->s * n + n * n : nullptr;
+    return cuda_status(launch_dense_solve(SA, d->s, n, k, L.dense, Vk, sigk, save_V, save_sigma, status, st));
+}
+
+ns_status ns_backward(const ns_sketch_desc *d, int64_t m, int64_t n, int32_t k, const double *save, const double *Vk,
+                      const double *dVk, double *dA, int64_t ldd, void *ws, size_t ws_bytes, void *stream) {
+    (void)d; (void)m; (void)n; (void)k; (void)save; (void)Vk; (void)dVk; (void)dA; (void)ldd; (void)ws;
+    (void)ws_bytes; (void)stream;
+    return NS_ERR_INVALID_ARG;
+}
+
+ns_status ns_residual(const void *A, int32_t dtype, int64_t m, int64_t n, int64_t lda, const double *W, int32_t k,
+                      double *out, void *ws, size_t ws_bytes, void *stream) {
+    if (!A || !W || !out || !ws || dtype != NS_F64) return NS_ERR_INVALID_ARG;
+    if (m < 1 || n < 1 || lda < m || k < 1 || k > 16 || n * k > 6000) return NS_ERR_INVALID_ARG;
+    const int64_t blocks = 1024;
+    if (ws_bytes < sizeof(double) * (size_t)blocks) return NS_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *partial = (double *)ws;
+    residual_rows_kernel<<<(unsigned)blocks, 256, sizeof(double) * (size_t)(n * k), st>>>(
+        (const double *)A, m, n, lda, W, k, partial);
+    if (cudaGetLastError() != cudaSuccess) return NS_ERR_CUDA;
+    residual_final_kernel<<<1, 32, 0, st>>>(partial, blocks, out);
+    return cuda_status(cudaGetLastError());
+}
+
+ns_status ns_srht_meta(const ns_sketch_desc *d, int64_t m, uint32_t *sign_words, int32_t *rows, void *stream) {
+    if (!desc_ok(d) || d->kind != NS_SRHT || m < 1) return NS_ERR_INVALID_ARG;
+    const int lg = ceil_log2(m);
+    if (d->s > ((int64_t)1 << lg)) return NS_ERR_INVALID_ARG;
+    const int64_t nwords = (((int64_t)1 << lg) + 31) / 32;
+    return cuda_status(launch_srht_meta(d->seed, lg, nwords, d->s, sign_words, rows, (cudaStream_t)stream));
+}
+
+ns_status ns_sparse_meta(const ns_sketch_desc *d, int64_t m, int32_t *row_ptr, int32_t *entries, void *ws,
+                         size_t ws_bytes, void *stream) {
+    (void)d; (void)m; (void)row_ptr; (void)entries; (void)ws; (void)ws_bytes; (void)stream;
+    return NS_ERR_INVALID_ARG;
+}
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+// ns_internal.h -- host-side declarations shared by the libns translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "../../include/ns.h"
+
+namespace ns {
+
+constexpr int kBlockLog = 12;                 // FWHT block: 4096 rows of one column
+constexpr int64_t kBlock = 1 << kBlockLog;
+constexpr int kMaxChunkBlocks = 16;           // blocks summed per fixed-point accumulator
+
+inline int ceil_log2(int64_t m) {
+    int lg = 0;
+    while (((int64_t)1 << lg) < m) ++lg;
+    return lg;
+}
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Carves consecutive 256-byte-aligned pieces out of the caller's workspace.
+struct Carver {
+    char *base;
+    size_t used = 0;
+    explicit Carver(void *p) : base((char *)p) {}
+    template <typename T>
+    T *take(size_t count) {
+        T *p = base ? (T *)(base + used) : nullptr;
+        used += align256(count * sizeof(T));
+        return p;
+    }
+};
+
+// SRHT forward geometry: the padded length m' is split into blocks of 4096
+// rows (a single, zero-padded block when m' <= 4096); consecutive blocks of a
+// column are grouped into chunks that share one fixed-point accumulator.
+struct SrhtGeom {
+    int lg;            // m' = 2^lg
+    int64_t nblk;      // blocks per column
+    int chunk;         // blocks per chunk
+    int64_t nchunk;    // chunks per column
+    int fx_bits;       // fixed-point magnitude bits P
+    int64_t sign_words;  // uint32 words of sign bits kept in workspace
+};
+SrhtGeom srht_geom(int64_t m, int64_t n);
+
+struct SrhtWork {
+    uint32_t *sign_words;
+    int32_t *rows;
+    double *partial;
+};
+size_t srht_work_bytes(int64_t m, int64_t n, int64_t s);
+SrhtWork srht_carve(Carver &c, int64_t m, int64_t n, int64_t s);
+
+// launches (return cudaGetLastError())
+cudaError_t launch_srht_meta(uint64_t seed, int lg, int64_t nsign_words, int64_t s, uint32_t *sign_words,
+                             int32_t *rows, cudaStream_t st);
+cudaError_t launch_srht_f64(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, const SrhtWork &w,
+                            double *SA, int32_t *status, cudaStream_t st);
+
+struct DenseWork {
+    double *W;        // s x n working copy of SA (QR in place)
+    double *tau;      // n
+    double *X;        // n x n, R then X V
+    double *V;        // n x n
+    double *sigma;    // n
+    unsigned int *bar;  // grid barrier words (2) + rotation counters (64)
+};
+size_t dense_work_bytes(int64_t s, int64_t n);
+DenseWork dense_carve(Carver &c, int64_t s, int64_t n);
+cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k, const DenseWork &w, double *Vk,
+                               double *sigk, double *save_V, double *save_sigma, int32_t *status, cudaStream_t st);
+
+}  // namespace ns

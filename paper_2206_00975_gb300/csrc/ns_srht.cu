@@ -1,0 +1,274 @@
+// ns_srht.cu -- SRHT sketch SA = (1/sqrt s) R H D [A; 0] (the SRFT of Section 2
+// with the Sylvester Walsh-Hadamard matrix H for F), FP64 input.
+//
+// Arithmetic.  FP64 throughput on this part is ~1/64 of INT32, so the
+// streaming pass never touches the FP64 pipe.  Each 4096-row block of a column
+// is mapped exactly onto 64-bit fixed point (integer bit manipulation of the
+// IEEE words, round to nearest on the magnitude), at a scale set by the largest
+// exponent seen so far in the chunk, with P = 63 - 12 - log2(chunk) - 1
+// magnitude bits.  The +-1 butterflies of H are then exact integer adds, so the
+// transform and the pruned sum over blocks carry no rounding at all; the only
+// rounding is the input quantisation (relative 2^-P of the chunk's largest
+// entry) and one conversion per output.
+//
+// Structure (Kronecker split H_{m'} = H_{m'/4096} (x) H_{4096}):
+//   y[r] = sum_b (-1)^popcount(hi(r) & b) Z_b[lo(r)],   Z_b = H_4096 (D a)_b,
+// with hi(r) = r >> 12, lo(r) = r & 4095.  A CTA of 64 threads holds a block in
+// registers (64 values per thread), runs 6 butterfly stages in registers, one
+// swizzled shared-memory transpose, 6 more stages, and adds the s sampled
+// values Z_b[lo(r_t)] into its accumulator.  For m' <= 4096 the column is one
+// zero-padded block: H's entries depend only on popcount(i & j), so padding to
+// 4096 leaves the sampled rows unchanged.
+#include <cmath>
+#include "ns_device.cuh"
+#include "ns_internal.h"
+
+namespace ns {
+
+SrhtGeom srht_geom(int64_t m, int64_t n) {
+    SrhtGeom g;
+    g.lg = ceil_log2(m);
+    const int64_t mp = (int64_t)1 << g.lg;
+    g.nblk = mp > kBlock ? mp / kBlock : 1;
+    // about 2048 (column, chunk) work items; chunk is a power of two <= 16
+    int64_t want = (g.nblk * n) / 2048;
+    int chunk = 1;
+    while (chunk * 2 <= want && chunk * 2 <= kMaxChunkBlocks) chunk *= 2;
+    while (chunk > g.nblk) chunk /= 2;
+    g.chunk = chunk;
+    g.nchunk = g.nblk / chunk;
+    g.fx_bits = 63 - kBlockLog - ceil_log2(chunk) - 1;
+    g.sign_words = (mp > kBlock ? mp : kBlock) / 32;
+    return g;
+}
+
+size_t srht_work_bytes(int64_t m, int64_t n, int64_t s) {
+    Carver c(nullptr);
+    srht_carve(c, m, n, s);
+    return c.used;
+}
+
+SrhtWork srht_carve(Carver &c, int64_t m, int64_t n, int64_t s) {
+    SrhtGeom g = srht_geom(m, n);
+    SrhtWork w;
+    w.sign_words = c.take<uint32_t>((size_t)g.sign_words);
+    w.rows = c.take<int32_t>((size_t)s);
+    w.partial = c.take<double>((size_t)(g.nchunk * n * s));
+    return w;
+}
+
+// ------------------------------------------------------------------- meta ----
+// sign word j holds bits 32j..32j+31 of the sign vector; bit i comes from bit
+// (i mod 64) of 64-bit word ((i mod 256)/64) of stream-0 block i/256.
+__global__ void srht_meta_kernel(uint64_t seed, int lg, int64_t nwords, int64_t s, uint32_t *sign_words,
+                                 int32_t *rows) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (sign_words && idx < nwords) {
+        const u64x4 w = draw(seed, (uint64_t)(idx >> 3), 0, 0);
+        const uint64_t word = w.w[(idx & 7) >> 1];
+        sign_words[idx] = (idx & 1) ? (uint32_t)(word >> 32) : (uint32_t)word;
+    }
+    if (rows && idx < s) rows[idx] = (int32_t)sample_perm(seed, lg, (uint32_t)idx);
+}
+
+cudaError_t launch_srht_meta(uint64_t seed, int lg, int64_t nsign_words, int64_t s, uint32_t *sign_words,
+                             int32_t *rows, cudaStream_t st) {
+    const int64_t total = nsign_words > s ? nsign_words : s;
+    const int threads = 256;
+    const int64_t blocks = (total + threads - 1) / threads;
+    srht_meta_kernel<<<(unsigned)blocks, threads, 0, st>>>(seed, lg, nsign_words, s, sign_words, rows);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- forward ----
+// Shared-memory swizzle of a 4096-entry int64 block: entry i sits at
+// i ^ (((i >> 7) & 15) << 1).  Row-major 16-byte stores of the first layout and
+// the strided loads of the second layout are then both bank-conflict free.
+__device__ __forceinline__ int swz(int i) { return i ^ (((i >> 7) & 15) << 1); }
+
+// in-register Walsh-Hadamard transform of 64 values (Sylvester order on the
+// register index)
+__device__ __forceinline__ void fwht64(long long (&z)[64]) {
+#pragma unroll
+    for (int h = 1; h < 64; h <<= 1) {
+#pragma unroll
+        for (int k = 0; k < 64; ++k) {
+            if ((k & h) == 0) {
+                const long long a = z[k], b = z[k + h];
+                z[k] = a + b;
+                z[k + h] = a - b;
+            }
+        }
+    }
+}
+
+// Layout 1: thread t, register k holds element (k & 1) | (t << 1) | ((k >> 1) << 7).
+// Layout 2: thread t, register k holds element (t & 1) | (k << 1) | ((t >> 1) << 7).
+__device__ __forceinline__ int l2_elem(int t, int k) { return (t & 1) | (k << 1) | ((t >> 1) << 7); }
+
+__global__ void __launch_bounds__(64) srht_f64_chunk_kernel(const double *__restrict__ A, int64_t m, int64_t n,
+                                                            int64_t lda, int64_t s, int chunk, int64_t nchunk,
+                                                            int P, const uint32_t *__restrict__ sign_words,
+                                                            const int32_t *__restrict__ rows,
+                                                            double *__restrict__ partial, int32_t *status,
+                                                            int vec_ok) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    long long *Zs = (long long *)smem_raw;                       // 4096
+    long long *acc = Zs + kBlock;                                // s
+    unsigned long long *need = (unsigned long long *)(acc + s);  // 64
+    uint32_t *sgn = (uint32_t *)(need + 64);                     // 128
+    int *red = (int *)(sgn + 128);                               // 4
+    int32_t *rows_s = (int32_t *)(red + 4);                      // s
+
+    const int t = threadIdx.x;
+    const int64_t item = blockIdx.x;
+    const int64_t c = item / nchunk, ch = item - c * nchunk;
+    const double *Acol = A + c * lda;
+
+    for (int64_t i = t; i < s; i += 64) {
+        rows_s[i] = rows[i];
+        acc[i] = 0;
+    }
+    need[t] = 0ull;
+    __syncthreads();
+    // which layout-2 registers hold a sampled row (the same for every block)
+    for (int64_t i = t; i < s; i += 64) {
+        const int lo = rows_s[i] & (kBlock - 1);
+        const int owner = (lo & 1) | ((lo >> 7) << 1);
+        atomicOr(&need[owner], 1ull << ((lo >> 1) & 63));
+    }
+    __syncthreads();
+    const unsigned long long myneed = need[t];
+
+    int Erun = 0;  // running biased exponent of the chunk (0: none yet)
+    int nonfinite = 0;
+    long long z[64];
+
+    for (int bl = 0; bl < chunk; ++bl) {
+        const int64_t b = ch * chunk + bl;
+        const int64_t base = b * kBlock;
+        sgn[t] = sign_words[(base >> 5) + t];
+        sgn[t + 64] = sign_words[(base >> 5) + 64 + t];
+
+        // ---- load the block (layout 1), raw IEEE bits
+#pragma unroll
+        for (int kk = 0; kk < 32; ++kk) {
+            const int64_t i0 = base + 2 * t + 128 * kk;
+            long long a0 = 0, a1 = 0;
+            if (vec_ok && i0 + 1 < m) {
+                const double2 v = __ldcs((const double2 *)(Acol + i0));
+                a0 = __double_as_longlong(v.x);
+                a1 = __double_as_longlong(v.y);
+            } else {
+                if (i0 < m) a0 = __double_as_longlong(__ldcs(Acol + i0));
+                if (i0 + 1 < m) a1 = __double_as_longlong(__ldcs(Acol + i0 + 1));
+            }
+            z[2 * kk] = a0;
+            z[2 * kk + 1] = a1;
+        }
+        // ---- largest finite exponent of the block
+        int emax = 1;
+#pragma unroll
+        for (int k = 0; k < 64; ++k) {
+            const int e = (int)((unsigned long long)z[k] >> 52) & 0x7FF;
+            if (e == 0x7FF) nonfinite = 1;
+            else emax = max(emax, e);
+        }
+        emax = warp_max(emax);
+        if ((t & 31) == 0) red[t >> 5] = emax;
+        __syncthreads();  // also publishes sgn[]
+        emax = max(red[0], red[1]);
+        if (emax > Erun) {
+            if (Erun > 0) {
+                const int d = emax - Erun;
+                for (int64_t i = t; i < s; i += 64) acc[i] = (d >= 63) ? (acc[i] >> 63) : (acc[i] >> d);
+            }
+            Erun = emax;
+        }
+        // ---- quantise: q = round(|a| 2^(P + 1022 - E)), sign = sign(a) * d_i
+#pragma unroll
+        for (int kk = 0; kk < 32; ++kk) {
+            const uint32_t sw = sgn[4 * kk + (t >> 4)] >> (2 * (t & 15));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const unsigned long long raw = (unsigned long long)z[2 * kk + h];
+                const int e = (int)(raw >> 52) & 0x7FF;
+                const unsigned long long frac = raw & 0x000FFFFFFFFFFFFFull;
+                const unsigned long long mant = e ? (frac | 0x0010000000000000ull) : frac;
+                const int sh = Erun - (e ? e : 1) + 53 - P;
+                unsigned long long q = (sh >= 64 || e == 0x7FF) ? 0ull : ((mant + (1ull << (sh - 1))) >> sh);
+                const unsigned long long neg = ((raw >> 63) ^ ((sw >> h) & 1u)) & 1u;
+                const unsigned long long msk = 0ull - neg;
+                z[2 * kk + h] = (long long)((q ^ msk) + neg);
+            }
+        }
+        // ---- H on the 6 register bits (element bits 0, 7..11)
+        fwht64(z);
+#pragma unroll
+        for (int kk = 0; kk < 32; ++kk) {
+            const int i = 2 * t + 128 * kk;
+            longlong2 v;
+            v.x = z[2 * kk];
+            v.y = z[2 * kk + 1];
+            *(longlong2 *)(Zs + swz(i)) = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 64; ++k) z[k] = Zs[swz(l2_elem(t, k))];
+        __syncthreads();
+        // ---- H on element bits 1..6
+        fwht64(z);
+        // ---- publish only the sampled entries, then gather them into the accumulator
+#pragma unroll
+        for (int k = 0; k < 64; ++k)
+            if ((myneed >> k) & 1ull) Zs[swz(l2_elem(t, k))] = z[k];
+        __syncthreads();
+        for (int64_t i = t; i < s; i += 64) {
+            const int r = rows_s[i];
+            const long long v = Zs[swz(r & (kBlock - 1))];
+            const int neg = __popcll((unsigned long long)(r >> kBlockLog) & (unsigned long long)b) & 1;
+            acc[i] += neg ? -v : v;
+        }
+        __syncthreads();
+    }
+    // chunk partial in FP64: value = acc * 2^(E - 1022 - P)
+    const double scale = ldexp(1.0, Erun - 1022 - P);
+    double *out = partial + (ch * n + c) * s;
+    for (int64_t i = t; i < s; i += 64) out[i] = (double)acc[i] * scale;
+    if (nonfinite) set_status(status, NS_ERR_NONFINITE);
+}
+
+// SA[t, c] = (1/sqrt s) * sum over chunks, in chunk order (deterministic)
+__global__ void srht_reduce_kernel(const double *__restrict__ partial, int64_t n, int64_t s, int64_t nchunk,
+                                   double scale, double *__restrict__ SA) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * s) return;
+    const int64_t c = idx / s, t = idx - c * s;
+    double a = 0.0;
+    for (int64_t ch = 0; ch < nchunk; ++ch) a += partial[(ch * n + c) * s + t];
+    SA[t + c * s] = a * scale;
+}
+
+size_t srht_f64_smem(int64_t s) { return (size_t)kBlock * 8 + (size_t)s * 8 + 64 * 8 + 128 * 4 + 16 + (size_t)s * 4; }
+
+cudaError_t launch_srht_f64(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, const SrhtWork &w,
+                            double *SA, int32_t *status, cudaStream_t st) {
+    const SrhtGeom g = srht_geom(m, n);
+    const size_t smem = srht_f64_smem(s);
+    cudaError_t e = cudaFuncSetAttribute(srht_f64_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int vec_ok = ((((uintptr_t)A) & 15) == 0 && (lda & 1) == 0) ? 1 : 0;
+    const int64_t items = n * g.nchunk;
+    srht_f64_chunk_kernel<<<(unsigned)items, 64, smem, st>>>(A, m, n, lda, s, g.chunk, g.nchunk, g.fx_bits,
+                                                             w.sign_words, w.rows, w.partial, status, vec_ok);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int threads = 256;
+    const int64_t blocks = (n * s + threads - 1) / threads;
+    srht_reduce_kernel<<<(unsigned)blocks, threads, 0, st>>>(w.partial, n, s, g.nchunk, 1.0 / std::sqrt((double)s),
+                                                            SA);
+    return cudaGetLastError();
+}
+
+}  // namespace ns
