@@ -172,6 +172,33 @@ ns_status ns_srht_meta(const ns_sketch_desc *desc, int64_t m, uint32_t *sign_wor
 ns_status ns_sparse_meta(const ns_sketch_desc *desc, int64_t m, int32_t *row_ptr, int32_t *entries, void *ws,
                          size_t ws_bytes, void *stream);
 
+/*
+ * ns_sketch_static -- the SRHT sketch of ns_sketch (FP64 input, NS_SRHT with
+ * NS_PREC_FP64 only, same result) without a caller-supplied workspace.  The
+ * paper has no counterpart of this call; it exists for callers that cannot
+ * allocate device memory: code embedded in a host application whose device
+ * memory is owned by the application's own pool allocator, or a service that
+ * must not allocate after start-up because an allocation can fail, block or
+ * fragment memory at an unpredictable moment.  Such callers still pass A and
+ * SA, but need no scratch of their own.
+ *
+ * The scratch lives in one fixed device array of 16 MiB inside libns; every
+ * GPU on which the library is used holds those 16 MiB until the process
+ * exits.  A problem whose scratch (sign words, sample rows and per-chunk
+ * partial sums, about 8 * n * s * (number of 65536-row chunks) bytes) does not
+ * fit returns NS_ERR_WORKSPACE; use ns_sketch with a workspace instead.  The
+ * call allocates nothing (no cudaMalloc, no cudaFree, no allocating library
+ * routine).
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before any stream
+ * capture.  Every call shares the one array and leaves its contents behind:
+ * calls whose work overlaps on the GPU (two streams, or two threads) race on
+ * it and must be serialised by the caller.
+ */
+ns_status ns_sketch_static(const ns_sketch_desc *desc, const void *A, int32_t dtype, int64_t m, int64_t n,
+                           int64_t lda, double *SA, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ NS_PREC_FP64, NS_PREC_FP32_STREAM, NS_PREC_BF16X3 = 0, 1, 2
 # every symbol include/ns.h declares
 EXPORTS = [
     "ns_status_string", "ns_version", "ns_workspace_size", "ns_save_size", "ns_sketch", "ns_solve",
-    "ns_backward", "ns_residual", "ns_srht_meta", "ns_sparse_meta",
+    "ns_backward", "ns_residual", "ns_srht_meta", "ns_sparse_meta", "ns_sketch_static",
 ]
 
 
@@ -59,6 +59,7 @@ def load():
         "ns_residual": (ctypes.c_int, [P, i32, i64, i64, i64, P, i32, P, P, sz, P]),
         "ns_srht_meta": (ctypes.c_int, [D, i64, P, P, P]),
         "ns_sparse_meta": (ctypes.c_int, [D, i64, P, P, P, sz, P]),
+        "ns_sketch_static": (ctypes.c_int, [D, P, i32, i64, i64, i64, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -147,3 +147,15 @@ def ns_srht_meta(d, m, stream=None, device="cuda"):
     st = _lib.load().ns_srht_meta(ctypes.byref(d), int(m), _p(words), _p(rows), _stream(stream))
     _lib.check(st, "ns_srht_meta")
     return words, rows
+
+
+def ns_sketch_static(d, A, SA=None, stream=None):
+    """SRHT sketch using the library's own fixed scratch array: no workspace is
+    passed and nothing is allocated by the call (the output SA is allocated
+    here only if the caller did not pass one)."""
+    m, n = A.shape
+    if SA is None:
+        SA = _empty_cm(d.s, n, A.device)
+    st = _lib.load().ns_sketch_static(ctypes.byref(d), _p(A), _dtype_code(A), m, n, _ld(A), _p(SA), _stream(stream))
+    _lib.check(st, "ns_sketch_static")
+    return SA
