@@ -1,21 +1,40 @@
-// ns_dense.cu -- Algorithm 1 lines 3-4 on the GPU, FP64: Householder QR of SA
-// (s x n), one-sided Jacobi SVD of the n x n factor R (SA and R share singular
-// values and right singular vectors, proof of Theorem 3.2), and extraction of
-// the k trailing right singular vectors (line 4).
+// ns_dense.cu -- Algorithm 1 lines 3-4 on the GPU in FP64: the SVD of SA
+// (s x n) through Householder QR and a one-sided Jacobi SVD of the n x n
+// triangular factor (SA and R share singular values and right singular
+// vectors, proof of Theorem 3.2), then the k trailing right singular vectors.
 //
-// FP64 runs at ~2 FMA/clock/SM on this part, so even a 256 x 256 problem has
-// to be spread over the whole GPU: both factorizations are cooperative
-// launches whose CTAs own columns round-robin and meet at a bounded grid
-// barrier once per Householder step / Jacobi step.
+// Preconditioned one-sided Jacobi (Drmac & Veselic, SIAM J. Matrix Anal.
+// Appl. 29 (2008)):
+//   1. SA P = Q1 R          Householder QR with column pivoting;
+//   2. R^T  = Q2 R2         Householder QR of the transpose (no pivoting);
+//   3. X = R2^T,  X Vx = U Sigma   one-sided Jacobi (Hestenes) on the columns;
+//   4. V = P Q2 Vx          right singular vectors of SA.
+// R = R2^T Q2^T, so SA P = Q1 X Q2^T and the right singular vectors of SA P are
+// Q2 Vx; Vx comes from accumulated rotations and Q2 from reflectors, both
+// orthogonal to working precision.  The pivoted, twice-factored X has nearly
+// orthogonal graded columns, so the Jacobi iteration needs about a third of
+// the sweeps it needs on R itself.
 //
-// Jacobi: pairs are scheduled by the round-robin (circle) ordering, n'/2
-// disjoint pairs per step, n'-1 steps per sweep (n' = n rounded up to even; an
-// odd n gets a phantom zero column).  A pair (p, q) is rotated when
-// |gamma| > tol sqrt(alpha beta) with alpha = |x_p|^2, beta = |x_q|^2,
-// gamma = x_p . x_q and tol = n 2^-53; the rotation (zeta = (beta-alpha)/(2
-// gamma), t = sign(zeta)/(|zeta| + sqrt(1+zeta^2)), c = 1/sqrt(1+t^2), s = c t)
-// makes the pair orthogonal.  A sweep without rotations ends the iteration;
-// 30 sweeps without convergence report NS_ERR_NOCONV.
+// FP64 runs at ~2 FMA/clock/SM on this part: the kernels spread the work over
+// the whole GPU (cooperative launches, one CTA per SM, columns owned
+// round-robin, a bounded grid barrier per Householder or Jacobi step) and keep
+// scalar FP64 chains (norms, reflector and rotation parameters) to one thread.
+//
+// Jacobi rule: a pair (p, q) is rotated when gamma^2 > tol^2 alpha beta with
+// alpha = |x_p|^2, beta = |x_q|^2, gamma = x_p . x_q, tol = n 2^-53; the
+// rotation (zeta = (beta - alpha)/(2 gamma), t = sign(zeta)/(|zeta| +
+// sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t) makes the pair orthogonal.
+// t needs only modest accuracy (it sets the angle; an inexact angle leaves a
+// small residual cosine for the next sweep), so it is formed in FP32 from
+// power-of-two-scaled alpha, beta, gamma; c is then computed from that t to full
+// FP64 accuracy (FP32 reciprocal-square-root seed and two Newton steps), so
+// every applied rotation is orthogonal to working precision.  Pairs follow the
+// round-robin (circle) ordering, n'/2 disjoint pairs per step, n'-1 steps per
+// sweep.  The iteration stops when a sweep makes no rotation.  When a sweep
+// made few rotations, the next one first runs a barrier-free check of all
+// pairs on the current columns; if no pair needs a rotation the iteration has
+// converged without a full barrier-separated sweep.  30 sweeps without
+// convergence report NS_ERR_NOCONV.
 #include <cmath>
 #include "ns_device.cuh"
 #include "ns_internal.h"
@@ -24,6 +43,7 @@ namespace ns {
 
 constexpr int kDenseThreads = 256;
 constexpr int kMaxSweeps = 30;
+constexpr int kCheckBelow = 4096;  // run the barrier-free check after a sweep with fewer rotations
 
 size_t dense_work_bytes(int64_t s, int64_t n) {
     Carver c(nullptr);
@@ -34,87 +54,235 @@ size_t dense_work_bytes(int64_t s, int64_t n) {
 DenseWork dense_carve(Carver &c, int64_t s, int64_t n) {
     DenseWork w;
     w.W = c.take<double>((size_t)(s * n));
-    w.tau = c.take<double>((size_t)n);
+    w.tau = c.take<double>((size_t)(2 * n));
     w.X = c.take<double>((size_t)(n * n));
     w.V = c.take<double>((size_t)(n * n));
     w.sigma = c.take<double>((size_t)n);
-    w.bar = c.take<unsigned int>(2 + 64);
+    w.L = c.take<double>((size_t)(n * n));
+    w.perm = c.take<int32_t>((size_t)n);
+    w.pivslot = c.take<unsigned long long>((size_t)n + 1);
+    w.bar = c.take<unsigned int>(2 + 2 * 64);
     return w;
 }
 
-// scaled 2-norm of x[0..len) over the block (every thread gets it)
-__device__ double block_norm2(const double *x, int64_t len, double *red) {
-    double mx = 0.0;
-    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) mx = fmax(mx, fabs(__ldcg(x + i)));
-    mx = block_max(mx, red);
-    if (mx == 0.0) return 0.0;
-    double v[1] = {0.0};
-    const double inv = 1.0 / mx;
-    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
-        const double y = __ldcg(x + i) * inv;
-        v[0] += y * y;
+// --------------------------------------------------------- reductions ----
+// Sum over the block of NV values per thread; the result is valid in thread 0
+// only.  A shared-memory halving tree down to one warp, then shuffles: about
+// log2(blockDim) dependent FP64 adds, executed by the fewest lanes possible.
+template <int NV>
+__device__ __forceinline__ void tree_sum(double (&v)[NV], double *red /* NV * blockDim */) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) red[i * nt + tid] = v[i];
+    __syncthreads();
+    for (int h = nt >> 1; h >= 32; h >>= 1) {
+        if (tid < h) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) red[i * nt + tid] += red[i * nt + tid + h];
+        }
+        __syncthreads();
     }
-    block_sum<1>(v, red);
-    return mx * sqrt(v[0]);
+    if (tid < 32) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] = warp_sum(red[i * nt + tid]);
+    }
+}
+
+// |x| as an ordered integer key (the bit pattern of a non-negative double
+// orders like the value); integer max keeps the FP64 pipe free.
+__device__ __forceinline__ long long abs_key(double x) { return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll; }
+
+// 2^-e with e the exponent of the largest |x| over the block: multiplying by it
+// is exact and brings the largest entry into [1, 2).  Returns the scale in every
+// thread (0 if all entries are zero).
+__device__ double block_pow2_scale(long long key, long long *redk) {
+    key = warp_max(key);
+    if ((threadIdx.x & 31) == 0) redk[threadIdx.x >> 5] = key;
+    __syncthreads();
+    long long k = redk[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) k = max(k, redk[w]);
+    __syncthreads();
+    if (k == 0) return 0.0;
+    const int e = (int)((unsigned long long)k >> 52);  // biased exponent of max |x|
+    int se = 2046 - e;                                  // 2^(1023 - e), biased
+    if (se < 1) se = 1;
+    if (se > 2046) se = 2046;
+    return __longlong_as_double((long long)se << 52);
 }
 
 // ------------------------------------------------------------------- QR ----
-// Reflector for column j (LAPACK-style): x = W[j:s, j]; H = I - tau u u^T with
-// u = [1; v]; afterwards W[j, j] = beta (= R[j, j]) and W[j+1:s, j] = v.
-__device__ void householder_column(double *x, int64_t len, double *tau_out, double *red) {
-    const double alpha = __ldcg(x);
-    const double xnorm = (len > 1) ? block_norm2(x + 1, len - 1, red) : 0.0;
-    if (xnorm == 0.0) {
-        if (threadIdx.x == 0) *tau_out = 0.0;
-        __syncthreads();
-        return;
-    }
-    const double beta = -copysign(hypot(alpha, xnorm), alpha);
-    const double tau = (beta - alpha) / beta;
-    const double inv = 1.0 / (alpha - beta);
-    for (int64_t i = 1 + threadIdx.x; i < len; i += blockDim.x) x[i] = __ldcg(x + i) * inv;
-    if (threadIdx.x == 0) {
-        x[0] = beta;
-        *tau_out = tau;
-    }
-    __threadfence();
-    __syncthreads();
-}
-
-__global__ void __launch_bounds__(kDenseThreads) qr_coop_kernel(double *W, int64_t s, int64_t n, double *tau,
-                                                               double *X, GridBarrier bar) {
-    extern __shared__ double vsh[];  // s doubles: the current reflector
-    __shared__ double red[64];
+// Cooperative Householder QR of W (rows x cols, ld = rows) with optional
+// column pivoting.  Logical column j is physical column perm[j].  Reflector j
+// (H = I - tau u u^T, u = [1; v]) is kept in W[j+1:rows, perm[j]] and tau[j].
+// The R factor (cols x cols, logical order) is written to Rout (ld = cols).
+// Every CTA forms reflector j itself from the (final) pivot column, so a step
+// needs one grid barrier.
+__global__ void __launch_bounds__(kDenseThreads) hqr_coop_kernel(double *W, int64_t rows, int64_t cols, int pivot,
+                                                                double *tau, int32_t *perm,
+                                                                unsigned long long *pivslot, double *Rout,
+                                                                GridBarrier bar) {
+    extern __shared__ double sh[];
+    double *vsh = sh;                            // rows
+    double *red = sh + rows;                     // 3 * blockDim
+    double *nrm = red + 3 * kDenseThreads;       // owned columns: current |.|^2
+    double *nref = nrm + (cols + gridDim.x - 1) / gridDim.x;  // value at the last recomputation
+    __shared__ long long redk[32];
+    __shared__ double par[4];                    // tau, beta, 1/(alpha - beta), pivot id
     const int64_t G = gridDim.x, me = blockIdx.x;
-    if (me == 0) householder_column(W, s, tau, red);
-    for (int64_t j = 0; j < n; ++j) {
-        if (!grid_sync(bar)) return;
-        const int64_t len = s - j;
-        const double tj = __ldcg(tau + j);
-        // first owned column after j
-        int64_t l0 = j + 1 + (((me - (j + 1)) % G) + G) % G;
-        if (tj != 0.0 && l0 < n) {
-            const double *v = W + j + j * s;
-            for (int64_t i = threadIdx.x; i < len; i += blockDim.x) vsh[i] = (i == 0) ? 1.0 : __ldcg(v + i);
+    const int tid = threadIdx.x;
+    const int64_t nown = (cols - me + G - 1) / G;  // owned physical columns me, me+G, ...
+    const int64_t steps = rows < cols ? rows : cols;
+
+    auto key_of = [&](double n2, int64_t l) -> unsigned long long {
+        return ((unsigned long long)__double_as_longlong(n2) & ~0x1FFFull) | (unsigned long long)(8191 - l);
+    };
+    // initial squared norms of owned columns and the first pivot candidate
+    if (pivot) {
+        unsigned long long best = 0;
+        for (int64_t o = 0; o < nown; ++o) {
+            const int64_t l = me + o * G;
+            const double *x = W + l * rows;
+            double v[1] = {0.0};
+            for (int64_t i = tid; i < rows; i += blockDim.x) {
+                const double a = x[i];
+                v[0] = fma(a, a, v[0]);
+            }
+            tree_sum<1>(v, red);
+            if (tid == 0) {
+                nrm[o] = v[0];
+                nref[o] = v[0];
+                const unsigned long long kk = key_of(v[0], l);
+                best = kk > best ? kk : best;
+            }
             __syncthreads();
-            for (int64_t l = l0; l < n; l += G) {
-                double *y = W + j + l * s;
-                double w[1] = {0.0};
-                for (int64_t i = threadIdx.x; i < len; i += blockDim.x) w[0] += vsh[i] * y[i];
-                block_sum<1>(w, red);
-                const double f = tj * w[0];
-                for (int64_t i = threadIdx.x; i < len; i += blockDim.x) y[i] -= f * vsh[i];
-                __syncthreads();
+        }
+        if (tid == 0 && nown > 0) atomicMax(pivslot, best);
+    }
+    for (int64_t j = 0; j < steps; ++j) {
+        if (!grid_sync(bar)) return;
+        int64_t p = j;
+        if (pivot) p = 8191 - (int64_t)(__ldcg(pivslot + j) & 0x1FFFull);
+        // ---- reflector of physical column p over rows j..rows-1 (every CTA)
+        const int64_t len = rows - j;
+        const double *xp = W + j + p * rows;
+        long long key = 0;
+        for (int64_t i = tid; i < len; i += blockDim.x) {
+            const double a = __ldcg(xp + i);
+            vsh[i] = a;
+            if (i > 0) key = max(key, abs_key(a));
+        }
+        const double sc = block_pow2_scale(key, redk);  // includes __syncthreads
+        double v1[1] = {0.0};
+        if (sc != 0.0)
+            for (int64_t i = 1 + tid; i < len; i += blockDim.x) {
+                const double a = vsh[i] * sc;
+                v1[0] = fma(a, a, v1[0]);
+            }
+        tree_sum<1>(v1, red);
+        if (tid == 0) {
+            const double alpha = vsh[0];
+            if (sc == 0.0) {
+                par[0] = 0.0;  // H = I
+                par[1] = alpha;
+                par[2] = 0.0;
+            } else {
+                const double xnorm = sqrt(v1[0]) / sc;
+                const double beta = -copysign(hypot(alpha, xnorm), alpha);
+                par[0] = (beta - alpha) / beta;
+                par[1] = beta;
+                par[2] = 1.0 / (alpha - beta);
             }
         }
+        __syncthreads();
+        const double tj = par[0], bj = par[1], inv = par[2];
+        for (int64_t i = 1 + tid; i < len; i += blockDim.x) vsh[i] *= inv;
+        if (tid == 0) vsh[0] = 1.0;
+        __syncthreads();
+        // the owner of p stores the reflector, R's diagonal entry and the permutation
+        if (p % G == me) {
+            double *xw = W + j + p * rows;
+            for (int64_t i = 1 + tid; i < len; i += blockDim.x) xw[i] = vsh[i];
+            if (tid == 0) {
+                xw[0] = bj;
+                tau[j] = tj;
+                perm[j] = (int32_t)p;
+                nrm[(p - me) / G] = -1.0;  // done
+            }
+        }
+        // ---- apply H_j to the owned remaining columns, downdate their norms
+        unsigned long long best = 0;
+        for (int64_t o = 0; o < nown; ++o) {
+            const int64_t l = me + o * G;
+            __syncthreads();
+            const bool remaining = pivot ? (nrm[o] >= 0.0) : (l > j);
+            if (!remaining || l == p) continue;
+            double *y = W + j + l * rows;
+            if (tj != 0.0) {
+                double w[1] = {0.0};
+                for (int64_t i = tid; i < len; i += blockDim.x) w[0] = fma(vsh[i], y[i], w[0]);
+                tree_sum<1>(w, red);
+                if (tid == 0) par[3] = tj * w[0];
+                __syncthreads();
+                const double f = par[3];
+                for (int64_t i = tid; i < len; i += blockDim.x) y[i] = fma(-f, vsh[i], y[i]);
+            }
+            if (pivot) {
+                __syncthreads();
+                if (tid == 0) {
+                    const double r = y[0];
+                    double n2 = nrm[o] - r * r;
+                    nrm[o] = n2;
+                    if (!(n2 > 1e-8 * nref[o])) nrm[o] = -2.0;  // recompute below
+                }
+                __syncthreads();
+                if (nrm[o] == -2.0) {
+                    double v[1] = {0.0};
+                    for (int64_t i = 1 + tid; i < len; i += blockDim.x) v[0] = fma(y[i], y[i], v[0]);
+                    tree_sum<1>(v, red);
+                    if (tid == 0) {
+                        nrm[o] = v[0];
+                        nref[o] = v[0];
+                    }
+                }
+                if (tid == 0) {
+                    const unsigned long long kk = key_of(nrm[o], l);
+                    best = kk > best ? kk : best;
+                }
+            }
+        }
+        if (pivot && tid == 0 && best) atomicMax(pivslot + j + 1, best);
         __threadfence();
-        // the owner of column j+1 forms its reflector (it applied H_j to it above)
-        if (j + 1 < n && (j + 1) % G == me) householder_column(W + (j + 1) + (j + 1) * s, s - j - 1, tau + j + 1, red);
     }
     if (!grid_sync(bar)) return;
-    // R = upper triangle of W
-    for (int64_t l = me; l < n; l += G)
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) X[i + l * n] = (i <= l) ? __ldcg(W + i + l * s) : 0.0;
+    // R in logical column order: R[i, j] = W[i, perm[j]] for i <= j
+    for (int64_t j = me; j < steps; j += G) {
+        const int64_t pj = __ldcg(perm + j);
+        for (int64_t i = tid; i < cols; i += blockDim.x)
+            Rout[i + j * cols] = (i <= j) ? __ldcg(W + i + pj * rows) : 0.0;
+    }
+}
+
+// ------------------------------------------------------------ transpose ----
+__global__ void transpose_kernel(const double *__restrict__ A, int64_t n, double *__restrict__ B) {
+    __shared__ double tile[32][33];
+    const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t i = bx + threadIdx.x, j = by + r;
+        if (i < n && j < n) tile[r][threadIdx.x] = A[i + j * n];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t i = by + threadIdx.x, j = bx + r;
+        if (i < n && j < n) B[i + j * n] = tile[threadIdx.x][r];
+    }
+}
+
+// X = R2^T from the QR of L (upper triangle of the output of hqr, in place)
+__global__ void r2t_kernel(const double *__restrict__ R2, int64_t n, double *__restrict__ X) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    const int64_t i = idx % n, j = idx / n;
+    X[i + j * n] = (i >= j) ? R2[j + i * n] : 0.0;
 }
 
 // --------------------------------------------------------------- Jacobi ----
@@ -122,16 +290,86 @@ __device__ __forceinline__ int64_t rr_player(int64_t pos, int64_t step, int64_t 
     return pos == 0 ? 0 : 1 + (pos - 1 + step) % (n2 - 1);
 }
 
+// Rotation for (alpha, beta, gamma): returns false if the pair is already
+// orthogonal to the tolerance.  One thread.
+__device__ __forceinline__ bool rotation(double alpha, double beta, double gamma, double tol2, double *c_out,
+                                         double *s_out) {
+    if (gamma == 0.0 || !(gamma * gamma > tol2 * alpha * beta)) return false;
+    const double mx = fmax(alpha, beta);
+    const int e = (int)(((unsigned long long)__double_as_longlong(mx) >> 52) & 0x7FF);
+    int se = 2046 - e;
+    se = se < 1 ? 1 : (se > 2046 ? 2046 : se);
+    const double sc = __longlong_as_double((long long)se << 52);
+    const float a32 = (float)(alpha * sc), b32 = (float)(beta * sc), g32 = (float)(gamma * sc);
+    double t;
+    if (fabsf(g32) < 1e-30f) {
+        t = gamma / (beta - alpha);  // tiny angle: t ~ gamma / (beta - alpha)
+    } else {
+        const float z = (b32 - a32) / (2.0f * g32);
+        float t32;
+        if (fabsf(z) > 1e18f) t32 = 0.5f / z;
+        else t32 = copysignf(1.0f, z) / (fabsf(z) + sqrtf(1.0f + z * z));
+        t = (double)t32;
+    }
+    const double tt = fma(t, t, 1.0);
+    double y = (double)rsqrtf((float)tt);
+    y = y * fma(-0.5 * tt, y * y, 1.5);
+    y = y * fma(-0.5 * tt, y * y, 1.5);
+    *c_out = y;
+    *s_out = y * t;
+    return true;
+}
+
+template <int RPT>
 __global__ void __launch_bounds__(kDenseThreads) jacobi_coop_kernel(double *X, double *V, int64_t n, double tol,
                                                                    GridBarrier bar, unsigned int *rotcount,
-                                                                   double *sigma, int32_t *status) {
-    __shared__ double red[96];
+                                                                   unsigned int *checkflag, double *sigma,
+                                                                   int32_t *status) {
+    __shared__ double red[3 * kDenseThreads];
+    __shared__ double par[3];
     const int64_t G = gridDim.x, me = blockIdx.x;
+    const int tid = threadIdx.x;
+    const double tol2 = tol * tol;
     for (int64_t l = me; l < n; l += G)
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) V[i + l * n] = (i == l) ? 1.0 : 0.0;
+        for (int64_t i = tid; i < n; i += blockDim.x) V[i + l * n] = (i == l) ? 1.0 : 0.0;
     const int64_t n2 = n + (n & 1), npairs = n2 / 2, steps = n2 - 1;
     bool converged = (n < 2);
+    unsigned int prev_rot = 0xFFFFFFFFu;
     for (int sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
+        if (prev_rot < (unsigned int)kCheckBelow) {
+            // ---- barrier-free check: does any pair need a rotation?  One warp per pair.
+            if (!grid_sync(bar)) return;
+            const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+            const int64_t total = n * (n - 1) / 2;
+            int any = 0;
+            for (int64_t pi = me * nw + wid; pi < total; pi += G * nw) {
+                int64_t p = (int64_t)((2.0 * n - 1 - sqrt((2.0 * n - 1) * (2.0 * n - 1) - 8.0 * pi)) / 2.0);
+                if (p < 0) p = 0;
+                while (p > 0 && p * (2 * n - p - 1) / 2 > pi) --p;
+                while ((p + 1) * (2 * n - p - 2) / 2 <= pi) ++p;
+                const int64_t q = pi - p * (2 * n - p - 1) / 2 + p + 1;
+                double a = 0.0, b = 0.0, g = 0.0;
+                for (int64_t i = lane; i < n; i += 32) {
+                    const double x = __ldcg(X + i + p * n), y = __ldcg(X + i + q * n);
+                    a = fma(x, x, a);
+                    b = fma(y, y, b);
+                    g = fma(x, y, g);
+                }
+                a = __shfl_sync(0xffffffffu, warp_sum(a), 0);
+                b = __shfl_sync(0xffffffffu, warp_sum(b), 0);
+                g = __shfl_sync(0xffffffffu, warp_sum(g), 0);
+                if (g != 0.0 && g * g > tol2 * a * b) {
+                    any = 1;
+                    break;
+                }
+            }
+            if (any && lane == 0) atomicAdd(checkflag + sweep, 1u);
+            if (!grid_sync(bar)) return;
+            if (*(volatile unsigned int *)(checkflag + sweep) == 0u) {
+                converged = true;
+                break;
+            }
+        }
         unsigned int local = 0;
         for (int64_t step = 0; step < steps; ++step) {
             if (!grid_sync(bar)) return;
@@ -142,165 +380,257 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_coop_kernel(double *X, d
                     p = q;
                     q = tmp;
                 }
-                if (q >= n) continue;  // phantom column
+                if (q >= n) continue;  // phantom column of an odd n
                 double *xp = X + p * n, *xq = X + q * n;
+                double ra[RPT], rb[RPT];
                 double a3[3] = {0.0, 0.0, 0.0};
-                for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-                    const double a = __ldcg(xp + i), b = __ldcg(xq + i);
-                    a3[0] += a * a;
-                    a3[1] += b * b;
-                    a3[2] += a * b;
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    const int64_t i = tid + (int64_t)r * kDenseThreads;
+                    ra[r] = (i < n) ? __ldcg(xp + i) : 0.0;
+                    rb[r] = (i < n) ? __ldcg(xq + i) : 0.0;
+                    a3[0] = fma(ra[r], ra[r], a3[0]);
+                    a3[1] = fma(rb[r], rb[r], a3[1]);
+                    a3[2] = fma(ra[r], rb[r], a3[2]);
                 }
-                block_sum<3>(a3, red);
-                const double alpha = a3[0], beta = a3[1], gamma = a3[2];
-                if (gamma == 0.0 || fabs(gamma) <= tol * sqrt(alpha) * sqrt(beta)) continue;
-                const double zeta = (beta - alpha) / (2.0 * gamma);
-                double t;
-                if (fabs(zeta) > 1e150) t = 0.5 / zeta;
-                else t = ((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                const double cs = 1.0 / sqrt(1.0 + t * t);
-                const double sn = cs * t;
+                tree_sum<3>(a3, red);
+                if (tid == 0) {
+                    double c = 1.0, s = 0.0;
+                    const bool rot = rotation(a3[0], a3[1], a3[2], tol2, &c, &s);
+                    par[0] = rot ? 1.0 : 0.0;
+                    par[1] = c;
+                    par[2] = s;
+                }
+                __syncthreads();
+                if (par[0] == 0.0) {
+                    __syncthreads();
+                    continue;
+                }
+                const double cs = par[1], sn = par[2];
                 double *vp = V + p * n, *vq = V + q * n;
-                for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-                    const double a = __ldcg(xp + i), b = __ldcg(xq + i);
-                    xp[i] = cs * a - sn * b;
-                    xq[i] = sn * a + cs * b;
-                    const double c = __ldcg(vp + i), d = __ldcg(vq + i);
-                    vp[i] = cs * c - sn * d;
-                    vq[i] = sn * c + cs * d;
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    const int64_t i = tid + (int64_t)r * kDenseThreads;
+                    if (i < n) {
+                        xp[i] = fma(cs, ra[r], -sn * rb[r]);
+                        xq[i] = fma(sn, ra[r], cs * rb[r]);
+                        const double c0 = __ldcg(vp + i), d0 = __ldcg(vq + i);
+                        vp[i] = fma(cs, c0, -sn * d0);
+                        vq[i] = fma(sn, c0, cs * d0);
+                    }
                 }
                 ++local;
+                __syncthreads();
             }
-            __threadfence();
         }
-        if (threadIdx.x == 0 && local) atomicAdd(rotcount + sweep, local);
+        if (tid == 0 && local) atomicAdd(rotcount + sweep, local);
         if (!grid_sync(bar)) return;
-        converged = (*(volatile unsigned int *)(rotcount + sweep) == 0u);
+        prev_rot = *(volatile unsigned int *)(rotcount + sweep);
+        converged = (prev_rot == 0u);
     }
-    if (!converged && me == 0 && threadIdx.x == 0) set_status(status, NS_ERR_NOCONV);
+    if (!converged && me == 0 && tid == 0) set_status(status, NS_ERR_NOCONV);
+    if (!grid_sync(bar)) return;
+    // sigma_l = |x_l| (scaled)
+    __shared__ long long redk[32];
     for (int64_t l = me; l < n; l += G) {
-        const double nv = block_norm2(X + l * n, n, red);
-        if (threadIdx.x == 0) sigma[l] = nv;
+        long long key = 0;
+        for (int64_t i = tid; i < n; i += blockDim.x) key = max(key, abs_key(__ldcg(X + i + l * n)));
+        const double sc = block_pow2_scale(key, redk);
+        double v[1] = {0.0};
+        if (sc != 0.0)
+            for (int64_t i = tid; i < n; i += blockDim.x) {
+                const double a = __ldcg(X + i + l * n) * sc;
+                v[0] = fma(a, a, v[0]);
+            }
+        tree_sum<1>(v, red);
+        if (tid == 0) sigma[l] = (sc == 0.0) ? 0.0 : sqrt(v[0]) / sc;
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------- V = P Q2 Vx (no barriers) ----
+// Q2 = H_0 H_1 ... H_{n-1} (reflectors of the QR of L = R^T kept in Lq); column c
+// of Q2 Vx is H_0 (H_1 (... (H_{n-1} vx_c))).  Row i of that product is row
+// perm[i] of V.
+__global__ void __launch_bounds__(kDenseThreads) apply_q2_kernel(const double *__restrict__ Lq,
+                                                                 const double *__restrict__ tau2,
+                                                                 const int32_t *__restrict__ perm,
+                                                                 const double *__restrict__ Vx, int64_t n,
+                                                                 double *__restrict__ V) {
+    extern __shared__ double col[];  // n
+    __shared__ double red[kDenseThreads];
+    __shared__ double fsh;
+    const int tid = threadIdx.x;
+    for (int64_t c = blockIdx.x; c < n; c += gridDim.x) {
+        for (int64_t i = tid; i < n; i += blockDim.x) col[i] = Vx[i + c * n];
+        __syncthreads();
+        for (int64_t j = n - 1; j >= 0; --j) {
+            const double tj = tau2[j];
+            if (tj == 0.0) continue;
+            const double *v = Lq + j * n;  // reflector j: u = [1; v(j+1:n)]
+            double w[1] = {0.0};
+            for (int64_t i = j + tid; i < n; i += blockDim.x) w[0] = fma(i == j ? 1.0 : v[i], col[i], w[0]);
+            tree_sum<1>(w, red);
+            if (tid == 0) fsh = tj * w[0];
+            __syncthreads();
+            const double f = fsh;
+            for (int64_t i = j + tid; i < n; i += blockDim.x) col[i] = fma(-f, i == j ? 1.0 : v[i], col[i]);
+            __syncthreads();
+        }
+        for (int64_t i = tid; i < n; i += blockDim.x) V[perm[i] + c * n] = col[i];
+        __syncthreads();
     }
 }
 
 // ----------------------------------------------------------- extraction ----
 // Order by non-increasing sigma (ties: lower index first); W = the last k
 // columns; each returned column is signed so its entry of largest magnitude
-// (lowest index on ties) is positive.
+// (lowest index on ties) is positive.  One CTA per returned column.
 __global__ void __launch_bounds__(kDenseThreads) extract_kernel(const double *V, const double *sigma, int64_t n,
-                                                               int32_t k, double *Vk, double *sigk, double *save_V,
-                                                               double *save_sigma) {
-    extern __shared__ int rank_sh[];  // n ints
-    __shared__ double redv[32];
-    __shared__ long long redi[32];
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+                                                               int32_t k, double *Vk, double *sigk) {
+    __shared__ int src_sh;
+    __shared__ long long bestk[32];
+    __shared__ int besti[32];
+    const int tid = threadIdx.x;
+    const int64_t col = blockIdx.x;  // output column
+    const int64_t want = (n - k) + col;  // rank of the wanted singular value
+    if (tid == 0) src_sh = -1;
+    __syncthreads();
+    for (int64_t i = tid; i < n; i += blockDim.x) {
         const double si = sigma[i];
-        int r = 0;
+        int64_t r = 0;
         for (int64_t j = 0; j < n; ++j) {
             const double sj = sigma[j];
             r += (sj > si || (sj == si && j < i)) ? 1 : 0;
         }
-        rank_sh[i] = r;
+        if (r == want) src_sh = (int)i;
     }
     __syncthreads();
-    if (save_V)
-        for (int64_t i = threadIdx.x; i < n * n; i += blockDim.x) save_V[i] = V[i];
-    if (save_sigma)
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) save_sigma[i] = sigma[i];
-    for (int64_t src = 0; src < n; ++src) {
-        const int r = rank_sh[src];
-        if (r < n - k) continue;
-        const int64_t col = r - (n - k);
-        const double *v = V + src * n;
-        // arg max |v| (lowest index on ties)
-        double best = -1.0;
-        long long bi = 0;
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-            const double a = fabs(v[i]);
-            if (a > best) {
-                best = a;
-                bi = i;
-            }
+    const int64_t src = src_sh;
+    const double *v = V + src * n;
+    long long bk = -1;
+    int bi = 0;
+    for (int64_t i = tid; i < n; i += blockDim.x) {
+        const long long kk = abs_key(v[i]);
+        if (kk > bk) {
+            bk = kk;
+            bi = (int)i;
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ob > best || (ob == best && oi < bi)) {
-                best = ob;
-                bi = oi;
-            }
-        }
-        if ((threadIdx.x & 31) == 0) {
-            redv[threadIdx.x >> 5] = best;
-            redi[threadIdx.x >> 5] = bi;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-                if (redv[w] > redv[0] || (redv[w] == redv[0] && redi[w] < redi[0])) {
-                    redv[0] = redv[w];
-                    redi[0] = redi[w];
-                }
-        }
-        __syncthreads();
-        const double sg = (v[redi[0]] < 0.0) ? -1.0 : 1.0;
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Vk[i + col * n] = sg * v[i];
-        if (threadIdx.x == 0) sigk[col] = sigma[src];
-        __syncthreads();
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ok > bk || (ok == bk && oi < bi)) {
+            bk = ok;
+            bi = oi;
+        }
+    }
+    if ((tid & 31) == 0) {
+        bestk[tid >> 5] = bk;
+        besti[tid >> 5] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (bestk[w] > bestk[0] || (bestk[w] == bestk[0] && besti[w] < besti[0])) {
+                bestk[0] = bestk[w];
+                besti[0] = besti[w];
+            }
+    }
+    __syncthreads();
+    const double sg = (v[besti[0]] < 0.0) ? -1.0 : 1.0;
+    for (int64_t i = tid; i < n; i += blockDim.x) Vk[i + col * n] = sg * v[i];
+    if (tid == 0) sigk[col] = sigma[src];
 }
 
-static int coop_blocks(const void *fn, int threads, size_t smem, int64_t want) {
-    int dev = 0, sms = 0, per_sm = 0;
+__global__ void copy_kernel(const double *__restrict__ a, int64_t len, double *__restrict__ b) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = a[i];
+}
+
+static int sm_count() {
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
-    const int64_t cap = (int64_t)sms * (per_sm > 0 ? (per_sm > 1 ? 1 : per_sm) : 1);
-    int64_t g = want < cap ? want : cap;
-    return (int)(g < 1 ? 1 : g);
+    return sms > 0 ? sms : 1;
+}
+
+template <int RPT>
+static cudaError_t launch_jacobi(const DenseWork &w, int64_t n, GridBarrier bar, int32_t *status, cudaStream_t st) {
+    const int64_t npairs = (n + (n & 1)) / 2;
+    int64_t G = npairs < sm_count() ? npairs : sm_count();
+    if (G < 1) G = 1;
+    double *X = w.X, *V = w.V, *sigma = w.sigma;
+    int64_t n_ = n;
+    double tol = (double)n * std::ldexp(1.0, -53);
+    unsigned int *rot = w.bar + 2, *chk = w.bar + 2 + 64;
+    int32_t *status_ = status;
+    void *args[] = {&X, &V, &n_, &tol, &bar, &rot, &chk, &sigma, &status_};
+    return cudaLaunchCooperativeKernel((const void *)jacobi_coop_kernel<RPT>, (int)G, kDenseThreads, args, 0, st);
+}
+
+static cudaError_t launch_hqr(double *W, int64_t rows, int64_t cols, int pivot, double *tau, int32_t *perm,
+                              unsigned long long *pivslot, double *Rout, GridBarrier bar, cudaStream_t st) {
+    int64_t G = cols < sm_count() ? cols : sm_count();
+    if (G < 1) G = 1;
+    const int64_t nown = (cols + G - 1) / G;
+    const size_t smem = sizeof(double) * (size_t)(rows + 3 * kDenseThreads + 2 * nown);
+    cudaError_t e = cudaFuncSetAttribute(hqr_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(pivslot, 0, sizeof(unsigned long long) * (size_t)(cols + 1), st);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&W, &rows, &cols, &pivot, &tau, &perm, &pivslot, &Rout, &bar};
+    return cudaLaunchCooperativeKernel((const void *)hqr_coop_kernel, (int)G, kDenseThreads, args, smem, st);
 }
 
 cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k, const DenseWork &w, double *Vk,
                                double *sigk, double *save_V, double *save_sigma, int32_t *status, cudaStream_t st) {
     cudaError_t e = cudaMemcpyAsync(w.W, SA, sizeof(double) * (size_t)(s * n), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * 66, st);
+    e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (2 + 2 * 64), st);
     if (e != cudaSuccess) return e;
     GridBarrier bar{w.bar, w.bar + 1, status};
-    // QR
+    // 1. SA P = Q1 R (pivoted); R (n x n) lands in X
+    e = launch_hqr(w.W, s, n, 1, w.tau, w.perm, w.pivslot, w.X, bar, st);
+    if (e != cudaSuccess) return e;
+    // 2. L = R^T; QR of L without pivoting: reflectors stay in L, R2 in V (scratch)
     {
-        const size_t smem = sizeof(double) * (size_t)s;
-        e = cudaFuncSetAttribute(qr_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        const int G = coop_blocks((const void *)qr_coop_kernel, kDenseThreads, smem, n);
-        double *W = w.W, *tau = w.tau, *X = w.X;
-        int64_t s_ = s, n_ = n;
-        void *args[] = {&W, &s_, &n_, &tau, &X, &bar};
-        e = cudaLaunchCooperativeKernel((const void *)qr_coop_kernel, G, kDenseThreads, args, smem, st);
-        if (e != cudaSuccess) return e;
+        dim3 tb(32, 8), grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
+        transpose_kernel<<<grid, tb, 0, st>>>(w.X, n, w.L);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    // Jacobi
+    e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * 2, st);
+    if (e != cudaSuccess) return e;
+    int32_t *perm2 = (int32_t *)w.sigma;  // unused permutation output of the unpivoted QR
+    e = launch_hqr(w.L, n, n, 0, w.tau + n, perm2, w.pivslot, w.V, bar, st);
+    if (e != cudaSuccess) return e;
+    // 3. X = R2^T; Jacobi on X (V receives Vx)
+    r2t_kernel<<<(unsigned)((n * n + 255) / 256), 256, 0, st>>>(w.V, n, w.X);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (2 + 2 * 64), st);
+    if (e != cudaSuccess) return e;
+    if (n <= 256) e = launch_jacobi<1>(w, n, bar, status, st);
+    else if (n <= 1024) e = launch_jacobi<4>(w, n, bar, status, st);
+    else e = launch_jacobi<16>(w, n, bar, status, st);
+    if (e != cudaSuccess) return e;
+    // 4. V = P Q2 Vx  (Vx is in w.V; the result goes to w.W, reused as n x n)
     {
-        e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * 66, st);
+        const size_t smem = sizeof(double) * (size_t)n;
+        e = cudaFuncSetAttribute(apply_q2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        const int64_t npairs = (n + (n & 1)) / 2;
-        const int G = coop_blocks((const void *)jacobi_coop_kernel, kDenseThreads, 0, npairs);
-        double *X = w.X, *V = w.V, *sigma = w.sigma;
-        int64_t n_ = n;
-        double tol = (double)n * std::ldexp(1.0, -53);
-        unsigned int *rot = w.bar + 2;
-        int32_t *status_ = status;
-        void *args[] = {&X, &V, &n_, &tol, &bar, &rot, &sigma, &status_};
-        e = cudaLaunchCooperativeKernel((const void *)jacobi_coop_kernel, G, kDenseThreads, args, 0, st);
-        if (e != cudaSuccess) return e;
+        const int64_t blocks = n < sm_count() * 4 ? n : sm_count() * 4;
+        apply_q2_kernel<<<(unsigned)blocks, kDenseThreads, smem, st>>>(w.L, w.tau + n, w.perm, w.V, n, w.W);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    // extraction
-    {
-        const size_t smem = sizeof(int) * (size_t)n;
-        e = cudaFuncSetAttribute(extract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        extract_kernel<<<1, kDenseThreads, smem, st>>>(w.V, w.sigma, n, k, Vk, sigk, save_V, save_sigma);
+    // 5. extraction (and the save buffers)
+    extract_kernel<<<(unsigned)k, kDenseThreads, 0, st>>>(w.W, w.sigma, n, k, Vk, sigk);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (save_V) {
+        copy_kernel<<<64, 256, 0, st>>>(w.W, n * n, save_V);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (save_sigma) {
+        copy_kernel<<<1, 256, 0, st>>>(w.sigma, n, save_sigma);
         e = cudaGetLastError();
     }
     return e;

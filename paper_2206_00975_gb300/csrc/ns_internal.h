@@ -59,12 +59,15 @@ cudaError_t launch_srht_f64(const double *A, int64_t m, int64_t n, int64_t lda, 
                             double *SA, int32_t *status, cudaStream_t st);
 
 struct DenseWork {
-    double *W;        // s x n working copy of SA (QR in place)
-    double *tau;      // n
-    double *X;        // n x n, R then X V
-    double *V;        // n x n
+    double *W;        // s x n working copy of SA (QR in place); later V (n x n)
+    double *tau;      // 2n: reflector factors of both QRs
+    double *X;        // n x n: R, then X = R2^T rotated into U Sigma
+    double *V;        // n x n: R2, then the accumulated rotations Vx
     double *sigma;    // n
-    unsigned int *bar;  // grid barrier words (2) + rotation counters (64)
+    double *L;        // n x n: R^T, then the reflectors of its QR
+    int32_t *perm;    // n: column pivots of the first QR
+    unsigned long long *pivslot;  // n + 1: pivot candidates (atomic max)
+    unsigned int *bar;  // grid barrier words (2), rotation counters (64), check flags (64)
 };
 size_t dense_work_bytes(int64_t s, int64_t n);
 DenseWork dense_carve(Carver &c, int64_t s, int64_t n);
