@@ -43,7 +43,8 @@ namespace ns {
 
 constexpr int kDenseThreads = 256;
 constexpr int kMaxSweeps = 30;
-constexpr int kCheckBelow = 4096;  // run the barrier-free check after a sweep with fewer rotations
+constexpr int kCheckBelow = 4096;        // run the barrier-free check after a sweep with fewer rotations
+constexpr int kBarWords = 64 + 2 * 64;   // barrier word (padded), rotation counts, check flags
 
 size_t dense_work_bytes(int64_t s, int64_t n) {
     Carver c(nullptr);
@@ -54,38 +55,15 @@ size_t dense_work_bytes(int64_t s, int64_t n) {
 DenseWork dense_carve(Carver &c, int64_t s, int64_t n) {
     DenseWork w;
     w.W = c.take<double>((size_t)(s * n));
-    w.tau = c.take<double>((size_t)(2 * n));
+    w.tau = c.take<double>((size_t)(4 * n));   // per reflector: u0 and coefficient, both QRs
     w.X = c.take<double>((size_t)(n * n));
     w.V = c.take<double>((size_t)(n * n));
     w.sigma = c.take<double>((size_t)n);
     w.L = c.take<double>((size_t)(n * n));
     w.perm = c.take<int32_t>((size_t)n);
     w.pivslot = c.take<unsigned long long>((size_t)n + 1);
-    w.bar = c.take<unsigned int>(2 + 2 * 64);
+    w.bar = c.take<unsigned int>(kBarWords);
     return w;
-}
-
-// --------------------------------------------------------- reductions ----
-// Sum over the block of NV values per thread; the result is valid in thread 0
-// only.  A shared-memory halving tree down to one warp, then shuffles: about
-// log2(blockDim) dependent FP64 adds, executed by the fewest lanes possible.
-template <int NV>
-__device__ __forceinline__ void tree_sum(double (&v)[NV], double *red /* NV * blockDim */) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-#pragma unroll
-    for (int i = 0; i < NV; ++i) red[i * nt + tid] = v[i];
-    __syncthreads();
-    for (int h = nt >> 1; h >= 32; h >>= 1) {
-        if (tid < h) {
-#pragma unroll
-            for (int i = 0; i < NV; ++i) red[i * nt + tid] += red[i * nt + tid + h];
-        }
-        __syncthreads();
-    }
-    if (tid < 32) {
-#pragma unroll
-        for (int i = 0; i < NV; ++i) v[i] = warp_sum(red[i * nt + tid]);
-    }
 }
 
 // |x| as an ordered integer key (the bit pattern of a non-negative double
@@ -106,48 +84,50 @@ __device__ double block_pow2_scale(long long key, long long *redk) {
     const int e = (int)((unsigned long long)k >> 52);  // biased exponent of max |x|
     int se = 2046 - e;                                  // 2^(1023 - e), biased
     if (se < 1) se = 1;
-    if (se > 2046) se = 2046;
+    if (se > 2045) se = 2045;                           // keeps 1/scale representable
     return __longlong_as_double((long long)se << 52);
 }
 
 // ------------------------------------------------------------------- QR ----
 // Cooperative Householder QR of W (rows x cols, ld = rows) with optional
-// column pivoting.  Logical column j is physical column perm[j].  Reflector j
-// (H = I - tau u u^T, u = [1; v]) is kept in W[j+1:rows, perm[j]] and tau[j].
-// The R factor (cols x cols, logical order) is written to Rout (ld = cols).
-// Every CTA forms reflector j itself from the (final) pivot column, so a step
-// needs one grid barrier.
+// column pivoting.  Logical column j is physical column perm[j].  With x the
+// pivot column's rows j..rows-1, beta = -sign(x_0) |x| and u = [x_0 - beta;
+// x_1; ...], reflector j is H = I - coef u u^T with coef = 1/(beta (beta - x_0))
+// (= 2/|u|^2).  The rows below the diagonal keep x itself (u below the first
+// entry); u0[j] = x_0 - beta and cf[j] = coef are kept aside and W[j, perm[j]]
+// receives beta = R[j, j].  Each step needs one square root and one
+// reciprocal, and one block reduction that also yields u . y for the CTA's
+// owned columns.  The R factor (logical column order) is written to Rout.
+// Every CTA forms reflector j from the final pivot column, so a step needs a
+// single grid barrier.
+template <int NB>
 __global__ void __launch_bounds__(kDenseThreads) hqr_coop_kernel(double *W, int64_t rows, int64_t cols, int pivot,
-                                                                double *tau, int32_t *perm,
+                                                                double *u0, double *cf, int32_t *perm,
                                                                 unsigned long long *pivslot, double *Rout,
                                                                 GridBarrier bar) {
     extern __shared__ double sh[];
-    double *vsh = sh;                            // rows
-    double *red = sh + rows;                     // 3 * blockDim
-    double *nrm = red + 3 * kDenseThreads;       // owned columns: current |.|^2
+    double *vsh = sh;                                   // rows
+    double *nrm = sh + rows;                            // owned columns: current |.|^2 (-1: done)
     double *nref = nrm + (cols + gridDim.x - 1) / gridDim.x;  // value at the last recomputation
+    __shared__ double red[32 * (NB + 1)];
     __shared__ long long redk[32];
-    __shared__ double par[4];                    // tau, beta, 1/(alpha - beta), pivot id
+    __shared__ double par[3];                           // coef, beta, u0
+    __shared__ double fsh[NB];
     const int64_t G = gridDim.x, me = blockIdx.x;
     const int tid = threadIdx.x;
-    const int64_t nown = (cols - me + G - 1) / G;  // owned physical columns me, me+G, ...
+    const int64_t nown = (cols - me + G - 1) / G;       // owned physical columns me, me+G, ...
     const int64_t steps = rows < cols ? rows : cols;
 
     auto key_of = [&](double n2, int64_t l) -> unsigned long long {
         return ((unsigned long long)__double_as_longlong(n2) & ~0x1FFFull) | (unsigned long long)(8191 - l);
     };
-    // initial squared norms of owned columns and the first pivot candidate
-    if (pivot) {
+    if (pivot) {  // initial squared norms of the owned columns, first pivot candidate
         unsigned long long best = 0;
         for (int64_t o = 0; o < nown; ++o) {
             const int64_t l = me + o * G;
-            const double *x = W + l * rows;
             double v[1] = {0.0};
-            for (int64_t i = tid; i < rows; i += blockDim.x) {
-                const double a = x[i];
-                v[0] = fma(a, a, v[0]);
-            }
-            tree_sum<1>(v, red);
+            for (int64_t i = tid; i < rows; i += blockDim.x) v[0] = fma(W[i + l * rows], W[i + l * rows], v[0]);
+            block_sum_t0<1>(v, red);
             if (tid == 0) {
                 nrm[o] = v[0];
                 nref[o] = v[0];
@@ -160,102 +140,115 @@ __global__ void __launch_bounds__(kDenseThreads) hqr_coop_kernel(double *W, int6
     }
     for (int64_t j = 0; j < steps; ++j) {
         if (!grid_sync(bar)) return;
-        int64_t p = j;
-        if (pivot) p = 8191 - (int64_t)(__ldcg(pivslot + j) & 0x1FFFull);
-        // ---- reflector of physical column p over rows j..rows-1 (every CTA)
+        const int64_t p = pivot ? 8191 - (int64_t)(__ldcg(pivslot + j) & 0x1FFFull) : j;
         const int64_t len = rows - j;
         const double *xp = W + j + p * rows;
         long long key = 0;
         for (int64_t i = tid; i < len; i += blockDim.x) {
             const double a = __ldcg(xp + i);
             vsh[i] = a;
-            if (i > 0) key = max(key, abs_key(a));
+            key = max(key, abs_key(a));
         }
+        if (pivot && p % G == me && tid == 0) nrm[(p - me) / G] = -1.0;  // the pivot column is done
         const double sc = block_pow2_scale(key, redk);  // includes __syncthreads
-        double v1[1] = {0.0};
-        if (sc != 0.0)
+        const double isc = (sc == 0.0) ? 0.0 : __longlong_as_double((2046ll << 52) - __double_as_longlong(sc));
+        const double alpha = vsh[0];
+        for (int64_t o0 = 0; o0 < nown || o0 == 0; o0 += NB) {
+            int64_t cl[NB];
+            int nb = 0;
+            for (int64_t o = o0; o < nown && nb < NB; ++o, ++nb) {
+                const int64_t l = me + o * G;
+                cl[nb] = (pivot ? (nrm[o] >= 0.0) : (l > j)) ? l : -1;
+            }
+            double acc[NB + 1];
+#pragma unroll
+            for (int b = 0; b <= NB; ++b) acc[b] = 0.0;
             for (int64_t i = 1 + tid; i < len; i += blockDim.x) {
-                const double a = vsh[i] * sc;
-                v1[0] = fma(a, a, v1[0]);
+                const double a = vsh[i];
+                if (o0 == 0) {
+                    const double as = a * sc;
+                    acc[0] = fma(as, as, acc[0]);
+                }
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+                    if (b < nb && cl[b] >= 0) acc[b + 1] = fma(a, W[j + i + cl[b] * rows], acc[b + 1]);
             }
-        tree_sum<1>(v1, red);
-        if (tid == 0) {
-            const double alpha = vsh[0];
-            if (sc == 0.0) {
-                par[0] = 0.0;  // H = I
-                par[1] = alpha;
-                par[2] = 0.0;
-            } else {
-                const double xnorm = sqrt(v1[0]) / sc;
-                const double beta = -copysign(hypot(alpha, xnorm), alpha);
-                par[0] = (beta - alpha) / beta;
-                par[1] = beta;
-                par[2] = 1.0 / (alpha - beta);
-            }
-        }
-        __syncthreads();
-        const double tj = par[0], bj = par[1], inv = par[2];
-        for (int64_t i = 1 + tid; i < len; i += blockDim.x) vsh[i] *= inv;
-        if (tid == 0) vsh[0] = 1.0;
-        __syncthreads();
-        // the owner of p stores the reflector, R's diagonal entry and the permutation
-        if (p % G == me) {
-            double *xw = W + j + p * rows;
-            for (int64_t i = 1 + tid; i < len; i += blockDim.x) xw[i] = vsh[i];
+            block_sum_t0<NB + 1>(acc, red);
             if (tid == 0) {
-                xw[0] = bj;
-                tau[j] = tj;
-                perm[j] = (int32_t)p;
-                nrm[(p - me) / G] = -1.0;  // done
+                if (o0 == 0) {
+                    if (sc == 0.0 || acc[0] == 0.0) {
+                        par[0] = 0.0;  // x[1:] = 0: H = I, R[j, j] = x_0
+                        par[1] = alpha;
+                        par[2] = 0.0;
+                    } else {
+                        const double as = alpha * sc;
+                        const double r = sqrt(fma(as, as, acc[0])) * isc;  // |x|
+                        const double beta = alpha >= 0.0 ? -r : r;
+                        par[0] = 1.0 / (beta * (beta - alpha));
+                        par[1] = beta;
+                        par[2] = alpha - beta;
+                    }
+                }
+                for (int b = 0; b < nb; ++b) {
+                    if (cl[b] < 0) continue;
+                    const double y0 = W[j + cl[b] * rows];
+                    fsh[b] = par[0] * fma(par[2], y0, acc[b + 1]);   // coef * (u . y)
+                }
             }
-        }
-        // ---- apply H_j to the owned remaining columns, downdate their norms
-        unsigned long long best = 0;
-        for (int64_t o = 0; o < nown; ++o) {
-            const int64_t l = me + o * G;
             __syncthreads();
-            const bool remaining = pivot ? (nrm[o] >= 0.0) : (l > j);
-            if (!remaining || l == p) continue;
-            double *y = W + j + l * rows;
-            if (tj != 0.0) {
-                double w[1] = {0.0};
-                for (int64_t i = tid; i < len; i += blockDim.x) w[0] = fma(vsh[i], y[i], w[0]);
-                tree_sum<1>(w, red);
-                if (tid == 0) par[3] = tj * w[0];
-                __syncthreads();
-                const double f = par[3];
-                for (int64_t i = tid; i < len; i += blockDim.x) y[i] = fma(-f, vsh[i], y[i]);
+            const double coef = par[0], ua = par[2];
+            if (coef != 0.0) {
+                for (int b = 0; b < nb; ++b) {
+                    if (cl[b] < 0) continue;
+                    double *y = W + j + cl[b] * rows;
+                    const double f = fsh[b];
+                    for (int64_t i = tid; i < len; i += blockDim.x) y[i] = fma(-f, i == 0 ? ua : vsh[i], y[i]);
+                }
             }
-            if (pivot) {
+            __syncthreads();
+            if (o0 + NB >= nown) break;
+        }
+        if (p % G == me && tid == 0) {  // owner: R's diagonal entry, reflector scalars, permutation
+            W[j + p * rows] = par[1];
+            cf[j] = par[0];
+            u0[j] = par[2];
+            perm[j] = (int32_t)p;
+        }
+        if (pivot) {  // downdate the owned norms; next pivot candidate
+            unsigned long long best = 0;
+            for (int64_t o = 0; o < nown; ++o) {
+                const int64_t l = me + o * G;
                 __syncthreads();
+                const bool skip = nrm[o] < 0.0;
+                __syncthreads();
+                if (skip) continue;
+                const double *y = W + j + l * rows;
                 if (tid == 0) {
                     const double r = y[0];
-                    double n2 = nrm[o] - r * r;
-                    nrm[o] = n2;
-                    if (!(n2 > 1e-8 * nref[o])) nrm[o] = -2.0;  // recompute below
+                    const double n2 = nrm[o] - r * r;
+                    nrm[o] = (n2 > 1e-8 * nref[o]) ? n2 : -2.0;  // -2: recompute below
                 }
                 __syncthreads();
                 if (nrm[o] == -2.0) {
                     double v[1] = {0.0};
                     for (int64_t i = 1 + tid; i < len; i += blockDim.x) v[0] = fma(y[i], y[i], v[0]);
-                    tree_sum<1>(v, red);
+                    block_sum_t0<1>(v, red);
                     if (tid == 0) {
                         nrm[o] = v[0];
                         nref[o] = v[0];
                     }
+                    __syncthreads();
                 }
                 if (tid == 0) {
                     const unsigned long long kk = key_of(nrm[o], l);
                     best = kk > best ? kk : best;
                 }
             }
+            if (tid == 0 && best) atomicMax(pivslot + j + 1, best);
         }
-        if (pivot && tid == 0 && best) atomicMax(pivslot + j + 1, best);
-        __threadfence();
     }
     if (!grid_sync(bar)) return;
-    // R in logical column order: R[i, j] = W[i, perm[j]] for i <= j
-    for (int64_t j = me; j < steps; j += G) {
+    for (int64_t j = me; j < steps; j += G) {  // R in logical column order
         const int64_t pj = __ldcg(perm + j);
         for (int64_t i = tid; i < cols; i += blockDim.x)
             Rout[i + j * cols] = (i <= j) ? __ldcg(W + i + pj * rows) : 0.0;
@@ -325,7 +318,7 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_coop_kernel(double *X, d
                                                                    GridBarrier bar, unsigned int *rotcount,
                                                                    unsigned int *checkflag, double *sigma,
                                                                    int32_t *status) {
-    __shared__ double red[3 * kDenseThreads];
+    __shared__ double red[32 * 3];
     __shared__ double par[3];
     const int64_t G = gridDim.x, me = blockIdx.x;
     const int tid = threadIdx.x;
@@ -393,7 +386,7 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_coop_kernel(double *X, d
                     a3[1] = fma(rb[r], rb[r], a3[1]);
                     a3[2] = fma(ra[r], rb[r], a3[2]);
                 }
-                tree_sum<3>(a3, red);
+                block_sum_t0<3>(a3, red);
                 if (tid == 0) {
                     double c = 1.0, s = 0.0;
                     const bool rot = rotation(a3[0], a3[1], a3[2], tol2, &c, &s);
@@ -442,39 +435,41 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_coop_kernel(double *X, d
                 const double a = __ldcg(X + i + l * n) * sc;
                 v[0] = fma(a, a, v[0]);
             }
-        tree_sum<1>(v, red);
+        block_sum_t0<1>(v, red);
         if (tid == 0) sigma[l] = (sc == 0.0) ? 0.0 : sqrt(v[0]) / sc;
         __syncthreads();
     }
 }
 
 // --------------------------------------------- V = P Q2 Vx (no barriers) ----
-// Q2 = H_0 H_1 ... H_{n-1} (reflectors of the QR of L = R^T kept in Lq); column c
-// of Q2 Vx is H_0 (H_1 (... (H_{n-1} vx_c))).  Row i of that product is row
-// perm[i] of V.
+// Q2 = H_0 H_1 ... H_{n-1} (reflectors of the QR of L = R^T: u = [u0[j];
+// L[j+1:n, j]], coefficient cf[j]); column c of Q2 Vx is H_0 (... (H_{n-1} vx_c)).
+// Row i of that product is row perm[i] of V.
 __global__ void __launch_bounds__(kDenseThreads) apply_q2_kernel(const double *__restrict__ Lq,
-                                                                 const double *__restrict__ tau2,
+                                                                 const double *__restrict__ u0,
+                                                                 const double *__restrict__ cf,
                                                                  const int32_t *__restrict__ perm,
                                                                  const double *__restrict__ Vx, int64_t n,
                                                                  double *__restrict__ V) {
     extern __shared__ double col[];  // n
-    __shared__ double red[kDenseThreads];
+    __shared__ double red[32];
     __shared__ double fsh;
     const int tid = threadIdx.x;
     for (int64_t c = blockIdx.x; c < n; c += gridDim.x) {
         for (int64_t i = tid; i < n; i += blockDim.x) col[i] = Vx[i + c * n];
         __syncthreads();
         for (int64_t j = n - 1; j >= 0; --j) {
-            const double tj = tau2[j];
-            if (tj == 0.0) continue;
-            const double *v = Lq + j * n;  // reflector j: u = [1; v(j+1:n)]
+            const double coef = cf[j];
+            if (coef == 0.0) continue;
+            const double *v = Lq + j * n;
+            const double ua = u0[j];
             double w[1] = {0.0};
-            for (int64_t i = j + tid; i < n; i += blockDim.x) w[0] = fma(i == j ? 1.0 : v[i], col[i], w[0]);
-            tree_sum<1>(w, red);
-            if (tid == 0) fsh = tj * w[0];
+            for (int64_t i = j + tid; i < n; i += blockDim.x) w[0] = fma(i == j ? ua : v[i], col[i], w[0]);
+            block_sum_t0<1>(w, red);
+            if (tid == 0) fsh = coef * w[0];
             __syncthreads();
             const double f = fsh;
-            for (int64_t i = j + tid; i < n; i += blockDim.x) col[i] = fma(-f, i == j ? 1.0 : v[i], col[i]);
+            for (int64_t i = j + tid; i < n; i += blockDim.x) col[i] = fma(-f, i == j ? ua : v[i], col[i]);
             __syncthreads();
         }
         for (int64_t i = tid; i < n; i += blockDim.x) V[perm[i] + c * n] = col[i];
@@ -563,51 +558,63 @@ static cudaError_t launch_jacobi(const DenseWork &w, int64_t n, GridBarrier bar,
     double *X = w.X, *V = w.V, *sigma = w.sigma;
     int64_t n_ = n;
     double tol = (double)n * std::ldexp(1.0, -53);
-    unsigned int *rot = w.bar + 2, *chk = w.bar + 2 + 64;
+    unsigned int *rot = w.bar + 64, *chk = w.bar + 64 + 64;
     int32_t *status_ = status;
     void *args[] = {&X, &V, &n_, &tol, &bar, &rot, &chk, &sigma, &status_};
     return cudaLaunchCooperativeKernel((const void *)jacobi_coop_kernel<RPT>, (int)G, kDenseThreads, args, 0, st);
 }
 
-static cudaError_t launch_hqr(double *W, int64_t rows, int64_t cols, int pivot, double *tau, int32_t *perm,
-                              unsigned long long *pivslot, double *Rout, GridBarrier bar, cudaStream_t st) {
+template <int NB>
+static cudaError_t launch_hqr_nb(double *W, int64_t rows, int64_t cols, int pivot, double *u0, double *cf,
+                                 int32_t *perm, unsigned long long *pivslot, double *Rout, GridBarrier bar, int64_t G,
+                                 cudaStream_t st) {
+    const int64_t nown = (cols + G - 1) / G;
+    const size_t smem = sizeof(double) * (size_t)(rows + 2 * nown);
+    cudaError_t e =
+        cudaFuncSetAttribute(hqr_coop_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&W, &rows, &cols, &pivot, &u0, &cf, &perm, &pivslot, &Rout, &bar};
+    return cudaLaunchCooperativeKernel((const void *)hqr_coop_kernel<NB>, (int)G, kDenseThreads, args, smem, st);
+}
+
+static cudaError_t launch_hqr(double *W, int64_t rows, int64_t cols, int pivot, double *u0, double *cf,
+                              int32_t *perm, unsigned long long *pivslot, double *Rout, GridBarrier bar,
+                              cudaStream_t st) {
     int64_t G = cols < sm_count() ? cols : sm_count();
     if (G < 1) G = 1;
+    cudaError_t e = cudaMemsetAsync(pivslot, 0, sizeof(unsigned long long) * (size_t)(cols + 1), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(bar.word, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
     const int64_t nown = (cols + G - 1) / G;
-    const size_t smem = sizeof(double) * (size_t)(rows + 3 * kDenseThreads + 2 * nown);
-    cudaError_t e = cudaFuncSetAttribute(hqr_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(pivslot, 0, sizeof(unsigned long long) * (size_t)(cols + 1), st);
-    if (e != cudaSuccess) return e;
-    void *args[] = {&W, &rows, &cols, &pivot, &tau, &perm, &pivslot, &Rout, &bar};
-    return cudaLaunchCooperativeKernel((const void *)hqr_coop_kernel, (int)G, kDenseThreads, args, smem, st);
+    if (nown <= 1) return launch_hqr_nb<1>(W, rows, cols, pivot, u0, cf, perm, pivslot, Rout, bar, G, st);
+    if (nown <= 2) return launch_hqr_nb<2>(W, rows, cols, pivot, u0, cf, perm, pivslot, Rout, bar, G, st);
+    if (nown <= 4) return launch_hqr_nb<4>(W, rows, cols, pivot, u0, cf, perm, pivslot, Rout, bar, G, st);
+    return launch_hqr_nb<8>(W, rows, cols, pivot, u0, cf, perm, pivslot, Rout, bar, G, st);
 }
 
 cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k, const DenseWork &w, double *Vk,
                                double *sigk, double *save_V, double *save_sigma, int32_t *status, cudaStream_t st) {
     cudaError_t e = cudaMemcpyAsync(w.W, SA, sizeof(double) * (size_t)(s * n), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (2 + 2 * 64), st);
-    if (e != cudaSuccess) return e;
-    GridBarrier bar{w.bar, w.bar + 1, status};
+    GridBarrier bar{w.bar, status};
+    double *u0a = w.tau, *cfa = w.tau + n, *u0b = w.tau + 2 * n, *cfb = w.tau + 3 * n;
     // 1. SA P = Q1 R (pivoted); R (n x n) lands in X
-    e = launch_hqr(w.W, s, n, 1, w.tau, w.perm, w.pivslot, w.X, bar, st);
+    e = launch_hqr(w.W, s, n, 1, u0a, cfa, w.perm, w.pivslot, w.X, bar, st);
     if (e != cudaSuccess) return e;
-    // 2. L = R^T; QR of L without pivoting: reflectors stay in L, R2 in V (scratch)
+    // 2. L = R^T; QR of L without pivoting: reflectors stay in L, R2 lands in V (scratch)
     {
         dim3 tb(32, 8), grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
         transpose_kernel<<<grid, tb, 0, st>>>(w.X, n, w.L);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * 2, st);
-    if (e != cudaSuccess) return e;
-    int32_t *perm2 = (int32_t *)w.sigma;  // unused permutation output of the unpivoted QR
-    e = launch_hqr(w.L, n, n, 0, w.tau + n, perm2, w.pivslot, w.V, bar, st);
+    int32_t *perm2 = (int32_t *)w.sigma;  // identity permutation of the unpivoted QR (unused)
+    e = launch_hqr(w.L, n, n, 0, u0b, cfb, perm2, w.pivslot, w.V, bar, st);
     if (e != cudaSuccess) return e;
     // 3. X = R2^T; Jacobi on X (V receives Vx)
     r2t_kernel<<<(unsigned)((n * n + 255) / 256), 256, 0, st>>>(w.V, n, w.X);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (2 + 2 * 64), st);
+    e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * kBarWords, st);
     if (e != cudaSuccess) return e;
     if (n <= 256) e = launch_jacobi<1>(w, n, bar, status, st);
     else if (n <= 1024) e = launch_jacobi<4>(w, n, bar, status, st);
@@ -619,7 +626,7 @@ cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k
         e = cudaFuncSetAttribute(apply_q2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         const int64_t blocks = n < sm_count() * 4 ? n : sm_count() * 4;
-        apply_q2_kernel<<<(unsigned)blocks, kDenseThreads, smem, st>>>(w.L, w.tau + n, w.perm, w.V, n, w.W);
+        apply_q2_kernel<<<(unsigned)blocks, kDenseThreads, smem, st>>>(w.L, u0b, cfb, w.perm, w.V, n, w.W);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // 5. extraction (and the save buffers)

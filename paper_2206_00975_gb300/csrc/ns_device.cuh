@@ -111,46 +111,78 @@ __device__ __forceinline__ double block_max(double v, double *scratch) {
 }
 
 // ---------------------------------------------------------- grid barrier ----
-// Barrier over all blocks of a cooperative launch.  State: two words that the
-// host zeroes before the launch.  The wait is bounded: after `limit` polls the
-// barrier records NS_ERR_TIMEOUT in *status and returns false; callers then
-// leave the kernel at the next check.
+// Barrier over all blocks of a cooperative launch on one 32-bit word: each
+// block adds 1 with release semantics, except block 0 which adds
+// 2^31 - (nblocks - 1), so the word's top bit flips exactly when the last block
+// arrives and its low bits return to their previous value.  Every block waits
+// (acquire loads) until the top bit differs from the one in the value its own
+// add returned.  The host zeroes the word before the launch.  The wait is
+// bounded: after `limit` polls the barrier records NS_ERR_TIMEOUT in *status
+// and returns false; callers then leave the kernel.
 struct GridBarrier {
-    unsigned int *count;
-    unsigned int *gen;
+    unsigned int *word;
     int32_t *status;
 };
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned int atom_add_release_u32(unsigned int *p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
 
 __device__ __forceinline__ bool grid_sync(const GridBarrier &b) {
     __syncthreads();
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         const unsigned int nblk = gridDim.x * gridDim.y * gridDim.z;
-        const unsigned int g = *(volatile unsigned int *)b.gen;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(b.count, 1u);
+        const bool first = (blockIdx.x | blockIdx.y | blockIdx.z) == 0;
+        const unsigned int inc = first ? (0x80000000u - (nblk - 1u)) : 1u;
+        const unsigned int old = atom_add_release_u32(b.word, inc);
         int ok = 1;
-        if (arrived == nblk - 1) {
-            *(volatile unsigned int *)b.count = 0u;
-            __threadfence();
-            atomicAdd(b.gen, 1u);
-        } else {
-            long long polls = 0;
-            const long long limit = 1ll << 24;  // ~ tens of ms; a healthy barrier takes ~2 us
-            while (*(volatile unsigned int *)b.gen == g) {
-                if (++polls > limit) {
-                    atomicMax(b.status, (int32_t)NS_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
+        long long polls = 0;
+        const long long limit = 1ll << 24;  // a healthy barrier needs a few hundred polls at most
+        while (((ld_acquire_u32(b.word) ^ old) & 0x80000000u) == 0u) {
+            if (++polls > limit) {
+                atomicMax(b.status, (int32_t)NS_ERR_TIMEOUT);
+                ok = 0;
+                break;
             }
         }
-        __threadfence();
         if (*(volatile int32_t *)b.status == NS_ERR_TIMEOUT) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// Sum over the block of NV values per thread, valid in thread 0: shuffles down
+// to lane 0 of each warp, then warp 0 adds the warp partials.
+template <int NV>
+__device__ __forceinline__ void block_sum_t0(double (&v)[NV], double *red /* 32 * NV */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) red[i * 32 + wid] = v[i];
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double a = lane < nw ? red[i * 32 + lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1)
+                if (o < nw) a += __shfl_down_sync(0xffffffffu, a, o);
+            v[i] = a;
+        }
+    }
 }
 
 __device__ __forceinline__ void set_status(int32_t *status, int32_t code) {
