@@ -209,9 +209,24 @@ def main():
             ms = float(t.item())
         return ms
 
+    # the same workload with the sparse-sign sketch (zeta = 8, s = 1024)
+    dsp = api.desc(api.NS_SPARSE_SIGN, s=S, seed=SEED, zeta=8)
+    ws_sp = api.workspace(dsp, M, N, K_NULL, dev)
+    status_sp = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def solve_sparse():
+        return api.ns_solve(dsp, A, K_NULL, save=False, status=status_sp, ws=ws_sp, stream=stream)
+
+    for _ in range(args.warmup):
+        solve_sparse()
+        api.ns_sketch(dsp, A, SA=SA, ws=ws_sp, stream=stream)
+    torch.cuda.synchronize()
+
     with ClockSampler(local) as clk:
         ms_solve = timed(lambda: solve(A), args.steps)
         ms_sketch = timed(lambda: api.ns_sketch(d, A, SA=SA, ws=ws, stream=stream), args.steps)
+        ms_solve_sp = timed(solve_sparse, args.steps)
+        ms_sketch_sp = timed(lambda: api.ns_sketch(dsp, A, SA=SA, ws=ws_sp, stream=stream), args.steps)
     clocks = clk.summary()
 
     # end to end through the public API: pinned host A in, V_k and sigma_k back to host
@@ -231,13 +246,17 @@ def main():
     # accuracy of the last solve
     Vk, sk, _, _ = solve(A)
     resid = float(api.ns_residual(A, Vk).item())
+    Vk_sp, sk_sp, _, _ = solve_sparse()
+    resid_sp = float(api.ns_residual(A, Vk_sp).item())
     torch.cuda.synchronize()
+    if int(status_sp.item()) != 0:
+        raise SystemExit("sparse-sign solve status %d" % int(status_sp.item()))
 
     n_ranks = world
+    sketch_bytes = M * N * 8 + S * N * 8                # read A once, write SA
     t_solve = ms_solve / 1e3
     value = n_ranks * args.steps / t_solve
     hbm_peak, peak_kind = peaks()
-    sketch_bytes = M * N * 8 + S * N * 8                # read A once, write SA
     sketch_gbs = sketch_bytes / (ms_sketch / args.steps / 1e3) / 1e9
     dense_ms = (ms_solve - ms_sketch) / args.steps
     line = {
@@ -251,6 +270,11 @@ def main():
                      "peak_source": peak_kind},
         "breakdown_ms": {"sketch": ms_sketch / args.steps, "qr_jacobi_extract": dense_ms},
         "accuracy": {"residual_AV_F": resid, "sigma_k": [float(x) for x in sk.cpu()]},
+        "sparse_sign": {"zeta": 8, "s": S, "solves_per_s": n_ranks * args.steps / (ms_solve_sp / 1e3),
+                        "sketch_ms": ms_sketch_sp / args.steps,
+                        "sketch_gbs": sketch_bytes / (ms_sketch_sp / args.steps / 1e3) / 1e9,
+                        "sketch_frac": sketch_bytes / (ms_sketch_sp / args.steps / 1e3) / 1e9 / hbm_peak,
+                        "residual_AV_F": resid_sp},
         "e2e": {"value": n_ranks * e2e_steps / (ms_e2e / 1e3), "unit": "solves/s",
                 "h2d_bytes_per_step": M * N * 8, "d2h_bytes_per_step": (N * K_NULL + K_NULL) * 8},
         "gpu_launches": 6 * args.steps,

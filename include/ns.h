@@ -164,13 +164,12 @@ ns_status ns_residual(const void *A, int32_t dtype, int64_t m, int64_t n, int64_
 ns_status ns_srht_meta(const ns_sketch_desc *desc, int64_t m, uint32_t *sign_words, int32_t *rows, void *stream);
 
 /*
- * ns_sparse_meta -- the sparse-sign sketch as buckets by output row (CSR of
- * S's transpose, stable in j): row_ptr (device, s+1 int32) and entries
- * (device, m*zeta int32): entry = j for d = +1 and ~j (bitwise not) for -1,
- * entries of row r ordered by increasing j.  ws as for ns_sketch.
+ * ns_sparse_meta -- the realisation of the sparse-sign sketch, column by column
+ * of S: rows (device, m*zeta int32) and signs (device, m*zeta int8); entries
+ * j*zeta .. j*zeta+zeta-1 describe column j of S: zeta distinct rows in [0, s)
+ * in draw order, each with value signs[.]/sqrt(zeta).
  */
-ns_status ns_sparse_meta(const ns_sketch_desc *desc, int64_t m, int32_t *row_ptr, int32_t *entries, void *ws,
-                         size_t ws_bytes, void *stream);
+ns_status ns_sparse_meta(const ns_sketch_desc *desc, int64_t m, int32_t *rows, int8_t *signs, void *stream);
 
 /*
  * ns_sketch_static -- the SRHT sketch of ns_sketch (FP64 input, NS_SRHT with

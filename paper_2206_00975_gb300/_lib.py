@@ -58,7 +58,7 @@ def load():
         "ns_backward": (ctypes.c_int, [D, i64, i64, i32, P, P, P, P, i64, P, sz, P]),
         "ns_residual": (ctypes.c_int, [P, i32, i64, i64, i64, P, i32, P, P, sz, P]),
         "ns_srht_meta": (ctypes.c_int, [D, i64, P, P, P]),
-        "ns_sparse_meta": (ctypes.c_int, [D, i64, P, P, P, sz, P]),
+        "ns_sparse_meta": (ctypes.c_int, [D, i64, P, P, P]),
         "ns_sketch_static": (ctypes.c_int, [D, P, i32, i64, i64, i64, P, P]),
     }
     for name, (res, args) in sig.items():

@@ -149,6 +149,15 @@ def ns_srht_meta(d, m, stream=None, device="cuda"):
     return words, rows
 
 
+def ns_sparse_meta(d, m, stream=None, device="cuda"):
+    """(rows m x zeta int32, signs m x zeta int8) of the sparse-sign realisation."""
+    rows = torch.empty((m, d.zeta), dtype=torch.int32, device=device)
+    signs = torch.empty((m, d.zeta), dtype=torch.int8, device=device)
+    st = _lib.load().ns_sparse_meta(ctypes.byref(d), int(m), _p(rows), _p(signs), _stream(stream))
+    _lib.check(st, "ns_sparse_meta")
+    return rows, signs
+
+
 def ns_sketch_static(d, A, SA=None, stream=None):
     """SRHT sketch using the library's own fixed scratch array: no workspace is
     passed and nothing is allocated by the call (the output SA is allocated

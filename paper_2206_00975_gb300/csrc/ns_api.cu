@@ -25,6 +25,7 @@ static bool desc_ok(const ns_sketch_desc *d) {
 // (kind, prec, dtype) triples with a GPU path
 static bool path_ok(const ns_sketch_desc *d, int32_t dtype) {
     if (d->kind == NS_SRHT) return d->prec == NS_PREC_FP64 && dtype == NS_F64;
+    if (d->kind == NS_SPARSE_SIGN) return d->prec == NS_PREC_FP64 && dtype == NS_F64;
     return false;
 }
 
@@ -37,6 +38,7 @@ static bool shape_ok(const ns_sketch_desc *d, int64_t m, int64_t n, int64_t lda)
 struct SolveLayout {
     int32_t *status_word;
     SrhtWork srht;
+    SparseWork sparse;
     double *SA;
     DenseWork dense;
     size_t bytes;
@@ -46,7 +48,10 @@ static SolveLayout solve_layout(void *ws, const ns_sketch_desc *d, int64_t m, in
     Carver c(ws);
     SolveLayout L;
     L.status_word = c.take<int32_t>(1);
-    L.srht = srht_carve(c, m, n, d->s);
+    L.srht = SrhtWork{nullptr, nullptr, nullptr};
+    L.sparse = SparseWork{nullptr, nullptr, nullptr};
+    if (d->kind == NS_SRHT) L.srht = srht_carve(c, m, n, d->s);
+    if (d->kind == NS_SPARSE_SIGN) L.sparse = sparse_carve(c, m, n, d->s, d->zeta);
     L.SA = need_sa ? c.take<double>((size_t)(d->s * n)) : nullptr;
     L.dense = dense_carve(c, d->s, n);
     L.bytes = c.used;
@@ -56,7 +61,11 @@ static SolveLayout solve_layout(void *ws, const ns_sketch_desc *d, int64_t m, in
 static ns_status cuda_status(cudaError_t e) { return e == cudaSuccess ? NS_OK : NS_ERR_CUDA; }
 
 static ns_status run_sketch(const ns_sketch_desc *d, const void *A, int64_t m, int64_t n, int64_t lda, double *SA,
-                            const SrhtWork &w, int32_t *status, cudaStream_t st) {
+                            const SolveLayout &L, int32_t *status, cudaStream_t st) {
+    if (d->kind == NS_SPARSE_SIGN)
+        return cuda_status(launch_sparse_f64(d->seed, (const double *)A, m, n, lda, d->s, d->zeta, L.sparse, SA,
+                                             status, st));
+    const SrhtWork &w = L.srht;
     const SrhtGeom g = srht_geom(m, n);
     cudaError_t e = launch_srht_meta(d->seed, g.lg, g.sign_words, d->s, w.sign_words, w.rows, st);
     if (e != cudaSuccess) return NS_ERR_CUDA;
@@ -134,13 +143,11 @@ ns_status ns_sketch(const ns_sketch_desc *d, const void *A, int32_t dtype, int64
     if (!desc_ok(d) || !A || !SA || !ws) return NS_ERR_INVALID_ARG;
     if (!path_ok(d, dtype) || !shape_ok(d, m, n, lda)) return NS_ERR_INVALID_ARG;
     if ((((uintptr_t)ws) & 255) != 0 || (((uintptr_t)A) & 7) != 0) return NS_ERR_INVALID_ARG;
-    Carver c(ws);
-    int32_t *status = c.take<int32_t>(1);
-    SrhtWork w = srht_carve(c, m, n, d->s);
-    if (c.used > ws_bytes) return NS_ERR_WORKSPACE;
+    SolveLayout L = solve_layout(ws, d, m, n, false);
+    if (L.bytes > ws_bytes) return NS_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemsetAsync(status, 0, sizeof(int32_t), st) != cudaSuccess) return NS_ERR_CUDA;
-    return run_sketch(d, A, m, n, lda, SA, w, status, st);
+    if (cudaMemsetAsync(L.status_word, 0, sizeof(int32_t), st) != cudaSuccess) return NS_ERR_CUDA;
+    return run_sketch(d, A, m, n, lda, SA, L, L.status_word, st);
 }
 
 ns_status ns_solve(const ns_sketch_desc *d, const void *A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
@@ -156,7 +163,7 @@ ns_status ns_solve(const ns_sketch_desc *d, const void *A, int32_t dtype, int64_
     int32_t *status = dev_status ? dev_status : L.status_word;
     if (cudaMemsetAsync(status, 0, sizeof(int32_t), st) != cudaSuccess) return NS_ERR_CUDA;
     double *SA = save ? save : L.SA;
-    ns_status r = run_sketch(d, A, m, n, lda, SA, L.srht, status, st);
+    ns_status r = run_sketch(d, A, m, n, lda, SA, L, status, st);
     if (r != NS_OK) return r;
     double *save_V = save ? save + d->s * n : nullptr;
     double *save_sigma = save ? save + d->s * n + n * n : nullptr;
@@ -193,10 +200,9 @@ ns_status ns_srht_meta(const ns_sketch_desc *d, int64_t m, uint32_t *sign_words,
     return cuda_status(launch_srht_meta(d->seed, lg, nwords, d->s, sign_words, rows, (cudaStream_t)stream));
 }
 
-ns_status ns_sparse_meta(const ns_sketch_desc *d, int64_t m, int32_t *row_ptr, int32_t *entries, void *ws,
-                         size_t ws_bytes, void *stream) {
-    (void)d; (void)m; (void)row_ptr; (void)entries; (void)ws; (void)ws_bytes; (void)stream;
-    return NS_ERR_INVALID_ARG;
+ns_status ns_sparse_meta(const ns_sketch_desc *d, int64_t m, int32_t *rows, int8_t *signs, void *stream) {
+    if (!desc_ok(d) || d->kind != NS_SPARSE_SIGN || m < 1 || !rows || !signs) return NS_ERR_INVALID_ARG;
+    return cuda_status(launch_sparse_meta(d->seed, d->s, d->zeta, m, rows, signs, (cudaStream_t)stream));
 }
 
 }  // extern "C"

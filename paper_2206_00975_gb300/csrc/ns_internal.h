@@ -58,6 +58,29 @@ cudaError_t launch_srht_meta(uint64_t seed, int lg, int64_t nsign_words, int64_t
 cudaError_t launch_srht_f64(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, const SrhtWork &w,
                             double *SA, int32_t *status, cudaStream_t st);
 
+struct SparseGeom {
+    int64_t ntile;        // 128-row tiles of A
+    int64_t nent;         // entries per tile (128 * zeta)
+    int64_t nsort;        // sort length (power of two >= nent)
+    int64_t ngrp16;       // 16-row groups of the output
+    int64_t nrowgrp;      // 256-row groups (CTAs along the output rows)
+    int64_t ncolgrp;      // 32-column groups
+    int64_t chunk_tiles;  // tiles per accumulator chunk
+    int64_t nchunk;
+    int fx_bits;          // fixed-point magnitude bits P
+};
+struct SparseWork {
+    uint32_t *entries;
+    int32_t *offsets;
+    double *partial;
+};
+SparseGeom sparse_geom(int64_t m, int64_t n, int64_t s, int zeta);
+SparseWork sparse_carve(Carver &c, int64_t m, int64_t n, int64_t s, int zeta);
+cudaError_t launch_sparse_meta(uint64_t seed, int64_t s, int zeta, int64_t m, int32_t *rows, int8_t *signs,
+                               cudaStream_t st);
+cudaError_t launch_sparse_f64(uint64_t seed, const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, int zeta,
+                              const SparseWork &w, double *SA, int32_t *status, cudaStream_t st);
+
 struct DenseWork {
     double *W;        // s x n working copy of SA (QR in place); later V (n x n)
     double *tau;      // 2n: reflector factors of both QRs
