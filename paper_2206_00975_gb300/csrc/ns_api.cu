@@ -24,7 +24,8 @@ static bool desc_ok(const ns_sketch_desc *d) {
 
 // (kind, prec, dtype) triples with a GPU path
 static bool path_ok(const ns_sketch_desc *d, int32_t dtype) {
-    if (d->kind == NS_SRHT) return d->prec == NS_PREC_FP64 && dtype == NS_F64;
+    if (d->kind == NS_SRHT)
+        return (d->prec == NS_PREC_FP64 && dtype == NS_F64) || (d->prec == NS_PREC_FP32_STREAM && dtype == NS_F32);
     if (d->kind == NS_SPARSE_SIGN) return d->prec == NS_PREC_FP64 && dtype == NS_F64;
     return false;
 }
@@ -69,6 +70,8 @@ static ns_status run_sketch(const ns_sketch_desc *d, const void *A, int64_t m, i
     const SrhtGeom g = srht_geom(m, n);
     cudaError_t e = launch_srht_meta(d->seed, g.lg, g.sign_words, d->s, w.sign_words, w.rows, st);
     if (e != cudaSuccess) return NS_ERR_CUDA;
+    if (d->prec == NS_PREC_FP32_STREAM)
+        return cuda_status(launch_srht_f32((const float *)A, m, n, lda, d->s, w, SA, status, st));
     return cuda_status(launch_srht_f64((const double *)A, m, n, lda, d->s, w, SA, status, st));
 }
 
@@ -133,16 +136,21 @@ int64_t ns_save_size(int64_t s, int64_t n) { return s * n + n * n + n; }
 
 size_t ns_workspace_size(const ns_sketch_desc *d, int64_t m, int64_t n, int32_t k) {
     if (!desc_ok(d) || m < 1 || n < 1 || n > kMaxN || k < 0) return 0;
-    const size_t solve = solve_layout(nullptr, d, m, n, true).bytes;
+    size_t need = solve_layout(nullptr, d, m, n, true).bytes;
     const size_t resid = align256(sizeof(double) * 4096);
-    return solve > resid ? solve : resid;
+    need = need > resid ? need : resid;
+    if (d->kind == NS_SRHT && k >= 1 && k < n) {
+        const size_t bw = backward_work_bytes(m, n, d->s, k);
+        need = need > bw ? need : bw;
+    }
+    return need;
 }
 
 ns_status ns_sketch(const ns_sketch_desc *d, const void *A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
                     double *SA, void *ws, size_t ws_bytes, void *stream) {
     if (!desc_ok(d) || !A || !SA || !ws) return NS_ERR_INVALID_ARG;
     if (!path_ok(d, dtype) || !shape_ok(d, m, n, lda)) return NS_ERR_INVALID_ARG;
-    if ((((uintptr_t)ws) & 255) != 0 || (((uintptr_t)A) & 7) != 0) return NS_ERR_INVALID_ARG;
+    if ((((uintptr_t)ws) & 255) != 0 || (((uintptr_t)A) & (dtype == NS_F32 ? 3 : 7)) != 0) return NS_ERR_INVALID_ARG;
     SolveLayout L = solve_layout(ws, d, m, n, false);
     if (L.bytes > ws_bytes) return NS_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
@@ -156,7 +164,7 @@ ns_status ns_solve(const ns_sketch_desc *d, const void *A, int32_t dtype, int64_
     if (!desc_ok(d) || !A || !Vk || !sigk || !ws) return NS_ERR_INVALID_ARG;
     if (!path_ok(d, dtype) || !shape_ok(d, m, n, lda)) return NS_ERR_INVALID_ARG;
     if (m < n || n > d->s || n > kMaxN || k < 1 || k > n) return NS_ERR_INVALID_ARG;
-    if ((((uintptr_t)ws) & 255) != 0 || (((uintptr_t)A) & 7) != 0) return NS_ERR_INVALID_ARG;
+    if ((((uintptr_t)ws) & 255) != 0 || (((uintptr_t)A) & (dtype == NS_F32 ? 3 : 7)) != 0) return NS_ERR_INVALID_ARG;
     SolveLayout L = solve_layout(ws, d, m, n, save == nullptr);
     if (L.bytes > ws_bytes) return NS_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
@@ -172,9 +180,15 @@ ns_status ns_solve(const ns_sketch_desc *d, const void *A, int32_t dtype, int64_
 
 ns_status ns_backward(const ns_sketch_desc *d, int64_t m, int64_t n, int32_t k, const double *save, const double *Vk,
                       const double *dVk, double *dA, int64_t ldd, void *ws, size_t ws_bytes, void *stream) {
-    (void)d; (void)m; (void)n; (void)k; (void)save; (void)Vk; (void)dVk; (void)dA; (void)ldd; (void)ws;
-    (void)ws_bytes; (void)stream;
-    return NS_ERR_INVALID_ARG;
+    if (!desc_ok(d) || d->kind != NS_SRHT || d->prec != NS_PREC_FP64) return NS_ERR_INVALID_ARG;
+    if (!save || !Vk || !dVk || !dA || !ws) return NS_ERR_INVALID_ARG;
+    if (m < n || n < 2 || n > kMaxN || k < 1 || k >= n || n > d->s || ldd < m) return NS_ERR_INVALID_ARG;
+    if (d->s > ((int64_t)1 << ceil_log2(m))) return NS_ERR_INVALID_ARG;
+    if ((((uintptr_t)ws) & 255) != 0) return NS_ERR_INVALID_ARG;
+    Carver c(ws);
+    BackwardWork w = backward_carve(c, m, n, d->s, k);
+    if (c.used > ws_bytes) return NS_ERR_WORKSPACE;
+    return cuda_status(launch_backward(d->seed, m, n, k, d->s, save, Vk, dVk, dA, ldd, w, (cudaStream_t)stream));
 }
 
 ns_status ns_residual(const void *A, int32_t dtype, int64_t m, int64_t n, int64_t lda, const double *W, int32_t k,

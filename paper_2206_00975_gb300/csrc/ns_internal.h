@@ -57,6 +57,8 @@ cudaError_t launch_srht_meta(uint64_t seed, int lg, int64_t nsign_words, int64_t
                              int32_t *rows, cudaStream_t st);
 cudaError_t launch_srht_f64(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, const SrhtWork &w,
                             double *SA, int32_t *status, cudaStream_t st);
+cudaError_t launch_srht_f32(const float *A, int64_t m, int64_t n, int64_t lda, int64_t s, const SrhtWork &w,
+                            double *SA, int32_t *status, cudaStream_t st);
 
 struct SparseGeom {
     int64_t ntile;        // 128-row tiles of A
@@ -80,6 +82,21 @@ cudaError_t launch_sparse_meta(uint64_t seed, int64_t s, int zeta, int64_t m, in
                                cudaStream_t st);
 cudaError_t launch_sparse_f64(uint64_t seed, const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, int zeta,
                               const SparseWork &w, double *SA, int32_t *status, cudaStream_t st);
+
+struct BackwardWork {
+    uint32_t *sign_words;
+    int32_t *rows;
+    int32_t *rank;
+    double *Y;         // n x k
+    double *P;         // s x 2k: SA Y, SA W
+    long long *q;      // s x n fixed-point image of dL/dSA / sqrt(s)
+    int32_t *colexp;   // n: fixed-point scale exponents
+};
+size_t backward_work_bytes(int64_t m, int64_t n, int64_t s, int32_t k);
+BackwardWork backward_carve(Carver &c, int64_t m, int64_t n, int64_t s, int32_t k);
+cudaError_t launch_backward(uint64_t seed, int64_t m, int64_t n, int32_t k, int64_t s, const double *save,
+                            const double *Vk, const double *dVk, double *dA, int64_t ldd, const BackwardWork &w,
+                            cudaStream_t st);
 
 struct DenseWork {
     double *W;        // s x n working copy of SA (QR in place); later V (n x n)

@@ -249,6 +249,138 @@ __global__ void srht_reduce_kernel(const double *__restrict__ partial, int64_t n
     SA[t + c * s] = a * scale;
 }
 
+// --------------------------------------------------------- FP32 stream ----
+// Precision variant: A stored in FP32 is streamed through the same blocked
+// transform in FP32 arithmetic.  The signs of D are applied exactly (sign-bit
+// flip); the +-1 butterflies and the sum over a chunk's blocks round in FP32;
+// chunk partials are summed in FP64.  Same layouts as the FP64 kernel.
+__device__ __forceinline__ void fwht64f(float (&z)[64]) {
+#pragma unroll
+    for (int h = 1; h < 64; h <<= 1) {
+#pragma unroll
+        for (int k = 0; k < 64; ++k) {
+            if ((k & h) == 0) {
+                const float a = z[k], b = z[k + h];
+                z[k] = a + b;
+                z[k + h] = a - b;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(64) srht_f32_chunk_kernel(const float *__restrict__ A, int64_t m, int64_t n,
+                                                            int64_t lda, int64_t s, int chunk, int64_t nchunk,
+                                                            const uint32_t *__restrict__ sign_words,
+                                                            const int32_t *__restrict__ rows,
+                                                            double *__restrict__ partial, int32_t *status,
+                                                            int vec_ok) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *Zs = (float *)smem_raw;                                 // 4096
+    float *acc = Zs + kBlock;                                      // s
+    unsigned long long *need = (unsigned long long *)(acc + ((s + 1) & ~1ll));  // 64
+    uint32_t *sgn = (uint32_t *)(need + 64);                       // 128
+    int32_t *rows_s = (int32_t *)(sgn + 128);                      // s
+
+    const int t = threadIdx.x;
+    const int64_t item = blockIdx.x;
+    const int64_t c = item / nchunk, ch = item - c * nchunk;
+    const float *Acol = A + c * lda;
+    for (int64_t i = t; i < s; i += 64) {
+        rows_s[i] = rows[i];
+        acc[i] = 0.0f;
+    }
+    need[t] = 0ull;
+    __syncthreads();
+    for (int64_t i = t; i < s; i += 64) {
+        const int lo = rows_s[i] & (kBlock - 1);
+        atomicOr(&need[(lo & 1) | ((lo >> 7) << 1)], 1ull << ((lo >> 1) & 63));
+    }
+    __syncthreads();
+    const unsigned long long myneed = need[t];
+    int nonfinite = 0;
+    float z[64];
+    for (int bl = 0; bl < chunk; ++bl) {
+        const int64_t b = ch * chunk + bl;
+        const int64_t base = b * kBlock;
+        sgn[t] = sign_words[(base >> 5) + t];
+        sgn[t + 64] = sign_words[(base >> 5) + 64 + t];
+#pragma unroll
+        for (int kk = 0; kk < 32; ++kk) {
+            const int64_t i0 = base + 2 * t + 128 * kk;
+            float a0 = 0.0f, a1 = 0.0f;
+            if (vec_ok && i0 + 1 < m) {
+                const float2 v = __ldcs((const float2 *)(Acol + i0));
+                a0 = v.x;
+                a1 = v.y;
+            } else {
+                if (i0 < m) a0 = __ldcs(Acol + i0);
+                if (i0 + 1 < m) a1 = __ldcs(Acol + i0 + 1);
+            }
+            z[2 * kk] = a0;
+            z[2 * kk + 1] = a1;
+        }
+        __syncthreads();  // publishes sgn[]
+#pragma unroll
+        for (int kk = 0; kk < 32; ++kk) {
+            const uint32_t sw = sgn[4 * kk + (t >> 4)] >> (2 * (t & 15));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t bits = __float_as_uint(z[2 * kk + h]);
+                if ((bits & 0x7F800000u) == 0x7F800000u) nonfinite = 1;
+                bits ^= ((sw >> h) & 1u) << 31;
+                z[2 * kk + h] = __uint_as_float(bits);
+            }
+        }
+        fwht64f(z);
+#pragma unroll
+        for (int kk = 0; kk < 32; ++kk) {
+            const int i = 2 * t + 128 * kk;
+            const int p = i ^ (((i >> 7) & 15) << 1);
+            *(float2 *)(Zs + p) = make_float2(z[2 * kk], z[2 * kk + 1]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 64; ++k) z[k] = Zs[swz(l2_elem(t, k))];
+        __syncthreads();
+        fwht64f(z);
+#pragma unroll
+        for (int k = 0; k < 64; ++k)
+            if ((myneed >> k) & 1ull) Zs[swz(l2_elem(t, k))] = z[k];
+        __syncthreads();
+        for (int64_t i = t; i < s; i += 64) {
+            const int r = rows_s[i];
+            const float v = Zs[swz(r & (kBlock - 1))];
+            const int neg = __popcll((unsigned long long)(r >> kBlockLog) & (unsigned long long)b) & 1;
+            acc[i] += neg ? -v : v;
+        }
+        __syncthreads();
+    }
+    double *out = partial + (ch * n + c) * s;
+    for (int64_t i = t; i < s; i += 64) out[i] = (double)acc[i];
+    if (nonfinite) set_status(status, NS_ERR_NONFINITE);
+}
+
+size_t srht_f32_smem(int64_t s) {
+    return (size_t)kBlock * 4 + (size_t)((s + 1) & ~1ll) * 4 + 64 * 8 + 128 * 4 + (size_t)s * 4;
+}
+
+cudaError_t launch_srht_f32(const float *A, int64_t m, int64_t n, int64_t lda, int64_t s, const SrhtWork &w,
+                            double *SA, int32_t *status, cudaStream_t st) {
+    const SrhtGeom g = srht_geom(m, n);
+    const size_t smem = srht_f32_smem(s);
+    cudaError_t e = cudaFuncSetAttribute(srht_f32_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int vec_ok = ((((uintptr_t)A) & 7) == 0 && (lda & 1) == 0) ? 1 : 0;
+    srht_f32_chunk_kernel<<<(unsigned)(n * g.nchunk), 64, smem, st>>>(A, m, n, lda, s, g.chunk, g.nchunk,
+                                                                      w.sign_words, w.rows, w.partial, status,
+                                                                      vec_ok);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    srht_reduce_kernel<<<(unsigned)((n * s + 255) / 256), 256, 0, st>>>(w.partial, n, s, g.nchunk,
+                                                                        1.0 / std::sqrt((double)s), SA);
+    return cudaGetLastError();
+}
+
 size_t srht_f64_smem(int64_t s) { return (size_t)kBlock * 8 + (size_t)s * 8 + 64 * 8 + 128 * 4 + 16 + (size_t)s * 4; }
 
 cudaError_t launch_srht_f64(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, const SrhtWork &w,

@@ -199,3 +199,31 @@ def test_residual_gpu(api):
     W = rng.standard_normal((12, 3))
     got = float(api.ns_residual(to_dev(api, A), api.colmajor(W, device="cuda")).item())
     assert abs(got - np.linalg.norm(A @ W)) <= 1e-12 * np.linalg.norm(A @ W)
+
+
+# ------------------------------------------------------------- FP32 stream ----
+@pytest.mark.parametrize("m,n,s", [(4096, 3, 128), (5000, 4, 256), ((1 << 18) + 3, 2, 2048)])
+def test_srht_fp32_stream_parity(api, m, n, s):
+    # FP32 arithmetic: error bound u32 * (log2 m' + 2) * ||A||_F per entry
+    rng = np.random.default_rng(m)
+    A32 = rng.standard_normal((m, n)).astype(np.float32)
+    d = api.desc(api.NS_SRHT, s=s, seed=4, prec=api.NS_PREC_FP32_STREAM)
+    SA = api.ns_sketch(d, api.colmajor(A32, device="cuda")).cpu().numpy()
+    A64 = A32.astype(np.float64)
+    ref = O.srht(4, s, A64)
+    tol = 2.0 ** -24 * (O.ceil_log2(m) + 2) * np.linalg.norm(A64)
+    assert np.max(np.abs(SA - ref)) <= tol
+
+
+def test_solve_fp32_stream_reports_error(api):
+    w = workloads.graded(seed=2, m=1 << 14, n=32, k=2, tail=1e-9, dtype=np.float32)
+    A32 = w["A"]
+    A64 = A32.astype(np.float64)
+    d = api.desc(api.NS_SRHT, s=128, seed=1, prec=api.NS_PREC_FP32_STREAM)
+    Vk, sk, _, status = api.ns_solve(d, api.colmajor(A32, device="cuda"), 2)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    ref = O.solve(O.SRHT, 1, 128, A64, 2)
+    r_gpu, r_or = O.residual(A64, Vk.cpu().numpy()), O.residual(A64, ref["Vk"])
+    # FP32 sketch noise ~ u32 ||A||: the residual stays within that of the FP64 oracle's
+    assert r_gpu <= r_or + 2.0 ** -24 * 20 * np.linalg.norm(A64)
