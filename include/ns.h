@@ -148,6 +148,43 @@ ns_status ns_backward(const ns_sketch_desc *desc, int64_t m, int64_t n, int32_t 
                       void *stream);
 
 /*
+ * One problem of a batch (ns_solve_batched).  Pointers are DEVICE pointers.
+ * For total least squares (Section 4) A = [X b] with n = n_X + 1 columns, k = 1
+ * and tls != 0: then x = -v(1:n-1)/v(n) is written to x (n-1 doubles), v the
+ * trailing right singular vector of the sketch.
+ */
+typedef struct {
+    const void *A;   /* m x n, column-major, leading dimension lda >= m; FP64 */
+    int64_t m, n, lda;
+    int64_t s;       /* SRHT sketch size: n <= s <= min(m', 16384) */
+    int32_t k;       /* trailing vectors, 1 <= k <= n */
+    int32_t tls;     /* nonzero: also solve the TLS problem (needs k = 1, n >= 2, x) */
+    uint64_t seed;   /* realisation of this problem's sketch */
+    double *Vk;      /* n x k out (ordering and signs as ns_solve) */
+    double *sigk;    /* k out */
+    double *x;       /* n - 1 out when tls != 0, else unused */
+} ns_problem;
+
+/* Workspace bytes for ns_solve_batched; host_problems is a HOST copy of the
+ * problem array.  Returns 0 if any problem is invalid. */
+size_t ns_batched_workspace_size(const ns_sketch_desc *desc, int32_t batch, const ns_problem *host_problems);
+
+/*
+ * ns_solve_batched -- Algorithm 1 (SRHT sketch, QR, Jacobi SVD, trailing
+ * vectors) on `batch` independent problems of arbitrary shapes in one
+ * sequence of launches with no host round trip: a persistent sketch kernel
+ * takes (problem, column) items from a device work counter, a persistent dense
+ * kernel takes whole problems.  desc: kind NS_SRHT, prec NS_PREC_FP64 (its s and
+ * seed are unused; each problem has its own).  host_problems and dev_problems
+ * hold the same array (host copy for validation and sizing, device copy for
+ * the kernels).  dev_status: device int32[batch], per-problem status
+ * (0, NS_ERR_NONFINITE, NS_ERR_NOCONV, NS_ERR_TLS_NOSOLUTION).
+ */
+ns_status ns_solve_batched(const ns_sketch_desc *desc, int32_t batch, const ns_problem *host_problems,
+                           const ns_problem *dev_problems, int32_t *dev_status, void *ws, size_t ws_bytes,
+                           void *stream);
+
+/*
  * ns_residual -- the objective of Problem 2.1, ||A W||_F, in one streaming
  * pass over A (evaluation only).  W is device n x k FP64; *out (device double)
  * receives the result.

@@ -20,12 +20,20 @@ NS_PREC_FP64, NS_PREC_FP32_STREAM, NS_PREC_BF16X3 = 0, 1, 2
 EXPORTS = [
     "ns_status_string", "ns_version", "ns_workspace_size", "ns_save_size", "ns_sketch", "ns_solve",
     "ns_backward", "ns_residual", "ns_srht_meta", "ns_sparse_meta", "ns_sketch_static",
+    "ns_batched_workspace_size", "ns_solve_batched",
 ]
 
 
 class SketchDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("zeta", ctypes.c_int32), ("s", ctypes.c_int64),
                 ("seed", ctypes.c_uint64), ("prec", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Problem(ctypes.Structure):
+    """ns_problem of include/ns.h (device pointers inside)."""
+    _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("lda", ctypes.c_int64),
+                ("s", ctypes.c_int64), ("k", ctypes.c_int32), ("tls", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("Vk", ctypes.c_void_p), ("sigk", ctypes.c_void_p), ("x", ctypes.c_void_p)]
 
 
 class NSError(RuntimeError):
@@ -60,6 +68,8 @@ def load():
         "ns_srht_meta": (ctypes.c_int, [D, i64, P, P, P]),
         "ns_sparse_meta": (ctypes.c_int, [D, i64, P, P, P]),
         "ns_sketch_static": (ctypes.c_int, [D, P, i32, i64, i64, i64, P, P]),
+        "ns_batched_workspace_size": (sz, [D, i32, P]),
+        "ns_solve_batched": (ctypes.c_int, [D, i32, P, P, P, P, sz, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

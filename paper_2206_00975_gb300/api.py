@@ -11,6 +11,7 @@ import ctypes
 import torch
 
 from . import _lib
+from ._lib import Problem  # noqa: F401
 from ._lib import (NS_F32, NS_F64, NS_GAUSSIAN, NS_PREC_BF16X3, NS_PREC_FP32_STREAM, NS_PREC_FP64,  # noqa: F401
                    NS_SPARSE_SIGN, NS_SRHT, NSError, SketchDesc)
 
@@ -168,3 +169,39 @@ def ns_sketch_static(d, A, SA=None, stream=None):
     st = _lib.load().ns_sketch_static(ctypes.byref(d), _p(A), _dtype_code(A), m, n, _ld(A), _p(SA), _stream(stream))
     _lib.check(st, "ns_sketch_static")
     return SA
+
+
+def ns_solve_batched(problems, stream=None, ws=None, device="cuda"):
+    """Batched Algorithm 1.  problems: list of dicts with A (column-major CUDA
+    tensor), s, k, seed and optionally tls=True.  Returns (list of (Vk, sigk, x),
+    status int32 tensor)."""
+    n_b = len(problems)
+    arr = (Problem * n_b)()
+    outs = []
+    for i, p in enumerate(problems):
+        A = p["A"]
+        m, n = A.shape
+        k = int(p.get("k", 1))
+        Vk = _empty_cm(n, k, A.device)
+        sigk = torch.empty(k, dtype=torch.float64, device=A.device)
+        x = torch.empty(max(n - 1, 1), dtype=torch.float64, device=A.device) if p.get("tls") else None
+        outs.append((Vk, sigk, x))
+        arr[i] = Problem(A.data_ptr(), m, n, _ld(A), int(p["s"]), k, 1 if p.get("tls") else 0,
+                         int(p.get("seed", 0)) & ((1 << 64) - 1), Vk.data_ptr(), sigk.data_ptr(),
+                         x.data_ptr() if x is not None else 0)
+    raw = bytes(arr)
+    dev_arr = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
+    status = torch.zeros(n_b, dtype=torch.int32, device=device)
+    d = desc(NS_SRHT, s=1, seed=0)
+    lib = _lib.load()
+    nbytes = int(lib.ns_batched_workspace_size(ctypes.byref(d), n_b, ctypes.byref(arr)))
+    if nbytes == 0:
+        raise NSError(_lib.NS_ERR_INVALID_ARG, "ns_batched_workspace_size")
+    if ws is None or ws.numel() < nbytes:
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    st = lib.ns_solve_batched(ctypes.byref(d), n_b, ctypes.byref(arr), _p(dev_arr), _p(status), _p(ws), ws.numel(),
+                              _stream(stream))
+    _lib.check(st, "ns_solve_batched")
+    # keep the device copy of the descriptors alive until the work is done
+    outs_ref = (outs, dev_arr, ws)
+    return outs_ref[0], status, outs_ref

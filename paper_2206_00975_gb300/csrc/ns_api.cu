@@ -191,6 +191,34 @@ ns_status ns_backward(const ns_sketch_desc *d, int64_t m, int64_t n, int32_t k, 
     return cuda_status(launch_backward(d->seed, m, n, k, d->s, save, Vk, dVk, dA, ldd, w, (cudaStream_t)stream));
 }
 
+static bool problem_ok(const ns_problem &p) {
+    if (!p.A || !p.Vk || !p.sigk) return false;
+    if (p.m < 1 || p.n < 1 || p.m < p.n || p.lda < p.m || p.n > kMaxN) return false;
+    if (p.s < p.n || p.s > kMaxS || p.s > ((int64_t)1 << ceil_log2(p.m))) return false;
+    if (p.k < 1 || p.k > p.n) return false;
+    if (p.tls && (p.k != 1 || p.n < 2 || !p.x)) return false;
+    if ((((uintptr_t)p.A) & 7) != 0) return false;
+    return true;
+}
+
+size_t ns_batched_workspace_size(const ns_sketch_desc *d, int32_t batch, const ns_problem *host) {
+    if (!d || d->kind != NS_SRHT || d->prec != NS_PREC_FP64 || batch < 1 || !host) return 0;
+    for (int32_t i = 0; i < batch; ++i)
+        if (!problem_ok(host[i])) return 0;
+    return batched_work_bytes(batch, host);
+}
+
+ns_status ns_solve_batched(const ns_sketch_desc *d, int32_t batch, const ns_problem *host, const ns_problem *dev,
+                           int32_t *dev_status, void *ws, size_t ws_bytes, void *stream) {
+    if (!d || d->kind != NS_SRHT || d->prec != NS_PREC_FP64) return NS_ERR_INVALID_ARG;
+    if (batch < 1 || !host || !dev || !dev_status || !ws) return NS_ERR_INVALID_ARG;
+    if ((((uintptr_t)ws) & 255) != 0) return NS_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < batch; ++i)
+        if (!problem_ok(host[i])) return NS_ERR_INVALID_ARG;
+    if (batched_work_bytes(batch, host) > ws_bytes) return NS_ERR_WORKSPACE;
+    return cuda_status(launch_batched(batch, host, dev, dev_status, ws, (cudaStream_t)stream));
+}
+
 ns_status ns_residual(const void *A, int32_t dtype, int64_t m, int64_t n, int64_t lda, const double *W, int32_t k,
                       double *out, void *ws, size_t ws_bytes, void *stream) {
     if (!A || !W || !out || !ws || dtype != NS_F64) return NS_ERR_INVALID_ARG;

@@ -98,6 +98,10 @@ cudaError_t launch_backward(uint64_t seed, int64_t m, int64_t n, int32_t k, int6
                             const double *Vk, const double *dVk, double *dA, int64_t ldd, const BackwardWork &w,
                             cudaStream_t st);
 
+size_t batched_work_bytes(int32_t batch, const ns_problem *host);
+cudaError_t launch_batched(int32_t batch, const ns_problem *host, const ns_problem *dev, int32_t *status, void *ws,
+                           cudaStream_t st);
+
 struct DenseWork {
     double *W;        // s x n working copy of SA (QR in place); later V (n x n)
     double *tau;      // 2n: reflector factors of both QRs

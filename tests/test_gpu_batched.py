@@ -1,0 +1,113 @@
+"""GPU parity of ns_solve_batched (uneven TLS and general problems) against the
+oracle, per problem, and against single-problem ns_solve.
+
+TLS (Section 4): x = -v(1:n)/v(n+1) from the trailing right singular vector of
+the sketched [X b]; compared with the oracle's sketched TLS on the same sketch
+(relative 1e-8, the gap sigma_n(X)/sigma_{n+1}([X b]) ~ 1e3 allows it).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2206_00975_gb300 import workloads
+from tests.helpers import sine
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+U53 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_00975_gb300 import build
+    build.build()
+    from paper_2206_00975_gb300 import api as a
+    return a
+
+
+def test_batched_tls_matches_oracle(api):
+    ms, ns = workloads.tls_batch_shapes(seed=3, batch=24, m_lo=2048, m_hi=20000, n_lo=8, n_hi=64)
+    rng = np.random.default_rng(5)
+    probs, host = [], []
+    for i, (m, n) in enumerate(zip(ms, ns)):
+        Xb, x_true = workloads.tls_problem(rng, int(m), int(n))
+        s = 2 * (int(n) + 1)
+        host.append((Xb, s, 100 + i))
+        probs.append({"A": api.colmajor(Xb, device="cuda"), "s": s, "k": 1, "seed": 100 + i, "tls": True})
+    outs, status, keep = api.ns_solve_batched(probs)
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    for (Xb, s, seed), (Vk, sk, x) in zip(host, outs):
+        x_or, v_or, st = O.tls(seed, s, Xb)
+        assert st == O.OK
+        xg = x.cpu().numpy()
+        assert np.linalg.norm(xg - x_or) <= 1e-8 * np.linalg.norm(x_or)
+        assert sine(v_or[:, None], Vk.cpu().numpy()) < 1e-8
+
+
+def test_batched_general_problems(api):
+    rng = np.random.default_rng(9)
+    shapes = [(5000, 24, 96, 2), (300, 3, 8, 1), (4096, 32, 128, 4), (9000, 17, 40, 17), (70000, 40, 200, 3)]
+    probs, refs = [], []
+    for i, (m, n, s, k) in enumerate(shapes):
+        w = workloads.graded(seed=i, m=m, n=n, k=min(k, n), tail=1e-9)
+        probs.append({"A": api.colmajor(w["A"], device="cuda"), "s": s, "k": k, "seed": 7 * i + 1})
+        refs.append((w["A"], O.solve(O.SRHT, 7 * i + 1, s, w["A"], k)))
+    outs, status, keep = api.ns_solve_batched(probs)
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    for (A, ref), (Vk, sk, _) in zip(refs, outs):
+        Vg = Vk.cpu().numpy()
+        n = A.shape[1]
+        r_gpu, r_or = O.residual(A, Vg), O.residual(A, ref["Vk"])
+        assert r_gpu <= (1 + 1e-10) * r_or + 10 * U53 * np.sqrt(n) * np.linalg.norm(A)
+        if Vg.shape[1] < n:
+            assert sine(ref["Vk"], Vg) < 1e-8
+        np.testing.assert_allclose(sk.cpu().numpy(), ref["sigk"], rtol=1e-6, atol=1e-14)
+
+
+def test_batched_matches_single_solves(api):
+    rng = np.random.default_rng(2)
+    probs, singles = [], []
+    for i in range(6):
+        m, n = int(rng.integers(3000, 9000)), int(rng.integers(5, 30))
+        A = np.asfortranarray(rng.standard_normal((m, n)))
+        Ad = api.colmajor(A, device="cuda")
+        probs.append({"A": Ad, "s": 2 * n, "k": 2, "seed": i})
+        d = api.desc(api.NS_SRHT, s=2 * n, seed=i)
+        Vk, sk, _, _ = api.ns_solve(d, Ad, 2)
+        singles.append((Vk.cpu().numpy(), sk.cpu().numpy()))
+    outs, status, keep = api.ns_solve_batched(probs)
+    torch.cuda.synchronize()
+    for (Vk, sk, _), (V1, s1) in zip(outs, singles):
+        np.testing.assert_allclose(sk.cpu().numpy(), s1, rtol=1e-12)
+        assert sine(V1, Vk.cpu().numpy()) < 1e-10
+
+
+def test_batched_per_problem_status(api):
+    rng = np.random.default_rng(1)
+    A1 = rng.standard_normal((2000, 6))
+    A2 = A1.copy()
+    A2[17, 3] = np.inf
+    X = rng.standard_normal((3000, 4))
+    X[:, 3] = X[:, 2]
+    Xb = np.column_stack([X, rng.standard_normal(3000)])  # null vector e3 - e4: no TLS solution
+    probs = [{"A": api.colmajor(A1, device="cuda"), "s": 12, "k": 1, "seed": 1},
+             {"A": api.colmajor(A2, device="cuda"), "s": 12, "k": 1, "seed": 1},
+             {"A": api.colmajor(Xb, device="cuda"), "s": 10, "k": 1, "seed": 2, "tls": True}]
+    outs, status, keep = api.ns_solve_batched(probs)
+    torch.cuda.synchronize()
+    st = status.cpu().numpy()
+    assert st[0] == 0
+    assert st[1] == api._lib.NS_ERR_NONFINITE
+    assert st[2] == api._lib.NS_ERR_TLS_NOSOLUTION
+
+
+def test_batched_rejects_invalid_problem(api):
+    A = api.colmajor(np.ones((100, 4)), device="cuda")
+    with pytest.raises(api.NSError):
+        api.ns_solve_batched([{"A": A, "s": 2, "k": 1, "seed": 0}])      # s < n
+    with pytest.raises(api.NSError):
+        api.ns_solve_batched([{"A": A, "s": 8, "k": 2, "seed": 0, "tls": True}])  # TLS needs k = 1
