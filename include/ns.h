@@ -185,6 +185,30 @@ ns_status ns_solve_batched(const ns_sketch_desc *desc, int32_t batch, const ns_p
                            void *stream);
 
 /*
+ * ns_aaa_real -- AAA rational approximation of f on real points x (Section
+ * 6) with a reused SRHT sketch: K iterations; iteration k picks the support
+ * point maximising |f - r| (r_0 = mean f; lowest index on ties), downdates the
+ * sketch by the new support row (Algorithm 3 with the non-Gaussian rule of
+ * Section 5.3; S e_j in closed form), sketches the new Loewner column
+ * (f_i - f_j)/(x_i - x_j), and takes the barycentric weights w as the trailing
+ * right singular vector of the first min(4k, s) rows of the s-row sketch
+ * (Algorithm 1 on the sketch).  Everything stays on the device: the call only
+ * enqueues kernels, so it can be captured in a CUDA graph (make one un-captured
+ * call first).
+ *   desc    NS_SRHT, NS_PREC_FP64, s = the sketch rows (K <= s <= m').
+ *   x, f    device, m FP64 (distinct points).
+ *   forced  device int64[K] or NULL: support points to use instead of the
+ *           greedy choice (teacher forcing).
+ *   support device int64[K] out; W device FP64 K x K out, row k-1 = weights of
+ *           iteration k (zero padded); errmax device FP64[K] out, max |f - r|
+ *           after iteration k; SAk_out device FP64 s x K or NULL (final sketch).
+ */
+size_t ns_aaa_workspace_size(const ns_sketch_desc *desc, int64_t m, int32_t K);
+ns_status ns_aaa_real(const ns_sketch_desc *desc, const double *x, const double *f, int64_t m, int32_t K,
+                      const int64_t *forced, int64_t *support, double *W, double *errmax, double *SAk_out,
+                      int32_t *dev_status, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * ns_residual -- the objective of Problem 2.1, ||A W||_F, in one streaming
  * pass over A (evaluation only).  W is device n x k FP64; *out (device double)
  * receives the result.

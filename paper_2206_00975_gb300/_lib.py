@@ -20,7 +20,7 @@ NS_PREC_FP64, NS_PREC_FP32_STREAM, NS_PREC_BF16X3 = 0, 1, 2
 EXPORTS = [
     "ns_status_string", "ns_version", "ns_workspace_size", "ns_save_size", "ns_sketch", "ns_solve",
     "ns_backward", "ns_residual", "ns_srht_meta", "ns_sparse_meta", "ns_sketch_static",
-    "ns_batched_workspace_size", "ns_solve_batched",
+    "ns_batched_workspace_size", "ns_solve_batched", "ns_aaa_workspace_size", "ns_aaa_real",
 ]
 
 
@@ -70,6 +70,8 @@ def load():
         "ns_sketch_static": (ctypes.c_int, [D, P, i32, i64, i64, i64, P, P]),
         "ns_batched_workspace_size": (sz, [D, i32, P]),
         "ns_solve_batched": (ctypes.c_int, [D, i32, P, P, P, P, sz, P]),
+        "ns_aaa_workspace_size": (sz, [D, i64, i32]),
+        "ns_aaa_real": (ctypes.c_int, [D, P, P, i64, i32, P, P, P, P, P, P, P, sz, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

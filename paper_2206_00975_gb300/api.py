@@ -205,3 +205,29 @@ def ns_solve_batched(problems, stream=None, ws=None, device="cuda"):
     # keep the device copy of the descriptors alive until the work is done
     outs_ref = (outs, dev_arr, ws)
     return outs_ref[0], status, outs_ref
+
+
+def ns_aaa_real(x, f, K, smax, seed=0, forced=None, want_sketch=False, ws=None, stream=None):
+    """AAA with a reused SRHT sketch (Section 6.2) on the GPU.  x, f: CUDA float64
+    vectors.  Returns dict(support, W, errmax, status[, SAk]) as device tensors."""
+    m = x.numel()
+    dev = x.device
+    d = desc(NS_SRHT, s=smax, seed=seed)
+    lib = _lib.load()
+    nbytes = int(lib.ns_aaa_workspace_size(ctypes.byref(d), m, int(K)))
+    if nbytes == 0:
+        raise NSError(_lib.NS_ERR_INVALID_ARG, "ns_aaa_workspace_size")
+    if ws is None:
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    out = {"support": torch.empty(K, dtype=torch.int64, device=dev),
+           "W": torch.empty((K, K), dtype=torch.float64, device=dev),
+           "errmax": torch.empty(K, dtype=torch.float64, device=dev),
+           "status": torch.zeros(1, dtype=torch.int32, device=dev)}
+    SAk = _empty_cm(smax, K, dev) if want_sketch else None
+    st = lib.ns_aaa_real(ctypes.byref(d), _p(x), _p(f), m, int(K), _p(forced), _p(out["support"]), _p(out["W"]),
+                         _p(out["errmax"]), _p(SAk), _p(out["status"]), _p(ws), ws.numel(), _stream(stream))
+    _lib.check(st, "ns_aaa_real")
+    if want_sketch:
+        out["SAk"] = SAk
+    out["_ws"] = ws
+    return out

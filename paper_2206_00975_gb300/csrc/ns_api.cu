@@ -219,6 +219,28 @@ ns_status ns_solve_batched(const ns_sketch_desc *d, int32_t batch, const ns_prob
     return cuda_status(launch_batched(batch, host, dev, dev_status, ws, (cudaStream_t)stream));
 }
 
+static bool aaa_ok(const ns_sketch_desc *d, int64_t m, int32_t K) {
+    if (!d || d->kind != NS_SRHT || d->prec != NS_PREC_FP64) return false;
+    if (m < 2 || K < 1 || K > 1024 || d->s < K || d->s > kMaxS) return false;
+    if (d->s > ((int64_t)1 << ceil_log2(m))) return false;
+    return true;
+}
+
+size_t ns_aaa_workspace_size(const ns_sketch_desc *d, int64_t m, int32_t K) {
+    if (!aaa_ok(d, m, K)) return 0;
+    return aaa_work_bytes(m, d->s, K);
+}
+
+ns_status ns_aaa_real(const ns_sketch_desc *d, const double *x, const double *f, int64_t m, int32_t K,
+                      const int64_t *forced, int64_t *support, double *W, double *errmax, double *SAk_out,
+                      int32_t *dev_status, void *ws, size_t ws_bytes, void *stream) {
+    if (!aaa_ok(d, m, K) || !x || !f || !support || !W || !errmax || !dev_status || !ws) return NS_ERR_INVALID_ARG;
+    if ((((uintptr_t)ws) & 255) != 0) return NS_ERR_INVALID_ARG;
+    if (aaa_work_bytes(m, d->s, K) > ws_bytes) return NS_ERR_WORKSPACE;
+    return cuda_status(launch_aaa(d->seed, x, f, m, K, d->s, (const long long *)forced, (long long *)support, W,
+                                  errmax, SAk_out, dev_status, ws, (cudaStream_t)stream));
+}
+
 ns_status ns_residual(const void *A, int32_t dtype, int64_t m, int64_t n, int64_t lda, const double *W, int32_t k,
                       double *out, void *ws, size_t ws_bytes, void *stream) {
     if (!A || !W || !out || !ws || dtype != NS_F64) return NS_ERR_INVALID_ARG;

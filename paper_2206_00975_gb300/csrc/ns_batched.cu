@@ -18,11 +18,11 @@
 #include "ns_device.cuh"
 #include "ns_internal.h"
 #include "ns_srht_core.cuh"
+#include "ns_dense_cta.cuh"
 
 namespace ns {
 
 constexpr int kBatchThreads = 256;
-constexpr int kBatchMaxSweeps = 30;
 
 struct BatchSlot {
     int64_t off;       // byte offset of the problem's workspace
@@ -183,228 +183,6 @@ __global__ void __launch_bounds__(64) batched_sketch_kernel(const ns_problem *__
     }
 }
 
-// ------------------------------------------------------- one-CTA dense ----
-__device__ __forceinline__ long long abskey(double x) { return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll; }
-
-// Householder QR of W (rows x cols, ld = rows) by one CTA, optionally with
-// column pivoting (physical swaps).  Reflector j: u = [u0[j]; W[j+1:, j]],
-// H = I - cf[j] u u^T; R is the upper triangle of W afterwards.
-__device__ void qr_cta(double *W, int64_t rows, int64_t cols, bool pivot, double *u0, double *cf, int32_t *perm,
-                       double *xs /* rows */, double *nrm /* cols */, double *nref /* cols */) {
-    __shared__ double red[32];
-    __shared__ long long redk[32];
-    __shared__ double par[3];
-    __shared__ int piv;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    for (int64_t l = tid; l < cols; l += blockDim.x) perm[l] = (int32_t)l;
-    if (pivot) {
-        for (int64_t l = wid; l < cols; l += nw) {
-            double a = 0.0;
-            for (int64_t i = lane; i < rows; i += 32) a = fma(W[i + l * rows], W[i + l * rows], a);
-            a = warp_sum(a);
-            if (lane == 0) {
-                nrm[l] = a;
-                nref[l] = a;
-            }
-        }
-    }
-    __syncthreads();
-    const int64_t steps = rows < cols ? rows : cols;
-    for (int64_t j = 0; j < steps; ++j) {
-        if (pivot) {
-            if (wid == 0) {  // argmax of the remaining norms, lowest index on ties
-                double best = -1.0;
-                int64_t bi = j;
-                for (int64_t l = j + lane; l < cols; l += 32)
-                    if (nrm[l] > best) {
-                        best = nrm[l];
-                        bi = l;
-                    }
-                for (int o = 16; o > 0; o >>= 1) {
-                    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-                    const long long oi = __shfl_xor_sync(0xffffffffu, (long long)bi, o);
-                    if (ob > best || (ob == best && oi < bi)) {
-                        best = ob;
-                        bi = oi;
-                    }
-                }
-                if (lane == 0) piv = (int)bi;
-            }
-            __syncthreads();
-            const int64_t p = piv;
-            if (p != j) {
-                for (int64_t i = tid; i < rows; i += blockDim.x) {
-                    const double a = W[i + j * rows];
-                    W[i + j * rows] = W[i + p * rows];
-                    W[i + p * rows] = a;
-                }
-                if (tid == 0) {
-                    double a = nrm[j]; nrm[j] = nrm[p]; nrm[p] = a;
-                    a = nref[j]; nref[j] = nref[p]; nref[p] = a;
-                    const int32_t q = perm[j]; perm[j] = perm[p]; perm[p] = q;
-                }
-            }
-            __syncthreads();
-        }
-        const int64_t len = rows - j;
-        double *x = W + j + j * rows;
-        long long key = 0;
-        for (int64_t i = tid; i < len; i += blockDim.x) {
-            const double a = x[i];
-            xs[i] = a;
-            key = max(key, abskey(a));
-        }
-        key = warp_max(key);
-        if (lane == 0) redk[wid] = key;
-        __syncthreads();
-        long long kmax = redk[0];
-        for (int w = 1; w < nw; ++w) kmax = max(kmax, redk[w]);
-        double sc = 0.0;
-        if (kmax != 0) {
-            int se = 2046 - (int)((unsigned long long)kmax >> 52);
-            se = se < 1 ? 1 : (se > 2045 ? 2045 : se);
-            sc = __longlong_as_double((long long)se << 52);
-        }
-        double ss[1] = {0.0};
-        if (sc != 0.0)
-            for (int64_t i = 1 + tid; i < len; i += blockDim.x) {
-                const double a = xs[i] * sc;
-                ss[0] = fma(a, a, ss[0]);
-            }
-        block_sum_t0<1>(ss, red);
-        if (tid == 0) {
-            const double alpha = xs[0];
-            if (sc == 0.0 || ss[0] == 0.0) {
-                par[0] = 0.0;
-                par[1] = alpha;
-                par[2] = 0.0;
-            } else {
-                const double isc = __longlong_as_double((2046ll << 52) - __double_as_longlong(sc));
-                const double as = alpha * sc;
-                const double r = sqrt(fma(as, as, ss[0])) * isc;
-                const double beta = alpha >= 0.0 ? -r : r;
-                par[0] = 1.0 / (beta * (beta - alpha));
-                par[1] = beta;
-                par[2] = alpha - beta;
-            }
-        }
-        __syncthreads();
-        const double coef = par[0], beta = par[1], ua = par[2];
-        // trailing columns, one warp per column
-        if (coef != 0.0) {
-            for (int64_t l = j + 1 + wid; l < cols; l += nw) {
-                double *y = W + j + l * rows;
-                double d = 0.0;
-                for (int64_t i = 1 + lane; i < len; i += 32) d = fma(xs[i], y[i], d);
-                d = warp_sum(d);
-                const double f = coef * fma(ua, y[0], d);
-                if (lane == 0) y[0] -= f * ua;
-                for (int64_t i = 1 + lane; i < len; i += 32) y[i] = fma(-f, xs[i], y[i]);
-                if (pivot) {
-                    __syncwarp();
-                    if (lane == 0) {
-                        const double r0 = y[0];
-                        nrm[l] -= r0 * r0;
-                    }
-                    __syncwarp();
-                    if (!(nrm[l] > 1e-8 * nref[l])) {  // recompute from the remaining rows
-                        double a = 0.0;
-                        for (int64_t i = 1 + lane; i < len; i += 32) a = fma(y[i], y[i], a);
-                        a = warp_sum(a);
-                        if (lane == 0) {
-                            nrm[l] = a;
-                            nref[l] = a;
-                        }
-                    }
-                }
-            }
-        } else if (pivot) {
-            for (int64_t l = j + 1 + wid; l < cols; l += nw) {
-                if (lane == 0) {
-                    const double r0 = W[j + l * rows];
-                    nrm[l] -= r0 * r0;
-                }
-            }
-        }
-        if (tid == 0) {
-            x[0] = beta;
-            u0[j] = ua;
-            cf[j] = coef;
-            if (pivot) nrm[j] = -1.0;
-        }
-        __syncthreads();
-    }
-}
-
-// one-sided Jacobi on X (n x n) by one CTA, one warp per pair of each
-// round-robin step; V receives the accumulated rotations.  Returns whether the
-// iteration converged.  Same rotation rule as the cooperative kernel.
-__device__ bool jacobi_cta(double *X, double *V, int64_t n, double *sigma) {
-    __shared__ unsigned int rot_sh;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    const double tol = (double)n * 1.1102230246251565e-16, tol2 = tol * tol;
-    for (int64_t i = tid; i < n * n; i += blockDim.x) V[i] = ((i % n) == (i / n)) ? 1.0 : 0.0;
-    const int64_t n2 = n + (n & 1), npairs = n2 / 2, steps = n2 - 1;
-    bool converged = n < 2;
-    for (int sweep = 0; sweep < kBatchMaxSweeps && !converged; ++sweep) {
-        if (tid == 0) rot_sh = 0;
-        __syncthreads();
-        unsigned int local = 0;
-        for (int64_t step = 0; step < steps; ++step) {
-            for (int64_t pi = wid; pi < npairs; pi += nw) {
-                int64_t p = (pi == 0) ? 0 : 1 + (pi - 1 + step) % (n2 - 1);
-                const int64_t qpos = n2 - 1 - pi;
-                int64_t q = (qpos == 0) ? 0 : 1 + (qpos - 1 + step) % (n2 - 1);
-                if (p > q) {
-                    const int64_t tmp = p;
-                    p = q;
-                    q = tmp;
-                }
-                if (q >= n) continue;
-                double *xp = X + p * n, *xq = X + q * n;
-                double a = 0.0, b = 0.0, g = 0.0;
-                for (int64_t i = lane; i < n; i += 32) {
-                    const double u = xp[i], w = xq[i];
-                    a = fma(u, u, a);
-                    b = fma(w, w, b);
-                    g = fma(u, w, g);
-                }
-                a = warp_sum(a);
-                b = warp_sum(b);
-                g = warp_sum(g);
-                if (g == 0.0 || !(g * g > tol2 * a * b)) continue;
-                const double zeta = (b - a) / (2.0 * g);
-                const double t = (fabs(zeta) > 1e150) ? 0.5 / zeta
-                                                      : copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-                const double cs = rsqrt(fma(t, t, 1.0)), sn = cs * t;
-                double *vp = V + p * n, *vq = V + q * n;
-                for (int64_t i = lane; i < n; i += 32) {
-                    const double u = xp[i], w = xq[i];
-                    xp[i] = fma(cs, u, -sn * w);
-                    xq[i] = fma(sn, u, cs * w);
-                    const double c0 = vp[i], d0 = vq[i];
-                    vp[i] = fma(cs, c0, -sn * d0);
-                    vq[i] = fma(sn, c0, cs * d0);
-                }
-                ++local;
-            }
-            __syncthreads();
-        }
-        if (lane == 0 && local) atomicAdd(&rot_sh, local);
-        __syncthreads();
-        converged = (rot_sh == 0);
-        __syncthreads();
-    }
-    for (int64_t l = wid; l < n; l += nw) {
-        double a = 0.0;
-        for (int64_t i = lane; i < n; i += 32) a = fma(X[i + l * n], X[i + l * n], a);
-        a = warp_sum(a);
-        if (lane == 0) sigma[l] = sqrt(a);
-    }
-    __syncthreads();
-    return converged;
-}
-
 __global__ void __launch_bounds__(kBatchThreads) batched_dense_kernel(const ns_problem *__restrict__ P, int32_t batch,
                                                                       const BatchSlot *__restrict__ slots, char *ws,
                                                                       unsigned long long *counters, int32_t *status) {
@@ -424,96 +202,9 @@ __global__ void __launch_bounds__(kBatchThreads) batched_dense_kernel(const ns_p
         const int64_t n = pr.n, s = pr.s;
         ProblemView v = problem_view(ws + slots[pi].off, pr.m, n, s);
         double *xs = dsh, *nrm = dsh + s, *nref = dsh + s + n;
-        // 1. SA P = Q1 R (pivoted), in place
-        qr_cta(v.SA, s, n, true, v.u0a, v.cfa, v.perm, xs, nrm, nref);
-        // 2. L = R^T
-        for (int64_t idx = tid; idx < n * n; idx += blockDim.x) {
-            const int64_t i = idx % n, j = idx / n;
-            v.L[i + j * n] = (i >= j) ? v.SA[j + i * s] : 0.0;
-        }
-        __syncthreads();
-        // 3. L = Q2 R2 (no pivoting); X = R2^T; perm of this QR is not used
-        qr_cta(v.L, n, n, false, v.u0b, v.cfb, (int32_t *)v.sigma, xs, nrm, nref);
-        for (int64_t idx = tid; idx < n * n; idx += blockDim.x) {
-            const int64_t i = idx % n, j = idx / n;
-            v.X[i + j * n] = (i >= j) ? v.L[j + i * n] : 0.0;
-        }
-        __syncthreads();
-        // 4. Jacobi on X: Vx in V
-        const bool conv = jacobi_cta(v.X, v.V, n, v.sigma);
-        if (!conv && tid == 0) atomicMax(status + pi, (int32_t)NS_ERR_NOCONV);
-        // 5. the k trailing columns of V = P Q2 Vx, one warp per column
-        for (int32_t c = 0; c < pr.k; ++c) {
-            // source column: the singular value of rank n - k + c (non-increasing, ties to lower index)
-            if (tid == 0) src_sh = -1;
-            __syncthreads();
-            for (int64_t i = tid; i < n; i += blockDim.x) {
-                const double si = v.sigma[i];
-                int64_t r = 0;
-                for (int64_t jj = 0; jj < n; ++jj) {
-                    const double sj = v.sigma[jj];
-                    r += (sj > si || (sj == si && jj < i)) ? 1 : 0;
-                }
-                if (r == n - pr.k + c) src_sh = (int)i;
-            }
-            __syncthreads();
-            const int64_t src = src_sh;
-            // column src of Vx -> apply H_{n-1} ... H_0 of the second QR (xs as the column)
-            for (int64_t i = tid; i < n; i += blockDim.x) xs[i] = v.V[i + src * n];
-            __syncthreads();
-            for (int64_t j = n - 1; j >= 0; --j) {
-                const double coef = v.cfb[j];
-                if (coef == 0.0) continue;
-                const double ua = v.u0b[j];
-                double d[1] = {0.0};
-                for (int64_t i = j + tid; i < n; i += blockDim.x) d[0] = fma(i == j ? ua : v.L[i + j * n], xs[i], d[0]);
-                block_sum_t0<1>(d, (double *)bk);
-                if (tid == 0) *(double *)&bk[31] = coef * d[0];
-                __syncthreads();
-                const double f = *(double *)&bk[31];
-                for (int64_t i = j + tid; i < n; i += blockDim.x) xs[i] = fma(-f, i == j ? ua : v.L[i + j * n], xs[i]);
-                __syncthreads();
-            }
-            // row i of Q2 Vx is row perm[i] of V; sign: largest |entry| positive (lowest index on ties)
-            long long best = -1;
-            int bi = 0;
-            for (int64_t i = tid; i < n; i += blockDim.x) {
-                const int64_t row = v.perm[i];
-                const long long kk = abskey(xs[i]);
-                if (kk > best || (kk == best && row < bi)) {
-                    best = kk;
-                    bi = (int)row;
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) {
-                    best = ob;
-                    bi = oi;
-                }
-            }
-            if (lane == 0) {
-                bk[wid] = best;
-                bi_sh[wid] = bi;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                for (int w = 1; w < nw; ++w)
-                    if (bk[w] > bk[0] || (bk[w] == bk[0] && bi_sh[w] < bi_sh[0])) {
-                        bk[0] = bk[w];
-                        bi_sh[0] = bi_sh[w];
-                    }
-            }
-            __syncthreads();
-            const int brow = bi_sh[0];
-            double sgn = 1.0;
-            for (int64_t i = 0; i < n; ++i)
-                if (v.perm[i] == brow) sgn = xs[i] < 0.0 ? -1.0 : 1.0;
-            for (int64_t i = tid; i < n; i += blockDim.x) pr.Vk[v.perm[i] + c * n] = sgn * xs[i];
-            if (tid == 0) pr.sigk[c] = v.sigma[src];
-            __syncthreads();
-        }
+        DenseScratch scr{v.X, v.V, v.L, v.u0a, v.cfa, v.u0b, v.cfb, v.sigma, v.perm};
+        if (!dense_solve_cta(v.SA, s, n, pr.k, scr, xs, nrm, nref, pr.Vk, pr.sigk) && tid == 0)
+            atomicMax(status + pi, (int32_t)NS_ERR_NOCONV);
         // 6. TLS: x = -v(1:n-1) / v(n)
         if (pr.tls && pr.x) {
             const double *w = pr.Vk;  // k = 1

@@ -102,6 +102,11 @@ size_t batched_work_bytes(int32_t batch, const ns_problem *host);
 cudaError_t launch_batched(int32_t batch, const ns_problem *host, const ns_problem *dev, int32_t *status, void *ws,
                            cudaStream_t st);
 
+size_t aaa_work_bytes(int64_t m, int64_t smax, int32_t K);
+cudaError_t launch_aaa(uint64_t seed, const double *x, const double *f, int64_t m, int32_t K, int64_t smax,
+                       const long long *forced, long long *support, double *Wout, double *errmax, double *SAk_out,
+                       int32_t *status, void *ws, cudaStream_t st);
+
 struct DenseWork {
     double *W;        // s x n working copy of SA (QR in place); later V (n x n)
     double *tau;      // 2n: reflector factors of both QRs
