@@ -208,20 +208,20 @@ int or_sparse_sign(uint64_t seed, int64_t s, int32_t zeta, const double *A, int6
 
 /* ------------------------------------------------------------------------ */
 /* Gaussian sketch G/sqrt(s) (Theorem 2.1 and the scaling of Section 5).     */
-/* Entry G[r, j]: block (j, r/8) of stream 3 gives four 64-bit words; word    */
-/* q = (r mod 8)/2 supplies u_a = (lo32 + 1/2)/2^32 and u_b = (hi32 + 1/2)/2^32 */
-/* and Box-Muller gives sqrt(-2 ln u_a) cos(2 pi u_b) for even r and         */
-/* sqrt(-2 ln u_a) sin(2 pi u_b) for odd r.                                   */
+/* Entry G[r, j]: block (r, j/8) of stream 3 gives four 64-bit words; word    */
+/* q = (j mod 8)/2 supplies u_a = (lo32 + 1/2)/2^32 and u_b = (hi32 + 1/2)/2^32 */
+/* and Box-Muller gives sqrt(-2 ln u_a) cos(2 pi u_b) for even j and          */
+/* sqrt(-2 ln u_a) sin(2 pi u_b) for odd j.                                   */
 /* ------------------------------------------------------------------------ */
 double or_gaussian_entry(uint64_t seed, int64_t r, int64_t j) {
     uint64_t w[4];
-    draw(seed, (uint64_t)j, (uint64_t)(r / 8), 3, w);
-    uint64_t word = w[(r % 8) / 2];
+    draw(seed, (uint64_t)r, (uint64_t)(j / 8), 3, w);
+    uint64_t word = w[(j % 8) / 2];
     double ua = ((double)(uint32_t)word + 0.5) / 4294967296.0;
     double ub = ((double)(uint32_t)(word >> 32) + 0.5) / 4294967296.0;
     double rad = sqrt(-2.0 * log(ua));
     double ang = 2.0 * 3.14159265358979323846 * ub;
-    return (r % 2 == 0) ? rad * cos(ang) : rad * sin(ang);
+    return (j % 2 == 0) ? rad * cos(ang) : rad * sin(ang);
 }
 
 /* SA = G A / sqrt(s), computed for the columns listed in cols (ncols of them;
