@@ -27,11 +27,13 @@ static bool path_ok(const ns_sketch_desc *d, int32_t dtype) {
     if (d->kind == NS_SRHT)
         return (d->prec == NS_PREC_FP64 && dtype == NS_F64) || (d->prec == NS_PREC_FP32_STREAM && dtype == NS_F32);
     if (d->kind == NS_SPARSE_SIGN) return d->prec == NS_PREC_FP64 && dtype == NS_F64;
+    if (d->kind == NS_GAUSSIAN) return d->prec == NS_PREC_BF16X3 && dtype == NS_F32;
     return false;
 }
 
 static bool shape_ok(const ns_sketch_desc *d, int64_t m, int64_t n, int64_t lda) {
     if (m < 1 || n < 1 || lda < m) return false;
+    if (d->kind == NS_GAUSSIAN && n > 512) return false;
     if (d->kind == NS_SRHT && d->s > ((int64_t)1 << ceil_log2(m))) return false;
     return true;
 }
@@ -40,6 +42,7 @@ struct SolveLayout {
     int32_t *status_word;
     SrhtWork srht;
     SparseWork sparse;
+    float *gauss_partial;
     double *SA;
     DenseWork dense;
     size_t bytes;
@@ -53,6 +56,11 @@ static SolveLayout solve_layout(void *ws, const ns_sketch_desc *d, int64_t m, in
     L.sparse = SparseWork{nullptr, nullptr, nullptr};
     if (d->kind == NS_SRHT) L.srht = srht_carve(c, m, n, d->s);
     if (d->kind == NS_SPARSE_SIGN) L.sparse = sparse_carve(c, m, n, d->s, d->zeta);
+    L.gauss_partial = nullptr;
+    if (d->kind == NS_GAUSSIAN) {
+        const GaussGeom g = gauss_geom(m, n, d->s);
+        L.gauss_partial = c.take<float>((size_t)(g.nsplit * n * d->s));
+    }
     L.SA = need_sa ? c.take<double>((size_t)(d->s * n)) : nullptr;
     L.dense = dense_carve(c, d->s, n);
     L.bytes = c.used;
@@ -63,6 +71,9 @@ static ns_status cuda_status(cudaError_t e) { return e == cudaSuccess ? NS_OK : 
 
 static ns_status run_sketch(const ns_sketch_desc *d, const void *A, int64_t m, int64_t n, int64_t lda, double *SA,
                             const SolveLayout &L, int32_t *status, cudaStream_t st) {
+    if (d->kind == NS_GAUSSIAN)
+        return cuda_status(launch_gauss_bf16x3(d->seed, (const float *)A, m, n, lda, d->s, L.gauss_partial, SA, status,
+                                               st));
     if (d->kind == NS_SPARSE_SIGN)
         return cuda_status(launch_sparse_f64(d->seed, (const double *)A, m, n, lda, d->s, d->zeta, L.sparse, SA,
                                              status, st));

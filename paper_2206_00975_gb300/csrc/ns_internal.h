@@ -107,6 +107,17 @@ cudaError_t launch_aaa(uint64_t seed, const double *x, const double *f, int64_t 
                        const long long *forced, long long *support, double *Wout, double *errmax, double *SAk_out,
                        int32_t *status, void *ws, cudaStream_t st);
 
+struct GaussGeom {
+    int64_t mtiles;   // 128-row tiles of G
+    int NP;           // n rounded up to 16
+    int64_t kper;     // K (= rows of A) per split
+    int64_t nsplit;
+};
+GaussGeom gauss_geom(int64_t m, int64_t n, int64_t s);
+size_t gauss_work_bytes(int64_t m, int64_t n, int64_t s);
+cudaError_t launch_gauss_bf16x3(uint64_t seed, const float *A, int64_t m, int64_t n, int64_t lda, int64_t s,
+                                float *partial, double *SA, int32_t *status, cudaStream_t st);
+
 struct DenseWork {
     double *W;        // s x n working copy of SA (QR in place); later V (n x n)
     double *tau;      // 2n: reflector factors of both QRs
