@@ -130,6 +130,27 @@ ns_status ns_solve(const ns_sketch_desc *desc, const void *A, int32_t dtype, int
                    size_t ws_bytes, void *stream);
 
 /*
+ * ns_solve_sketched -- Algorithm 1 lines 3-4 on a sketch the caller already
+ * holds: SA (device, s x n FP64, ld s, s = desc->s) -> QR, Jacobi SVD, the k
+ * trailing right singular vectors.  Outputs as ns_solve (save receives a copy
+ * of SA, then V and sigma).  SA is not modified.
+ */
+ns_status ns_solve_sketched(const ns_sketch_desc *desc, const double *SA, int64_t n, int32_t k, double *Vk,
+                           double *sigk, double *save, int32_t *dev_status, void *ws, size_t ws_bytes,
+                           void *stream);
+
+/*
+ * ns_solve_stats / ns_sketched_stats -- statistics of the Jacobi iteration of
+ * the last ns_solve (ns_solve_sketched) that ran in workspace ws with the same
+ * desc and shape: dev_out (device int64[3]) receives the number of full
+ * sweeps, the number of rotations and the number of barrier-free check passes.
+ * Enqueued on stream after that call.
+ */
+ns_status ns_solve_stats(const ns_sketch_desc *desc, int64_t m, int64_t n, const void *ws, int64_t *dev_out,
+                         void *stream);
+ns_status ns_sketched_stats(const ns_sketch_desc *desc, int64_t n, const void *ws, int64_t *dev_out, void *stream);
+
+/*
  * ns_backward -- adjoint of ns_solve for a loss L that depends on W only
  * through the projector W W^T (a loss that is invariant under W -> W Q).
  * With M = SA^T SA = V Sigma^2 V^T, T the trailing k indices and N the others:

@@ -231,3 +231,33 @@ def ns_aaa_real(x, f, K, smax, seed=0, forced=None, want_sketch=False, ws=None, 
         out["SAk"] = SAk
     out["_ws"] = ws
     return out
+
+
+def ns_solve_sketched(d, SA, k, save=False, status=None, ws=None, stream=None):
+    """Lines 3-4 of Algorithm 1 on a given sketch SA (s x n, column-major)."""
+    s_, n = SA.shape
+    dev = SA.device
+    Vk = _empty_cm(n, k, dev)
+    sigk = torch.empty(k, dtype=torch.float64, device=dev)
+    sv = torch.empty(save_size(d.s, n), dtype=torch.float64, device=dev) if save is True else (
+        save if isinstance(save, torch.Tensor) else None)
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+    if ws is None:
+        ws = workspace(d, max(n, d.s), n, k, dev)
+    st = _lib.load().ns_solve_sketched(ctypes.byref(d), _p(SA), n, int(k), _p(Vk), _p(sigk), _p(sv), _p(status),
+                                       _p(ws), ws.numel(), _stream(stream))
+    _lib.check(st, "ns_solve_sketched")
+    return Vk, sigk, sv, status
+
+
+def jacobi_stats(d, m, n, ws, sketched=False, stream=None):
+    """(full sweeps, rotations, check passes) of the last solve in workspace ws."""
+    out = torch.zeros(3, dtype=torch.int64, device=ws.device)
+    lib = _lib.load()
+    if sketched:
+        st = lib.ns_sketched_stats(ctypes.byref(d), int(n), _p(ws), _p(out), _stream(stream))
+    else:
+        st = lib.ns_solve_stats(ctypes.byref(d), int(m), int(n), _p(ws), _p(out), _stream(stream))
+    _lib.check(st, "jacobi_stats")
+    return [int(v) for v in out.cpu()]

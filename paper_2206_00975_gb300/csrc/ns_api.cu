@@ -189,6 +189,44 @@ ns_status ns_solve(const ns_sketch_desc *d, const void *A, int32_t dtype, int64_
     return cuda_status(launch_dense_solve(SA, d->s, n, k, L.dense, Vk, sigk, save_V, save_sigma, status, st));
 }
 
+ns_status ns_solve_sketched(const ns_sketch_desc *d, const double *SA, int64_t n, int32_t k, double *Vk, double *sigk,
+                           double *save, int32_t *dev_status, void *ws, size_t ws_bytes, void *stream) {
+    if (!desc_ok(d) || !SA || !Vk || !sigk || !ws) return NS_ERR_INVALID_ARG;
+    if (n < 1 || n > d->s || n > kMaxN || k < 1 || k > n) return NS_ERR_INVALID_ARG;
+    if ((((uintptr_t)ws) & 255) != 0) return NS_ERR_INVALID_ARG;
+    Carver c(ws);
+    int32_t *status_word = c.take<int32_t>(1);
+    DenseWork w = dense_carve(c, d->s, n);
+    if (c.used > ws_bytes) return NS_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *status = dev_status ? dev_status : status_word;
+    if (cudaMemsetAsync(status, 0, sizeof(int32_t), st) != cudaSuccess) return NS_ERR_CUDA;
+    double *save_V = nullptr, *save_sigma = nullptr;
+    if (save) {
+        if (cudaMemcpyAsync(save, SA, sizeof(double) * (size_t)(d->s * n), cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess)
+            return NS_ERR_CUDA;
+        save_V = save + d->s * n;
+        save_sigma = save + d->s * n + n * n;
+    }
+    return cuda_status(launch_dense_solve(SA, d->s, n, k, w, Vk, sigk, save_V, save_sigma, status, st));
+}
+
+ns_status ns_solve_stats(const ns_sketch_desc *d, int64_t m, int64_t n, const void *ws, int64_t *dev_out,
+                         void *stream) {
+    if (!desc_ok(d) || !ws || !dev_out || m < 1 || n < 1 || n > kMaxN) return NS_ERR_INVALID_ARG;
+    SolveLayout L = solve_layout(const_cast<void *>(ws), d, m, n, true);
+    return cuda_status(launch_dense_stats(L.dense, dev_out, (cudaStream_t)stream));
+}
+
+ns_status ns_sketched_stats(const ns_sketch_desc *d, int64_t n, const void *ws, int64_t *dev_out, void *stream) {
+    if (!desc_ok(d) || !ws || !dev_out || n < 1 || n > kMaxN) return NS_ERR_INVALID_ARG;
+    Carver c(const_cast<void *>(ws));
+    c.take<int32_t>(1);
+    DenseWork w = dense_carve(c, d->s, n);
+    return cuda_status(launch_dense_stats(w, dev_out, (cudaStream_t)stream));
+}
+
 ns_status ns_backward(const ns_sketch_desc *d, int64_t m, int64_t n, int32_t k, const double *save, const double *Vk,
                       const double *dVk, double *dA, int64_t ldd, void *ws, size_t ws_bytes, void *stream) {
     if (!desc_ok(d) || d->kind != NS_SRHT || d->prec != NS_PREC_FP64) return NS_ERR_INVALID_ARG;

@@ -44,7 +44,7 @@ namespace ns {
 constexpr int kDenseThreads = 256;
 constexpr int kMaxSweeps = 30;
 constexpr int kCheckBelow = 4096;        // run the barrier-free check after a sweep with fewer rotations
-constexpr int kBarWords = 64 + 2 * 64;   // barrier word (padded), rotation counts, check flags
+constexpr int kBarWords = 64 + 2 * 64 + 8;  // barrier word (padded), rotation counts, check flags, stats
 
 size_t dense_work_bytes(int64_t s, int64_t n) {
     Carver c(nullptr);
@@ -328,8 +328,10 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_coop_kernel(double *X, d
     const int64_t n2 = n + (n & 1), npairs = n2 / 2, steps = n2 - 1;
     bool converged = (n < 2);
     unsigned int prev_rot = 0xFFFFFFFFu;
+    int full_sweeps = 0, check_passes = 0;
     for (int sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
         if (prev_rot < (unsigned int)kCheckBelow) {
+            ++check_passes;
             // ---- barrier-free check: does any pair need a rotation?  One warp per pair.
             if (!grid_sync(bar)) return;
             const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
@@ -364,6 +366,7 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_coop_kernel(double *X, d
             }
         }
         unsigned int local = 0;
+        ++full_sweeps;
         for (int64_t step = 0; step < steps; ++step) {
             if (!grid_sync(bar)) return;
             for (int64_t pi = me; pi < npairs; pi += G) {
@@ -422,6 +425,13 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_coop_kernel(double *X, d
         converged = (prev_rot == 0u);
     }
     if (!converged && me == 0 && tid == 0) set_status(status, NS_ERR_NOCONV);
+    if (me == 0 && tid == 0) {  // statistics: full sweeps, rotations, barrier-free checks
+        unsigned int rots = 0;
+        for (int sw = 0; sw < kMaxSweeps; ++sw) rots += *(volatile unsigned int *)(rotcount + sw);
+        rotcount[128] = (unsigned int)full_sweeps;
+        rotcount[129] = rots;
+        rotcount[130] = (unsigned int)check_passes;
+    }
     if (!grid_sync(bar)) return;
     // sigma_l = |x_l| (scaled)
     __shared__ long long redk[32];
@@ -591,6 +601,19 @@ static cudaError_t launch_hqr(double *W, int64_t rows, int64_t cols, int pivot, 
     if (nown <= 2) return launch_hqr_nb<2>(W, rows, cols, pivot, u0, cf, perm, pivslot, Rout, bar, G, st);
     if (nown <= 4) return launch_hqr_nb<4>(W, rows, cols, pivot, u0, cf, perm, pivslot, Rout, bar, G, st);
     return launch_hqr_nb<8>(W, rows, cols, pivot, u0, cf, perm, pivslot, Rout, bar, G, st);
+}
+
+__global__ void dense_stats_kernel(const unsigned int *bar, int64_t *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        out[0] = bar[64 + 128];
+        out[1] = bar[64 + 129];
+        out[2] = bar[64 + 130];
+    }
+}
+
+cudaError_t launch_dense_stats(const DenseWork &w, int64_t *out, cudaStream_t st) {
+    dense_stats_kernel<<<1, 32, 0, st>>>(w.bar, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k, const DenseWork &w, double *Vk,

@@ -131,6 +131,7 @@ struct DenseWork {
 };
 size_t dense_work_bytes(int64_t s, int64_t n);
 DenseWork dense_carve(Carver &c, int64_t s, int64_t n);
+cudaError_t launch_dense_stats(const DenseWork &w, int64_t *out, cudaStream_t st);
 cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k, const DenseWork &w, double *Vk,
                                double *sigk, double *save_V, double *save_sigma, int32_t *status, cudaStream_t st);
 
