@@ -312,10 +312,11 @@ def profile_case(args, torch, api, dev):
         SA = torch.randn((n, s), generator=g, device=dev, dtype=torch.float64).t()
         d = api.desc(api.NS_SRHT, s=s, seed=0)
         ws = api.workspace(d, s, n, K_NULL, dev)
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
         for _ in range(args.steps):
-            api.ns_solve_sketched(d, SA, K_NULL, ws=ws)
+            api.ns_solve_sketched(d, SA, K_NULL, status=status, ws=ws)
         torch.cuda.synchronize()
-        print(json.dumps({"case": args.case, "n": n, "s": s, "steps": args.steps}))
+        print(json.dumps({"case": args.case, "n": n, "s": s, "steps": args.steps, "status": int(status.item())}))
         return
     else:
         raise SystemExit("unknown case " + args.case)

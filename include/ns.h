@@ -231,8 +231,10 @@ ns_status ns_aaa_real(const ns_sketch_desc *desc, const double *x, const double 
 
 /*
  * ns_residual -- the objective of Problem 2.1, ||A W||_F, in one streaming
- * pass over A (evaluation only).  W is device n x k FP64; *out (device double)
- * receives the result.
+ * pass over A (evaluation only).  W is device n x k FP64 (1 <= k <= 16 and
+ * n * k' <= 25600 with k' = k rounded up to a power of two; A FP64 only);
+ * *out (device double) receives the result.  ws needs 8 KiB.  One thread per
+ * row of A accumulates A(row, :) W in FP64.
  */
 ns_status ns_residual(const void *A, int32_t dtype, int64_t m, int64_t n, int64_t lda, const double *W, int32_t k,
                       double *out, void *ws, size_t ws_bytes, void *stream);

@@ -87,26 +87,43 @@ static ns_status run_sketch(const ns_sketch_desc *d, const void *A, int64_t m, i
 }
 
 // ---------------------------------------------------------------- residual --
-__global__ void residual_rows_kernel(const double *__restrict__ A, int64_t m, int64_t n, int64_t lda,
-                                     const double *__restrict__ W, int32_t k, double *__restrict__ partial) {
-    extern __shared__ double wsh[];  // n * k
+// One thread per row: y = A(row, :) W, accumulated in FP64.  K is the number
+// of columns of W rounded up to a power of two, so no predicated-off FP64 FMA
+// occupies the (slow) FP64 pipe.
+template <int K>
+__global__ void __launch_bounds__(256) residual_rows_kernel(const double *__restrict__ A, int64_t m, int64_t n,
+                                                            int64_t lda, const double *__restrict__ W, int32_t k,
+                                                            double *__restrict__ partial) {
+    extern __shared__ double wsh[];  // n * K, row-major: wsh[j * K + c]
     __shared__ double red[32];
-    for (int64_t i = threadIdx.x; i < n * k; i += blockDim.x) wsh[i] = W[i];
+    for (int64_t i = threadIdx.x; i < n * K; i += blockDim.x) {
+        const int64_t j = i / K, c = i - j * K;
+        wsh[i] = (c < k) ? W[j + c * n] : 0.0;
+    }
     __syncthreads();
     double ss = 0.0;
     for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < m; row += (int64_t)gridDim.x * blockDim.x) {
-        double y[16];
+        double y[K];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) y[c] = 0.0;
-        for (int64_t j = 0; j < n; ++j) {
-            const double a = __ldcs(A + row + j * lda);
+        for (int c = 0; c < K; ++c) y[c] = 0.0;
+        const double *a_row = A + row;
+        int64_t j = 0;
+        for (; j + 4 <= n; j += 4) {
+            double a[4];
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
-                if (c < k) y[c] = fma(a, wsh[j + c * n], y[c]);
+            for (int u = 0; u < 4; ++u) a[u] = __ldcs(a_row + (j + u) * lda);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int c = 0; c < K; ++c) y[c] = fma(a[u], wsh[(j + u) * K + c], y[c]);
+        }
+        for (; j < n; ++j) {
+            const double a = __ldcs(a_row + j * lda);
+#pragma unroll
+            for (int c = 0; c < K; ++c) y[c] = fma(a, wsh[j * K + c], y[c]);
         }
 #pragma unroll
-        for (int c = 0; c < 16; ++c)
-            if (c < k) ss = fma(y[c], y[c], ss);
+        for (int c = 0; c < K; ++c) ss = fma(y[c], y[c], ss);
     }
     double v[1] = {ss};
     block_sum<1>(v, red);
@@ -119,6 +136,16 @@ __global__ void residual_final_kernel(const double *partial, int64_t np, double 
         for (int64_t i = 0; i < np; ++i) a += partial[i];  // fixed order
         *out = sqrt(a);
     }
+}
+
+template <int K>
+static cudaError_t launch_residual(const double *A, int64_t m, int64_t n, int64_t lda, const double *W, int32_t k,
+                                   double *partial, int64_t blocks, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(residual_rows_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    residual_rows_kernel<K><<<(unsigned)blocks, 256, smem, st>>>(A, m, n, lda, W, k, partial);
+    return cudaGetLastError();
 }
 
 }  // namespace ns
@@ -293,14 +320,23 @@ ns_status ns_aaa_real(const ns_sketch_desc *d, const double *x, const double *f,
 ns_status ns_residual(const void *A, int32_t dtype, int64_t m, int64_t n, int64_t lda, const double *W, int32_t k,
                       double *out, void *ws, size_t ws_bytes, void *stream) {
     if (!A || !W || !out || !ws || dtype != NS_F64) return NS_ERR_INVALID_ARG;
-    if (m < 1 || n < 1 || lda < m || k < 1 || k > 16 || n * k > 6000) return NS_ERR_INVALID_ARG;
+    if (m < 1 || n < 1 || lda < m || k < 1 || k > 16 || n > kMaxN) return NS_ERR_INVALID_ARG;
     const int64_t blocks = 1024;
     if (ws_bytes < sizeof(double) * (size_t)blocks) return NS_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     double *partial = (double *)ws;
-    residual_rows_kernel<<<(unsigned)blocks, 256, sizeof(double) * (size_t)(n * k), st>>>(
-        (const double *)A, m, n, lda, W, k, partial);
-    if (cudaGetLastError() != cudaSuccess) return NS_ERR_CUDA;
+    const int K = k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : k <= 8 ? 8 : 16;
+    const size_t smem = sizeof(double) * (size_t)(n * K);
+    if (smem > 200 * 1024) return NS_ERR_INVALID_ARG;
+    cudaError_t e = cudaSuccess;
+    switch (K) {
+        case 1: e = launch_residual<1>((const double *)A, m, n, lda, W, k, partial, blocks, smem, st); break;
+        case 2: e = launch_residual<2>((const double *)A, m, n, lda, W, k, partial, blocks, smem, st); break;
+        case 4: e = launch_residual<4>((const double *)A, m, n, lda, W, k, partial, blocks, smem, st); break;
+        case 8: e = launch_residual<8>((const double *)A, m, n, lda, W, k, partial, blocks, smem, st); break;
+        default: e = launch_residual<16>((const double *)A, m, n, lda, W, k, partial, blocks, smem, st); break;
+    }
+    if (e != cudaSuccess) return NS_ERR_CUDA;
     residual_final_kernel<<<1, 32, 0, st>>>(partial, blocks, out);
     return cuda_status(cudaGetLastError());
 }

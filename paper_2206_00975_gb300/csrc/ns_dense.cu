@@ -255,6 +255,182 @@ __global__ void __launch_bounds__(kDenseThreads) hqr_coop_kernel(double *W, int6
     }
 }
 
+// ------------------------------------------------------- pipelined QR ----
+// Householder QR without pivoting, pipelined instead of barrier-separated.
+// CTA me owns columns me, me + G, ... and keeps them in shared memory.
+// Reflector j (same form and storage as hqr_coop_kernel: tail in W below the
+// diagonal, u0[j], cf[j], R[j, j] = beta) is formed by the owner of column j
+// as soon as reflectors 0..j-1 have reached that column, written to global
+// memory and announced by flag[j].  The owner of column j + 1 applies
+// reflector j to that column before its other columns (look-ahead), so the
+// chain from one reflector to the next runs through one CTA and one flag;
+// every other CTA only waits for the flags of the reflectors it applies.
+constexpr int kPipeThreads = 256;
+
+__device__ __forceinline__ unsigned int ld_acquire_flag(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Sum over the CTA, result in every thread (fixed order).
+__device__ __forceinline__ double pipe_sum(double v, double *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double a = 0.0;
+#pragma unroll
+    for (int w = 0; w < kPipeThreads / 32; ++w) a += red[w];
+    __syncthreads();
+    return a;
+}
+
+// Form reflector j from the owned column x (shared memory, rows entries):
+// publishes the tail, u0, cf and the flag; leaves u (u0 at index j) in ush,
+// the coefficient in *coef_sh and returns beta (every thread).  The scalar
+// chain (square root, reciprocal) runs in thread 0 only: FP64 is scarce.
+__device__ double pipe_form(double *W, int64_t rows, int64_t j, const double *x, double *ush, double *u0, double *cf,
+                            unsigned int *flag, double *red, double *coef_sh) {
+    __shared__ double s_par[2];
+    const int tid = threadIdx.x;
+    double ss = 0.0;
+    for (int64_t i = j + 1 + tid; i < rows; i += kPipeThreads) ss = fma(x[i], x[i], ss);
+    double nrm2 = pipe_sum(ss, red);
+    double sc = 1.0;
+    if (nrm2 != 0.0 && (nrm2 < 1e-280 || nrm2 > 1e280)) {
+        // rescale by a power of two from the largest entry (rare)
+        long long key = 0;
+        for (int64_t i = j + tid; i < rows; i += kPipeThreads) key = max(key, abs_key(x[i]));
+        __shared__ long long redk[32];
+        sc = block_pow2_scale(key, redk);
+        ss = 0.0;
+        for (int64_t i = j + 1 + tid; i < rows; i += kPipeThreads) {
+            const double a = x[i] * sc;
+            ss = fma(a, a, ss);
+        }
+        nrm2 = pipe_sum(ss, red);
+    }
+    for (int64_t i = j + 1 + tid; i < rows; i += kPipeThreads) {
+        const double v = x[i];
+        ush[i] = v;
+        W[i + j * rows] = v;
+    }
+    if (tid == 0) {
+        const double x0 = x[j];
+        double beta, ua, coef;
+        if (nrm2 == 0.0) {  // H = I
+            beta = x0;
+            ua = 0.0;
+            coef = 0.0;
+        } else {
+            const double xs = x0 * sc;
+            const double r = sqrt(fma(xs, xs, nrm2)) / sc;
+            beta = x0 >= 0.0 ? -r : r;
+            ua = x0 - beta;
+            coef = 1.0 / (beta * (beta - x0));
+        }
+        ush[j] = ua;
+        u0[j] = ua;
+        cf[j] = coef;
+        *coef_sh = coef;
+        s_par[0] = beta;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flag + j), "r"(1u) : "memory");
+    }
+    return s_par[0];
+}
+
+// y <- H_j y on rows j.. (u in ush, coefficient coef)
+__device__ __forceinline__ void pipe_apply(int64_t rows, int64_t j, const double *ush, double coef, double *y,
+                                           double *red) {
+    const int tid = threadIdx.x;
+    double d = 0.0;
+    for (int64_t i = j + tid; i < rows; i += kPipeThreads) d = fma(ush[i], y[i], d);
+    const double f = coef * pipe_sum(d, red);
+    for (int64_t i = j + tid; i < rows; i += kPipeThreads) y[i] = fma(-f, ush[i], y[i]);
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(double *W, int64_t rows, int64_t cols, int64_t nown_max,
+                                                               double *u0, double *cf, int32_t *perm,
+                                                               unsigned int *flag, double *Rout, int32_t *status) {
+    extern __shared__ double sm[];
+    double *own = sm;                          // nown_max * rows: owned columns
+    double *ubuf = sm + nown_max * rows;       // 2 * rows: reflectors j (even/odd)
+    double *beta = ubuf + 2 * rows;            // nown_max: R's diagonal of owned columns
+    __shared__ double red[kPipeThreads / 32];
+    __shared__ double s_coef[2];
+    __shared__ int s_ok;
+    const int tid = threadIdx.x;
+    const int64_t G = gridDim.x, me = blockIdx.x;
+    const int64_t nown = (cols - me + G - 1) / G;
+    const int64_t steps = rows < cols ? rows : cols;
+    for (int64_t o = 0; o < nown; ++o)
+        for (int64_t i = tid; i < rows; i += kPipeThreads) own[o * rows + i] = W[i + (me + o * G) * rows];
+    if (tid == 0) s_ok = 1;
+    __syncthreads();
+    if (me == 0 && steps > 0) {
+        const double b0 = pipe_form(W, rows, 0, own, ubuf, u0, cf, flag, red, &s_coef[0]);
+        if (tid == 0) beta[0] = b0;
+        __syncthreads();
+    }
+    for (int64_t j = 0; j < steps; ++j) {
+        double *ush = ubuf + (j & 1) * rows;
+        if (j % G != me) {  // wait for reflector j, then fetch it
+            if (tid == 0) {
+                const long long t0 = clock64();
+                while (ld_acquire_flag(flag + j) == 0u) {
+                    if (clock64() - t0 > (1ll << 32)) {  // ~2 s; a healthy pipeline waits microseconds
+                        set_status(status, NS_ERR_TIMEOUT);
+                        s_ok = 0;
+                        break;
+                    }
+                }
+                s_coef[j & 1] = __ldcg(cf + j);
+            }
+            __syncthreads();
+            if (!s_ok) return;
+            for (int64_t i = j + 1 + tid; i < rows; i += kPipeThreads) ush[i] = __ldcg(W + i + j * rows);
+            if (tid == 0) ush[j] = __ldcg(u0 + j);
+            __syncthreads();
+        }
+        const double coef = s_coef[j & 1];
+        // owned columns c > j; the owner of column j + 1 takes it first and
+        // forms reflector j + 1 right away
+        const int64_t o_first = (j + 1 - me + G - 1) / G;  // first owned column index > j
+        if (j + 1 < steps && (j + 1) % G == me) {
+            const int64_t o = (j + 1 - me) / G;
+            double *y = own + o * rows;
+            if (coef != 0.0) pipe_apply(rows, j, ush, coef, y, red);
+            const double bj = pipe_form(W, rows, j + 1, y, ubuf + ((j + 1) & 1) * rows, u0, cf, flag, red,
+                                        &s_coef[(j + 1) & 1]);
+            if (tid == 0) beta[o] = bj;
+        }
+        if (coef != 0.0)
+            for (int64_t o = o_first; o < nown; ++o) {
+                const int64_t c = me + o * G;
+                if (c == j + 1 && j + 1 < steps) continue;
+                pipe_apply(rows, j, ush, coef, own + o * rows, red);
+            }
+        __syncthreads();
+    }
+    // R (logical column order = physical, no pivoting) and the identity permutation
+    for (int64_t o = 0; o < nown; ++o) {
+        const int64_t c = me + o * G;
+        for (int64_t i = tid; i < cols; i += kPipeThreads) {
+            double r = 0.0;
+            if (i < c && i < rows) r = own[o * rows + i];
+            else if (i == c) r = (c < steps) ? beta[o] : own[o * rows + c];
+            Rout[i + c * cols] = r;
+        }
+        if (tid == 0) perm[c] = (int32_t)c;
+    }
+}
+
 // ------------------------------------------------------------ transpose ----
 __global__ void transpose_kernel(const double *__restrict__ A, int64_t n, double *__restrict__ B) {
     __shared__ double tile[32][33];
@@ -313,6 +489,74 @@ __device__ __forceinline__ bool rotation(double alpha, double beta, double gamma
     return true;
 }
 
+// Barrier-free convergence check over all n(n-1)/2 pairs of the columns of X
+// (one warp per pair, all CTAs of the grid).  Returns 1 if the check ran and
+// no pair needs a rotation, 0 if some pair does, -1 if a grid barrier timed out.
+__device__ int jacobi_check_pass(const double *X, int64_t n, double tol2, GridBarrier bar, unsigned int *flag) {
+    if (!grid_sync(bar)) return -1;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int64_t G = gridDim.x, me = blockIdx.x;
+    const int64_t total = n * (n - 1) / 2;
+    int any = 0;
+    for (int64_t pi = me * nw + wid; pi < total; pi += G * nw) {
+        int64_t p = (int64_t)((2.0 * n - 1 - sqrt((2.0 * n - 1) * (2.0 * n - 1) - 8.0 * pi)) / 2.0);
+        if (p < 0) p = 0;
+        while (p > 0 && p * (2 * n - p - 1) / 2 > pi) --p;
+        while ((p + 1) * (2 * n - p - 2) / 2 <= pi) ++p;
+        const int64_t q = pi - p * (2 * n - p - 1) / 2 + p + 1;
+        double a = 0.0, b = 0.0, g = 0.0;
+        for (int64_t i = lane; i < n; i += 32) {
+            const double x = __ldcg(X + i + p * n), y = __ldcg(X + i + q * n);
+            a = fma(x, x, a);
+            b = fma(y, y, b);
+            g = fma(x, y, g);
+        }
+        a = __shfl_sync(0xffffffffu, warp_sum(a), 0);
+        b = __shfl_sync(0xffffffffu, warp_sum(b), 0);
+        g = __shfl_sync(0xffffffffu, warp_sum(g), 0);
+        if (g != 0.0 && g * g > tol2 * a * b) {
+            any = 1;
+            break;
+        }
+    }
+    if (any && lane == 0) atomicAdd(flag, 1u);
+    if (!grid_sync(bar)) return -1;
+    return (*(volatile unsigned int *)flag == 0u) ? 1 : 0;
+}
+
+// sigma_l = |x_l| for the columns of X (power-of-two scaled, CTAs round-robin)
+__device__ void jacobi_sigma(const double *X, int64_t n, double *sigma) {
+    __shared__ double red[32];
+    __shared__ long long redk[32];
+    const int64_t G = gridDim.x, me = blockIdx.x;
+    const int tid = threadIdx.x;
+    for (int64_t l = me; l < n; l += G) {
+        long long key = 0;
+        for (int64_t i = tid; i < n; i += blockDim.x) key = max(key, abs_key(__ldcg(X + i + l * n)));
+        const double sc = block_pow2_scale(key, redk);
+        double v[1] = {0.0};
+        if (sc != 0.0)
+            for (int64_t i = tid; i < n; i += blockDim.x) {
+                const double a = __ldcg(X + i + l * n) * sc;
+                v[0] = fma(a, a, v[0]);
+            }
+        block_sum_t0<1>(v, red);
+        if (tid == 0) sigma[l] = (sc == 0.0) ? 0.0 : sqrt(v[0]) / sc;
+        __syncthreads();
+    }
+}
+
+// statistics of the iteration: full sweeps, rotations, barrier-free checks
+__device__ __forceinline__ void jacobi_record_stats(unsigned int *rotcount, int full_sweeps, int check_passes) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned int rots = 0;
+        for (int sw = 0; sw < kMaxSweeps; ++sw) rots += *(volatile unsigned int *)(rotcount + sw);
+        rotcount[128] = (unsigned int)full_sweeps;
+        rotcount[129] = rots;
+        rotcount[130] = (unsigned int)check_passes;
+    }
+}
+
 template <int RPT>
 __global__ void __launch_bounds__(kDenseThreads) jacobi_coop_kernel(double *X, double *V, int64_t n, double tol,
                                                                    GridBarrier bar, unsigned int *rotcount,
@@ -332,35 +576,9 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_coop_kernel(double *X, d
     for (int sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
         if (prev_rot < (unsigned int)kCheckBelow) {
             ++check_passes;
-            // ---- barrier-free check: does any pair need a rotation?  One warp per pair.
-            if (!grid_sync(bar)) return;
-            const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-            const int64_t total = n * (n - 1) / 2;
-            int any = 0;
-            for (int64_t pi = me * nw + wid; pi < total; pi += G * nw) {
-                int64_t p = (int64_t)((2.0 * n - 1 - sqrt((2.0 * n - 1) * (2.0 * n - 1) - 8.0 * pi)) / 2.0);
-                if (p < 0) p = 0;
-                while (p > 0 && p * (2 * n - p - 1) / 2 > pi) --p;
-                while ((p + 1) * (2 * n - p - 2) / 2 <= pi) ++p;
-                const int64_t q = pi - p * (2 * n - p - 1) / 2 + p + 1;
-                double a = 0.0, b = 0.0, g = 0.0;
-                for (int64_t i = lane; i < n; i += 32) {
-                    const double x = __ldcg(X + i + p * n), y = __ldcg(X + i + q * n);
-                    a = fma(x, x, a);
-                    b = fma(y, y, b);
-                    g = fma(x, y, g);
-                }
-                a = __shfl_sync(0xffffffffu, warp_sum(a), 0);
-                b = __shfl_sync(0xffffffffu, warp_sum(b), 0);
-                g = __shfl_sync(0xffffffffu, warp_sum(g), 0);
-                if (g != 0.0 && g * g > tol2 * a * b) {
-                    any = 1;
-                    break;
-                }
-            }
-            if (any && lane == 0) atomicAdd(checkflag + sweep, 1u);
-            if (!grid_sync(bar)) return;
-            if (*(volatile unsigned int *)(checkflag + sweep) == 0u) {
+            const int c = jacobi_check_pass(X, n, tol2, bar, checkflag + sweep);
+            if (c < 0) return;
+            if (c == 1) {
                 converged = true;
                 break;
             }
@@ -425,30 +643,342 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_coop_kernel(double *X, d
         converged = (prev_rot == 0u);
     }
     if (!converged && me == 0 && tid == 0) set_status(status, NS_ERR_NOCONV);
-    if (me == 0 && tid == 0) {  // statistics: full sweeps, rotations, barrier-free checks
-        unsigned int rots = 0;
-        for (int sw = 0; sw < kMaxSweeps; ++sw) rots += *(volatile unsigned int *)(rotcount + sw);
-        rotcount[128] = (unsigned int)full_sweeps;
-        rotcount[129] = rots;
-        rotcount[130] = (unsigned int)check_passes;
-    }
+    jacobi_record_stats(rotcount, full_sweeps, check_passes);
     if (!grid_sync(bar)) return;
-    // sigma_l = |x_l| (scaled)
-    __shared__ long long redk[32];
-    for (int64_t l = me; l < n; l += G) {
-        long long key = 0;
-        for (int64_t i = tid; i < n; i += blockDim.x) key = max(key, abs_key(__ldcg(X + i + l * n)));
-        const double sc = block_pow2_scale(key, redk);
-        double v[1] = {0.0};
-        if (sc != 0.0)
-            for (int64_t i = tid; i < n; i += blockDim.x) {
-                const double a = __ldcg(X + i + l * n) * sc;
-                v[0] = fma(a, a, v[0]);
-            }
-        block_sum_t0<1>(v, red);
-        if (tid == 0) sigma[l] = (sc == 0.0) ? 0.0 : sqrt(v[0]) / sc;
-        __syncthreads();
+    jacobi_sigma(X, n, sigma);
+}
+
+// ------------------------------------------------- Jacobi, cluster ring ----
+// The same iteration as jacobi_coop_kernel (same rotation rule, threshold and
+// stopping test, every pair visited once per sweep), in an order that lets
+// most parallel steps run without a grid barrier.  For n <= 2 G kRingC the
+// n' = 2 G kRingC columns (columns >= n are zero and never rotate) form 2G
+// blocks of kRingC columns.  A sweep visits the block pairs round-robin: 2G - 1
+// outer steps with G disjoint block pairs each, cluster g (kRingC CTAs) taking
+// block pair g.  Within an outer step CTA i keeps column i of block P in
+// registers while the columns of block Q travel around the cluster: in round j
+// CTA i rotates the pair (P[i], Q[(i + j) mod kRingC]) and hands its Q column
+// to CTA i - 1 with st.async into that CTA's shared memory, the bytes counted
+// on the receiver's mbarrier.  A round thus waits only for one neighbour's
+// column.  The pairs inside each block are visited at the first outer step of
+// a sweep (kRingC - 1 round-robin rounds through global memory, one grid
+// barrier each).  Blocks move between clusters through global memory with one
+// grid barrier per outer step.  kRingT threads with kRingR rows each: four
+// warps keep all four FP64 units of the SM busy while the reduction tree stays
+// short (FP64 runs at 2 operations per clock per SM here, so every add of a
+// reduction counts).
+constexpr int kRingC = 8;      // CTAs per cluster = columns per block
+constexpr int kRingT = 128;    // threads per CTA
+constexpr int kRingR = 2;      // rows per thread: n <= kRingT * kRingR
+constexpr int kRingN = kRingT * kRingR;
+
+// Warp sums of three values with six additions per lane: two butterfly levels
+// that halve a 4-vector (the fourth entry is zero), then three levels on the
+// remaining value.  Afterwards lanes 0-7 hold the total of v0, lanes 8-15 of
+// v1, lanes 16-23 of v2.  The order of the additions is fixed.
+__device__ __forceinline__ double warp_sum3(double v0, double v1, double v2) {
+    const int lane = threadIdx.x & 31;
+    const bool hi4 = (lane & 16) != 0, hi3 = (lane & 8) != 0;
+    const double s0 = hi4 ? v0 : v2, s1 = hi4 ? v1 : 0.0;
+    double k0 = hi4 ? v2 : v0, k1 = hi4 ? 0.0 : v1;
+    k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+    k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+    const double s2 = hi3 ? k0 : k1;
+    double k = hi3 ? k1 : k0;
+    k += __shfl_xor_sync(0xffffffffu, s2, 8);
+    k += __shfl_xor_sync(0xffffffffu, k, 4);
+    k += __shfl_xor_sync(0xffffffffu, k, 2);
+    k += __shfl_xor_sync(0xffffffffu, k, 1);
+    return k;
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t peer_addr(uint32_t local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t shared_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// bounded wait for phase `parity` of a local mbarrier that peers complete
+__device__ __forceinline__ bool ring_wait(uint32_t mbar, uint32_t parity) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > (1ll << 32)) return false;  // ~2 s: a healthy ring waits microseconds
     }
+}
+
+// Sums (alpha, beta, gamma) over the CTA's kRingT threads; thread 0 then
+// forms the rotation into par[] (par[0] = 1 if the pair is rotated).  Two
+// __syncthreads; par is valid in every thread afterwards.
+__device__ __forceinline__ void ring_pair_rotation(double a, double b, double g, double tol2, double *red,
+                                                  double *par) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const double k = warp_sum3(a, b, g);
+    if ((lane & 7) == 0 && lane < 24) red[(lane >> 3) * 4 + wid] = k;
+    __syncthreads();
+    if (tid < 32) {
+        double t = 0.0;
+        if (lane < 3) t = (red[lane * 4 + 0] + red[lane * 4 + 1]) + (red[lane * 4 + 2] + red[lane * 4 + 3]);
+        const double al = __shfl_sync(0xffffffffu, t, 0), be = __shfl_sync(0xffffffffu, t, 1),
+                     ga = __shfl_sync(0xffffffffu, t, 2);
+        if (lane == 0) {
+            double c = 1.0, s = 0.0;
+            par[0] = rotation(al, be, ga, tol2, &c, &s) ? 1.0 : 0.0;
+            par[1] = c;
+            par[2] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// one pair of columns through global memory (CTA-uniform p, q).  Returns 1 in
+// thread 0 if the pair was rotated.
+__device__ unsigned int jacobi_pair_global(double *X, double *V, int64_t n, int64_t p, int64_t q, double tol2,
+                                           double *red, double *par) {
+    if (p >= n || q >= n) return 0u;
+    const int tid = threadIdx.x;
+    double xa[kRingR], xb[kRingR];
+    double a = 0.0, b = 0.0, g = 0.0;
+#pragma unroll
+    for (int r = 0; r < kRingR; ++r) {
+        const int64_t i = tid + r * kRingT;
+        xa[r] = (i < n) ? __ldcg(X + i + p * n) : 0.0;
+        xb[r] = (i < n) ? __ldcg(X + i + q * n) : 0.0;
+        a = fma(xa[r], xa[r], a);
+        b = fma(xb[r], xb[r], b);
+        g = fma(xa[r], xb[r], g);
+    }
+    ring_pair_rotation(a, b, g, tol2, red, par);
+    const bool rot = par[0] != 0.0;
+    if (rot) {
+        const double cs = par[1], sn = par[2];
+#pragma unroll
+        for (int r = 0; r < kRingR; ++r) {
+            const int64_t i = tid + r * kRingT;
+            if (i < n) {
+                X[i + p * n] = fma(cs, xa[r], -sn * xb[r]);
+                X[i + q * n] = fma(sn, xa[r], cs * xb[r]);
+                const double va = __ldcg(V + i + p * n), vb = __ldcg(V + i + q * n);
+                V[i + p * n] = fma(cs, va, -sn * vb);
+                V[i + q * n] = fma(sn, va, cs * vb);
+            }
+        }
+    }
+    __syncthreads();  // par is rewritten by the next pair
+    return rot ? 1u : 0u;
+}
+
+__global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingT)
+    jacobi_ring_kernel(double *X, double *V, int64_t n, int64_t G, double tol, GridBarrier bar,
+                       unsigned int *rotcount, unsigned int *checkflag, double *sigma, int32_t *status) {
+    // Slot j receives the Q column of round j: rows tid and tid + kRingT of X in
+    // xbuf[j][tid] and of V in vbuf[j][tid].  X and V travel separately (two
+    // mbarriers per slot) so the next CTA can start its dot products while this
+    // one still rotates V.
+    static_assert(kRingR == 2, "one double2 per thread and slot");
+    __shared__ __align__(16) double2 xbuf[kRingC][kRingT];
+    __shared__ __align__(16) double2 vbuf[kRingC][kRingT];
+    __shared__ __align__(8) unsigned long long mbx[kRingC], mbv[kRingC];
+    __shared__ double red[16];
+    __shared__ double par[3];
+    __shared__ volatile int s_abort;
+    const int tid = threadIdx.x;
+    {
+        // The ring needs the launch geometry it was built for: kRingC CTAs per
+        // cluster and G clusters.  A launch that did not honour the cluster
+        // dimension (a tool that re-issues the launch, say) leaves without
+        // touching distributed shared memory and reports NS_ERR_CUDA.
+        uint32_t ncta, ncl;
+        asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(ncta));
+        asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(ncl));
+        if (ncta != (uint32_t)kRingC || (int64_t)ncl != G || (int64_t)gridDim.x != G * kRingC ||
+            blockDim.x != (unsigned)kRingT) {
+            if (tid == 0) set_status(status, NS_ERR_CUDA);
+            return;
+        }
+    }
+    const uint32_t ci = cluster_rank();
+    const int64_t g = blockIdx.x / kRingC;
+    const int64_t nblk = 2 * G, nouter = nblk - 1;
+    const double tol2 = tol * tol;
+    if (tid == 0) {
+        for (int j = 0; j < kRingC; ++j) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(shared_addr(&mbx[j])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(shared_addr(&mbv[j])) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    for (int64_t l = blockIdx.x; l < n; l += gridDim.x)
+        for (int64_t i = tid; i < n; i += blockDim.x) V[i + l * n] = (i == l) ? 1.0 : 0.0;
+    cluster_sync_all();  // every mbarrier of the cluster is initialised before the first st.async
+    const uint32_t peer = (ci + kRingC - 1) % kRingC;
+    const uint32_t xb_peer = peer_addr(shared_addr(&xbuf[0][0]), peer);
+    const uint32_t vb_peer = peer_addr(shared_addr(&vbuf[0][0]), peer);
+    const uint32_t mx_peer = peer_addr(shared_addr(&mbx[0]), peer);
+    const uint32_t mv_peer = peer_addr(shared_addr(&mbv[0]), peer);
+    const int64_t i0 = tid, i1 = tid + kRingT;
+    const bool r0 = i0 < n, r1 = i1 < n;
+
+    bool converged = (n < 2), ok = true;
+    unsigned int prev_rot = 0xFFFFFFFFu;
+    int full_sweeps = 0, check_passes = 0;
+    uint32_t ostep = 0;  // outer steps so far: phase parity of the receive mbarriers
+    for (int sweep = 0; sweep < kMaxSweeps && !converged && ok; ++sweep) {
+        if (prev_rot < (unsigned int)kCheckBelow) {
+            ++check_passes;
+            const int c = jacobi_check_pass(X, n, tol2, bar, checkflag + sweep);
+            if (c < 0) {
+                ok = false;
+                break;
+            }
+            if (c == 1) {
+                converged = true;
+                break;
+            }
+        }
+        ++full_sweeps;
+        unsigned int local = 0;
+        if (!grid_sync(bar)) {
+            ok = false;
+            break;
+        }
+        for (int64_t t = 0; t < nouter; ++t) {
+            const int64_t P = rr_player(g, t, nblk), Q = rr_player(nblk - 1 - g, t, nblk);
+            if (t == 0) {  // pairs inside blocks P and Q
+                const int half = kRingC / 2;
+                const int64_t B = ((int)ci < half) ? P : Q;
+                const int k = (int)ci % half;
+                for (int j = 0; j < kRingC - 1 && ok; ++j) {
+                    const int64_t a = B * kRingC + rr_player(k, j, kRingC);
+                    const int64_t b = B * kRingC + rr_player(kRingC - 1 - k, j, kRingC);
+                    local += jacobi_pair_global(X, V, n, a, b, tol2, red, par);
+                    ok = grid_sync(bar);
+                }
+                if (!ok) break;
+            }
+            if (tid == 0)
+                for (int j = 1; j < kRingC; ++j) {
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(shared_addr(&mbx[j])),
+                                 "r"((uint32_t)(kRingT * sizeof(double2)))
+                                 : "memory");
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(shared_addr(&mbv[j])),
+                                 "r"((uint32_t)(kRingT * sizeof(double2)))
+                                 : "memory");
+                }
+            const int64_t cp = P * kRingC + ci, cq0 = Q * kRingC + ci;
+            const bool lp = cp < n, lq = cq0 < n;
+            double xp0 = (r0 && lp) ? __ldcg(X + i0 + cp * n) : 0.0, xp1 = (r1 && lp) ? __ldcg(X + i1 + cp * n) : 0.0;
+            double vp0 = (r0 && lp) ? __ldcg(V + i0 + cp * n) : 0.0, vp1 = (r1 && lp) ? __ldcg(V + i1 + cp * n) : 0.0;
+            double xq0 = (r0 && lq) ? __ldcg(X + i0 + cq0 * n) : 0.0, xq1 = (r1 && lq) ? __ldcg(X + i1 + cq0 * n) : 0.0;
+            double vq0 = (r0 && lq) ? __ldcg(V + i0 + cq0 * n) : 0.0, vq1 = (r1 && lq) ? __ldcg(V + i1 + cq0 * n) : 0.0;
+            for (int j = 0; j < kRingC; ++j) {
+                if (j > 0) {
+                    if (!s_abort && !ring_wait(shared_addr(&mbx[j]), ostep & 1u)) {
+                        s_abort = 1;
+                        set_status(status, NS_ERR_TIMEOUT);
+                    }
+                    const double2 in = xbuf[j][tid];
+                    xq0 = in.x;
+                    xq1 = in.y;
+                }
+                const double a = fma(xp1, xp1, xp0 * xp0), b = fma(xq1, xq1, xq0 * xq0),
+                             gm = fma(xp1, xq1, xp0 * xq0);
+                ring_pair_rotation(a, b, gm, tol2, red, par);
+                const bool rot = par[0] != 0.0;
+                const double cs = par[1], sn = par[2];
+                if (rot) {
+                    if (tid == 0) ++local;
+                    const double a0 = xp0, a1 = xp1, b0 = xq0, b1 = xq1;
+                    xp0 = fma(cs, a0, -sn * b0);
+                    xp1 = fma(cs, a1, -sn * b1);
+                    xq0 = fma(sn, a0, cs * b0);
+                    xq1 = fma(sn, a1, cs * b1);
+                }
+                const int64_t cq = Q * kRingC + (ci + kRingC - 1) % kRingC;  // Q column held after the last round
+                if (j < kRingC - 1) {
+                    const uint32_t off = (uint32_t)(((j + 1) * kRingT + tid) * sizeof(double2));
+                    asm volatile(
+                        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(
+                            xb_peer + off),
+                        "d"(xq0), "d"(xq1), "r"(mx_peer + (uint32_t)((j + 1) * 8))
+                        : "memory");
+                } else {
+                    if (r0 && cq < n) X[i0 + cq * n] = xq0;
+                    if (r1 && cq < n) X[i1 + cq * n] = xq1;
+                }
+                // V: the incoming column's V part, then the same rotation
+                if (j > 0) {
+                    if (!s_abort && !ring_wait(shared_addr(&mbv[j]), ostep & 1u)) {
+                        s_abort = 1;
+                        set_status(status, NS_ERR_TIMEOUT);
+                    }
+                    const double2 in = vbuf[j][tid];
+                    vq0 = in.x;
+                    vq1 = in.y;
+                }
+                if (rot) {
+                    const double a0 = vp0, a1 = vp1, b0 = vq0, b1 = vq1;
+                    vp0 = fma(cs, a0, -sn * b0);
+                    vp1 = fma(cs, a1, -sn * b1);
+                    vq0 = fma(sn, a0, cs * b0);
+                    vq1 = fma(sn, a1, cs * b1);
+                }
+                if (j < kRingC - 1) {
+                    const uint32_t off = (uint32_t)(((j + 1) * kRingT + tid) * sizeof(double2));
+                    asm volatile(
+                        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(
+                            vb_peer + off),
+                        "d"(vq0), "d"(vq1), "r"(mv_peer + (uint32_t)((j + 1) * 8))
+                        : "memory");
+                } else {
+                    if (r0 && cq < n) V[i0 + cq * n] = vq0;
+                    if (r1 && cq < n) V[i1 + cq * n] = vq1;
+                }
+            }
+            if (lp) {
+                if (r0) {
+                    X[i0 + cp * n] = xp0;
+                    V[i0 + cp * n] = vp0;
+                }
+                if (r1) {
+                    X[i1 + cp * n] = xp1;
+                    V[i1 + cp * n] = vp1;
+                }
+            }
+            ++ostep;
+            if (t == nouter - 1 && tid == 0 && local) atomicAdd(rotcount + sweep, local);
+            if (!grid_sync(bar)) {
+                ok = false;
+                break;
+            }
+        }
+        if (!ok) break;
+        prev_rot = *(volatile unsigned int *)(rotcount + sweep);
+        converged = (prev_rot == 0u);
+    }
+    if (ok) {
+        if (!converged && blockIdx.x == 0 && tid == 0) set_status(status, NS_ERR_NOCONV);
+        jacobi_record_stats(rotcount, full_sweeps, check_passes);
+        if (grid_sync(bar)) jacobi_sigma(X, n, sigma);
+    }
+    cluster_sync_all();  // no CTA leaves while a peer may still address its shared memory
 }
 
 // --------------------------------------------- V = P Q2 Vx (no barriers) ----
@@ -574,6 +1104,49 @@ static cudaError_t launch_jacobi(const DenseWork &w, int64_t n, GridBarrier bar,
     return cudaLaunchCooperativeKernel((const void *)jacobi_coop_kernel<RPT>, (int)G, kDenseThreads, args, 0, st);
 }
 
+// The ring Jacobi (cluster size fixed at compile time) needs its G clusters,
+// 2 G kRingC >= n columns, resident at once: a cooperative launch.  Falls
+// back (sets *used = false) when the device cannot hold them or rejects the
+// launch.
+static cudaError_t launch_jacobi_ring(const DenseWork &w, int64_t n, GridBarrier bar, int32_t *status,
+                                      cudaStream_t st, bool *used) {
+    static int state[64] = {0};  // per device: 0 unknown, 1 usable, -1 not usable
+    *used = false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaSuccess;
+    if (state[dev] < 0) return cudaSuccess;
+    int64_t G = (n + 2 * kRingC - 1) / (2 * kRingC);
+    if (G < 1) G = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(G * kRingC), 1, 1);
+    cfg.blockDim = dim3(kRingT, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 0;
+    int maxc = 0;
+    if (cudaOccupancyMaxActiveClusters(&maxc, (void *)jacobi_ring_kernel, &cfg) != cudaSuccess || maxc < G) {
+        cudaGetLastError();
+        return cudaSuccess;
+    }
+    cfg.numAttrs = 1;
+    double *X = w.X, *V = w.V, *sigma = w.sigma;
+    unsigned int *rot = w.bar + 64, *chk = w.bar + 64 + 64;
+    const double tol = (double)n * std::ldexp(1.0, -53);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, jacobi_ring_kernel, X, V, n, G, tol, bar, rot, chk, sigma, status);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        state[dev] = -1;
+        return cudaSuccess;
+    }
+    state[dev] = 1;
+    *used = true;
+    return cudaSuccess;
+}
+
 template <int NB>
 static cudaError_t launch_hqr_nb(double *W, int64_t rows, int64_t cols, int pivot, double *u0, double *cf,
                                  int32_t *perm, unsigned long long *pivslot, double *Rout, GridBarrier bar, int64_t G,
@@ -585,6 +1158,25 @@ static cudaError_t launch_hqr_nb(double *W, int64_t rows, int64_t cols, int pivo
     if (e != cudaSuccess) return e;
     void *args[] = {&W, &rows, &cols, &pivot, &u0, &cf, &perm, &pivslot, &Rout, &bar};
     return cudaLaunchCooperativeKernel((const void *)hqr_coop_kernel<NB>, (int)G, kDenseThreads, args, smem, st);
+}
+
+// Pipelined QR (no pivoting) when the owned columns fit in shared memory;
+// returns false (nothing launched) otherwise.
+static bool launch_hqr_pipe(double *W, int64_t rows, int64_t cols, double *u0, double *cf, int32_t *perm,
+                            unsigned int *flags, double *Rout, int32_t *status, cudaStream_t st, cudaError_t *err) {
+    int64_t G = cols < sm_count() ? cols : sm_count();
+    if (G < 1) G = 1;
+    const int64_t nown = (cols + G - 1) / G;
+    const size_t smem = sizeof(double) * (size_t)(nown * rows + 2 * rows + nown);
+    if (smem > 200 * 1024) return false;
+    *err = cudaMemsetAsync(flags, 0, sizeof(unsigned int) * (size_t)cols, st);
+    if (*err != cudaSuccess) return true;
+    *err = cudaFuncSetAttribute(hqr_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (*err != cudaSuccess) return true;
+    int64_t nown_ = nown;
+    void *args[] = {&W, &rows, &cols, &nown_, &u0, &cf, &perm, &flags, &Rout, &status};
+    *err = cudaLaunchCooperativeKernel((const void *)hqr_pipe_kernel, (int)G, kPipeThreads, args, smem, st);
+    return true;
 }
 
 static cudaError_t launch_hqr(double *W, int64_t rows, int64_t cols, int pivot, double *u0, double *cf,
@@ -622,8 +1214,11 @@ cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k
     if (e != cudaSuccess) return e;
     GridBarrier bar{w.bar, status};
     double *u0a = w.tau, *cfa = w.tau + n, *u0b = w.tau + 2 * n, *cfb = w.tau + 3 * n;
-    // 1. SA P = Q1 R (pivoted); R (n x n) lands in X
-    e = launch_hqr(w.W, s, n, 1, u0a, cfa, w.perm, w.pivslot, w.X, bar, st);
+    // 1. SA P = Q1 R; R (n x n) lands in X.  Pipelined without pivoting when it
+    // fits (P = I), else barrier-separated with column pivoting.
+    unsigned int *flags = (unsigned int *)w.pivslot;  // 2 (n + 1) words >= n flags
+    if (!launch_hqr_pipe(w.W, s, n, u0a, cfa, w.perm, flags, w.X, status, st, &e))
+        e = launch_hqr(w.W, s, n, 1, u0a, cfa, w.perm, w.pivslot, w.X, bar, st);
     if (e != cudaSuccess) return e;
     // 2. L = R^T; QR of L without pivoting: reflectors stay in L, R2 lands in V (scratch)
     {
@@ -632,14 +1227,21 @@ cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     int32_t *perm2 = (int32_t *)w.sigma;  // identity permutation of the unpivoted QR (unused)
-    e = launch_hqr(w.L, n, n, 0, u0b, cfb, perm2, w.pivslot, w.V, bar, st);
+    if (!launch_hqr_pipe(w.L, n, n, u0b, cfb, perm2, flags, w.V, status, st, &e))
+        e = launch_hqr(w.L, n, n, 0, u0b, cfb, perm2, w.pivslot, w.V, bar, st);
     if (e != cudaSuccess) return e;
     // 3. X = R2^T; Jacobi on X (V receives Vx)
     r2t_kernel<<<(unsigned)((n * n + 255) / 256), 256, 0, st>>>(w.V, n, w.X);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * kBarWords, st);
     if (e != cudaSuccess) return e;
-    if (n <= 256) e = launch_jacobi<1>(w, n, bar, status, st);
+    bool ring = false;
+    if (n <= kRingN) {
+        e = launch_jacobi_ring(w, n, bar, status, st, &ring);
+        if (e != cudaSuccess) return e;
+    }
+    if (ring) e = cudaSuccess;
+    else if (n <= 256) e = launch_jacobi<1>(w, n, bar, status, st);
     else if (n <= 1024) e = launch_jacobi<4>(w, n, bar, status, st);
     else e = launch_jacobi<16>(w, n, bar, status, st);
     if (e != cudaSuccess) return e;
