@@ -111,7 +111,7 @@ def dense_flops(s, n, k, stats):
     pivoted Householder QR of s x n, Householder QR of n x n, one-sided Jacobi
     (dot products 6n per visited pair, rotation of two columns of X and of V 12n),
     and the k trailing columns of V = P Q2 Vx (4 n^2 k)."""
-    sweeps, rots, checks = stats
+    sweeps, rots, checks = stats[:3]
     pairs = n * (n - 1) / 2
     qr1 = 2.0 * n * n * (s - n / 3.0)
     qr2 = 4.0 / 3.0 * n ** 3
@@ -448,7 +448,8 @@ def main():
                   "frac": dense_tf / fp64_peak, "traffic": None,
                   "kernel": "FP64 dense stage (hqr_coop x2, jacobi_coop, apply_q2, extract) via ns_solve_sketched",
                   "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x sampled SM clock",
-                  "algorithmic_flops": dflops, "jacobi_sweeps_rotations_checks": stats}
+                  "algorithmic_flops": dflops, "jacobi_sweeps_rotations_checks": stats[:3],
+                  "jacobi_kernel": "cluster ring" if stats[3] == 1 else "barrier-separated"}
     dominant = dense_roof if t_dense > t_sketch else sketch_roof
     line = {
         "metric": METRIC, "value": n_ranks * args.steps / (ms_solve / 1e3), "unit": "solves/s", "n_gpus": n_ranks,
@@ -467,7 +468,7 @@ def main():
                         "residual_AV_F": resid_sp},
         "e2e": {"value": n_ranks * e2e_steps / (ms_e2e / 1e3), "unit": "solves/s",
                 "h2d_bytes_per_step": M * N * 8, "d2h_bytes_per_step": (N * K_NULL + K_NULL) * 8},
-        "gpu_launches": 12 * args.steps,
+        "gpu_launches": 15 * args.steps,
         "clocks": clocks,
     }
     if args.extra and rank == 0:

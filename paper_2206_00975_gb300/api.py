@@ -252,8 +252,8 @@ def ns_solve_sketched(d, SA, k, save=False, status=None, ws=None, stream=None):
 
 
 def jacobi_stats(d, m, n, ws, sketched=False, stream=None):
-    """(full sweeps, rotations, check passes) of the last solve in workspace ws."""
-    out = torch.zeros(3, dtype=torch.int64, device=ws.device)
+    """(full sweeps, rotations, check passes, ring kernel used) of the last solve in workspace ws."""
+    out = torch.zeros(4, dtype=torch.int64, device=ws.device)
     lib = _lib.load()
     if sketched:
         st = lib.ns_sketched_stats(ctypes.byref(d), int(n), _p(ws), _p(out), _stream(stream))

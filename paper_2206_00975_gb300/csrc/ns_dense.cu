@@ -273,17 +273,33 @@ __device__ __forceinline__ unsigned int ld_acquire_flag(const unsigned int *p) {
     return v;
 }
 
-// Sum over the CTA, result in every thread (fixed order).
+// Sum over the CTA, result in every thread (fixed order).  The tree adds only
+// in the lanes whose sums survive: FP64 issue is scarce, idle lanes are not.
+__device__ __forceinline__ double lane0_sum(double v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double w = __shfl_down_sync(0xffffffffu, v, o);
+        if (lane < o) v += w;
+    }
+    return v;  // valid in lane 0
+}
 __device__ __forceinline__ double pipe_sum(double v, double *red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    v = warp_sum(v);
+    v = lane0_sum(v);
     if (lane == 0) red[wid] = v;
     __syncthreads();
-    double a = 0.0;
+    if (wid == 0) {
+        double a = lane < kPipeThreads / 32 ? red[lane] : 0.0;
 #pragma unroll
-    for (int w = 0; w < kPipeThreads / 32; ++w) a += red[w];
+        for (int o = kPipeThreads / 64; o > 0; o >>= 1) {
+            const double w = __shfl_down_sync(0xffffffffu, a, o);
+            if (lane < o) a += w;
+        }
+        if (lane == 0) red[kPipeThreads / 32] = a;
+    }
     __syncthreads();
-    return a;
+    return red[kPipeThreads / 32];
 }
 
 // Form reflector j from the owned column x (shared memory, rows entries):
@@ -336,11 +352,8 @@ __device__ double pipe_form(double *W, int64_t rows, int64_t j, const double *x,
         *coef_sh = coef;
         s_par[0] = beta;
     }
-    __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flag + j), "r"(1u) : "memory");
-    }
+    __syncthreads();  // orders every thread's stores before thread 0's release
+    if (tid == 0) asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flag + j), "r"(1u) : "memory");
     return s_par[0];
 }
 
@@ -362,7 +375,7 @@ __global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(double *W, int64
     double *own = sm;                          // nown_max * rows: owned columns
     double *ubuf = sm + nown_max * rows;       // 2 * rows: reflectors j (even/odd)
     double *beta = ubuf + 2 * rows;            // nown_max: R's diagonal of owned columns
-    __shared__ double red[kPipeThreads / 32];
+    __shared__ double red[kPipeThreads / 32 + 1];
     __shared__ double s_coef[2];
     __shared__ int s_ok;
     const int tid = threadIdx.x;
@@ -418,7 +431,7 @@ __global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(double *W, int64
             }
         __syncthreads();
     }
-    // R (logical column order = physical, no pivoting) and the identity permutation
+    // R (column order as stored in W)
     for (int64_t o = 0; o < nown; ++o) {
         const int64_t c = me + o * G;
         for (int64_t i = tid; i < cols; i += kPipeThreads) {
@@ -427,7 +440,81 @@ __global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(double *W, int64
             else if (i == c) r = (c < steps) ? beta[o] : own[o * rows + c];
             Rout[i + c * cols] = r;
         }
-        if (tid == 0) perm[c] = (int32_t)c;
+    }
+}
+
+// ------------------------------------------------- static column order ----
+// The pipelined QR does not pivot.  For the relative accuracy of the
+// preconditioned Jacobi on column-graded inputs the rows of R must be graded,
+// which column pivoting achieves; ordering the columns once by decreasing norm
+// before the QR achieves it for column-scaled matrices (row i of R is bounded
+// by the norm of column i).  perm[j] = the column of SA placed at position j.
+__global__ void __launch_bounds__(256) colnorm_kernel(const double *__restrict__ SA, int64_t s, int64_t n,
+                                                      double *__restrict__ key) {
+    __shared__ double red[32];
+    __shared__ long long redk[32];
+    for (int64_t c = blockIdx.x; c < n; c += gridDim.x) {
+        const double *a = SA + c * s;
+        long long mx = 0;
+        for (int64_t i = threadIdx.x; i < s; i += blockDim.x) mx = max(mx, abs_key(a[i]));
+        const double sc = block_pow2_scale(mx, redk);  // largest entry scaled into [1, 2)
+        double v[1] = {0.0};
+        for (int64_t i = threadIdx.x; i < s; i += blockDim.x) {
+            const double x = a[i] * sc;
+            v[0] = fma(x, x, v[0]);
+        }
+        block_sum_t0<1>(v, red);
+        if (threadIdx.x == 0) {
+            // log2 |a|^2 = log2(scaled |a|^2) - 2 log2(sc); -inf-like for a zero column
+            const int esc = (int)((__double_as_longlong(sc) >> 52) & 0x7FF) - 1023;
+            key[c] = (sc == 0.0 || v[0] == 0.0) ? -1e300 : log2(v[0]) - 2.0 * (double)esc;
+        }
+        __syncthreads();
+    }
+}
+
+// one CTA: perm = the columns by decreasing key, ties to the lower index
+// (bitonic sort of np2 >= n entries in dynamic shared memory, n <= 4096)
+__global__ void __launch_bounds__(1024) sort_perm_kernel(const double *__restrict__ key, int64_t n, int64_t np2,
+                                                         int32_t *__restrict__ perm) {
+    extern __shared__ double sk[];                // np2 keys
+    int32_t *si = (int32_t *)(sk + np2);          // np2 indices
+    for (int64_t i = threadIdx.x; i < np2; i += blockDim.x) {
+        sk[i] = i < n ? key[i] : -2e300;
+        si[i] = (int32_t)i;
+    }
+    __syncthreads();
+    for (int64_t k = 2; k <= np2; k <<= 1) {
+        for (int64_t j = k >> 1; j > 0; j >>= 1) {
+            for (int64_t i = threadIdx.x; i < np2; i += blockDim.x) {
+                const int64_t l = i ^ j;
+                if (l > i) {
+                    // "x before y": larger key, then smaller index
+                    const bool l_before_i = sk[l] > sk[i] || (sk[l] == sk[i] && si[l] < si[i]);
+                    const bool up = (i & k) == 0;
+                    if (up ? l_before_i : !l_before_i) {
+                        const double tk = sk[i];
+                        const int32_t ti = si[i];
+                        sk[i] = sk[l];
+                        si[i] = si[l];
+                        sk[l] = tk;
+                        si[l] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) perm[i] = si[i];
+}
+
+// W[:, j] = SA[:, perm[j]]
+__global__ void permute_cols_kernel(const double *__restrict__ SA, int64_t s, int64_t n,
+                                    const int32_t *__restrict__ perm, double *__restrict__ W) {
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
+        const double *a = SA + (int64_t)perm[j] * s;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s; i += (int64_t)gridDim.x * blockDim.x)
+            W[i + j * s] = a[i];
     }
 }
 
@@ -463,7 +550,10 @@ __device__ __forceinline__ int64_t rr_player(int64_t pos, int64_t step, int64_t 
 // orthogonal to the tolerance.  One thread.
 __device__ __forceinline__ bool rotation(double alpha, double beta, double gamma, double tol2, double *c_out,
                                          double *s_out) {
-    if (gamma == 0.0 || !(gamma * gamma > tol2 * alpha * beta)) return false;
+    const double gg = gamma * gamma, ab = alpha * beta;
+    if (gamma == 0.0 || !(gg > tol2 * ab)) return false;
+    // FP32 images of alpha, beta, gamma scaled by the same power of two (the
+    // larger of alpha, beta lands in [1, 2)); integer work on the exponent
     const double mx = fmax(alpha, beta);
     const int e = (int)(((unsigned long long)__double_as_longlong(mx) >> 52) & 0x7FF);
     int se = 2046 - e;
@@ -471,19 +561,32 @@ __device__ __forceinline__ bool rotation(double alpha, double beta, double gamma
     const double sc = __longlong_as_double((long long)se << 52);
     const float a32 = (float)(alpha * sc), b32 = (float)(beta * sc), g32 = (float)(gamma * sc);
     double t;
-    if (fabsf(g32) < 1e-30f) {
-        t = gamma / (beta - alpha);  // tiny angle: t ~ gamma / (beta - alpha)
-    } else {
+    if (fabsf(g32) >= 1e-30f) {
         const float z = (b32 - a32) / (2.0f * g32);
-        float t32;
-        if (fabsf(z) > 1e18f) t32 = 0.5f / z;
-        else t32 = copysignf(1.0f, z) / (fabsf(z) + sqrtf(1.0f + z * z));
-        t = (double)t32;
+        t = (double)((fabsf(z) > 1e18f) ? 0.5f / z : copysignf(1.0f, z) / (fabsf(z) + sqrtf(1.0f + z * z)));
+    } else {
+        // tiny angle: t ~ gamma / (beta - alpha), from the mantissas and the
+        // exponents separately (the scaled FP32 image of gamma underflows)
+        const double d = beta - alpha;
+        if (d == 0.0) {
+            t = gamma > 0.0 ? 1.0 : -1.0;  // alpha = beta: the 45-degree rotation
+        } else {
+            const long long gb = __double_as_longlong(gamma), db = __double_as_longlong(d);
+            const int eg = (int)((gb >> 52) & 0x7FF), ed = (int)((db >> 52) & 0x7FF), k = eg - ed + 1023;
+            if (eg == 0 || ed == 0 || k < 1 || k > 2046) {
+                t = gamma / d;  // subnormal operands or an extreme ratio (rare)
+            } else {
+                const float gm = (float)__longlong_as_double((gb & 0x800FFFFFFFFFFFFFll) | (1023ll << 52));
+                const float dm = (float)__longlong_as_double((db & 0x800FFFFFFFFFFFFFll) | (1023ll << 52));
+                t = (double)(gm / dm) * __longlong_as_double((long long)k << 52);
+            }
+        }
     }
     const double tt = fma(t, t, 1.0);
     double y = (double)rsqrtf((float)tt);
-    y = y * fma(-0.5 * tt, y * y, 1.5);
-    y = y * fma(-0.5 * tt, y * y, 1.5);
+    const double h = -0.5 * tt;
+    y = y * fma(h, y * y, 1.5);
+    y = y * fma(h, y * y, 1.5);
     *c_out = y;
     *s_out = y * t;
     return true;
@@ -546,14 +649,17 @@ __device__ void jacobi_sigma(const double *X, int64_t n, double *sigma) {
     }
 }
 
-// statistics of the iteration: full sweeps, rotations, barrier-free checks
-__device__ __forceinline__ void jacobi_record_stats(unsigned int *rotcount, int full_sweeps, int check_passes) {
+// statistics of the iteration: full sweeps, rotations, barrier-free checks,
+// and which kernel ran (1: cluster ring, 0: barrier-separated)
+__device__ __forceinline__ void jacobi_record_stats(unsigned int *rotcount, int full_sweeps, int check_passes,
+                                                    int ring) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         unsigned int rots = 0;
         for (int sw = 0; sw < kMaxSweeps; ++sw) rots += *(volatile unsigned int *)(rotcount + sw);
         rotcount[128] = (unsigned int)full_sweeps;
         rotcount[129] = rots;
         rotcount[130] = (unsigned int)check_passes;
+        rotcount[131] = (unsigned int)ring;
     }
 }
 
@@ -643,7 +749,7 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_coop_kernel(double *X, d
         converged = (prev_rot == 0u);
     }
     if (!converged && me == 0 && tid == 0) set_status(status, NS_ERR_NOCONV);
-    jacobi_record_stats(rotcount, full_sweeps, check_passes);
+    jacobi_record_stats(rotcount, full_sweeps, check_passes, 0);
     if (!grid_sync(bar)) return;
     jacobi_sigma(X, n, sigma);
 }
@@ -723,21 +829,123 @@ __device__ __forceinline__ bool ring_wait(uint32_t mbar, uint32_t parity) {
     }
 }
 
-// Sums (alpha, beta, gamma) over the CTA's kRingT threads; thread 0 then
-// forms the rotation into par[] (par[0] = 1 if the pair is rotated).  Two
-// __syncthreads; par is valid in every thread afterwards.
-__device__ __forceinline__ void ring_pair_rotation(double a, double b, double g, double tol2, double *red,
-                                                  double *par) {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+// CTA layout (kRingCta threads): warp 0 is the scalar warp (the angle of
+// each pair, the column scales, the hand-over of the scales), warps 1-4 hold
+// rows of the X columns, warps 5-8 the same rows of the V columns.  The row
+// warps never wait on the scalar chain of the previous round, and the V
+// update of one round overlaps the X work of the next.
+constexpr int kRingCta = 32 + 2 * kRingT;
+constexpr int kRingBar = 32 + kRingT;  // scalar warp + X row warps (named barrier 1)
+
+__device__ __forceinline__ void xbar() { asm volatile("bar.sync 1, %0;" ::"n"(kRingBar) : "memory"); }
+
+// bounded wait for phase `parity` of a local mbarrier completed inside the CTA
+__device__ __forceinline__ bool ring_wait_cta(uint32_t mbar, uint32_t parity) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > (1ll << 32)) return false;
+    }
+}
+
+// FP32 image of x * 2^-shift from the IEEE fields (integer work, mantissa
+// truncated; zero, subnormal and below-range values give 0).
+__device__ __forceinline__ float f32_image(double x, int shift) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF), fe = e - shift - 1023 + 127;
+    if (e == 0 || fe <= 0) return 0.0f;
+    const unsigned int f = ((unsigned int)(b >> 32) & 0x80000000u) | ((unsigned int)min(fe, 254) << 23) |
+                           (unsigned int)((b >> 29) & 0x7FFFFFu);
+    return __uint_as_float(f);
+}
+// exact FP64 value of a normal or zero FP32 number (integer work)
+__device__ __forceinline__ double f64_of(float f) {
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int e = (u >> 23) & 0xFF;
+    if (e == 0) return 0.0;
+    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
+                                 ((unsigned long long)(e - 127 + 1023) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
+// Jacobi angle of a pair held as scaled columns x = d x~ (ring kernel):
+// a, b, g are |x~_p|^2, |x~_q|^2 and x~_p . x~_q; dp2, dq2, dpq the squares and
+// product of the scales (FP32).  The threshold test does not depend on the
+// scales.  t = tan(theta) needs only modest accuracy (the applied rotation is
+// orthogonal whatever t is), so it comes from FP32 images of the scaled sums.
+__device__ __forceinline__ bool ring_angle(double a, double b, double g, double tol2, float dp2, float dq2,
+                                           float dpq, double dp, double dq, double *t_out) {
+    if (g == 0.0 || !(g * g > tol2 * (a * b))) return false;
+    const long long ka = __double_as_longlong(a), kb = __double_as_longlong(b);
+    const int shift = (int)(((ka > kb ? ka : kb) >> 52) & 0x7FF) - 1023;
+    const float a32 = f32_image(a, shift) * dp2, b32 = f32_image(b, shift) * dq2, g32 = f32_image(g, shift) * dpq;
+    if (fabsf(g32) >= 1e-30f) {
+        const float z = __fdividef(b32 - a32, 2.0f * g32), az = fabsf(z);
+        float t32;
+        if (az > 1e18f) {
+            t32 = __fdividef(0.5f, z);
+        } else {
+            const float w = fmaf(z, z, 1.0f);
+            t32 = copysignf(__fdividef(1.0f, az + w * rsqrtf(w)), z);
+        }
+        *t_out = f64_of(t32);
+        return true;
+    }
+    // tiny angle: t ~ gamma / (beta - alpha) with the true (scaled) sums (rare)
+    const double al = a * dp * dp, be = b * dq * dq, ga = g * dp * dq, d = be - al;
+    *t_out = (d == 0.0) ? (ga > 0.0 ? 1.0 : -1.0) : ga / d;
+    return true;
+}
+
+// Combines the X row warps' partial sums (red[v * 4 + w]: value v of row
+// warp w) in lanes 0-2 of the scalar warp and returns them in every lane.
+__device__ __forceinline__ void ring_combine(const double *red, double *al, double *be, double *ga) {
+    const int lane = threadIdx.x & 31;
+    double v = 0.0;
+    if (lane < 3) v = (red[lane * 4 + 0] + red[lane * 4 + 1]) + (red[lane * 4 + 2] + red[lane * 4 + 3]);
+    *al = __shfl_sync(0xffffffffu, v, 0);
+    *be = __shfl_sync(0xffffffffu, v, 1);
+    *ga = __shfl_sync(0xffffffffu, v, 2);
+}
+
+// The X row warps' share of a pair's sums: warp sums in red[v * 4 + w].
+__device__ __forceinline__ void ring_partials(double a, double b, double g, int t, double *red) {
     const double k = warp_sum3(a, b, g);
-    if ((lane & 7) == 0 && lane < 24) red[(lane >> 3) * 4 + wid] = k;
-    __syncthreads();
-    if (tid < 32) {
-        double t = 0.0;
-        if (lane < 3) t = (red[lane * 4 + 0] + red[lane * 4 + 1]) + (red[lane * 4 + 2] + red[lane * 4 + 3]);
-        const double al = __shfl_sync(0xffffffffu, t, 0), be = __shfl_sync(0xffffffffu, t, 1),
-                     ga = __shfl_sync(0xffffffffu, t, 2);
-        if (lane == 0) {
+    if ((t & 7) == 0 && (t & 31) < 24) red[((t & 31) >> 3) * 4 + (t >> 5)] = k;
+}
+
+// one pair of columns through global memory (CTA-uniform p, q), all threads
+// of the CTA; plain (unscaled) rotation.  Returns 1 in thread 0 if rotated.
+__device__ unsigned int jacobi_pair_global(double *X, double *V, int64_t n, int64_t p, int64_t q, double tol2,
+                                           double *red, double *par) {
+    if (p >= n || q >= n) return 0u;
+    const int tid = threadIdx.x;
+    const bool scalar = tid < 32, isx = tid >= 32 && tid < 32 + kRingT;
+    const int t = isx ? tid - 32 : tid - 32 - kRingT;
+    double *M = isx ? X : V;
+    double ya[kRingR] = {0.0, 0.0}, yb[kRingR] = {0.0, 0.0};
+    if (!scalar) {
+#pragma unroll
+        for (int r = 0; r < kRingR; ++r) {
+            const int64_t i = t + r * kRingT;
+            ya[r] = (i < n) ? __ldcg(M + i + p * n) : 0.0;
+            yb[r] = (i < n) ? __ldcg(M + i + q * n) : 0.0;
+        }
+    }
+    if (isx) ring_partials(fma(ya[1], ya[1], ya[0] * ya[0]), fma(yb[1], yb[1], yb[0] * yb[0]),
+                           fma(ya[1], yb[1], ya[0] * yb[0]), t, red);
+    if (scalar || isx) xbar();
+    if (scalar) {
+        double al, be, ga;
+        ring_combine(red, &al, &be, &ga);
+        if (tid == 0) {
             double c = 1.0, s = 0.0;
             par[0] = rotation(al, be, ga, tol2, &c, &s) ? 1.0 : 0.0;
             par[1] = c;
@@ -745,58 +953,55 @@ __device__ __forceinline__ void ring_pair_rotation(double a, double b, double g,
         }
     }
     __syncthreads();
-}
-
-// one pair of columns through global memory (CTA-uniform p, q).  Returns 1 in
-// thread 0 if the pair was rotated.
-__device__ unsigned int jacobi_pair_global(double *X, double *V, int64_t n, int64_t p, int64_t q, double tol2,
-                                           double *red, double *par) {
-    if (p >= n || q >= n) return 0u;
-    const int tid = threadIdx.x;
-    double xa[kRingR], xb[kRingR];
-    double a = 0.0, b = 0.0, g = 0.0;
-#pragma unroll
-    for (int r = 0; r < kRingR; ++r) {
-        const int64_t i = tid + r * kRingT;
-        xa[r] = (i < n) ? __ldcg(X + i + p * n) : 0.0;
-        xb[r] = (i < n) ? __ldcg(X + i + q * n) : 0.0;
-        a = fma(xa[r], xa[r], a);
-        b = fma(xb[r], xb[r], b);
-        g = fma(xa[r], xb[r], g);
-    }
-    ring_pair_rotation(a, b, g, tol2, red, par);
     const bool rot = par[0] != 0.0;
-    if (rot) {
+    if (rot && !scalar) {
         const double cs = par[1], sn = par[2];
 #pragma unroll
         for (int r = 0; r < kRingR; ++r) {
-            const int64_t i = tid + r * kRingT;
+            const int64_t i = t + r * kRingT;
             if (i < n) {
-                X[i + p * n] = fma(cs, xa[r], -sn * xb[r]);
-                X[i + q * n] = fma(sn, xa[r], cs * xb[r]);
-                const double va = __ldcg(V + i + p * n), vb = __ldcg(V + i + q * n);
-                V[i + p * n] = fma(cs, va, -sn * vb);
-                V[i + q * n] = fma(sn, va, cs * vb);
+                M[i + p * n] = fma(cs, ya[r], -sn * yb[r]);
+                M[i + q * n] = fma(sn, ya[r], cs * yb[r]);
             }
         }
     }
-    __syncthreads();  // par is rewritten by the next pair
+    __syncthreads();  // par and red are rewritten by the next pair
     return rot ? 1u : 0u;
 }
 
-__global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingT)
+__device__ __forceinline__ void mbar_arm(unsigned long long *mb, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(shared_addr(mb)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void send_pair(uint32_t dst, double a, double b, uint32_t mb) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(dst),
+                 "d"(a), "d"(b), "r"(mb)
+                 : "memory");
+}
+
+__global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
     jacobi_ring_kernel(double *X, double *V, int64_t n, int64_t G, double tol, GridBarrier bar,
                        unsigned int *rotcount, unsigned int *checkflag, double *sigma, int32_t *status) {
-    // Slot j receives the Q column of round j: rows tid and tid + kRingT of X in
-    // xbuf[j][tid] and of V in vbuf[j][tid].  X and V travel separately (two
-    // mbarriers per slot) so the next CTA can start its dot products while this
-    // one still rotates V.
+    // Slot j receives the Q column of round j: rows t and t + kRingT of X in
+    // xbuf[j][t] and of V in vbuf[j][t], and its scale pair in sbuf[j], each
+    // completed on its own mbarrier (mbx, mbv, mbs).  Columns are held scaled,
+    // x = d x~, so a rotation costs one FMA per entry:
+    //   x~_p <- x~_p - mu x~_q,  x~_q <- x~_q + nu x~_p,  mu = t d_q / d_p,
+    //   nu = t d_p / d_q,  d_p, d_q <- c d_p, c d_q  (c = cos, t = tan of the angle),
+    // the same first-order rounding as the plain rotation; the scales stay in
+    // [2^-4, 1] within an outer step (at most 8 rotations per column) and are
+    // folded back into the columns when they are stored.  par[j] = (rotated,
+    // mu, nu) of round j, announced to the V warps by mbr[j]; mbf announces
+    // the final scales of the outer step to the row warps.
     static_assert(kRingR == 2, "one double2 per thread and slot");
     __shared__ __align__(16) double2 xbuf[kRingC][kRingT];
     __shared__ __align__(16) double2 vbuf[kRingC][kRingT];
-    __shared__ __align__(8) unsigned long long mbx[kRingC], mbv[kRingC];
+    __shared__ __align__(16) double2 sbuf[kRingC];
+    __shared__ __align__(8) unsigned long long mbx[kRingC], mbv[kRingC], mbs[kRingC], mbr[kRingC], mbf;
     __shared__ double red[16];
-    __shared__ double par[3];
+    __shared__ double par[kRingC][3];
+    __shared__ double s_fin[2];
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x;
     {
@@ -808,11 +1013,13 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingT)
         asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(ncta));
         asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(ncl));
         if (ncta != (uint32_t)kRingC || (int64_t)ncl != G || (int64_t)gridDim.x != G * kRingC ||
-            blockDim.x != (unsigned)kRingT) {
+            blockDim.x != (unsigned)kRingCta) {
             if (tid == 0) set_status(status, NS_ERR_CUDA);
             return;
         }
     }
+    const bool scalar = tid < 32, isx = tid >= 32 && tid < 32 + kRingT;
+    const int t = isx ? tid - 32 : tid - 32 - kRingT;  // row thread index (unused in the scalar warp)
     const uint32_t ci = cluster_rank();
     const int64_t g = blockIdx.x / kRingC;
     const int64_t nblk = 2 * G, nouter = nblk - 1;
@@ -821,7 +1028,10 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingT)
         for (int j = 0; j < kRingC; ++j) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(shared_addr(&mbx[j])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(shared_addr(&mbv[j])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(shared_addr(&mbs[j])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(shared_addr(&mbr[j])) : "memory");
         }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(shared_addr(&mbf)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
     }
@@ -831,15 +1041,18 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingT)
     const uint32_t peer = (ci + kRingC - 1) % kRingC;
     const uint32_t xb_peer = peer_addr(shared_addr(&xbuf[0][0]), peer);
     const uint32_t vb_peer = peer_addr(shared_addr(&vbuf[0][0]), peer);
+    const uint32_t sb_peer = peer_addr(shared_addr(&sbuf[0]), peer);
     const uint32_t mx_peer = peer_addr(shared_addr(&mbx[0]), peer);
     const uint32_t mv_peer = peer_addr(shared_addr(&mbv[0]), peer);
-    const int64_t i0 = tid, i1 = tid + kRingT;
-    const bool r0 = i0 < n, r1 = i1 < n;
+    const uint32_t ms_peer = peer_addr(shared_addr(&mbs[0]), peer);
+    double *M = isx ? X : V;
+    const int64_t i0 = t, i1 = t + kRingT;
+    const bool r0 = !scalar && i0 < n, r1 = !scalar && i1 < n;
 
     bool converged = (n < 2), ok = true;
     unsigned int prev_rot = 0xFFFFFFFFu;
     int full_sweeps = 0, check_passes = 0;
-    uint32_t ostep = 0;  // outer steps so far: phase parity of the receive mbarriers
+    uint32_t ostep = 0;  // outer steps so far: phase parity of the slot mbarriers
     for (int sweep = 0; sweep < kMaxSweeps && !converged && ok; ++sweep) {
         if (prev_rot < (unsigned int)kCheckBelow) {
             ++check_passes;
@@ -859,111 +1072,147 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingT)
             ok = false;
             break;
         }
-        for (int64_t t = 0; t < nouter; ++t) {
-            const int64_t P = rr_player(g, t, nblk), Q = rr_player(nblk - 1 - g, t, nblk);
-            if (t == 0) {  // pairs inside blocks P and Q
+        for (int64_t ot = 0; ot < nouter; ++ot) {
+            const int64_t P = rr_player(g, ot, nblk), Q = rr_player(nblk - 1 - g, ot, nblk);
+            if (ot == 0) {  // pairs inside blocks P and Q
                 const int half = kRingC / 2;
                 const int64_t B = ((int)ci < half) ? P : Q;
                 const int k = (int)ci % half;
                 for (int j = 0; j < kRingC - 1 && ok; ++j) {
                     const int64_t a = B * kRingC + rr_player(k, j, kRingC);
                     const int64_t b = B * kRingC + rr_player(kRingC - 1 - k, j, kRingC);
-                    local += jacobi_pair_global(X, V, n, a, b, tol2, red, par);
+                    local += jacobi_pair_global(X, V, n, a, b, tol2, red, &par[0][0]);
                     ok = grid_sync(bar);
                 }
                 if (!ok) break;
             }
             if (tid == 0)
                 for (int j = 1; j < kRingC; ++j) {
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(shared_addr(&mbx[j])),
-                                 "r"((uint32_t)(kRingT * sizeof(double2)))
-                                 : "memory");
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(shared_addr(&mbv[j])),
-                                 "r"((uint32_t)(kRingT * sizeof(double2)))
-                                 : "memory");
+                    mbar_arm(&mbx[j], (uint32_t)(kRingT * sizeof(double2)));
+                    mbar_arm(&mbv[j], (uint32_t)(kRingT * sizeof(double2)));
+                    mbar_arm(&mbs[j], (uint32_t)sizeof(double2));
                 }
+            const uint32_t parity = ostep & 1u;
             const int64_t cp = P * kRingC + ci, cq0 = Q * kRingC + ci;
+            const int64_t cq = Q * kRingC + (ci + kRingC - 1) % kRingC;  // Q column held after the last round
             const bool lp = cp < n, lq = cq0 < n;
-            double xp0 = (r0 && lp) ? __ldcg(X + i0 + cp * n) : 0.0, xp1 = (r1 && lp) ? __ldcg(X + i1 + cp * n) : 0.0;
-            double vp0 = (r0 && lp) ? __ldcg(V + i0 + cp * n) : 0.0, vp1 = (r1 && lp) ? __ldcg(V + i1 + cp * n) : 0.0;
-            double xq0 = (r0 && lq) ? __ldcg(X + i0 + cq0 * n) : 0.0, xq1 = (r1 && lq) ? __ldcg(X + i1 + cq0 * n) : 0.0;
-            double vq0 = (r0 && lq) ? __ldcg(V + i0 + cq0 * n) : 0.0, vq1 = (r1 && lq) ? __ldcg(V + i1 + cq0 * n) : 0.0;
-            for (int j = 0; j < kRingC; ++j) {
-                if (j > 0) {
-                    if (!s_abort && !ring_wait(shared_addr(&mbx[j]), ostep & 1u)) {
-                        s_abort = 1;
-                        set_status(status, NS_ERR_TIMEOUT);
+            double p0 = (r0 && lp) ? __ldcg(M + i0 + cp * n) : 0.0, p1 = (r1 && lp) ? __ldcg(M + i1 + cp * n) : 0.0;
+            double q0 = (r0 && lq) ? __ldcg(M + i0 + cq0 * n) : 0.0, q1 = (r1 && lq) ? __ldcg(M + i1 + cq0 * n) : 0.0;
+            if (scalar) {
+                // the scales of the held columns (x = d x~, e = 1/d); the Q
+                // column's arrive after its entries, on their own mbarrier
+                double dP = 1.0, eP = 1.0, dQ = 1.0, eQ = 1.0;
+                for (int j = 0; j < kRingC; ++j) {
+                    xbar();  // the row warps' partial sums of round j are in red
+                    double al, be, ga;
+                    ring_combine(red, &al, &be, &ga);
+                    double tn = 0.0;
+                    bool rot = false;
+                    if (tid == 0) {
+                        if (j > 0) {
+                            if (!s_abort && !ring_wait(shared_addr(&mbs[j]), parity)) {
+                                s_abort = 1;
+                                set_status(status, NS_ERR_TIMEOUT);
+                            }
+                            const double2 sc = sbuf[j];
+                            dQ = sc.x;
+                            eQ = sc.y;
+                        }
+                        rot = ring_angle(al, be, ga, tol2, (float)(dP * dP), (float)(dQ * dQ), (float)(dP * dQ), dP,
+                                         dQ, &tn);
+                        par[j][0] = rot ? 1.0 : 0.0;
+                        par[j][1] = rot ? tn * dQ * eP : 0.0;  // mu: x~_p -= mu x~_q
+                        par[j][2] = rot ? tn * dP * eQ : 0.0;  // nu: x~_q += nu x~_p
+                        asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(
+                                         shared_addr(&mbr[j]))
+                                     : "memory");
                     }
-                    const double2 in = xbuf[j][tid];
-                    xq0 = in.x;
-                    xq1 = in.y;
-                }
-                const double a = fma(xp1, xp1, xp0 * xp0), b = fma(xq1, xq1, xq0 * xq0),
-                             gm = fma(xp1, xq1, xp0 * xq0);
-                ring_pair_rotation(a, b, gm, tol2, red, par);
-                const bool rot = par[0] != 0.0;
-                const double cs = par[1], sn = par[2];
-                if (rot) {
-                    if (tid == 0) ++local;
-                    const double a0 = xp0, a1 = xp1, b0 = xq0, b1 = xq1;
-                    xp0 = fma(cs, a0, -sn * b0);
-                    xp1 = fma(cs, a1, -sn * b1);
-                    xq0 = fma(sn, a0, cs * b0);
-                    xq1 = fma(sn, a1, cs * b1);
-                }
-                const int64_t cq = Q * kRingC + (ci + kRingC - 1) % kRingC;  // Q column held after the last round
-                if (j < kRingC - 1) {
-                    const uint32_t off = (uint32_t)(((j + 1) * kRingT + tid) * sizeof(double2));
-                    asm volatile(
-                        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(
-                            xb_peer + off),
-                        "d"(xq0), "d"(xq1), "r"(mx_peer + (uint32_t)((j + 1) * 8))
-                        : "memory");
-                } else {
-                    if (r0 && cq < n) X[i0 + cq * n] = xq0;
-                    if (r1 && cq < n) X[i1 + cq * n] = xq1;
-                }
-                // V: the incoming column's V part, then the same rotation
-                if (j > 0) {
-                    if (!s_abort && !ring_wait(shared_addr(&mbv[j]), ostep & 1u)) {
-                        s_abort = 1;
-                        set_status(status, NS_ERR_TIMEOUT);
+                    xbar();  // par[j] is visible to the X row warps
+                    if (tid == 0) {
+                        if (rot) {  // new scales: d <- c d, e <- e / c, c = 1/sqrt(1 + t^2)
+                            ++local;
+                            const double tt = fma(tn, tn, 1.0), h = -0.5 * tt;
+                            double c = f64_of(rsqrtf(f32_image(tt, 0)));
+                            c = c * fma(h, c * c, 1.5);
+                            c = c * fma(h, c * c, 1.5);
+                            const double ic = tt * c;
+                            dP *= c;
+                            dQ *= c;
+                            eP *= ic;
+                            eQ *= ic;
+                        }
+                        if (j < kRingC - 1)
+                            send_pair(sb_peer + (uint32_t)((j + 1) * sizeof(double2)), dQ, eQ,
+                                      ms_peer + (uint32_t)((j + 1) * 8));
                     }
-                    const double2 in = vbuf[j][tid];
-                    vq0 = in.x;
-                    vq1 = in.y;
                 }
-                if (rot) {
-                    const double a0 = vp0, a1 = vp1, b0 = vq0, b1 = vq1;
-                    vp0 = fma(cs, a0, -sn * b0);
-                    vp1 = fma(cs, a1, -sn * b1);
-                    vq0 = fma(sn, a0, cs * b0);
-                    vq1 = fma(sn, a1, cs * b1);
+                if (tid == 0) {  // final scales of the held columns
+                    s_fin[0] = dP;
+                    s_fin[1] = dQ;
+                    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(shared_addr(&mbf))
+                                 : "memory");
                 }
-                if (j < kRingC - 1) {
-                    const uint32_t off = (uint32_t)(((j + 1) * kRingT + tid) * sizeof(double2));
-                    asm volatile(
-                        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(
-                            vb_peer + off),
-                        "d"(vq0), "d"(vq1), "r"(mv_peer + (uint32_t)((j + 1) * 8))
-                        : "memory");
-                } else {
-                    if (r0 && cq < n) V[i0 + cq * n] = vq0;
-                    if (r1 && cq < n) V[i1 + cq * n] = vq1;
+            } else {
+                for (int j = 0; j < kRingC; ++j) {
+                    if (isx) {
+                        if (j > 0) {
+                            if (!s_abort && !ring_wait(shared_addr(&mbx[j]), parity)) {
+                                s_abort = 1;
+                                set_status(status, NS_ERR_TIMEOUT);
+                            }
+                            const double2 in = xbuf[j][t];
+                            q0 = in.x;
+                            q1 = in.y;
+                        }
+                        ring_partials(fma(p1, p1, p0 * p0), fma(q1, q1, q0 * q0), fma(p1, q1, p0 * q0), t, red);
+                        xbar();  // sums to the scalar warp
+                        xbar();  // par[j] from the scalar warp
+                    } else {
+                        if (!s_abort && !ring_wait_cta(shared_addr(&mbr[j]), parity)) {
+                            s_abort = 1;
+                            set_status(status, NS_ERR_TIMEOUT);
+                        }
+                        if (j > 0) {
+                            if (!s_abort && !ring_wait(shared_addr(&mbv[j]), parity)) {
+                                s_abort = 1;
+                                set_status(status, NS_ERR_TIMEOUT);
+                            }
+                            const double2 in = vbuf[j][t];
+                            q0 = in.x;
+                            q1 = in.y;
+                        }
+                    }
+                    if (par[j][0] != 0.0) {
+                        const double mu = par[j][1], nu = par[j][2];
+                        const double a0 = p0, a1 = p1;
+                        p0 = fma(-mu, q0, a0);
+                        p1 = fma(-mu, q1, a1);
+                        q0 = fma(nu, a0, q0);
+                        q1 = fma(nu, a1, q1);
+                    }
+                    if (j < kRingC - 1) {
+                        const uint32_t off = (uint32_t)(((j + 1) * kRingT + t) * sizeof(double2));
+                        if (isx) send_pair(xb_peer + off, q0, q1, mx_peer + (uint32_t)((j + 1) * 8));
+                        else send_pair(vb_peer + off, q0, q1, mv_peer + (uint32_t)((j + 1) * 8));
+                    }
                 }
-            }
-            if (lp) {
-                if (r0) {
-                    X[i0 + cp * n] = xp0;
-                    V[i0 + cp * n] = vp0;
+                if (!s_abort && !ring_wait_cta(shared_addr(&mbf), parity)) {
+                    s_abort = 1;
+                    set_status(status, NS_ERR_TIMEOUT);
                 }
-                if (r1) {
-                    X[i1 + cp * n] = xp1;
-                    V[i1 + cp * n] = vp1;
+                // unscale and store the held columns (P and the last Q)
+                const double fP = s_fin[0], fQ = s_fin[1];
+                if (lp) {
+                    if (r0) M[i0 + cp * n] = p0 * fP;
+                    if (r1) M[i1 + cp * n] = p1 * fP;
+                }
+                if (cq < n) {
+                    if (r0) M[i0 + cq * n] = q0 * fQ;
+                    if (r1) M[i1 + cq * n] = q1 * fQ;
                 }
             }
             ++ostep;
-            if (t == nouter - 1 && tid == 0 && local) atomicAdd(rotcount + sweep, local);
+            if (ot == nouter - 1 && tid == 0 && local) atomicAdd(rotcount + sweep, local);
             if (!grid_sync(bar)) {
                 ok = false;
                 break;
@@ -975,7 +1224,7 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingT)
     }
     if (ok) {
         if (!converged && blockIdx.x == 0 && tid == 0) set_status(status, NS_ERR_NOCONV);
-        jacobi_record_stats(rotcount, full_sweeps, check_passes);
+        jacobi_record_stats(rotcount, full_sweeps, check_passes, 1);
         if (grid_sync(bar)) jacobi_sigma(X, n, sigma);
     }
     cluster_sync_all();  // no CTA leaves while a peer may still address its shared memory
@@ -1119,7 +1368,7 @@ static cudaError_t launch_jacobi_ring(const DenseWork &w, int64_t n, GridBarrier
     if (G < 1) G = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(G * kRingC), 1, 1);
-    cfg.blockDim = dim3(kRingT, 1, 1);
+    cfg.blockDim = dim3(kRingCta, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -1162,13 +1411,21 @@ static cudaError_t launch_hqr_nb(double *W, int64_t rows, int64_t cols, int pivo
 
 // Pipelined QR (no pivoting) when the owned columns fit in shared memory;
 // returns false (nothing launched) otherwise.
+static size_t pipe_smem(int64_t rows, int64_t cols) {
+    int64_t G = cols < sm_count() ? cols : sm_count();
+    if (G < 1) G = 1;
+    const int64_t nown = (cols + G - 1) / G;
+    return sizeof(double) * (size_t)(nown * rows + 2 * rows + nown);
+}
+static bool pipe_fits(int64_t rows, int64_t cols) { return pipe_smem(rows, cols) <= 200 * 1024 && cols <= 4096; }
+
 static bool launch_hqr_pipe(double *W, int64_t rows, int64_t cols, double *u0, double *cf, int32_t *perm,
                             unsigned int *flags, double *Rout, int32_t *status, cudaStream_t st, cudaError_t *err) {
     int64_t G = cols < sm_count() ? cols : sm_count();
     if (G < 1) G = 1;
     const int64_t nown = (cols + G - 1) / G;
-    const size_t smem = sizeof(double) * (size_t)(nown * rows + 2 * rows + nown);
-    if (smem > 200 * 1024) return false;
+    const size_t smem = pipe_smem(rows, cols);
+    if (!pipe_fits(rows, cols)) return false;
     *err = cudaMemsetAsync(flags, 0, sizeof(unsigned int) * (size_t)cols, st);
     if (*err != cudaSuccess) return true;
     *err = cudaFuncSetAttribute(hqr_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1200,6 +1457,7 @@ __global__ void dense_stats_kernel(const unsigned int *bar, int64_t *out) {
         out[0] = bar[64 + 128];
         out[1] = bar[64 + 129];
         out[2] = bar[64 + 130];
+        out[3] = bar[64 + 131];
     }
 }
 
@@ -1210,15 +1468,33 @@ cudaError_t launch_dense_stats(const DenseWork &w, int64_t *out, cudaStream_t st
 
 cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k, const DenseWork &w, double *Vk,
                                double *sigk, double *save_V, double *save_sigma, int32_t *status, cudaStream_t st) {
-    cudaError_t e = cudaMemcpyAsync(w.W, SA, sizeof(double) * (size_t)(s * n), cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
     GridBarrier bar{w.bar, status};
     double *u0a = w.tau, *cfa = w.tau + n, *u0b = w.tau + 2 * n, *cfb = w.tau + 3 * n;
-    // 1. SA P = Q1 R; R (n x n) lands in X.  Pipelined without pivoting when it
-    // fits (P = I), else barrier-separated with column pivoting.
+    // 1. SA P = Q1 R; R (n x n) lands in X.  Pipelined after a static ordering
+    // of the columns by decreasing norm when it fits, else barrier-separated
+    // with column pivoting.
     unsigned int *flags = (unsigned int *)w.pivslot;  // 2 (n + 1) words >= n flags
-    if (!launch_hqr_pipe(w.W, s, n, u0a, cfa, w.perm, flags, w.X, status, st, &e))
+    if (pipe_fits(s, n)) {
+        double *key = w.X;  // n doubles; X is free until the QR writes R
+        colnorm_kernel<<<(unsigned)(n < 1024 ? n : 1024), 256, 0, st>>>(SA, s, n, key);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        int64_t np2 = 1;
+        while (np2 < n) np2 <<= 1;
+        const size_t sort_smem = (size_t)np2 * (sizeof(double) + sizeof(int32_t));
+        e = cudaFuncSetAttribute(sort_perm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem);
+        if (e != cudaSuccess) return e;
+        sort_perm_kernel<<<1, 1024, sort_smem, st>>>(key, n, np2, w.perm);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        dim3 grid((unsigned)((s + 255) / 256 < 8 ? (s + 255) / 256 : 8), (unsigned)(n < 1024 ? n : 1024));
+        permute_cols_kernel<<<grid, 256, 0, st>>>(SA, s, n, w.perm, w.W);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        launch_hqr_pipe(w.W, s, n, u0a, cfa, w.perm, flags, w.X, status, st, &e);
+    } else {
+        e = cudaMemcpyAsync(w.W, SA, sizeof(double) * (size_t)(s * n), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
         e = launch_hqr(w.W, s, n, 1, u0a, cfa, w.perm, w.pivslot, w.X, bar, st);
+    }
     if (e != cudaSuccess) return e;
     // 2. L = R^T; QR of L without pivoting: reflectors stay in L, R2 lands in V (scratch)
     {

@@ -1,0 +1,105 @@
+"""GPU dense stage (lines 3-4 of Algorithm 1 on a given sketch) against the
+oracle's Householder QR + one-sided Jacobi on the same SA.
+
+The GPU preconditions with two QRs and orders the Jacobi pairs differently
+(cluster ring), so results agree up to rounding, not bit for bit: singular
+values to relative 1e-12 of sigma_1 (absolute) and 1e-9 (relative, where
+sigma_i / sigma_1 > 1e-6), the trailing subspace by its sine when the gap
+allows (u sigma_1 / gap <= 1e-10), and V orthonormal to 1e-13.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2206_00975_gb300 import workloads
+from tests.helpers import sine
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U53 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_00975_gb300 import build
+    build.build()
+    from paper_2206_00975_gb300 import api as a
+    return a
+
+
+def sketch_like(seed, s, n, null_dim):
+    # SA = Q diag(sigma) V^T with sigma log-spaced 1..1e-5 and null_dim zeros
+    rng = np.random.default_rng(seed)
+    Q = workloads.orthonormal(rng, s, n)
+    V = workloads.orthonormal(rng, n, n)
+    sig = np.concatenate([np.logspace(0, -5, n - null_dim), np.zeros(null_dim)])
+    return np.asfortranarray(workloads.from_svd(Q, sig, V)), V, sig
+
+
+@pytest.mark.parametrize("s,n,k", [(1024, 256, 4), (400, 100, 3), (68, 17, 2), (512, 250, 5), (64, 16, 1)])
+def test_dense_stage_parity(api, s, n, k):
+    SA, Vtrue, sig = sketch_like(s + n, s, n, k)
+    d = api.desc(api.NS_SRHT, s=s, seed=0)
+    ws = api.workspace(d, s, n, k, "cuda")
+    Vk, sk, sv, status = api.ns_solve_sketched(d, api.colmajor(SA, device="cuda"), k, save=True, ws=ws)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    stats = api.jacobi_stats(d, s, n, ws, sketched=True)
+    assert stats[3] == 1, "the cluster-ring Jacobi should run for n <= 256"
+    Vk_or, sk_or, V_or, sig_or, _, st = O.solve_sketched(SA, k)
+    assert st == 0
+    _, V, sigma = api.unpack_save(sv, s, n)
+    V = V.cpu().numpy()
+    sigma = np.sort(sigma.cpu().numpy())[::-1]
+    s1 = sig_or.max()
+    assert np.linalg.norm(V.T @ V - np.eye(n)) < 1e-13 * n
+    ref = np.sort(sig_or)[::-1]
+    assert np.max(np.abs(sigma - ref)) <= 1e-12 * s1
+    big = ref > 1e-6 * s1
+    assert np.max(np.abs(sigma[big] - ref[big]) / ref[big]) <= 1e-9
+    # trailing subspace (exact zeros: gap sigma_{n-k} = 1e-5 sigma_1)
+    gap = ref[n - k - 1] - ref[n - k]
+    assert U53 * s1 / gap <= 1e-10
+    assert sine(Vk_or, Vk.cpu().numpy()) < 1e-8
+    assert sine(Vtrue[:, -k:], Vk.cpu().numpy()) < 1e-8
+
+
+def test_dense_stage_repeatable(api):
+    # the same sketch twice in a row through the same workspace: identical bits
+    SA, _, _ = sketch_like(5, 1024, 256, 4)
+    d = api.desc(api.NS_SRHT, s=1024, seed=0)
+    ws = api.workspace(d, 1024, 256, 4, "cuda")
+    SAd = api.colmajor(SA, device="cuda")
+    a = api.ns_solve_sketched(d, SAd, 4, ws=ws)[0].clone()
+    b = api.ns_solve_sketched(d, SAd, 4, ws=ws)[0]
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_dense_stage_wide_range(api):
+    # a full-rank sketch (sigma 1 .. 1e-5) with column scales spanning 1e-60 ..
+    # 1e60: one-sided Jacobi determines every singular value to high relative
+    # accuracy here (the column-equilibrated matrix has condition ~1e5), so the
+    # static norm ordering before the unpivoted QR must keep it, and the FP32
+    # images of the scaled sums and the tiny-angle path must keep converging.
+    # (Far wider ranges make the products alpha beta of the threshold test
+    # underflow, and plain one-sided Jacobi, the oracle's included, stalls.)
+    rng = np.random.default_rng(11)
+    s, n, k = 256, 48, 2
+    Q = workloads.orthonormal(rng, s, n)
+    V = workloads.orthonormal(rng, n, n)
+    SA = workloads.from_svd(Q, np.logspace(0, -5, n), V)
+    D = np.logspace(-60, 60, n)
+    SAs = np.asfortranarray(SA * D[None, :])
+    d = api.desc(api.NS_SRHT, s=s, seed=0)
+    Vk, sk, sv, status = api.ns_solve_sketched(d, api.colmajor(SAs, device="cuda"), k, save=True)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    Vk_or, sk_or, _, sig_or, _, st = O.solve_sketched(SAs, k)
+    assert st == 0
+    _, _, sigma = api.unpack_save(sv, s, n)
+    np.testing.assert_allclose(np.sort(sigma.cpu().numpy()), np.sort(sig_or), rtol=1e-8, atol=0)
+    np.testing.assert_allclose(sk.cpu().numpy(), sk_or, rtol=1e-8, atol=0)
