@@ -164,17 +164,17 @@ __global__ void __launch_bounds__(64) batched_sketch_kernel(const ns_problem *__
         ProblemView v = problem_view(ws + sl.off, pr.m, pr.n, pr.s);
         const int64_t s = pr.s;
         for (int64_t i = t; i < s; i += 64) {
-            rows_s[i] = v.rows[i];
+            rows_s[i] = srht_pack_row(v.rows[i]);
             acc[i] = 0;
         }
-        const unsigned long long myneed = srht_need_mask(rows_s, s, need);
+        __syncthreads();
         const double *Acol = (const double *)pr.A + c * pr.lda;
         const int vec_ok = ((((uintptr_t)pr.A) & 15) == 0 && (pr.lda & 1) == 0) ? 1 : 0;
         const int P_bits = 63 - kBlockLog - clog2(sl.nblk) - 1;
         int Erun = 0, nonfinite = 0;
         for (int64_t b = 0; b < sl.nblk; ++b)
-            srht_f64_block(Acol, pr.m, s, b, P_bits, v.sign_words, rows_s, myneed, Zs, acc, sgn, red, vec_ok, Erun,
-                           nonfinite);
+            srht_f64_block(Acol, pr.m, s, b, P_bits, v.sign_words, rows_s, Zs, acc, sgn, red, vec_ok, Erun,
+                           nonfinite, b + 1 < sl.nblk);
         const double scale = ldexp(1.0, Erun - 1022 - P_bits) / sqrt((double)s);
         double *out = v.SA + c * s;
         for (int64_t i = t; i < s; i += 64) out[i] = (double)acc[i] * scale;

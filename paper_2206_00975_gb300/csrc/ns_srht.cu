@@ -90,8 +90,7 @@ __global__ void __launch_bounds__(64) srht_f64_chunk_kernel(const double *__rest
     extern __shared__ __align__(16) unsigned char smem_raw[];
     long long *Zs = (long long *)smem_raw;                       // 4096
     long long *acc = Zs + kBlock;                                // s
-    unsigned long long *need = (unsigned long long *)(acc + s);  // 64
-    uint32_t *sgn = (uint32_t *)(need + 64);                     // 128
+    uint32_t *sgn = (uint32_t *)(acc + s);                       // 128
     int *red = (int *)(sgn + 128);                               // 4
     int32_t *rows_s = (int32_t *)(red + 4);                      // s
 
@@ -101,25 +100,16 @@ __global__ void __launch_bounds__(64) srht_f64_chunk_kernel(const double *__rest
     const double *Acol = A + c * lda;
 
     for (int64_t i = t; i < s; i += 64) {
-        rows_s[i] = rows[i];
+        rows_s[i] = srht_pack_row(rows[i]);
         acc[i] = 0;
     }
-    need[t] = 0ull;
     __syncthreads();
-    // which layout-2 registers hold a sampled row (the same for every block)
-    for (int64_t i = t; i < s; i += 64) {
-        const int lo = rows_s[i] & (kBlock - 1);
-        const int owner = (lo & 1) | ((lo >> 7) << 1);
-        atomicOr(&need[owner], 1ull << ((lo >> 1) & 63));
-    }
-    __syncthreads();
-    const unsigned long long myneed = need[t];
 
     int Erun = 0;  // running biased exponent of the chunk (0: none yet)
     int nonfinite = 0;
     for (int bl = 0; bl < chunk; ++bl)
-        srht_f64_block(Acol, m, s, ch * chunk + bl, P, sign_words, rows_s, myneed, Zs, acc, sgn, red, vec_ok, Erun,
-                       nonfinite);
+        srht_f64_block(Acol, m, s, ch * chunk + bl, P, sign_words, rows_s, Zs, acc, sgn, red, vec_ok, Erun,
+                       nonfinite, bl + 1 < chunk);
     // chunk partial in FP64: value = acc * 2^(E - 1022 - P)
     const double scale = ldexp(1.0, Erun - 1022 - P);
     double *out = partial + (ch * n + c) * s;

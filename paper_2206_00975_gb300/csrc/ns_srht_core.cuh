@@ -34,43 +34,46 @@ __device__ __forceinline__ int l2_elem(int t, int k) { return (t & 1) | (k << 1)
 // One 4096-row block b of a column (64 threads): load, quantise at the running
 // exponent Erun (rescaling the accumulator when it grows), H_4096 in two
 // register phases around a swizzled shared-memory transpose, and the signed
-// gather of the sampled rows into acc[0..s).  Ends with __syncthreads().
+// gather of the sampled rows (rows_s packed by srht_pack_row) into acc[0..s).
+// Ends with __syncthreads().
 __device__ __forceinline__ void srht_f64_block(const double *__restrict__ Acol, int64_t m, int64_t s, int64_t b,
                                                int P, const uint32_t *__restrict__ sign_words,
-                                               const int32_t *rows_s, unsigned long long myneed, long long *Zs,
+                                               const int32_t *rows_s, long long *Zs,
                                                long long *acc, uint32_t *sgn, int *red, int vec_ok, int &Erun,
-                                               int &nonfinite) {
+                                               int &nonfinite, bool prefetch_next) {
     const int t = threadIdx.x;
     const int64_t base = b * kBlock;
     sgn[t] = sign_words[(base >> 5) + t];
     sgn[t + 64] = sign_words[(base >> 5) + 64 + t];
+    if (t == 0 && prefetch_next && vec_ok && base + 2 * kBlock <= m)  // the next block, into L2 (one bulk copy)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(Acol + base + kBlock),
+                     "r"((uint32_t)(kBlock * 8))
+                     : "memory");
     long long z[64];
+    if (vec_ok && base + kBlock <= m) {  // whole block, 16-byte aligned: no bounds tests
 #pragma unroll
-    for (int kk = 0; kk < 32; ++kk) {
-        const int64_t i0 = base + 2 * t + 128 * kk;
-        long long a0 = 0, a1 = 0;
-        if (vec_ok && i0 + 1 < m) {
-            const double2 v = __ldcs((const double2 *)(Acol + i0));
-            a0 = __double_as_longlong(v.x);
-            a1 = __double_as_longlong(v.y);
-        } else {
-            if (i0 < m) a0 = __double_as_longlong(__ldcs(Acol + i0));
-            if (i0 + 1 < m) a1 = __double_as_longlong(__ldcs(Acol + i0 + 1));
+        for (int kk = 0; kk < 32; ++kk) {
+            const double2 v = __ldcs((const double2 *)(Acol + base + 2 * t + 128 * kk));
+            z[2 * kk] = __double_as_longlong(v.x);
+            z[2 * kk + 1] = __double_as_longlong(v.y);
         }
-        z[2 * kk] = a0;
-        z[2 * kk + 1] = a1;
-    }
-    int emax = 1;
+    } else {
 #pragma unroll
-    for (int k = 0; k < 64; ++k) {
-        const int e = (int)((unsigned long long)z[k] >> 52) & 0x7FF;
-        if (e == 0x7FF) nonfinite = 1;
-        else emax = max(emax, e);
+        for (int kk = 0; kk < 32; ++kk) {
+            const int64_t i0 = base + 2 * t + 128 * kk;
+            z[2 * kk] = (i0 < m) ? __double_as_longlong(__ldcs(Acol + i0)) : 0;
+            z[2 * kk + 1] = (i0 + 1 < m) ? __double_as_longlong(__ldcs(Acol + i0 + 1)) : 0;
+        }
     }
-    emax = warp_max(emax);
-    if ((t & 31) == 0) red[t >> 5] = emax;
+    // largest biased exponent (an Inf or NaN shows up as 0x7FF and is flagged)
+    unsigned int hmax = 0x00100000u;  // biased exponent 1
+#pragma unroll
+    for (int k = 0; k < 64; ++k) hmax = max(hmax, (unsigned int)((unsigned long long)z[k] >> 32) & 0x7FF00000u);
+    hmax = warp_max(hmax);
+    if ((t & 31) == 0) red[t >> 5] = (int)(hmax >> 20);
     __syncthreads();  // also publishes sgn[]
-    emax = max(red[0], red[1]);
+    const int emax = max(red[0], red[1]);
+    if (emax == 0x7FF) nonfinite = 1;
     if (emax > Erun) {
         if (Erun > 0) {
             const int d = emax - Erun;
@@ -78,20 +81,26 @@ __device__ __forceinline__ void srht_f64_block(const double *__restrict__ Acol, 
         }
         Erun = emax;
     }
+    // quantise: magnitude rounded to nearest at 2^(Erun - 1022 - P), sign of the
+    // entry times d_i, two's complement (subnormals exact: exponent 1, no
+    // hidden bit; shifts of 64 or more give 0)
+    const int sh1b = Erun + 52 - P;  // shift - 1 = sh1b - max(e, 1)
 #pragma unroll
     for (int kk = 0; kk < 32; ++kk) {
         const uint32_t sw = sgn[4 * kk + (t >> 4)] >> (2 * (t & 15));
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const unsigned long long raw = (unsigned long long)z[2 * kk + h];
-            const int e = (int)(raw >> 52) & 0x7FF;
-            const unsigned long long frac = raw & 0x000FFFFFFFFFFFFFull;
-            const unsigned long long mant = e ? (frac | 0x0010000000000000ull) : frac;
-            const int sh = Erun - (e ? e : 1) + 53 - P;
-            unsigned long long q = (sh >= 64 || e == 0x7FF) ? 0ull : ((mant + (1ull << (sh - 1))) >> sh);
-            const unsigned long long neg = ((raw >> 63) ^ ((sw >> h) & 1u)) & 1u;
-            const unsigned long long msk = 0ull - neg;
-            z[2 * kk + h] = (long long)((q ^ msk) + neg);
+            const uint32_t hi = (uint32_t)(raw >> 32);
+            const int e = (int)((hi >> 20) & 0x7FF), e1 = max(e, 1);
+            const uint32_t sh1 = (uint32_t)(sh1b - e1);
+            const uint32_t mhi = (hi & 0x000FFFFFu) | ((uint32_t)(1 - (e1 - e)) << 20);
+            const unsigned long long mant = ((unsigned long long)mhi << 32) | (uint32_t)raw;
+            unsigned long long q1;
+            asm("shr.b64 %0, %1, %2;" : "=l"(q1) : "l"(mant), "r"(sh1));  // clamps shifts >= 64 to 0
+            const unsigned long long q = (q1 + 1ull) >> 1;
+            const long long msk = (long long)(int)((hi ^ (sw << (31 - h))) & 0x80000000u) >> 31;
+            z[2 * kk + h] = ((long long)q ^ msk) - msk;
         }
     }
     fwht64(z);
@@ -109,31 +118,20 @@ __device__ __forceinline__ void srht_f64_block(const double *__restrict__ Acol, 
     __syncthreads();
     fwht64(z);
 #pragma unroll
-    for (int k = 0; k < 64; ++k)
-        if ((myneed >> k) & 1ull) Zs[swz(l2_elem(t, k))] = z[k];
+    for (int k = 0; k < 64; ++k) Zs[swz(l2_elem(t, k))] = z[k];  // all of them: cheaper than testing
     __syncthreads();
     for (int64_t i = t; i < s; i += 64) {
-        const int r = rows_s[i];
-        const long long v = Zs[swz(r & (kBlock - 1))];
-        const int neg = __popcll((unsigned long long)(r >> kBlockLog) & (unsigned long long)b) & 1;
-        acc[i] += neg ? -v : v;
+        const uint32_t pr = (uint32_t)rows_s[i];  // srht_pack_row: (hi(r) << 12) | swz(lo(r))
+        const long long v = Zs[pr & (kBlock - 1)];
+        const long long msk = -(long long)(__popc(pr >> kBlockLog & (uint32_t)b) & 1);
+        acc[i] += (v ^ msk) - msk;
     }
     __syncthreads();
 }
 
-// layout-2 registers that hold a sampled row (the same for every block): one
-// 64-bit mask per thread, built in need[64] from rows_s[0..s)
-__device__ __forceinline__ unsigned long long srht_need_mask(const int32_t *rows_s, int64_t s,
-                                                             unsigned long long *need) {
-    const int t = threadIdx.x;
-    need[t] = 0ull;
-    __syncthreads();
-    for (int64_t i = t; i < s; i += 64) {
-        const int lo = rows_s[i] & (kBlock - 1);
-        atomicOr(&need[(lo & 1) | ((lo >> 7) << 1)], 1ull << ((lo >> 1) & 63));
-    }
-    __syncthreads();
-    return need[t];
+// sample row r as the gather uses it: (hi(r) << 12) | swz(lo(r)) (r < 2^31)
+__device__ __forceinline__ int32_t srht_pack_row(int32_t r) {
+    return (int32_t)(((uint32_t)r >> kBlockLog << kBlockLog) | (uint32_t)swz(r & (kBlock - 1)));
 }
 
 }  // namespace ns
