@@ -63,10 +63,9 @@ cudaError_t launch_srht_f32(const float *A, int64_t m, int64_t n, int64_t lda, i
 struct SparseGeom {
     int64_t ntile;        // 128-row tiles of A
     int64_t nent;         // entries per tile (128 * zeta)
-    int64_t nsort;        // sort length (power of two >= nent)
-    int64_t ngrp16;       // 16-row groups of the output
-    int64_t nrowgrp;      // 256-row groups (CTAs along the output rows)
-    int64_t ncolgrp;      // 32-column groups
+    int64_t ntgrp;        // target groups of 1024 output rows (one accumulator each)
+    int64_t nbucket;      // entry buckets per tile: ntgrp * 32 owners
+    int64_t ncolgrp;      // 16-column groups
     int64_t chunk_tiles;  // tiles per accumulator chunk
     int64_t nchunk;
     int fx_bits;          // fixed-point magnitude bits P

@@ -5,15 +5,18 @@
 // draws t = floor(w_i (b+1) / 2^64) with b = s - zeta + i and keeps t unless
 // already taken, else b; sign = low bit of w_i).
 //
-// Deterministic bucketed reduction without floating-point atomics:
-//   1. for every 128-row tile of A the (row, sign) pairs of its 128 columns of S
-//      are generated and sorted by output row (one CTA per tile, bitonic sort of
-//      keys r*256 + j_local*2 + sign); offsets per 16-row group are kept;
-//   2. a CTA of 16 warps owns 256 output rows x 32 columns of A for a chunk of
-//      tiles: it maps each 128 x 32 tile of A exactly onto 64-bit fixed point in
-//      shared memory (per-column running exponent, as for the SRHT), and each
-//      warp adds the tile's entries of its 16 rows into integer accumulators in
-//      registers (lane = column), walking the sorted entries;
+// Deterministic reduction without floating-point atomics:
+//   1. for every 128-row tile of A the tile's (target row, row, sign) entries
+//      are generated and bucketed by owner, bucket = (r / 1024) * 32 + r % 32
+//      (counting sort; the order inside a bucket is irrelevant, see below);
+//   2. a CTA of 16 warps owns 16 columns of A, one group of 1024 target rows
+//      and a chunk of tiles.  It keeps the 1024 x 16 accumulator in shared
+//      memory as 64-bit fixed point (per-column running exponent, as for the
+//      SRHT), quantises each 128 x 16 tile of A into shared memory (each entry
+//      with both signs, so the key indexes the signed value), and half
+//      warp h of warp w (lane = column) applies the entries of owner 2w + h:
+//      the two halves of a warp never touch the same target row, and one
+//      half walks its entries in order, so no update races;
 //   3. one FP64 partial per chunk is summed over chunks in a fixed order.
 // Integer addition is exact and associative, so the result does not depend on
 // the order of the updates.
@@ -23,30 +26,32 @@
 
 namespace ns {
 
-constexpr int kSpTile = 128;         // rows of A per tile
-constexpr int kSpRowsPerWarp = 16;
-constexpr int kSpWarps = 16;
-constexpr int kSpRowGroup = kSpRowsPerWarp * kSpWarps;  // 256 output rows per CTA
-constexpr int kSpCols = 32;          // columns of A per CTA (lane = column)
+constexpr int kSpTile = 128;      // rows of A per tile
+constexpr int kSpCols = 16;       // columns of A per CTA (lane % 16 = column)
+constexpr int kSpWarps = 16;      // owners 2w, 2w + 1 per warp
+constexpr int kSpOwners = 2 * kSpWarps;
+constexpr int kSpGroup = 1024;    // target rows per accumulator
+constexpr int kSpThreads = kSpWarps * 32;
+constexpr int kSpTileStride = 2 * kSpTile + 1;  // per column: +v, -v of each row, padded (conflict-free reads)
+constexpr int kSpMaxEntPerThread = kSpTile * 64 / kSpThreads;  // zeta <= 64
 
 SparseGeom sparse_geom(int64_t m, int64_t n, int64_t s, int zeta) {
     SparseGeom g;
     g.ntile = (m + kSpTile - 1) / kSpTile;
     g.nent = (int64_t)kSpTile * zeta;
-    g.nsort = 1;
-    while (g.nsort < g.nent) g.nsort <<= 1;
-    g.ngrp16 = (s + kSpRowsPerWarp - 1) / kSpRowsPerWarp;
-    g.nrowgrp = (s + kSpRowGroup - 1) / kSpRowGroup;
+    g.ntgrp = (s + kSpGroup - 1) / kSpGroup;
+    g.nbucket = g.ntgrp * kSpOwners;
     g.ncolgrp = (n + kSpCols - 1) / kSpCols;
-    // about 1024 CTAs; chunks of whole tiles
-    int64_t per = g.nrowgrp * g.ncolgrp;
-    int64_t want_chunks = 1024 / (per > 0 ? per : 1);
-    if (want_chunks < 1) want_chunks = 1;
-    g.chunk_tiles = (g.ntile + want_chunks - 1) / want_chunks;
-    if (g.chunk_tiles < 8) g.chunk_tiles = g.ntile < 8 ? g.ntile : 8;
+    // about two CTAs per SM over (column group, target group, chunk)
+    const int64_t per = g.ncolgrp * g.ntgrp;
+    int64_t want = (2 * 152 + per - 1) / per;
+    if (want < 1) want = 1;
+    if (want > g.ntile) want = g.ntile;
+    g.chunk_tiles = (g.ntile + want - 1) / want;
     g.nchunk = (g.ntile + g.chunk_tiles - 1) / g.chunk_tiles;
-    // |acc| <= rows per chunk * 2^P < 2^63
+    // |acc| <= rows per chunk * 2^P < 2^63; at most the 52 bits of the mantissa
     g.fx_bits = 62 - ceil_log2(g.chunk_tiles * kSpTile);
+    if (g.fx_bits > 52) g.fx_bits = 52;
     return g;
 }
 
@@ -54,7 +59,7 @@ SparseWork sparse_carve(Carver &c, int64_t m, int64_t n, int64_t s, int zeta) {
     SparseGeom g = sparse_geom(m, n, s, zeta);
     SparseWork w;
     w.entries = c.take<uint32_t>((size_t)(g.ntile * g.nent));
-    w.offsets = c.take<int32_t>((size_t)(g.ntile * (g.ngrp16 + 1)));
+    w.offsets = c.take<int32_t>((size_t)(g.ntile * (g.nbucket + 1)));
     w.partial = c.take<double>((size_t)(g.nchunk * n * s));
     return w;
 }
@@ -95,15 +100,17 @@ __global__ void sparse_meta_kernel(uint64_t seed, int64_t s, int zeta, int64_t m
     }
 }
 
-// one CTA per tile: generate, sort by (row, j_local), store entries and the
-// offsets of every 16-row group
-__global__ void __launch_bounds__(256) sparse_tile_sort_kernel(uint64_t seed, int64_t s, int zeta, int64_t m,
-                                                               int64_t nent, int64_t nsort, int64_t ngrp16,
-                                                               uint32_t *entries, int32_t *offsets) {
-    extern __shared__ uint32_t keys[];  // nsort
+// one CTA per tile: generate the tile's entries, key (r << 8) | (j_local << 1)
+// | sign, and bucket them by owner (counting sort); offsets[tile][b] is the
+// first entry of bucket b, offsets[tile][nbucket] = nent
+__global__ void __launch_bounds__(256) sparse_bucket_kernel(uint64_t seed, int64_t s, int zeta, int64_t m,
+                                                            int64_t nent, int64_t nbucket, uint32_t *entries,
+                                                            int32_t *offsets) {
+    extern __shared__ int32_t cnt[];  // nbucket + 1
+    __shared__ uint32_t keys[kSpTile * 64];
     const int64_t tile = blockIdx.x;
     const int tid = threadIdx.x;
-    for (int64_t i = tid; i < nsort; i += blockDim.x) keys[i] = 0xFFFFFFFFu;
+    for (int64_t b = tid; b <= nbucket; b += blockDim.x) cnt[b] = 0;
     __syncthreads();
     for (int jl = tid; jl < kSpTile; jl += blockDim.x) {
         const int64_t j = tile * kSpTile + jl;
@@ -111,141 +118,146 @@ __global__ void __launch_bounds__(256) sparse_tile_sort_kernel(uint64_t seed, in
         int32_t r[64];
         int8_t g[64];
         sparse_column(seed, s, zeta, j, r, g);
-        for (int i = 0; i < zeta; ++i)
-            keys[jl * zeta + i] = ((uint32_t)r[i] << 8) | ((uint32_t)jl << 1) | (g[i] < 0 ? 1u : 0u);
+        for (int i = 0; i < zeta; ++i) {
+            const uint32_t key = ((uint32_t)r[i] << 8) | ((uint32_t)jl << 1) | (g[i] < 0 ? 1u : 0u);
+            keys[jl * zeta + i] = key;
+            atomicAdd(&cnt[(r[i] >> 10) * kSpOwners + (r[i] & (kSpOwners - 1))], 1);
+        }
     }
     __syncthreads();
-    // bitonic sort of nsort keys (padding keys sort last)
-    for (int64_t k = 2; k <= nsort; k <<= 1) {
-        for (int64_t jj = k >> 1; jj > 0; jj >>= 1) {
-            for (int64_t i = tid; i < nsort; i += blockDim.x) {
-                const int64_t l = i ^ jj;
-                if (l > i) {
-                    const uint32_t a = keys[i], b = keys[l];
-                    const bool up = (i & k) == 0;
-                    if ((a > b) == up) {
-                        keys[i] = b;
-                        keys[l] = a;
-                    }
-                }
-            }
-            __syncthreads();
+    if (tid == 0) {  // exclusive prefix sum (nbucket <= 512)
+        int32_t run = 0;
+        for (int64_t b = 0; b < nbucket; ++b) {
+            const int32_t c = cnt[b];
+            cnt[b] = run;
+            run += c;
         }
+        cnt[nbucket] = run;
     }
-    for (int64_t i = tid; i < nent; i += blockDim.x) entries[tile * nent + i] = keys[i];
-    // offsets: first entry whose row >= 16 g, for g = 0..ngrp16 (binary search)
-    for (int64_t gI = tid; gI <= ngrp16; gI += blockDim.x) {
-        const uint32_t lim = (uint32_t)(gI * kSpRowsPerWarp) << 8;
-        int64_t lo = 0, hi = nent;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (keys[mid] < lim) lo = mid + 1;
-            else hi = mid;
-        }
-        offsets[tile * (ngrp16 + 1) + gI] = (int32_t)lo;
+    __syncthreads();
+    int32_t *off = offsets + tile * (nbucket + 1);
+    for (int64_t b = tid; b <= nbucket; b += blockDim.x) off[b] = cnt[b];
+    __syncthreads();
+    uint32_t *ent = entries + tile * nent;
+    const int64_t live = ((tile + 1) * kSpTile <= m ? kSpTile : m - tile * kSpTile) * zeta;
+    for (int64_t e = tid; e < live; e += blockDim.x) {
+        const uint32_t key = keys[e];
+        const int r = (int)(key >> 8);
+        const int pos = atomicAdd(&cnt[(r >> 10) * kSpOwners + (r & (kSpOwners - 1))], 1);
+        ent[pos] = key;
     }
 }
 
-__global__ void __launch_bounds__(kSpWarps * 32, 2) sparse_f64_kernel(
-    const double *__restrict__ A, int64_t m, int64_t n, int64_t lda, int64_t s, int64_t nent, int64_t ngrp16,
+// grid (column group, target group, chunk); 16 warps
+__global__ void __launch_bounds__(kSpThreads, 1) sparse_acc_kernel(
+    const double *__restrict__ A, int64_t m, int64_t n, int64_t lda, int64_t s, int64_t nent, int64_t nbucket,
     int64_t chunk_tiles, int64_t ntile, int P, const uint32_t *__restrict__ entries,
     const int32_t *__restrict__ offsets, double *__restrict__ partial, int32_t *status) {
-    __shared__ long long tq[kSpTile][kSpCols + 1];  // quantised tile, [row][column]
-    __shared__ int Ecol[kSpCols], Enew[kSpCols];
-    __shared__ int nonfinite;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int64_t rg = blockIdx.x, cg = blockIdx.y, ch = blockIdx.z;
-    const int64_t col = cg * kSpCols + lane;
-    const int64_t row0 = rg * kSpRowGroup + (int64_t)wid * kSpRowsPerWarp;  // this warp's first output row
-    const int64_t g16 = row0 / kSpRowsPerWarp;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    long long *acc = (long long *)smem_raw;                        // kSpGroup x kSpCols
+    long long *tq = acc + kSpGroup * kSpCols;                      // kSpCols x kSpTileStride (signed pairs)
+    uint32_t *ents = (uint32_t *)(tq + kSpCols * kSpTileStride);   // this tile's entries of the target group
+    __shared__ int32_t boff[kSpOwners + 1];
+    __shared__ int Ecol[kSpCols];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int64_t cg = blockIdx.x, tg = blockIdx.y, ch = blockIdx.z;
+    const int c = lane & (kSpCols - 1), h = lane >> 4;  // column of this lane, owner half
+    const int64_t col = cg * kSpCols + c;
+    const int64_t lcol = cg * kSpCols + w;               // column this warp loads
+    for (int i = tid; i < kSpGroup * kSpCols; i += kSpThreads) acc[i] = 0;
     if (tid < kSpCols) Ecol[tid] = 0;
-    if (tid == 0) nonfinite = 0;
-    long long acc[kSpRowsPerWarp];
-#pragma unroll
-    for (int r = 0; r < kSpRowsPerWarp; ++r) acc[r] = 0;
-    int Emine = 0;  // running exponent of this lane's column (mirrors Ecol[lane])
+    int nonfinite = 0;
     const int64_t t0 = ch * chunk_tiles, t1 = (t0 + chunk_tiles < ntile) ? t0 + chunk_tiles : ntile;
+    __syncthreads();
     for (int64_t t = t0; t < t1; ++t) {
-        __syncthreads();
-        // ---- load the tile (raw bits), 128 rows x 32 columns; column c handled by
-        // 16 threads, 8 rows each (coalesced along rows)
-        const int c = tid >> 4, part = tid & 15;
-        const int64_t gc = cg * kSpCols + c;
-        long long raw[8];
+        // ---- tile: warp w loads column lcol, rows lane + 32 q (coalesced)
+        long long raw[4];
         int emax = 1;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int jl = part + 16 * q;
-            const int64_t j = t * kSpTile + jl;
+        for (int q = 0; q < 4; ++q) {
+            const int64_t j = t * kSpTile + lane + 32 * q;
             long long v = 0;
-            if (gc < n && j < m) v = __double_as_longlong(__ldcs(A + j + gc * lda));
+            if (lcol < n && j < m) v = __double_as_longlong(__ldcs(A + j + lcol * lda));
             raw[q] = v;
             const int e = (int)((unsigned long long)v >> 52) & 0x7FF;
-            if (e == 0x7FF) nonfinite = 1;
-            else emax = max(emax, e);
+            emax = (e == 0x7FF) ? emax : max(emax, e);
+            nonfinite |= (e == 0x7FF);
         }
-        // column max exponent over its 16 threads (a half warp)
+        emax = warp_max(emax);
+        // ---- this tile's entries of the target group, into registers
+        const int32_t *off = offsets + t * (nbucket + 1) + tg * kSpOwners;
+        const int32_t e0 = __ldg(off), e1 = __ldg(off + kSpOwners);
+        uint32_t pre[kSpMaxEntPerThread];
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-        if (part == 0) Enew[c] = max(Ecol[c], emax);
-        __syncthreads();
-        const int E = Enew[c];
+        for (int q = 0; q < kSpMaxEntPerThread; ++q) {
+            const int32_t e = e0 + tid + q * kSpThreads;
+            pre[q] = (e < e1) ? __ldg(entries + t * nent + e) : 0u;
+        }
+        const int32_t myoff = (tid <= kSpOwners) ? __ldg(off + tid) : 0;
+        __syncthreads();  // the previous tile is fully applied
+        if (tid <= kSpOwners) boff[tid] = myoff;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int jl = part + 16 * q;
+        for (int q = 0; q < kSpMaxEntPerThread; ++q) {
+            const int32_t e = e0 + tid + q * kSpThreads;
+            if (e < e1) ents[e - e0] = pre[q];
+        }
+        // ---- running exponent of the warp's column; rescale its accumulator
+        const int Eold = Ecol[w];
+        const int E = max(Eold, emax);
+        if (E > Eold && Eold > 0) {
+            const int d = E - Eold;
+            for (int r = lane; r < kSpGroup; r += 32) {
+                long long &a = acc[r * kSpCols + w];
+                a = (d >= 63) ? (a >> 63) : (a >> d);
+            }
+        }
+        // quantise at 2^(E - 1022 - P), magnitude rounded to nearest
+        const int sh1b = E + 52 - P;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
             const unsigned long long b = (unsigned long long)raw[q];
-            const int e = (int)(b >> 52) & 0x7FF;
-            const unsigned long long frac = b & 0x000FFFFFFFFFFFFFull;
-            const unsigned long long mant = e ? (frac | 0x0010000000000000ull) : frac;
-            const int sh = E - (e ? e : 1) + 53 - P;
-            unsigned long long q64 = (sh >= 64 || e == 0x7FF) ? 0ull
-                                     : (sh <= 0 ? (mant << (-sh)) : ((mant + (1ull << (sh - 1))) >> sh));
-            tq[jl][c] = (b >> 63) ? -(long long)q64 : (long long)q64;
+            const uint32_t hi = (uint32_t)(b >> 32);
+            const int e = (int)((hi >> 20) & 0x7FF), e1b = max(e, 1);
+            const uint32_t sh1 = (uint32_t)(sh1b - e1b);
+            const unsigned long long mant = (b & 0x000FFFFFFFFFFFFFull) | ((unsigned long long)(1 - (e1b - e)) << 52);
+            unsigned long long q1;
+            asm("shr.b64 %0, %1, %2;" : "=l"(q1) : "l"(mant), "r"(sh1));
+            unsigned long long qv = (q1 + 1ull) >> 1;
+            if (e == 0x7FF) qv = 0ull;
+            const long long msk = (long long)(int)(hi & 0x80000000u) >> 31;
+            const long long zq = ((long long)qv ^ msk) - msk;
+            long long *dst = tq + w * kSpTileStride + 2 * (lane + 32 * q);
+            dst[0] = zq;
+            dst[1] = -zq;
         }
-        __syncthreads();
-        // ---- rescale this lane's accumulators if its column's exponent grew
-        const int En = Enew[lane];
-        if (En > Emine) {
-            if (Emine > 0) {
-                const int d = En - Emine;
-#pragma unroll
-                for (int r = 0; r < kSpRowsPerWarp; ++r) acc[r] = (d >= 63) ? (acc[r] >> 63) : (acc[r] >> d);
-            }
-            Emine = En;
-        }
-        if (tid < kSpCols) Ecol[tid] = Enew[tid];
-        // ---- this warp's entries: rows row0 .. row0+15, sorted by row
-        if (row0 < s) {
-            const uint32_t *ent = entries + t * nent;
-            int64_t e = offsets[t * (ngrp16 + 1) + g16];
-            const int64_t e_end = offsets[t * (ngrp16 + 1) + g16 + 1];
-#pragma unroll
-            for (int r = 0; r < kSpRowsPerWarp; ++r) {
-                const uint32_t rk = (uint32_t)(row0 + r);
-                while (e < e_end) {
-                    const uint32_t k = __ldg(ent + e);
-                    if ((k >> 8) != rk) break;
-                    const long long v = tq[(k >> 1) & 127][lane];
-                    acc[r] += (k & 1u) ? -v : v;
-                    ++e;
-                }
+        if (lane == 0) Ecol[w] = E;
+        __syncthreads();  // tile, entries, offsets and exponents in place
+        // ---- half warp h of warp w applies the entries of owner 2w + h
+        const int o = 2 * w + h;
+        const int32_t b0 = boff[o] - boff[0], cntme = boff[o + 1] - boff[o];
+        const int cnt_other = __shfl_xor_sync(0xffffffffu, cntme, 16);
+        const int steps = max(cntme, cnt_other);
+        const long long *tqc = tq + c * kSpTileStride;  // +v at 2 jl, -v at 2 jl + 1
+        long long *accc = acc + c;
+        for (int i = 0; i < steps; ++i) {
+            if (i < cntme) {
+                const uint32_t key = ents[b0 + i];
+                accc[((key >> 8) & (kSpGroup - 1)) * kSpCols] += tqc[key & (2 * kSpTile - 1)];
             }
         }
-    }
-    // chunk partial in FP64: value = acc * 2^(E - 1022 - P)
-    if (col < n && Emine > 0) {
-        const double scale = ldexp(1.0, Emine - 1022 - P);
-        double *out = partial + (ch * n + col) * s;
-#pragma unroll
-        for (int r = 0; r < kSpRowsPerWarp; ++r)
-            if (row0 + r < s) out[row0 + r] = (double)acc[r] * scale;
-    } else if (col < n) {
-        double *out = partial + (ch * n + col) * s;
-        for (int r = 0; r < kSpRowsPerWarp; ++r)
-            if (row0 + r < s) out[row0 + r] = 0.0;
     }
     __syncthreads();
-    if (tid == 0 && nonfinite) set_status(status, NS_ERR_NONFINITE);
+    // chunk partial in FP64: value = acc * 2^(E - 1022 - P)
+    if (col < n) {
+        const int E = Ecol[c];
+        const double scale = E > 0 ? ldexp(1.0, E - 1022 - P) : 0.0;
+        double *out = partial + (ch * n + col) * s;
+        for (int r = w * 2 + h; r < kSpGroup; r += 2 * kSpWarps) {
+            const int64_t rg = tg * kSpGroup + r;
+            if (rg < s) out[rg] = (double)acc[r * kSpCols + c] * scale;
+        }
+    }
+    if (nonfinite) set_status(status, NS_ERR_NONFINITE);
 }
 
 __global__ void chunk_reduce_kernel(const double *__restrict__ partial, int64_t n, int64_t s, int64_t nchunk,
@@ -267,15 +279,17 @@ cudaError_t launch_sparse_meta(uint64_t seed, int64_t s, int zeta, int64_t m, in
 cudaError_t launch_sparse_f64(uint64_t seed, const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, int zeta,
                               const SparseWork &w, double *SA, int32_t *status, cudaStream_t st) {
     const SparseGeom g = sparse_geom(m, n, s, zeta);
-    const size_t sort_smem = sizeof(uint32_t) * (size_t)g.nsort;
-    cudaError_t e =
-        cudaFuncSetAttribute(sparse_tile_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem);
+    const size_t bsmem = sizeof(int32_t) * (size_t)(g.nbucket + 1);
+    sparse_bucket_kernel<<<(unsigned)g.ntile, 256, bsmem, st>>>(seed, s, zeta, m, g.nent, g.nbucket, w.entries,
+                                                                w.offsets);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    sparse_tile_sort_kernel<<<(unsigned)g.ntile, 256, sort_smem, st>>>(seed, s, zeta, m, g.nent, g.nsort, g.ngrp16,
-                                                                        w.entries, w.offsets);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    dim3 grid((unsigned)g.nrowgrp, (unsigned)g.ncolgrp, (unsigned)g.nchunk);
-    sparse_f64_kernel<<<grid, kSpWarps * 32, 0, st>>>(A, m, n, lda, s, g.nent, g.ngrp16, g.chunk_tiles, g.ntile,
+    const size_t smem = sizeof(long long) * (size_t)(kSpGroup * kSpCols + kSpCols * kSpTileStride) +
+                        sizeof(uint32_t) * (size_t)g.nent;
+    e = cudaFuncSetAttribute(sparse_acc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)g.ncolgrp, (unsigned)g.ntgrp, (unsigned)g.nchunk);
+    sparse_acc_kernel<<<grid, kSpThreads, smem, st>>>(A, m, n, lda, s, g.nent, g.nbucket, g.chunk_tiles, g.ntile,
                                                       g.fx_bits, w.entries, w.offsets, w.partial, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     chunk_reduce_kernel<<<(unsigned)((n * s + 255) / 256), 256, 0, st>>>(w.partial, n, s, g.nchunk,
