@@ -63,6 +63,7 @@ DenseWork dense_carve(Carver &c, int64_t s, int64_t n) {
     w.perm = c.take<int32_t>((size_t)n);
     w.pivslot = c.take<unsigned long long>((size_t)n + 1);
     w.bar = c.take<unsigned int>(kBarWords);
+    w.colver = c.take<unsigned int>((size_t)n + 16);
     return w;
 }
 
@@ -768,8 +769,10 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_coop_kernel(double *X, d
 // on the receiver's mbarrier.  A round thus waits only for one neighbour's
 // column.  The pairs inside each block are visited at the first outer step of
 // a sweep (kRingC - 1 round-robin rounds through global memory, one grid
-// barrier each).  Blocks move between clusters through global memory with one
-// grid barrier per outer step.  kRingT threads with kRingR rows each: four
+// barrier each).  Blocks move between clusters through global memory: each
+// CTA publishes the two columns it stores with a release of their version
+// and the next outer step's reader acquires exactly those versions, so only a
+// sweep's end (rotation count) takes a grid barrier.  kRingT threads with kRingR rows each: four
 // warps keep all four FP64 units of the SM busy while the reduction tree stays
 // short (FP64 runs at 2 operations per clock per SM here, so every add of a
 // reduction counts).
@@ -982,7 +985,8 @@ __device__ __forceinline__ void send_pair(uint32_t dst, double a, double b, uint
 
 __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
     jacobi_ring_kernel(double *X, double *V, int64_t n, int64_t G, double tol, GridBarrier bar,
-                       unsigned int *rotcount, unsigned int *checkflag, double *sigma, int32_t *status) {
+                       unsigned int *rotcount, unsigned int *checkflag, double *sigma, unsigned int *colver,
+                       int32_t *status) {
     // Slot j receives the Q column of round j: rows t and t + kRingT of X in
     // xbuf[j][t] and of V in vbuf[j][t], and its scale pair in sbuf[j], each
     // completed on its own mbarrier (mbx, mbv, mbs).  Columns are held scaled,
@@ -1085,6 +1089,28 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
                     ok = grid_sync(bar);
                 }
                 if (!ok) break;
+            }
+            if (ot > 0) {
+                // the two columns this CTA loads were stored at the previous outer
+                // step by CTAs of other clusters: wait for their versions
+                __shared__ int s_late;
+                if (tid == 0) {
+                    const int64_t a = P * kRingC + ci, b = Q * kRingC + ci;
+                    const long long t0 = clock64();
+                    int late = 0;
+                    while (ld_acquire_u32(colver + a) < ostep || ld_acquire_u32(colver + b) < ostep) {
+                        if (s_abort || clock64() - t0 > (1ll << 32)) {
+                            late = 1;
+                            break;
+                        }
+                    }
+                    s_late = late;
+                }
+                __syncthreads();
+                if (s_late && !s_abort) {
+                    s_abort = 1;
+                    set_status(status, NS_ERR_TIMEOUT);
+                }
             }
             if (tid == 0)
                 for (int j = 1; j < kRingC; ++j) {
@@ -1212,10 +1238,20 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
                 }
             }
             ++ostep;
-            if (ot == nouter - 1 && tid == 0 && local) atomicAdd(rotcount + sweep, local);
-            if (!grid_sync(bar)) {
-                ok = false;
-                break;
+            if (ot < nouter - 1) {
+                // publish this CTA's two stored columns (version = outer steps done)
+                __syncthreads();
+                if (tid == 0) {
+                    const int64_t a = P * kRingC + ci, b = Q * kRingC + (ci + kRingC - 1) % kRingC;
+                    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(colver + a), "r"(ostep) : "memory");
+                    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(colver + b), "r"(ostep) : "memory");
+                }
+            } else {
+                if (tid == 0 && local) atomicAdd(rotcount + sweep, local);
+                if (!grid_sync(bar)) {  // end of the sweep: rotation count, every column stored
+                    ok = false;
+                    break;
+                }
             }
         }
         if (!ok) break;
@@ -1385,7 +1421,10 @@ static cudaError_t launch_jacobi_ring(const DenseWork &w, int64_t n, GridBarrier
     double *X = w.X, *V = w.V, *sigma = w.sigma;
     unsigned int *rot = w.bar + 64, *chk = w.bar + 64 + 64;
     const double tol = (double)n * std::ldexp(1.0, -53);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, jacobi_ring_kernel, X, V, n, G, tol, bar, rot, chk, sigma, status);
+    unsigned int *colver = w.colver;
+    cudaError_t e = cudaMemsetAsync(colver, 0, sizeof(unsigned int) * (size_t)(n + 16), st);
+    if (e != cudaSuccess) return e;
+    e = cudaLaunchKernelEx(&cfg, jacobi_ring_kernel, X, V, n, G, tol, bar, rot, chk, sigma, colver, status);
     if (e != cudaSuccess) {
         cudaGetLastError();
         state[dev] = -1;
