@@ -11,7 +11,8 @@
 //   3. column update: the new Loewner column (f_i - f_j)/(x_i - x_j) (support
 //      rows zero) is sketched with the FP64 SRHT kernels;
 //   4. the weights w solve min |A w|, |w| = 1, on the first min(4k, s) rows of
-//      the s-row sketch (Algorithm 1 on the sketch, one CTA);
+//      the s-row sketch (Algorithm 1 on the sketch: one CTA while k is small,
+//      the whole-GPU dense stage of ns_solve from kAaaWideFrom columns on);
 //   5. r(x) = sum_l w_l f_l/(x - x_l) / sum_l w_l/(x - x_l) at every point, and
 //      the largest error and its index (deterministic reduction).
 // Every step reads the current support index from device memory, so the loop
@@ -25,6 +26,7 @@ namespace ns {
 
 constexpr int kAaaThreads = 256;
 constexpr int kAaaEvalBlocks = 512;
+constexpr int kAaaWideFrom = 24;  // iterations k >= this solve on the whole GPU
 
 struct AaaWork {
     SrhtWork srht;
@@ -41,6 +43,7 @@ struct AaaWork {
     long long *bidx;    // kAaaEvalBlocks
     long long *cur;     // current support index
     double *mean;       // 1
+    DenseWork dw;       // smax x K: the whole-GPU dense solve of the larger iterations
 };
 
 static AaaWork aaa_carve(Carver &c, int64_t m, int64_t smax, int32_t K) {
@@ -66,6 +69,7 @@ static AaaWork aaa_carve(Carver &c, int64_t m, int64_t smax, int32_t K) {
     w.bidx = c.take<long long>(kAaaEvalBlocks);
     w.cur = c.take<long long>(1);
     w.mean = c.take<double>(1);
+    w.dw = dense_carve(c, smax, K);
     return w;
 }
 
@@ -201,6 +205,26 @@ __global__ void __launch_bounds__(kAaaThreads) aaa_dense_kernel(const double *SA
     for (int32_t l = threadIdx.x; l < K; l += blockDim.x) Wout[(int64_t)(k - 1) * K + l] = (l < k) ? w.w[l] : 0.0;
 }
 
+// the first sk rows of the k sketch columns, contiguous (ld sk)
+__global__ void aaa_prefix_kernel(const double *__restrict__ SAk, int64_t smax, int32_t k, int64_t sk,
+                                  double *__restrict__ SAc) {
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < sk * k;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = idx % sk, l = idx / sk;
+        SAc[t + l * sk] = SAk[t + l * smax];
+    }
+}
+
+// weights of iteration k from the trailing right singular vector
+__global__ void aaa_store_w_kernel(const double *__restrict__ vk, int32_t k, int32_t K, double *__restrict__ wts,
+                                   double *__restrict__ Wout) {
+    for (int32_t l = threadIdx.x; l < K; l += blockDim.x) {
+        const double v = (l < k) ? vk[l] : 0.0;
+        if (l < k) wts[l] = v;
+        Wout[(int64_t)(k - 1) * K + l] = v;
+    }
+}
+
 // r at every point and |f - r| (0 at support points)
 __global__ void __launch_bounds__(kAaaThreads) aaa_eval_kernel(const double *__restrict__ x,
                                                                const double *__restrict__ f,
@@ -260,7 +284,15 @@ cudaError_t launch_aaa(uint64_t seed, const double *x, const double *f, int64_t 
         e = launch_srht_f64(w.col, m, 1, m, smax, w.srht, w.SAk + (int64_t)(k - 1) * smax, status, st);
         if (e != cudaSuccess) return e;
         const int64_t sk = (4 * (int64_t)k < smax) ? 4 * (int64_t)k : smax;
-        aaa_dense_kernel<<<1, kAaaThreads, dsmem, st>>>(w.SAk, smax, k, sk, w, Wout, K, status);
+        if (k < kAaaWideFrom || sk < k) {  // small problems: one CTA, no grid-wide launches
+            aaa_dense_kernel<<<1, kAaaThreads, dsmem, st>>>(w.SAk, smax, k, sk, w, Wout, K, status);
+        } else {  // larger ones: the whole-GPU QR and cluster-ring Jacobi of ns_solve
+            aaa_prefix_kernel<<<64, kAaaThreads, 0, st>>>(w.SAk, smax, k, sk, w.SAc);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            e = launch_dense_solve(w.SAc, sk, k, 1, w.dw, w.X, w.sigk, nullptr, nullptr, status, st);
+            if (e != cudaSuccess) return e;
+            aaa_store_w_kernel<<<1, kAaaThreads, 0, st>>>(w.X, k, K, w.w, Wout);
+        }
         aaa_eval_kernel<<<nb, kAaaThreads, sizeof(double) * 3 * (size_t)k, st>>>(x, f, w.sup, support, w.w, k, m,
                                                                                  w.err);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

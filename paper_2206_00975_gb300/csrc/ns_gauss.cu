@@ -15,7 +15,7 @@
 //
 // CTA tile: 128 rows of G (= rows of SA) x all n <= 512 columns of A (two
 // accumulators of up to 256 columns in TMEM), over a slice of K = m (split-K
-// across CTAs).  Per K chunk of 32: the 256 threads write Gh, Gl (128 x 32) and
+// across CTAs).  Per K chunk of 32: the 512 threads write Gh, Gl (128 x 32) and
 // Ah, Al (n x 32) into shared memory in the canonical K-major no-swizzle layout
 // (8x8 core matrices, 128 bytes apart along K, 512 bytes apart along M/N), then
 // one thread issues 2 K-steps x 2 N-halves x 3 products of
@@ -31,7 +31,7 @@ namespace ns {
 
 constexpr int kGM = 128;        // rows of G per CTA (MMA M)
 constexpr int kGK = 32;         // K per pipeline stage
-constexpr int kGThreads = 256;
+constexpr int kGThreads = 512;
 constexpr int kGMaxN = 512;
 constexpr int kGSbo = (kGK / 8) * 128;  // bytes between 8-row groups (512)
 constexpr int kGStageG = kGM * kGK * 2;  // bytes of one bf16 G tile (8 KB)
@@ -130,6 +130,26 @@ __global__ void __launch_bounds__(kGThreads, 1) gauss_bf16x3_kernel(const float 
         unsigned char *st = gsm + (size_t)b * stage_bytes;
         unsigned char *sGh = st, *sGl = st + kGStageG, *sAh = st + 2 * kGStageG, *sAl = sAh + NP * kGK * 2;
         const int64_t k0 = kbeg + (int64_t)it * kGK;
+        // ---- A: NP columns x 4 octets of K, loads issued first so that the
+        // generation of G below hides their latency
+        constexpr int kAItems = kGMaxN * (kGK / 8) / kGThreads;  // items per thread (8)
+        float za[kAItems][8];
+#pragma unroll
+        for (int q = 0; q < kAItems; ++q) {
+            const int id = tid + q * kGThreads;
+            const int c = id >> 2, o = id & 3;
+            const int64_t j0 = k0 + 8 * o;
+            if (c < NP && c < n && j0 + 8 <= kend && (((uintptr_t)(A + j0 + c * lda)) & 15) == 0) {
+                const float4 v0 = __ldcs((const float4 *)(A + j0 + c * lda));
+                const float4 v1 = __ldcs((const float4 *)(A + j0 + c * lda) + 1);
+                za[q][0] = v0.x; za[q][1] = v0.y; za[q][2] = v0.z; za[q][3] = v0.w;
+                za[q][4] = v1.x; za[q][5] = v1.y; za[q][6] = v1.z; za[q][7] = v1.w;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    za[q][u] = (c < NP && c < n && j0 + u < kend) ? A[j0 + u + c * lda] : 0.0f;
+            }
+        }
         // ---- G: 128 rows x 4 octets of K, one Philox block per (row, octet)
         for (int id = tid; id < kGM * (kGK / 8); id += kGThreads) {
             const int r = id >> 2, o = id & 3;
@@ -157,25 +177,18 @@ __global__ void __launch_bounds__(kGThreads, 1) gauss_bf16x3_kernel(const float 
             *(uint4 *)(sGh + off) = hi;
             *(uint4 *)(sGl + off) = lo;
         }
-        // ---- A: NP columns x 4 octets of K (FP32 -> bf16 hi/lo)
-        for (int id = tid; id < NP * (kGK / 8); id += kGThreads) {
-            const int c = id >> 2, o = id & 3;
-            const int64_t j0 = k0 + 8 * o;
-            float z[8];
-            if (c < n && j0 + 8 <= kend && (((uintptr_t)(A + j0 + c * lda)) & 15) == 0) {
-                const float4 v0 = __ldcs((const float4 *)(A + j0 + c * lda));
-                const float4 v1 = __ldcs((const float4 *)(A + j0 + c * lda) + 1);
-                z[0] = v0.x; z[1] = v0.y; z[2] = v0.z; z[3] = v0.w;
-                z[4] = v1.x; z[5] = v1.y; z[6] = v1.z; z[7] = v1.w;
-            } else {
+        // ---- A: split into bf16 hi / lo core-matrix rows
 #pragma unroll
-                for (int q = 0; q < 8; ++q) z[q] = (c < n && j0 + q < kend) ? A[j0 + q + c * lda] : 0.0f;
+        for (int q = 0; q < kAItems; ++q) {
+            const int id = tid + q * kGThreads;
+            const int c = id >> 2, o = id & 3;
+            if (c < NP) {
+                uint4 hi, lo;
+                split8(za[q], hi, lo);
+                const int off = (c >> 3) * kGSbo + o * 128 + (c & 7) * 16;
+                *(uint4 *)(sAh + off) = hi;
+                *(uint4 *)(sAl + off) = lo;
             }
-            uint4 hi, lo;
-            split8(z, hi, lo);
-            const int off = (c >> 3) * kGSbo + o * 128 + (c & 7) * 16;
-            *(uint4 *)(sAh + off) = hi;
-            *(uint4 *)(sAl + off) = lo;
         }
         asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();
@@ -215,9 +228,10 @@ __global__ void __launch_bounds__(kGThreads, 1) gauss_bf16x3_kernel(const float 
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!timed_out && nstages > 0) {
-        // TMEM lanes 32 (warp % 4) .. +31 = rows; warps 0-3 take columns [0, NP/2), 4-7 the rest
-        const int half = NP / 2 >= 16 ? ((NP / 2) / 16) * 16 : NP;
-        const int c0 = (warp < 4) ? 0 : half, c1 = (warp < 4) ? half : NP;
+        // TMEM lanes 32 (warp % 4) .. +31 = rows; warp group warp / 4 takes a
+        // quarter of the columns (16-column granules)
+        const int granules = NP / 16, g4 = warp >> 2;
+        const int c0 = 16 * ((granules * g4) / 4), c1 = 16 * ((granules * (g4 + 1)) / 4);
         const int64_t r = row0 + 32 * (warp & 3) + lane;
         for (int cb = c0; cb < c1; cb += 16) {
             uint32_t v[16];
