@@ -446,7 +446,7 @@ def main():
                    "peak_source": peak_kind, "algorithmic_bytes": sketch_bytes}
     dense_roof = {"bound": "alu", "achieved": dense_tf, "peak": fp64_peak, "unit": "TFLOP/s",
                   "frac": dense_tf / fp64_peak, "traffic": None,
-                  "kernel": "FP64 dense stage (hqr_coop x2, jacobi_coop, apply_q2, extract) via ns_solve_sketched",
+                  "kernel": "FP64 dense stage (column order, hqr_pipe x2, jacobi_ring, apply_q2, extract) via ns_solve_sketched",
                   "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x sampled SM clock",
                   "algorithmic_flops": dflops, "jacobi_sweeps_rotations_checks": stats[:3],
                   "jacobi_kernel": "cluster ring" if stats[3] == 1 else "barrier-separated"}
