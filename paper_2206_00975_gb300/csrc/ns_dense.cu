@@ -262,15 +262,20 @@ __global__ void __launch_bounds__(kDenseThreads) hqr_coop_kernel(double *W, int6
 // Reflector j (same form and storage as hqr_coop_kernel: tail in W below the
 // diagonal, u0[j], cf[j], R[j, j] = beta) is formed by the owner of column j
 // as soon as reflectors 0..j-1 have reached that column, written to global
-// memory and announced by flag[j].  The owner of column j + 1 applies
+// memory and announced by flag[j], which carries the coefficient itself (the
+// bits of cf[j]; all ones = not yet formed), with u0[j] also stored in the
+// diagonal slot of W: a consumer needs one acquire and one read of W's
+// column.  The owner of column j + 1 applies
 // reflector j to that column before its other columns (look-ahead), so the
 // chain from one reflector to the next runs through one CTA and one flag;
 // every other CTA only waits for the flags of the reflectors it applies.
 constexpr int kPipeThreads = 256;
 
-__device__ __forceinline__ unsigned int ld_acquire_flag(const unsigned int *p) {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+constexpr unsigned long long kPipeEmpty = ~0ull;  // flag word of a reflector not formed yet
+
+__device__ __forceinline__ unsigned long long ld_acquire_flag(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -308,7 +313,7 @@ __device__ __forceinline__ double pipe_sum(double v, double *red) {
 // the coefficient in *coef_sh and returns beta (every thread).  The scalar
 // chain (square root, reciprocal) runs in thread 0 only: FP64 is scarce.
 __device__ double pipe_form(double *W, int64_t rows, int64_t j, const double *x, double *ush, double *u0, double *cf,
-                            unsigned int *flag, double *red, double *coef_sh) {
+                            unsigned long long *flag, double *red, double *coef_sh) {
     __shared__ double s_par[2];
     const int tid = threadIdx.x;
     double ss = 0.0;
@@ -342,19 +347,25 @@ __device__ double pipe_form(double *W, int64_t rows, int64_t j, const double *x,
             coef = 0.0;
         } else {
             const double xs = x0 * sc;
-            const double r = sqrt(fma(xs, xs, nrm2)) / sc;
+            double r = sqrt(fma(xs, xs, nrm2));
+            if (sc != 1.0) r /= sc;  // rescaled column (rare): an exact power of two
             beta = x0 >= 0.0 ? -r : r;
             ua = x0 - beta;
             coef = 1.0 / (beta * (beta - x0));
         }
         ush[j] = ua;
         u0[j] = ua;
+        W[j + j * rows] = ua;
         cf[j] = coef;
         *coef_sh = coef;
         s_par[0] = beta;
     }
     __syncthreads();  // orders every thread's stores before thread 0's release
-    if (tid == 0) asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flag + j), "r"(1u) : "memory");
+    if (tid == 0) {
+        unsigned long long fw = (unsigned long long)__double_as_longlong(*coef_sh);
+        if (fw == kPipeEmpty) fw = 0x7FF8000000000000ull;  // a NaN coefficient keeps a NaN flag word
+        asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(flag + j), "l"(fw) : "memory");
+    }
     return s_par[0];
 }
 
@@ -371,7 +382,8 @@ __device__ __forceinline__ void pipe_apply(int64_t rows, int64_t j, const double
 
 __global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(double *W, int64_t rows, int64_t cols, int64_t nown_max,
                                                                double *u0, double *cf, int32_t *perm,
-                                                               unsigned int *flag, double *Rout, int32_t *status) {
+                                                               unsigned long long *flag, double *Rout,
+                                                               int32_t *status) {
     extern __shared__ double sm[];
     double *own = sm;                          // nown_max * rows: owned columns
     double *ubuf = sm + nown_max * rows;       // 2 * rows: reflectors j (even/odd)
@@ -397,19 +409,19 @@ __global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(double *W, int64
         if (j % G != me) {  // wait for reflector j, then fetch it
             if (tid == 0) {
                 const long long t0 = clock64();
-                while (ld_acquire_flag(flag + j) == 0u) {
+                unsigned long long fw;
+                while ((fw = ld_acquire_flag(flag + j)) == kPipeEmpty) {
                     if (clock64() - t0 > (1ll << 32)) {  // ~2 s; a healthy pipeline waits microseconds
                         set_status(status, NS_ERR_TIMEOUT);
                         s_ok = 0;
                         break;
                     }
                 }
-                s_coef[j & 1] = __ldcg(cf + j);
+                s_coef[j & 1] = __longlong_as_double((long long)fw);
             }
             __syncthreads();
             if (!s_ok) return;
-            for (int64_t i = j + 1 + tid; i < rows; i += kPipeThreads) ush[i] = __ldcg(W + i + j * rows);
-            if (tid == 0) ush[j] = __ldcg(u0 + j);
+            for (int64_t i = j + tid; i < rows; i += kPipeThreads) ush[i] = __ldcg(W + i + j * rows);
             __syncthreads();
         }
         const double coef = s_coef[j & 1];
@@ -822,7 +834,7 @@ __device__ __forceinline__ bool ring_wait(uint32_t mbar, uint32_t parity) {
     for (;;) {
         uint32_t done;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
             : "r"(mbar), "r"(parity)
@@ -848,7 +860,7 @@ __device__ __forceinline__ bool ring_wait_cta(uint32_t mbar, uint32_t parity) {
     for (;;) {
         uint32_t done;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
             : "r"(mbar), "r"(parity)
@@ -883,9 +895,35 @@ __device__ __forceinline__ double f64_of(float f) {
 // product of the scales (FP32).  The threshold test does not depend on the
 // scales.  t = tan(theta) needs only modest accuracy (the applied rotation is
 // orthogonal whatever t is), so it comes from FP32 images of the scaled sums.
+// FP32 value in [1, 2) of the leading 23 fraction bits of an IEEE double
+__device__ __forceinline__ float lead_mant(unsigned long long k) {
+    return __uint_as_float(0x3F800000u | (unsigned int)((k >> 29) & 0x7FFFFFu));
+}
+
+// The threshold test g^2 > tol2 a b (a, b >= 0) on the exponents and the
+// leading 23 fraction bits: no FP64 instruction on the common path, and no
+// overflow or underflow of the products.  It can differ from the exact
+// comparison only within a relative 2^-21 of the threshold.  Zero, subnormal
+// and non-finite operands take the FP64 form.
+__device__ __forceinline__ bool ring_above(double a, double b, double g, double tol2) {
+    const unsigned long long ka = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long kb = (unsigned long long)__double_as_longlong(b);
+    const unsigned long long kg = (unsigned long long)__double_as_longlong(g) & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned long long kt = (unsigned long long)__double_as_longlong(tol2);
+    const int ea = (int)(ka >> 52), eb = (int)(kb >> 52), eg = (int)(kg >> 52), et = (int)(kt >> 52);
+    if (ea == 0 || eb == 0 || eg == 0 || ea >= 0x7FF || eb >= 0x7FF || eg == 0x7FF)
+        return g != 0.0 && g * g > tol2 * (a * b);
+    // g^2 / (tol2 a b) = 2^k mg^2 / (mt ma mb), mg^2 in [1, 4), mt ma mb in [1, 8)
+    const int k = 2 * eg - ea - eb - et + 1023;
+    if (k >= 3) return true;
+    if (k <= -2) return false;
+    const float mg = lead_mant(kg);
+    return (mg * mg) * __uint_as_float((unsigned int)(127 + k) << 23) > (lead_mant(kt) * lead_mant(ka)) * lead_mant(kb);
+}
+
 __device__ __forceinline__ bool ring_angle(double a, double b, double g, double tol2, float dp2, float dq2,
                                            float dpq, double dp, double dq, double *t_out) {
-    if (g == 0.0 || !(g * g > tol2 * (a * b))) return false;
+    if (!ring_above(a, b, g, tol2)) return false;
     const long long ka = __double_as_longlong(a), kb = __double_as_longlong(b);
     const int shift = (int)(((ka > kb ? ka : kb) >> 52) & 0x7FF) - 1023;
     const float a32 = f32_image(a, shift) * dp2, b32 = f32_image(b, shift) * dq2, g32 = f32_image(g, shift) * dpq;
@@ -1125,56 +1163,75 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
             double p0 = (r0 && lp) ? __ldcg(M + i0 + cp * n) : 0.0, p1 = (r1 && lp) ? __ldcg(M + i1 + cp * n) : 0.0;
             double q0 = (r0 && lq) ? __ldcg(M + i0 + cq0 * n) : 0.0, q1 = (r1 && lq) ? __ldcg(M + i1 + cq0 * n) : 0.0;
             if (scalar) {
-                // the scales of the held columns (x = d x~, e = 1/d); the Q
-                // column's arrive after its entries, on their own mbarrier
-                double dP = 1.0, eP = 1.0, dQ = 1.0, eQ = 1.0;
+                // The scales of the held columns, one per lane (x = d x~, e = 1/d):
+                // lane 0 d_P, lane 1 d_Q, lane 2 e_P, lane 3 e_Q.  A warp
+                // instruction costs the FP64 pipe the same for one lane as for
+                // four, so independent scalar steps share instructions.  The Q
+                // column's scales arrive after its entries, on their own mbarrier.
+                const int lane = tid;
+                double sv = 1.0;
                 for (int j = 0; j < kRingC; ++j) {
-                    xbar();  // the row warps' partial sums of round j are in red
-                    double al, be, ga;
-                    ring_combine(red, &al, &be, &ga);
-                    double tn = 0.0;
-                    bool rot = false;
-                    if (tid == 0) {
-                        if (j > 0) {
-                            if (!s_abort && !ring_wait(shared_addr(&mbs[j]), parity)) {
-                                s_abort = 1;
-                                set_status(status, NS_ERR_TIMEOUT);
-                            }
-                            const double2 sc = sbuf[j];
-                            dQ = sc.x;
-                            eQ = sc.y;
+                    if (j > 0) {
+                        if (!s_abort && !ring_wait(shared_addr(&mbs[j]), parity) && lane == 0) {
+                            s_abort = 1;
+                            set_status(status, NS_ERR_TIMEOUT);
                         }
-                        rot = ring_angle(al, be, ga, tol2, (float)(dP * dP), (float)(dQ * dQ), (float)(dP * dQ), dP,
-                                         dQ, &tn);
+                        const double2 sc = sbuf[j];
+                        if (lane == 1) sv = sc.x;
+                        if (lane == 3) sv = sc.y;
+                    }
+                    // before the sums arrive: d_Q e_P (lane 0, for mu), d_P e_Q
+                    // (lane 1, for nu) and the FP32 images of the scales
+                    const double dP = __shfl_sync(0xffffffffu, sv, 0), dQ = __shfl_sync(0xffffffffu, sv, 1);
+                    const double ee = __shfl_sync(0xffffffffu, sv, lane == 0 ? 2 : 3);
+                    const double rr = (lane == 0 ? dQ : dP) * ee;
+                    const float fP = f32_image(dP, 0), fQ = f32_image(dQ, 0);
+                    xbar();  // the row warps' partial sums of round j are in red
+                    // (red[v4] + red[v4+1]) + (red[v4+2] + red[v4+3]): lanes 0-5, then 0-2
+                    double hsum = 0.0;
+                    if (lane < 6) {
+                        const int b = (lane >> 1) * 4 + 2 * (lane & 1);
+                        hsum = red[b] + red[b + 1];
+                    }
+                    const double h0 = __shfl_sync(0xffffffffu, hsum, (2 * lane) & 31);
+                    const double h1 = __shfl_sync(0xffffffffu, hsum, (2 * lane + 1) & 31);
+                    double vs = 0.0;
+                    if (lane < 3) vs = h0 + h1;
+                    const double al = __shfl_sync(0xffffffffu, vs, 0), be = __shfl_sync(0xffffffffu, vs, 1),
+                                 ga = __shfl_sync(0xffffffffu, vs, 2);
+                    double tn = 0.0;
+                    const bool rot = ring_angle(al, be, ga, tol2, fP * fP, fQ * fQ, fP * fQ, dP, dQ, &tn);
+                    const double mn = tn * rr;  // lane 0: mu (x~_p -= mu x~_q), lane 1: nu (x~_q += nu x~_p)
+                    const double nu = __shfl_sync(0xffffffffu, mn, 1);
+                    if (lane == 0) {
                         par[j][0] = rot ? 1.0 : 0.0;
-                        par[j][1] = rot ? tn * dQ * eP : 0.0;  // mu: x~_p -= mu x~_q
-                        par[j][2] = rot ? tn * dP * eQ : 0.0;  // nu: x~_q += nu x~_p
+                        par[j][1] = rot ? mn : 0.0;
+                        par[j][2] = rot ? nu : 0.0;
                         asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(
                                          shared_addr(&mbr[j]))
                                      : "memory");
                     }
                     xbar();  // par[j] is visible to the X row warps
-                    if (tid == 0) {
-                        if (rot) {  // new scales: d <- c d, e <- e / c, c = 1/sqrt(1 + t^2)
-                            ++local;
-                            const double tt = fma(tn, tn, 1.0), h = -0.5 * tt;
-                            double c = f64_of(rsqrtf(f32_image(tt, 0)));
-                            c = c * fma(h, c * c, 1.5);
-                            c = c * fma(h, c * c, 1.5);
-                            const double ic = tt * c;
-                            dP *= c;
-                            dQ *= c;
-                            eP *= ic;
-                            eQ *= ic;
-                        }
-                        if (j < kRingC - 1)
-                            send_pair(sb_peer + (uint32_t)((j + 1) * sizeof(double2)), dQ, eQ,
+                    if (rot) {  // new scales: d <- c d, e <- e / c, c = 1/sqrt(1 + t^2)
+                        ++local;
+                        const double tt = fma(tn, tn, 1.0), h = -0.5 * tt;
+                        double c = f64_of(rsqrtf(f32_image(tt, 0)));
+                        c = c * fma(h, c * c, 1.5);
+                        c = c * fma(h, c * c, 1.5);
+                        const double ic = tt * c;
+                        sv *= (lane < 2) ? c : ic;
+                    }
+                    if (j < kRingC - 1) {
+                        const double sQ = __shfl_sync(0xffffffffu, sv, 1), eQ = __shfl_sync(0xffffffffu, sv, 3);
+                        if (lane == 0)
+                            send_pair(sb_peer + (uint32_t)((j + 1) * sizeof(double2)), sQ, eQ,
                                       ms_peer + (uint32_t)((j + 1) * 8));
                     }
                 }
-                if (tid == 0) {  // final scales of the held columns
-                    s_fin[0] = dP;
-                    s_fin[1] = dQ;
+                const double fPs = __shfl_sync(0xffffffffu, sv, 0), fQs = __shfl_sync(0xffffffffu, sv, 1);
+                if (lane == 0) {  // final scales of the held columns
+                    s_fin[0] = fPs;
+                    s_fin[1] = fQs;
                     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(shared_addr(&mbf))
                                  : "memory");
                 }
@@ -1208,18 +1265,22 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
                             q1 = in.y;
                         }
                     }
-                    if (par[j][0] != 0.0) {
-                        const double mu = par[j][1], nu = par[j][2];
-                        const double a0 = p0, a1 = p1;
-                        p0 = fma(-mu, q0, a0);
-                        p1 = fma(-mu, q1, a1);
-                        q0 = fma(nu, a0, q0);
-                        q1 = fma(nu, a1, q1);
+                    // the Q half first: it is what the neighbour waits for
+                    const bool rj = par[j][0] != 0.0;
+                    const double mu = par[j][1], nu = par[j][2];
+                    const double oq0 = q0, oq1 = q1;
+                    if (rj) {
+                        q0 = fma(nu, p0, q0);
+                        q1 = fma(nu, p1, q1);
                     }
                     if (j < kRingC - 1) {
                         const uint32_t off = (uint32_t)(((j + 1) * kRingT + t) * sizeof(double2));
                         if (isx) send_pair(xb_peer + off, q0, q1, mx_peer + (uint32_t)((j + 1) * 8));
                         else send_pair(vb_peer + off, q0, q1, mv_peer + (uint32_t)((j + 1) * 8));
+                    }
+                    if (rj) {
+                        p0 = fma(-mu, oq0, p0);
+                        p1 = fma(-mu, oq1, p1);
                     }
                 }
                 if (!s_abort && !ring_wait_cta(shared_addr(&mbf), parity)) {
@@ -1459,13 +1520,14 @@ static size_t pipe_smem(int64_t rows, int64_t cols) {
 static bool pipe_fits(int64_t rows, int64_t cols) { return pipe_smem(rows, cols) <= 200 * 1024 && cols <= 4096; }
 
 static bool launch_hqr_pipe(double *W, int64_t rows, int64_t cols, double *u0, double *cf, int32_t *perm,
-                            unsigned int *flags, double *Rout, int32_t *status, cudaStream_t st, cudaError_t *err) {
+                            unsigned long long *flags, double *Rout, int32_t *status, cudaStream_t st,
+                            cudaError_t *err) {
     int64_t G = cols < sm_count() ? cols : sm_count();
     if (G < 1) G = 1;
     const int64_t nown = (cols + G - 1) / G;
     const size_t smem = pipe_smem(rows, cols);
     if (!pipe_fits(rows, cols)) return false;
-    *err = cudaMemsetAsync(flags, 0, sizeof(unsigned int) * (size_t)cols, st);
+    *err = cudaMemsetAsync(flags, 0xFF, sizeof(unsigned long long) * (size_t)cols, st);  // kPipeEmpty
     if (*err != cudaSuccess) return true;
     *err = cudaFuncSetAttribute(hqr_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (*err != cudaSuccess) return true;
@@ -1513,7 +1575,7 @@ cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k
     // 1. SA P = Q1 R; R (n x n) lands in X.  Pipelined after a static ordering
     // of the columns by decreasing norm when it fits, else barrier-separated
     // with column pivoting.
-    unsigned int *flags = (unsigned int *)w.pivslot;  // 2 (n + 1) words >= n flags
+    unsigned long long *flags = w.pivslot;  // n + 1 words >= n flags
     if (pipe_fits(s, n)) {
         double *key = w.X;  // n doubles; X is free until the QR writes R
         colnorm_kernel<<<(unsigned)(n < 1024 ? n : 1024), 256, 0, st>>>(SA, s, n, key);

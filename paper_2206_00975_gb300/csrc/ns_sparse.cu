@@ -148,7 +148,9 @@ __global__ void __launch_bounds__(256) sparse_bucket_kernel(uint64_t seed, int64
     }
 }
 
-// grid (column group, target group, chunk); 16 warps
+// grid (column group, target group, chunk); 16 warps; EPT >= entries per
+// tile / threads (a tile holds kSpTile * zeta entries)
+template <int EPT>
 __global__ void __launch_bounds__(kSpThreads, 1) sparse_acc_kernel(
     const double *__restrict__ A, int64_t m, int64_t n, int64_t lda, int64_t s, int64_t nent, int64_t nbucket,
     int64_t chunk_tiles, int64_t ntile, int P, const uint32_t *__restrict__ entries,
@@ -187,9 +189,9 @@ __global__ void __launch_bounds__(kSpThreads, 1) sparse_acc_kernel(
         // ---- this tile's entries of the target group, into registers
         const int32_t *off = offsets + t * (nbucket + 1) + tg * kSpOwners;
         const int32_t e0 = __ldg(off), e1 = __ldg(off + kSpOwners);
-        uint32_t pre[kSpMaxEntPerThread];
+        uint32_t pre[EPT];
 #pragma unroll
-        for (int q = 0; q < kSpMaxEntPerThread; ++q) {
+        for (int q = 0; q < EPT; ++q) {
             const int32_t e = e0 + tid + q * kSpThreads;
             pre[q] = (e < e1) ? __ldg(entries + t * nent + e) : 0u;
         }
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(kSpThreads, 1) sparse_acc_kernel(
         __syncthreads();  // the previous tile is fully applied
         if (tid <= kSpOwners) boff[tid] = myoff;
 #pragma unroll
-        for (int q = 0; q < kSpMaxEntPerThread; ++q) {
+        for (int q = 0; q < EPT; ++q) {
             const int32_t e = e0 + tid + q * kSpThreads;
             if (e < e1) ents[e - e0] = pre[q];
         }
@@ -286,11 +288,18 @@ cudaError_t launch_sparse_f64(uint64_t seed, const double *A, int64_t m, int64_t
     if (e != cudaSuccess) return e;
     const size_t smem = sizeof(long long) * (size_t)(kSpGroup * kSpCols + kSpCols * kSpTileStride) +
                         sizeof(uint32_t) * (size_t)g.nent;
-    e = cudaFuncSetAttribute(sparse_acc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t need = (g.nent + kSpThreads - 1) / kSpThreads;  // entries per thread, at most
+    const int ept = need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : kSpMaxEntPerThread;
+    auto kern = ept == 1 ? sparse_acc_kernel<1>
+                : ept == 2 ? sparse_acc_kernel<2>
+                : ept == 4 ? sparse_acc_kernel<4>
+                : ept == 8 ? sparse_acc_kernel<8>
+                           : sparse_acc_kernel<kSpMaxEntPerThread>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)g.ncolgrp, (unsigned)g.ntgrp, (unsigned)g.nchunk);
-    sparse_acc_kernel<<<grid, kSpThreads, smem, st>>>(A, m, n, lda, s, g.nent, g.nbucket, g.chunk_tiles, g.ntile,
-                                                      g.fx_bits, w.entries, w.offsets, w.partial, status);
+    kern<<<grid, kSpThreads, smem, st>>>(A, m, n, lda, s, g.nent, g.nbucket, g.chunk_tiles, g.ntile, g.fx_bits,
+                                         w.entries, w.offsets, w.partial, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     chunk_reduce_kernel<<<(unsigned)((n * s + 255) / 256), 256, 0, st>>>(w.partial, n, s, g.nchunk,
                                                                           1.0 / std::sqrt((double)zeta), SA);
