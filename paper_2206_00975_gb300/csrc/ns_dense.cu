@@ -256,6 +256,31 @@ __global__ void __launch_bounds__(kDenseThreads) hqr_coop_kernel(double *W, int6
     }
 }
 
+// FP32 image of x * 2^-shift from the IEEE fields (integer work, mantissa
+// truncated; zero, subnormal and below-range values give 0).
+__device__ __forceinline__ float f32_image(double x, int shift) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF), fe = e - shift - 1023 + 127;
+    if (e == 0 || fe <= 0) return 0.0f;
+    const unsigned int f = ((unsigned int)(b >> 32) & 0x80000000u) | ((unsigned int)min(fe, 254) << 23) |
+                           (unsigned int)((b >> 29) & 0x7FFFFFu);
+    return __uint_as_float(f);
+}
+// exact FP64 value of a normal or zero FP32 number (integer work)
+__device__ __forceinline__ double f64_of(float f) {
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int e = (u >> 23) & 0xFF;
+    if (e == 0) return 0.0;
+    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
+                                 ((unsigned long long)(e - 127 + 1023) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
+// biased exponent field of an IEEE double
+__device__ __forceinline__ uint32_t exp_field(double x) {
+    return (uint32_t)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FFu;
+}
+
 // ------------------------------------------------------- pipelined QR ----
 // Householder QR without pivoting, pipelined instead of barrier-separated.
 // CTA me owns columns me, me + G, ... and keeps them in shared memory.
@@ -302,18 +327,83 @@ __device__ __forceinline__ double pipe_sum(double v, double *red) {
             const double w = __shfl_down_sync(0xffffffffu, a, o);
             if (lane < o) a += w;
         }
-        if (lane == 0) red[kPipeThreads / 32] = a;
+        if (lane == 0) red[2 * (kPipeThreads / 32)] = a;
     }
     __syncthreads();
-    return red[kPipeThreads / 32];
+    return red[2 * (kPipeThreads / 32)];
+}
+
+// Sums of two values over the CTA (fixed order), valid in thread 0 only.
+// Lanes 0-15 carry a and lanes 16-31 b after the first exchange, so every
+// warp level costs one FP64 add for both; red needs 2 * warps entries.
+__device__ __forceinline__ void pipe_sum2_t0(double &a, double &b, double *red) {
+    constexpr int kW = kPipeThreads / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const bool hi = lane >= 16;
+    double v = (hi ? b : a) + __shfl_xor_sync(0xffffffffu, hi ? a : b, 16);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+        const double w = __shfl_down_sync(0xffffffffu, v, o);
+        if ((lane & 15) < o) v += w;
+    }
+    if ((lane & 15) == 0) red[(hi ? kW : 0) + wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        double x = (lane & 15) < kW ? red[(lane >= 16 ? kW : 0) + (lane & 15)] : 0.0;
+#pragma unroll
+        for (int o = kW / 2; o > 0; o >>= 1) {
+            const double w = __shfl_down_sync(0xffffffffu, x, o);
+            if ((lane & 15) < o) x += w;
+        }
+        const double bb = __shfl_sync(0xffffffffu, x, 16);
+        if (lane == 0) {
+            a = x;
+            b = bb;
+        }
+    }
+}
+
+// x 2^k for a positive normal x and a normal result (integer work)
+__device__ __forceinline__ double exp_shift(double x, int k) {
+    return __longlong_as_double(__double_as_longlong(x) + ((long long)k << 52));
+}
+
+// Reflector parameters for head x0 and tail norm^2 nrm2 > 0 when
+// t = x0^2 + nrm2 needs no rescaling: r = sqrt(t), beta = -sign(x0) r,
+// ua = x0 - beta and coef = 1 / (beta (beta - x0)) = 1 / (r (r + |x0|)).
+// FP64 square root and division are long serial chains on this part, so r and
+// coef come from FP32 seeds (exponent-shifted images) refined by one
+// third-order step of the binomial series each: y <- y (1 + e/2 + 3e^2/8),
+// e = 1 - t y^2, for t^(-1/2), and z <- z (1 + e + e^2), e = 1 - s z, for
+// 1/s.  The seeds' relative error (< 2^-21) becomes < 2^-60.  Returns false
+// (nothing written) when t is not a normal number.
+__device__ __forceinline__ bool pipe_reflector(double x0, double nrm2, double *beta, double *ua, double *coef) {
+    const double t = fma(x0, x0, nrm2);
+    const uint32_t eb = exp_field(t);
+    if (eb < 64 || eb > 2046 - 64) return false;
+    const int sh = ((int)eb - 1023) & ~1;  // even: the image of t lies in [1, 4)
+    double y = exp_shift(f64_of(rsqrtf(f32_image(t, sh))), -(sh / 2));
+    const double ty = t * y, e = fma(-ty, y, 1.0);
+    y = fma(y, e * fma(e, 0.375, 0.5), y);
+    const double r = t * y, sv = r + fabs(x0);
+    const int es = (int)exp_field(sv) - 1023;
+    double z = exp_shift(f64_of(__frcp_rn(f32_image(sv, es))), -es);
+    const double e2 = fma(-sv, z, 1.0);
+    z = fma(z, fma(e2, e2, e2), z);
+    *beta = x0 >= 0.0 ? -r : r;
+    *ua = x0 - *beta;
+    *coef = y * z;  // y = 1/r to within a few units of the last place
+    return true;
 }
 
 // Form reflector j from the owned column x (shared memory, rows entries):
 // publishes the tail, u0, cf and the flag; leaves u (u0 at index j) in ush,
 // the coefficient in *coef_sh and returns beta (every thread).  The scalar
 // chain (square root, reciprocal) runs in thread 0 only: FP64 is scarce.
+// The tail norm^2 |u[j+1:]|^2 goes to *unrm_sh and, for j >= 1, to the unused
+// slot W[j-1, j] for the consumers (NaN when the column was rescaled).
 __device__ double pipe_form(double *W, int64_t rows, int64_t j, const double *x, double *ush, double *u0, double *cf,
-                            unsigned long long *flag, double *red, double *coef_sh) {
+                            unsigned long long *flag, double *red, double *coef_sh, double *unrm_sh) {
     __shared__ double s_par[2];
     const int tid = threadIdx.x;
     double ss = 0.0;
@@ -345,7 +435,7 @@ __device__ double pipe_form(double *W, int64_t rows, int64_t j, const double *x,
             beta = x0;
             ua = 0.0;
             coef = 0.0;
-        } else {
+        } else if (sc != 1.0 || !pipe_reflector(x0, nrm2, &beta, &ua, &coef)) {
             const double xs = x0 * sc;
             double r = sqrt(fma(xs, xs, nrm2));
             if (sc != 1.0) r /= sc;  // rescaled column (rare): an exact power of two
@@ -353,6 +443,9 @@ __device__ double pipe_form(double *W, int64_t rows, int64_t j, const double *x,
             ua = x0 - beta;
             coef = 1.0 / (beta * (beta - x0));
         }
+        const double tn = (sc == 1.0) ? nrm2 : __longlong_as_double(0x7FF8000000000000ll);
+        *unrm_sh = tn;
+        if (j >= 1) W[j - 1 + j * rows] = tn;
         ush[j] = ua;
         u0[j] = ua;
         W[j + j * rows] = ua;
@@ -380,6 +473,76 @@ __device__ __forceinline__ void pipe_apply(int64_t rows, int64_t j, const double
     __syncthreads();
 }
 
+// The owner of column j + 1 (j >= 1): y <- H_j y, then reflector j + 1 from
+// the updated column, with one CTA reduction for both.  The tail norm of the
+// updated column follows from sums over the old one (norm downdating):
+//   |y'_T|^2 = S_yy - 2 f S_uy + f^2 S_uu,   f = coef (u . y),   T = rows j+2..,
+// with S_uu = |u[j+1:]|^2 - u_{j+1}^2 (published with reflector j) and
+// S_uy = u . y - u_j y_j - u_{j+1} y_{j+1}.  Where the terms cancel (the
+// result below 1/16 of their magnitudes) or the norm would need rescaling, the
+// norm is recomputed from the updated column (pipe_form).
+__device__ double pipe_apply_form(double *W, int64_t rows, int64_t j, const double *ush, double coef, double unrm2,
+                                  double *y, double *ushn, double *u0, double *cf, unsigned long long *flag,
+                                  double *red, double *coef_sh, double *unrm_sh) {
+    __shared__ double s_f, s_beta;
+    __shared__ int s_redo;
+    const int tid = threadIdx.x;
+    const int64_t jn = j + 1;
+    double d = 0.0, syy = 0.0;
+    for (int64_t i = j + tid; i < rows; i += kPipeThreads) {
+        const double yi = y[i];
+        d = fma(ush[i], yi, d);
+        if (i > jn) syy = fma(yi, yi, syy);
+    }
+    double yj = 0.0, yn = 0.0, uj = 0.0, un = 0.0;  // head entries, read before the update
+    if (tid == 0) {
+        yj = y[j];
+        uj = ush[j];
+        yn = y[jn];
+        un = ush[jn];
+    }
+    pipe_sum2_t0(d, syy, red);
+    if (tid == 0) s_f = coef * d;
+    __syncthreads();
+    const double f = s_f;
+    for (int64_t i = j + tid; i < rows; i += kPipeThreads) {
+        const double v = fma(-f, ush[i], y[i]);
+        y[i] = v;
+        if (i > jn) {
+            ushn[i] = v;
+            W[i + jn * rows] = v;
+        }
+    }
+    if (tid == 0) {
+        const double x0 = fma(-f, un, yn);  // y'_{j+1}, as the update computes it
+        const double suy = (d - uj * yj) - un * yn, suu = unrm2 - un * un;
+        const double n2 = fma(f, fma(f, suu, -2.0 * suy), syy);
+        const double mag = syy + fabs(f) * fma(fabs(f), fabs(suu), 2.0 * fabs(suy));
+        bool ok = n2 >= 0.0625 * mag && mag <= 1e280 && (n2 == 0.0 || n2 >= 1e-280);
+        double beta = x0, ua = 0.0, cfn = 0.0;  // n2 == 0: H = I
+        if (ok && n2 != 0.0) ok = pipe_reflector(x0, n2, &beta, &ua, &cfn);
+        if (ok) {
+            ushn[jn] = ua;
+            u0[jn] = ua;
+            W[jn + jn * rows] = ua;
+            W[j + jn * rows] = n2;  // the tail-norm slot of reflector j + 1
+            cf[jn] = cfn;
+            *coef_sh = cfn;
+            *unrm_sh = n2;
+            s_beta = beta;
+        }
+        s_redo = ok ? 0 : 1;
+    }
+    __syncthreads();  // the update, the tail and the parameters are in place
+    if (s_redo) return pipe_form(W, rows, jn, y, ushn, u0, cf, flag, red, coef_sh, unrm_sh);
+    if (tid == 0) {
+        unsigned long long fw = (unsigned long long)__double_as_longlong(*coef_sh);
+        if (fw == kPipeEmpty) fw = 0x7FF8000000000000ull;
+        asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(flag + jn), "l"(fw) : "memory");
+    }
+    return s_beta;
+}
+
 __global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(double *W, int64_t rows, int64_t cols, int64_t nown_max,
                                                                double *u0, double *cf, int32_t *perm,
                                                                unsigned long long *flag, double *Rout,
@@ -388,8 +551,8 @@ __global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(double *W, int64
     double *own = sm;                          // nown_max * rows: owned columns
     double *ubuf = sm + nown_max * rows;       // 2 * rows: reflectors j (even/odd)
     double *beta = ubuf + 2 * rows;            // nown_max: R's diagonal of owned columns
-    __shared__ double red[kPipeThreads / 32 + 1];
-    __shared__ double s_coef[2];
+    __shared__ double red[2 * (kPipeThreads / 32) + 1];
+    __shared__ double s_coef[2], s_unrm[2];  // coefficient and tail norm^2 of reflectors j (by parity)
     __shared__ int s_ok;
     const int tid = threadIdx.x;
     const int64_t G = gridDim.x, me = blockIdx.x;
@@ -400,7 +563,7 @@ __global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(double *W, int64
     if (tid == 0) s_ok = 1;
     __syncthreads();
     if (me == 0 && steps > 0) {
-        const double b0 = pipe_form(W, rows, 0, own, ubuf, u0, cf, flag, red, &s_coef[0]);
+        const double b0 = pipe_form(W, rows, 0, own, ubuf, u0, cf, flag, red, &s_coef[0], &s_unrm[0]);
         if (tid == 0) beta[0] = b0;
         __syncthreads();
     }
@@ -422,6 +585,7 @@ __global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(double *W, int64
             __syncthreads();
             if (!s_ok) return;
             for (int64_t i = j + tid; i < rows; i += kPipeThreads) ush[i] = __ldcg(W + i + j * rows);
+            if (tid == 0) s_unrm[j & 1] = (j >= 1) ? __ldcg(W + j - 1 + j * rows) : 0.0;
             __syncthreads();
         }
         const double coef = s_coef[j & 1];
@@ -431,9 +595,16 @@ __global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(double *W, int64
         if (j + 1 < steps && (j + 1) % G == me) {
             const int64_t o = (j + 1 - me) / G;
             double *y = own + o * rows;
-            if (coef != 0.0) pipe_apply(rows, j, ush, coef, y, red);
-            const double bj = pipe_form(W, rows, j + 1, y, ubuf + ((j + 1) & 1) * rows, u0, cf, flag, red,
-                                        &s_coef[(j + 1) & 1]);
+            double *ushn = ubuf + ((j + 1) & 1) * rows;
+            double bj;
+            if (j >= 1) {
+                bj = pipe_apply_form(W, rows, j, ush, coef, s_unrm[j & 1], y, ushn, u0, cf, flag, red,
+                                     &s_coef[(j + 1) & 1], &s_unrm[(j + 1) & 1]);
+            } else {
+                if (coef != 0.0) pipe_apply(rows, j, ush, coef, y, red);
+                bj = pipe_form(W, rows, j + 1, y, ushn, u0, cf, flag, red, &s_coef[(j + 1) & 1],
+                               &s_unrm[(j + 1) & 1]);
+            }
             if (tid == 0) beta[o] = bj;
         }
         if (coef != 0.0)
@@ -870,63 +1041,62 @@ __device__ __forceinline__ bool ring_wait_cta(uint32_t mbar, uint32_t parity) {
     }
 }
 
-// FP32 image of x * 2^-shift from the IEEE fields (integer work, mantissa
-// truncated; zero, subnormal and below-range values give 0).
-__device__ __forceinline__ float f32_image(double x, int shift) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)((b >> 52) & 0x7FF), fe = e - shift - 1023 + 127;
-    if (e == 0 || fe <= 0) return 0.0f;
-    const unsigned int f = ((unsigned int)(b >> 32) & 0x80000000u) | ((unsigned int)min(fe, 254) << 23) |
-                           (unsigned int)((b >> 29) & 0x7FFFFFu);
-    return __uint_as_float(f);
-}
-// exact FP64 value of a normal or zero FP32 number (integer work)
-__device__ __forceinline__ double f64_of(float f) {
-    const unsigned int u = __float_as_uint(f);
-    const unsigned int e = (u >> 23) & 0xFF;
-    if (e == 0) return 0.0;
-    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
-                                 ((unsigned long long)(e - 127 + 1023) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
-    return __longlong_as_double((long long)b);
-}
-
-// Jacobi angle of a pair held as scaled columns x = d x~ (ring kernel):
-// a, b, g are |x~_p|^2, |x~_q|^2 and x~_p . x~_q; dp2, dq2, dpq the squares and
-// product of the scales (FP32).  The threshold test does not depend on the
-// scales.  t = tan(theta) needs only modest accuracy (the applied rotation is
-// orthogonal whatever t is), so it comes from FP32 images of the scaled sums.
 // FP32 value in [1, 2) of the leading 23 fraction bits of an IEEE double
 __device__ __forceinline__ float lead_mant(unsigned long long k) {
     return __uint_as_float(0x3F800000u | (unsigned int)((k >> 29) & 0x7FFFFFu));
 }
+// 2^k as an FP32 number (0 below the normal range; k <= 127)
+__device__ __forceinline__ float pow2f(int k) { return k < -126 ? 0.0f : __uint_as_float((unsigned int)(127 + k) << 23); }
 
-// The threshold test g^2 > tol2 a b (a, b >= 0) on the exponents and the
-// leading 23 fraction bits: no FP64 instruction on the common path, and no
-// overflow or underflow of the products.  It can differ from the exact
-// comparison only within a relative 2^-21 of the threshold.  Zero, subnormal
-// and non-finite operands take the FP64 form.
-__device__ __forceinline__ bool ring_above(double a, double b, double g, double tol2) {
-    const unsigned long long ka = (unsigned long long)__double_as_longlong(a);
-    const unsigned long long kb = (unsigned long long)__double_as_longlong(b);
-    const unsigned long long kg = (unsigned long long)__double_as_longlong(g) & 0x7FFFFFFFFFFFFFFFull;
+// The ring kernel's sums of a pair.  The squared norms need only modest
+// accuracy (no cancellation; they set the angle and the threshold test), so
+// they are FP32 sums of FP32 images: alpha = fa 4^(Ea - 1023) with Ea the
+// largest biased exponent of the column's entries, likewise beta.  The inner
+// product can cancel and stays FP64.
+struct RingSums {
+    float fa, fb;
+    int Ea, Eb;
+    double g;
+};
+
+// unbiased exponent of alpha = fa 4^(E - 1023) (fa > 0 normal)
+__device__ __forceinline__ int ring_lexp(float f, int E) { return (int)((__float_as_uint(f) >> 23) & 0xFF) - 127 + 2 * (E - 1023); }
+
+// The threshold test g^2 > tol2 alpha beta on the exponents and the leading 23
+// fraction bits: no FP64 instruction, and no overflow or underflow of the
+// products.  It can differ from the exact comparison only within a relative
+// 2^-20 of the threshold (plus the FP32 rounding of the norms).  A zero or
+// subnormal gamma, or a column whose entries are all zero or subnormal, is
+// below the threshold.
+__device__ __forceinline__ bool ring_above(const RingSums &r, double tol2) {
+    const unsigned long long kg = (unsigned long long)__double_as_longlong(r.g) & 0x7FFFFFFFFFFFFFFFull;
     const unsigned long long kt = (unsigned long long)__double_as_longlong(tol2);
-    const int ea = (int)(ka >> 52), eb = (int)(kb >> 52), eg = (int)(kg >> 52), et = (int)(kt >> 52);
-    if (ea == 0 || eb == 0 || eg == 0 || ea >= 0x7FF || eb >= 0x7FF || eg == 0x7FF)
-        return g != 0.0 && g * g > tol2 * (a * b);
-    // g^2 / (tol2 a b) = 2^k mg^2 / (mt ma mb), mg^2 in [1, 4), mt ma mb in [1, 8)
-    const int k = 2 * eg - ea - eb - et + 1023;
+    const int eg = (int)(kg >> 52), et = (int)(kt >> 52);
+    if (eg == 0) return false;
+    if (eg == 0x7FF) return kg == 0x7FF0000000000000ull;  // infinite gamma: rotate; NaN: no
+    const uint32_t ua = __float_as_uint(r.fa), ub = __float_as_uint(r.fb);
+    if (((ua >> 23) & 0xFF) == 0 || ((ub >> 23) & 0xFF) == 0) return false;
+    // gamma^2 / (tol2 alpha beta) = 2^k mg^2 / (mt ma mb), mg^2 in [1, 4), mt ma mb in [1, 8)
+    const int k = 2 * (eg - 1023) - ring_lexp(r.fa, r.Ea) - ring_lexp(r.fb, r.Eb) - (et - 1023);
     if (k >= 3) return true;
     if (k <= -2) return false;
-    const float mg = lead_mant(kg);
-    return (mg * mg) * __uint_as_float((unsigned int)(127 + k) << 23) > (lead_mant(kt) * lead_mant(ka)) * lead_mant(kb);
+    const float mg = lead_mant(kg), ma = __uint_as_float(0x3F800000u | (ua & 0x7FFFFFu)),
+                mb = __uint_as_float(0x3F800000u | (ub & 0x7FFFFFu));
+    return (mg * mg) * pow2f(k) > (lead_mant(kt) * ma) * mb;
 }
 
-__device__ __forceinline__ bool ring_angle(double a, double b, double g, double tol2, float dp2, float dq2,
-                                           float dpq, double dp, double dq, double *t_out) {
-    if (!ring_above(a, b, g, tol2)) return false;
-    const long long ka = __double_as_longlong(a), kb = __double_as_longlong(b);
-    const int shift = (int)(((ka > kb ? ka : kb) >> 52) & 0x7FF) - 1023;
-    const float a32 = f32_image(a, shift) * dp2, b32 = f32_image(b, shift) * dq2, g32 = f32_image(g, shift) * dpq;
+// Jacobi angle of a pair held as scaled columns x = d x~ (ring kernel): the
+// sums are those of x~_p, x~_q; dp2, dq2, dpq the squares and product of the
+// scales (FP32).  The threshold test does not depend on the scales.
+// t = tan(theta) needs only modest accuracy (the applied rotation is
+// orthogonal whatever t is), so it comes from FP32 images of the scaled sums.
+__device__ __forceinline__ bool ring_angle(const RingSums &r, double tol2, float dp2, float dq2, float dpq, double dp,
+                                           double dq, double *t_out) {
+    if (!ring_above(r, tol2)) return false;
+    const int la = ring_lexp(r.fa, r.Ea), lb = ring_lexp(r.fb, r.Eb), shift = max(la, lb);
+    const float a32 = r.fa * pow2f(2 * (r.Ea - 1023) - shift) * dp2;
+    const float b32 = r.fb * pow2f(2 * (r.Eb - 1023) - shift) * dq2;
+    const float g32 = f32_image(r.g, shift) * dpq;
     if (fabsf(g32) >= 1e-30f) {
         const float z = __fdividef(b32 - a32, 2.0f * g32), az = fabsf(z);
         float t32;
@@ -940,7 +1110,8 @@ __device__ __forceinline__ bool ring_angle(double a, double b, double g, double 
         return true;
     }
     // tiny angle: t ~ gamma / (beta - alpha) with the true (scaled) sums (rare)
-    const double al = a * dp * dp, be = b * dq * dq, ga = g * dp * dq, d = be - al;
+    const double a = ldexp(f64_of(r.fa), 2 * (r.Ea - 1023)), b = ldexp(f64_of(r.fb), 2 * (r.Eb - 1023));
+    const double al = a * dp * dp, be = b * dq * dq, ga = r.g * dp * dq, d = be - al;
     *t_out = (d == 0.0) ? (ga > 0.0 ? 1.0 : -1.0) : ga / d;
     return true;
 }
@@ -1042,6 +1213,9 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
     __shared__ __align__(16) double2 sbuf[kRingC];
     __shared__ __align__(8) unsigned long long mbx[kRingC], mbv[kRingC], mbs[kRingC], mbr[kRingC], mbf;
     __shared__ double red[16];
+    __shared__ double rg[4];          // per X row warp: x~_p . x~_q
+    __shared__ float2 rab[4];         // per X row warp: FP32 images of |x~_p|^2, |x~_q|^2
+    __shared__ uint32_t rexp[4];      // per X row warp: (E_p << 16) | E_q, the images' exponents
     __shared__ double par[kRingC][3];
     __shared__ double s_fin[2];
     __shared__ volatile int s_abort;
@@ -1186,21 +1360,33 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
                     const double ee = __shfl_sync(0xffffffffu, sv, lane == 0 ? 2 : 3);
                     const double rr = (lane == 0 ? dQ : dP) * ee;
                     const float fP = f32_image(dP, 0), fQ = f32_image(dQ, 0);
-                    xbar();  // the row warps' partial sums of round j are in red
-                    // (red[v4] + red[v4+1]) + (red[v4+2] + red[v4+3]): lanes 0-5, then 0-2
-                    double hsum = 0.0;
-                    if (lane < 6) {
-                        const int b = (lane >> 1) * 4 + 2 * (lane & 1);
-                        hsum = red[b] + red[b + 1];
+                    xbar();  // the row warps' sums of round j are in rg, rab, rexp
+                    // lanes 0-3 hold row warp w = lane; sums in the order (w0 + w1) + (w2 + w3)
+                    RingSums rs;
+                    {
+                        const bool lw = lane < 4;
+                        const double gw = lw ? rg[lane] : 0.0;
+                        const float2 abw = lw ? rab[lane] : make_float2(0.0f, 0.0f);
+                        const uint32_t ew = lw ? rexp[lane] : 0u;
+                        uint32_t em = __vmaxu2(ew, __shfl_xor_sync(0xffffffffu, ew, 1));
+                        em = __vmaxu2(em, __shfl_xor_sync(0xffffffffu, em, 2));
+                        const int Ea = (int)(em >> 16), Eb = (int)(em & 0xFFFFu);
+                        float fa = abw.x * pow2f(2 * ((int)(ew >> 16) - Ea));
+                        float fb = abw.y * pow2f(2 * ((int)(ew & 0xFFFFu) - Eb));
+                        double gs = gw + __shfl_xor_sync(0xffffffffu, gw, 1);
+                        fa += __shfl_xor_sync(0xffffffffu, fa, 1);
+                        fb += __shfl_xor_sync(0xffffffffu, fb, 1);
+                        gs += __shfl_xor_sync(0xffffffffu, gs, 2);
+                        fa += __shfl_xor_sync(0xffffffffu, fa, 2);
+                        fb += __shfl_xor_sync(0xffffffffu, fb, 2);
+                        rs.g = __shfl_sync(0xffffffffu, gs, 0);
+                        rs.fa = __shfl_sync(0xffffffffu, fa, 0);
+                        rs.fb = __shfl_sync(0xffffffffu, fb, 0);
+                        rs.Ea = __shfl_sync(0xffffffffu, Ea, 0);
+                        rs.Eb = __shfl_sync(0xffffffffu, Eb, 0);
                     }
-                    const double h0 = __shfl_sync(0xffffffffu, hsum, (2 * lane) & 31);
-                    const double h1 = __shfl_sync(0xffffffffu, hsum, (2 * lane + 1) & 31);
-                    double vs = 0.0;
-                    if (lane < 3) vs = h0 + h1;
-                    const double al = __shfl_sync(0xffffffffu, vs, 0), be = __shfl_sync(0xffffffffu, vs, 1),
-                                 ga = __shfl_sync(0xffffffffu, vs, 2);
                     double tn = 0.0;
-                    const bool rot = ring_angle(al, be, ga, tol2, fP * fP, fQ * fQ, fP * fQ, dP, dQ, &tn);
+                    const bool rot = ring_angle(rs, tol2, fP * fP, fQ * fQ, fP * fQ, dP, dQ, &tn);
                     const double mn = tn * rr;  // lane 0: mu (x~_p -= mu x~_q), lane 1: nu (x~_q += nu x~_p)
                     const double nu = __shfl_sync(0xffffffffu, mn, 1);
                     if (lane == 0) {
@@ -1212,14 +1398,27 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
                                      : "memory");
                     }
                     xbar();  // par[j] is visible to the X row warps
-                    if (rot) {  // new scales: d <- c d, e <- e / c, c = 1/sqrt(1 + t^2)
+                    if (rot) {  // new scales: d <- c d, e <- e / c, c = (1 + t^2)^(-1/2)
                         ++local;
-                        const double tt = fma(tn, tn, 1.0), h = -0.5 * tt;
-                        double c = f64_of(rsqrtf(f32_image(tt, 0)));
-                        c = c * fma(h, c * c, 1.5);
-                        c = c * fma(h, c * c, 1.5);
-                        const double ic = tt * c;
-                        sv *= (lane < 2) ? c : ic;
+                        const double u = tn * tn;
+                        double m;
+                        if (u < 0x1p-12) {
+                            // binomial series to u^4 (the next term is below 2^-62):
+                            // (1 + u)^(-1/2) in lanes 0-1, (1 + u)^(1/2) in lanes 2-3
+                            const bool cl = lane < 2;
+                            double q = cl ? 35.0 / 128.0 : -5.0 / 128.0;
+                            q = fma(u, q, cl ? -5.0 / 16.0 : 1.0 / 16.0);
+                            q = fma(u, q, cl ? 3.0 / 8.0 : -1.0 / 8.0);
+                            q = fma(u, q, cl ? -0.5 : 0.5);
+                            m = fma(u, q, 1.0);
+                        } else {  // FP32 seed and two Newton steps for the inverse square root
+                            const double tt = 1.0 + u, h = -0.5 * tt;
+                            double c = f64_of(rsqrtf(f32_image(tt, 0)));
+                            c = c * fma(h, c * c, 1.5);
+                            c = c * fma(h, c * c, 1.5);
+                            m = (lane < 2) ? c : tt * c;
+                        }
+                        sv *= m;
                     }
                     if (j < kRingC - 1) {
                         const double sQ = __shfl_sync(0xffffffffu, sv, 1), eQ = __shfl_sync(0xffffffffu, sv, 3);
@@ -1247,7 +1446,27 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
                             q0 = in.x;
                             q1 = in.y;
                         }
-                        ring_partials(fma(p1, p1, p0 * p0), fma(q1, q1, q0 * q0), fma(p1, q1, p0 * q0), t, red);
+                        // FP32 images at the warp's largest exponent of each column (the
+                        // largest entry lands in [1, 2)), FP64 inner product
+                        uint32_t e2 = (max(exp_field(p0), exp_field(p1)) << 16) | max(exp_field(q0), exp_field(q1));
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) e2 = __vmaxu2(e2, __shfl_xor_sync(0xffffffffu, e2, o));
+                        const int sp = (int)(e2 >> 16) - 1023, sq = (int)(e2 & 0xFFFFu) - 1023;
+                        const float a0 = f32_image(p0, sp), a1 = f32_image(p1, sp);
+                        const float b0 = f32_image(q0, sq), b1 = f32_image(q1, sq);
+                        float fa = fmaf(a1, a1, a0 * a0), fb = fmaf(b1, b1, b0 * b0);
+                        double gg = fma(p1, q1, p0 * q0);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {  // every lane ends with the same sums
+                            gg += __shfl_xor_sync(0xffffffffu, gg, o);
+                            fa += __shfl_xor_sync(0xffffffffu, fa, o);
+                            fb += __shfl_xor_sync(0xffffffffu, fb, o);
+                        }
+                        if ((t & 31) == 0) {
+                            rg[t >> 5] = gg;
+                            rab[t >> 5] = make_float2(fa, fb);
+                            rexp[t >> 5] = e2;
+                        }
                         xbar();  // sums to the scalar warp
                         xbar();  // par[j] from the scalar warp
                     } else {
