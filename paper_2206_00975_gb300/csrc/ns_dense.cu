@@ -60,6 +60,7 @@ DenseWork dense_carve(Carver &c, int64_t s, int64_t n) {
     w.V = c.take<double>((size_t)(n * n));
     w.sigma = c.take<double>((size_t)n);
     w.L = c.take<double>((size_t)(n * n));
+    w.U = c.take<double>((size_t)(s * n));
     w.perm = c.take<int32_t>((size_t)n);
     w.pivslot = c.take<unsigned long long>((size_t)n + 1);
     w.bar = c.take<unsigned int>(kBarWords);
@@ -288,15 +289,30 @@ __device__ __forceinline__ uint32_t exp_field(double x) {
 // diagonal, u0[j], cf[j], R[j, j] = beta) is formed by the owner of column j
 // as soon as reflectors 0..j-1 have reached that column, written to global
 // memory and announced by flag[j], which carries the coefficient itself (the
-// bits of cf[j]; all ones = not yet formed), with u0[j] also stored in the
-// diagonal slot of W: a consumer needs one acquire and one read of W's
-// column.  The owner of column j + 1 applies
+// bits of cf[j]; all ones = not yet formed).  The reflectors go to U (same
+// layout as W: tail below the diagonal, u0[j] on it, |u[j+1:]|^2 in the slot
+// above it), which starts filled with all-ones words: the owner of column
+// j + 1, the only consumer on the critical path, polls its rows of U[:, j]
+// directly instead of the flag and then the data; every other CTA takes the
+// flag (acquire) and then reads U.  The owner of column j + 1 applies
 // reflector j to that column before its other columns (look-ahead), so the
 // chain from one reflector to the next runs through one CTA and one flag;
 // every other CTA only waits for the flags of the reflectors it applies.
 constexpr int kPipeThreads = 256;
 
-constexpr unsigned long long kPipeEmpty = ~0ull;  // flag word of a reflector not formed yet
+constexpr unsigned long long kPipeEmpty = ~0ull;  // flag and U words of a reflector not formed yet
+
+// publish one FP64 word of a reflector (never the all-ones pattern)
+__device__ __forceinline__ void st_pub(double *p, double v) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    if (b == kPipeEmpty) b = 0x7FF8000000000000ull;
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(b) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const double *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 
 __device__ __forceinline__ unsigned long long ld_acquire_flag(const unsigned long long *p) {
     unsigned long long v;
@@ -400,9 +416,9 @@ __device__ __forceinline__ bool pipe_reflector(double x0, double nrm2, double *b
 // publishes the tail, u0, cf and the flag; leaves u (u0 at index j) in ush,
 // the coefficient in *coef_sh and returns beta (every thread).  The scalar
 // chain (square root, reciprocal) runs in thread 0 only: FP64 is scarce.
-// The tail norm^2 |u[j+1:]|^2 goes to *unrm_sh and, for j >= 1, to the unused
-// slot W[j-1, j] for the consumers (NaN when the column was rescaled).
-__device__ double pipe_form(double *W, int64_t rows, int64_t j, const double *x, double *ush, double *u0, double *cf,
+// The tail norm^2 |u[j+1:]|^2 goes to *unrm_sh and, for j >= 1, to the slot
+// U[j-1, j] for the consumers (NaN when the column was rescaled).
+__device__ double pipe_form(double *U, int64_t rows, int64_t j, const double *x, double *ush, double *u0, double *cf,
                             unsigned long long *flag, double *red, double *coef_sh, double *unrm_sh) {
     __shared__ double s_par[2];
     const int tid = threadIdx.x;
@@ -426,7 +442,7 @@ __device__ double pipe_form(double *W, int64_t rows, int64_t j, const double *x,
     for (int64_t i = j + 1 + tid; i < rows; i += kPipeThreads) {
         const double v = x[i];
         ush[i] = v;
-        W[i + j * rows] = v;
+        st_pub(U + i + j * rows, v);
     }
     if (tid == 0) {
         const double x0 = x[j];
@@ -445,10 +461,10 @@ __device__ double pipe_form(double *W, int64_t rows, int64_t j, const double *x,
         }
         const double tn = (sc == 1.0) ? nrm2 : __longlong_as_double(0x7FF8000000000000ll);
         *unrm_sh = tn;
-        if (j >= 1) W[j - 1 + j * rows] = tn;
+        if (j >= 1) st_pub(U + j - 1 + j * rows, tn);
         ush[j] = ua;
         u0[j] = ua;
-        W[j + j * rows] = ua;
+        st_pub(U + j + j * rows, ua);
         cf[j] = coef;
         *coef_sh = coef;
         s_par[0] = beta;
@@ -481,7 +497,7 @@ __device__ __forceinline__ void pipe_apply(int64_t rows, int64_t j, const double
 // S_uy = u . y - u_j y_j - u_{j+1} y_{j+1}.  Where the terms cancel (the
 // result below 1/16 of their magnitudes) or the norm would need rescaling, the
 // norm is recomputed from the updated column (pipe_form).
-__device__ double pipe_apply_form(double *W, int64_t rows, int64_t j, const double *ush, double coef, double unrm2,
+__device__ double pipe_apply_form(double *U, int64_t rows, int64_t j, const double *ush, double coef, double unrm2,
                                   double *y, double *ushn, double *u0, double *cf, unsigned long long *flag,
                                   double *red, double *coef_sh, double *unrm_sh) {
     __shared__ double s_f, s_beta;
@@ -510,7 +526,7 @@ __device__ double pipe_apply_form(double *W, int64_t rows, int64_t j, const doub
         y[i] = v;
         if (i > jn) {
             ushn[i] = v;
-            W[i + jn * rows] = v;
+            st_pub(U + i + jn * rows, v);
         }
     }
     if (tid == 0) {
@@ -524,8 +540,8 @@ __device__ double pipe_apply_form(double *W, int64_t rows, int64_t j, const doub
         if (ok) {
             ushn[jn] = ua;
             u0[jn] = ua;
-            W[jn + jn * rows] = ua;
-            W[j + jn * rows] = n2;  // the tail-norm slot of reflector j + 1
+            st_pub(U + jn + jn * rows, ua);
+            st_pub(U + j + jn * rows, n2);  // the tail-norm slot of reflector j + 1
             cf[jn] = cfn;
             *coef_sh = cfn;
             *unrm_sh = n2;
@@ -534,7 +550,7 @@ __device__ double pipe_apply_form(double *W, int64_t rows, int64_t j, const doub
         s_redo = ok ? 0 : 1;
     }
     __syncthreads();  // the update, the tail and the parameters are in place
-    if (s_redo) return pipe_form(W, rows, jn, y, ushn, u0, cf, flag, red, coef_sh, unrm_sh);
+    if (s_redo) return pipe_form(U, rows, jn, y, ushn, u0, cf, flag, red, coef_sh, unrm_sh);
     if (tid == 0) {
         unsigned long long fw = (unsigned long long)__double_as_longlong(*coef_sh);
         if (fw == kPipeEmpty) fw = 0x7FF8000000000000ull;
@@ -543,8 +559,8 @@ __device__ double pipe_apply_form(double *W, int64_t rows, int64_t j, const doub
     return s_beta;
 }
 
-__global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(double *W, int64_t rows, int64_t cols, int64_t nown_max,
-                                                               double *u0, double *cf, int32_t *perm,
+__global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(const double *W, double *U, int64_t rows,
+                                                               int64_t cols, int64_t nown_max, double *u0, double *cf,
                                                                unsigned long long *flag, double *Rout,
                                                                int32_t *status) {
     extern __shared__ double sm[];
@@ -555,7 +571,7 @@ __global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(double *W, int64
     __shared__ double s_coef[2], s_unrm[2];  // coefficient and tail norm^2 of reflectors j (by parity)
     __shared__ int s_ok;
     const int tid = threadIdx.x;
-    const int64_t G = gridDim.x, me = blockIdx.x;
+    const int G = (int)gridDim.x, me = (int)blockIdx.x;
     const int64_t nown = (cols - me + G - 1) / G;
     const int64_t steps = rows < cols ? rows : cols;
     for (int64_t o = 0; o < nown; ++o)
@@ -563,57 +579,87 @@ __global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(double *W, int64
     if (tid == 0) s_ok = 1;
     __syncthreads();
     if (me == 0 && steps > 0) {
-        const double b0 = pipe_form(W, rows, 0, own, ubuf, u0, cf, flag, red, &s_coef[0], &s_unrm[0]);
+        const double b0 = pipe_form(U, rows, 0, own, ubuf, u0, cf, flag, red, &s_coef[0], &s_unrm[0]);
         if (tid == 0) beta[0] = b0;
         __syncthreads();
     }
+    int jm = 0;                                // j mod G: the CTA that formed reflector j
+    int64_t o_first = (me > 0) ? 0 : 1;        // first owned column (index into own) after column j
     for (int64_t j = 0; j < steps; ++j) {
         double *ush = ubuf + (j & 1) * rows;
-        if (j % G != me) {  // wait for reflector j, then fetch it
-            if (tid == 0) {
-                const long long t0 = clock64();
-                unsigned long long fw;
-                while ((fw = ld_acquire_flag(flag + j)) == kPipeEmpty) {
-                    if (clock64() - t0 > (1ll << 32)) {  // ~2 s; a healthy pipeline waits microseconds
-                        set_status(status, NS_ERR_TIMEOUT);
-                        s_ok = 0;
-                        break;
-                    }
+        const int jn_owner = (jm + 1 == G) ? 0 : jm + 1;
+        const bool mine = (j + 1 < steps) && jn_owner == me;  // this CTA forms reflector j + 1
+        if (jm != me) {
+            const long long t0 = clock64();
+            if (mine) {  // poll this thread's rows of U[:, j] (and the scalars) directly
+                bool late = false;
+                for (int64_t i = j + tid; i < rows && !late; i += kPipeThreads) {
+                    unsigned long long b;
+                    while ((b = ld_relaxed_u64(U + i + j * rows)) == kPipeEmpty)
+                        if (clock64() - t0 > (1ll << 32)) {  // ~2 s; a healthy pipeline waits microseconds
+                            late = true;
+                            break;
+                        }
+                    ush[i] = __longlong_as_double((long long)b);
                 }
-                s_coef[j & 1] = __longlong_as_double((long long)fw);
+                if (tid == 0 && !late) {
+                    unsigned long long fw, nw = 0;
+                    while ((fw = ld_acquire_flag(flag + j)) == kPipeEmpty)
+                        if (clock64() - t0 > (1ll << 32)) {
+                            late = true;
+                            break;
+                        }
+                    while (!late && j >= 1 && (nw = ld_relaxed_u64(U + j - 1 + j * rows)) == kPipeEmpty)
+                        if (clock64() - t0 > (1ll << 32)) late = true;
+                    s_coef[j & 1] = __longlong_as_double((long long)fw);
+                    s_unrm[j & 1] = __longlong_as_double((long long)nw);
+                }
+                if (late) {
+                    set_status(status, NS_ERR_TIMEOUT);
+                    s_ok = 0;
+                }
+                __syncthreads();
+                if (!s_ok) return;
+            } else {  // wait for flag j (acquire), then read U[:, j]
+                if (tid == 0) {
+                    unsigned long long fw;
+                    while ((fw = ld_acquire_flag(flag + j)) == kPipeEmpty) {
+                        if (clock64() - t0 > (1ll << 32)) {
+                            set_status(status, NS_ERR_TIMEOUT);
+                            s_ok = 0;
+                            break;
+                        }
+                    }
+                    s_coef[j & 1] = __longlong_as_double((long long)fw);
+                }
+                __syncthreads();
+                if (!s_ok) return;
+                for (int64_t i = j + tid; i < rows; i += kPipeThreads) ush[i] = __ldcg(U + i + j * rows);
+                __syncthreads();
             }
-            __syncthreads();
-            if (!s_ok) return;
-            for (int64_t i = j + tid; i < rows; i += kPipeThreads) ush[i] = __ldcg(W + i + j * rows);
-            if (tid == 0) s_unrm[j & 1] = (j >= 1) ? __ldcg(W + j - 1 + j * rows) : 0.0;
-            __syncthreads();
         }
         const double coef = s_coef[j & 1];
-        // owned columns c > j; the owner of column j + 1 takes it first and
-        // forms reflector j + 1 right away
-        const int64_t o_first = (j + 1 - me + G - 1) / G;  // first owned column index > j
-        if (j + 1 < steps && (j + 1) % G == me) {
-            const int64_t o = (j + 1 - me) / G;
-            double *y = own + o * rows;
+        // the owner of column j + 1 takes it first and forms reflector j + 1
+        // right away (look-ahead), then applies reflector j to its other columns
+        if (mine) {
+            double *y = own + o_first * rows;
             double *ushn = ubuf + ((j + 1) & 1) * rows;
             double bj;
             if (j >= 1) {
-                bj = pipe_apply_form(W, rows, j, ush, coef, s_unrm[j & 1], y, ushn, u0, cf, flag, red,
+                bj = pipe_apply_form(U, rows, j, ush, coef, s_unrm[j & 1], y, ushn, u0, cf, flag, red,
                                      &s_coef[(j + 1) & 1], &s_unrm[(j + 1) & 1]);
             } else {
                 if (coef != 0.0) pipe_apply(rows, j, ush, coef, y, red);
-                bj = pipe_form(W, rows, j + 1, y, ushn, u0, cf, flag, red, &s_coef[(j + 1) & 1],
+                bj = pipe_form(U, rows, j + 1, y, ushn, u0, cf, flag, red, &s_coef[(j + 1) & 1],
                                &s_unrm[(j + 1) & 1]);
             }
-            if (tid == 0) beta[o] = bj;
+            if (tid == 0) beta[o_first] = bj;
         }
         if (coef != 0.0)
-            for (int64_t o = o_first; o < nown; ++o) {
-                const int64_t c = me + o * G;
-                if (c == j + 1 && j + 1 < steps) continue;
-                pipe_apply(rows, j, ush, coef, own + o * rows, red);
-            }
+            for (int64_t o = o_first + (mine ? 1 : 0); o < nown; ++o) pipe_apply(rows, j, ush, coef, own + o * rows, red);
+        if (jn_owner == me) ++o_first;
         __syncthreads();
+        if (++jm == G) jm = 0;
     }
     // R (column order as stored in W)
     for (int64_t o = 0; o < nown; ++o) {
@@ -1738,7 +1784,7 @@ static size_t pipe_smem(int64_t rows, int64_t cols) {
 }
 static bool pipe_fits(int64_t rows, int64_t cols) { return pipe_smem(rows, cols) <= 200 * 1024 && cols <= 4096; }
 
-static bool launch_hqr_pipe(double *W, int64_t rows, int64_t cols, double *u0, double *cf, int32_t *perm,
+static bool launch_hqr_pipe(const double *W, double *U, int64_t rows, int64_t cols, double *u0, double *cf,
                             unsigned long long *flags, double *Rout, int32_t *status, cudaStream_t st,
                             cudaError_t *err) {
     int64_t G = cols < sm_count() ? cols : sm_count();
@@ -1748,10 +1794,12 @@ static bool launch_hqr_pipe(double *W, int64_t rows, int64_t cols, double *u0, d
     if (!pipe_fits(rows, cols)) return false;
     *err = cudaMemsetAsync(flags, 0xFF, sizeof(unsigned long long) * (size_t)cols, st);  // kPipeEmpty
     if (*err != cudaSuccess) return true;
+    *err = cudaMemsetAsync(U, 0xFF, sizeof(double) * (size_t)(rows * cols), st);  // kPipeEmpty
+    if (*err != cudaSuccess) return true;
     *err = cudaFuncSetAttribute(hqr_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (*err != cudaSuccess) return true;
     int64_t nown_ = nown;
-    void *args[] = {&W, &rows, &cols, &nown_, &u0, &cf, &perm, &flags, &Rout, &status};
+    void *args[] = {&W, &U, &rows, &cols, &nown_, &u0, &cf, &flags, &Rout, &status};
     *err = cudaLaunchCooperativeKernel((const void *)hqr_pipe_kernel, (int)G, kPipeThreads, args, smem, st);
     return true;
 }
@@ -1809,7 +1857,7 @@ cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k
         dim3 grid((unsigned)((s + 255) / 256 < 8 ? (s + 255) / 256 : 8), (unsigned)(n < 1024 ? n : 1024));
         permute_cols_kernel<<<grid, 256, 0, st>>>(SA, s, n, w.perm, w.W);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        launch_hqr_pipe(w.W, s, n, u0a, cfa, w.perm, flags, w.X, status, st, &e);
+        launch_hqr_pipe(w.W, w.U, s, n, u0a, cfa, flags, w.X, status, st, &e);
     } else {
         e = cudaMemcpyAsync(w.W, SA, sizeof(double) * (size_t)(s * n), cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
@@ -1823,8 +1871,11 @@ cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     int32_t *perm2 = (int32_t *)w.sigma;  // identity permutation of the unpivoted QR (unused)
-    if (!launch_hqr_pipe(w.L, n, n, u0b, cfb, perm2, flags, w.V, status, st, &e))
+    const double *Lq = w.U;  // the reflectors of the second QR
+    if (!launch_hqr_pipe(w.L, w.U, n, n, u0b, cfb, flags, w.V, status, st, &e)) {
         e = launch_hqr(w.L, n, n, 0, u0b, cfb, perm2, w.pivslot, w.V, bar, st);
+        Lq = w.L;
+    }
     if (e != cudaSuccess) return e;
     // 3. X = R2^T; Jacobi on X (V receives Vx)
     r2t_kernel<<<(unsigned)((n * n + 255) / 256), 256, 0, st>>>(w.V, n, w.X);
@@ -1847,7 +1898,7 @@ cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k
         e = cudaFuncSetAttribute(apply_q2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         const int64_t blocks = n < sm_count() * 4 ? n : sm_count() * 4;
-        apply_q2_kernel<<<(unsigned)blocks, kDenseThreads, smem, st>>>(w.L, u0b, cfb, w.perm, w.V, n, w.W);
+        apply_q2_kernel<<<(unsigned)blocks, kDenseThreads, smem, st>>>(Lq, u0b, cfb, w.perm, w.V, n, w.W);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // 5. extraction (and the save buffers)

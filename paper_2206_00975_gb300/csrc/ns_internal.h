@@ -123,7 +123,8 @@ struct DenseWork {
     double *X;        // n x n: R, then X = R2^T rotated into U Sigma
     double *V;        // n x n: R2, then the accumulated rotations Vx
     double *sigma;    // n
-    double *L;        // n x n: R^T, then the reflectors of its QR
+    double *L;        // n x n: R^T, then the reflectors of its QR (coop fallback)
+    double *U;        // s x n: reflectors published by the pipelined QRs
     int32_t *perm;    // n: column pivots of the first QR
     unsigned long long *pivslot;  // n + 1: pivot candidates (atomic max)
     unsigned int *bar;  // grid barrier words (2), rotation counters (64), check flags (64)
