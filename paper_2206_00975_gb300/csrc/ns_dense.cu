@@ -823,34 +823,41 @@ __device__ __forceinline__ bool rotation(double alpha, double beta, double gamma
 }
 
 // Barrier-free convergence check over all n(n-1)/2 pairs of the columns of X
-// (one warp per pair, all CTAs of the grid).  Returns 1 if the check ran and
-// no pair needs a rotation, 0 if some pair does, -1 if a grid barrier timed out.
-__device__ int jacobi_check_pass(const double *X, int64_t n, double tol2, GridBarrier bar, unsigned int *flag) {
+// (all CTAs of the grid; nrm: n doubles of scratch).  Returns 1 if the check
+// ran and no pair needs a rotation, 0 if some pair does, -1 if a grid barrier
+// timed out.
+__device__ int jacobi_check_pass(const double *X, int64_t n, double tol2, GridBarrier bar, unsigned int *flag,
+                                 double *nrm) {
+    // column norms once (one warp per column, into nrm), then one warp per
+    // pair for the inner product only; pairs are indexed p-major and found by
+    // an integer binary search
     if (!grid_sync(bar)) return -1;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    const int64_t G = gridDim.x, me = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = blockDim.x >> 5, gw = (int64_t)blockIdx.x * nw + (threadIdx.x >> 5), Wn = gridDim.x * nw;
+    for (int64_t c = gw; c < n; c += Wn) {
+        double a = 0.0;
+        for (int64_t i = lane; i < n; i += 32) {
+            const double x = __ldcg(X + i + c * n);
+            a = fma(x, x, a);
+        }
+        a = warp_sum(a);
+        if (lane == 0) nrm[c] = a;
+    }
+    if (!grid_sync(bar)) return -1;
     const int64_t total = n * (n - 1) / 2;
     int any = 0;
-    for (int64_t pi = me * nw + wid; pi < total; pi += G * nw) {
-        int64_t p = (int64_t)((2.0 * n - 1 - sqrt((2.0 * n - 1) * (2.0 * n - 1) - 8.0 * pi)) / 2.0);
-        if (p < 0) p = 0;
-        while (p > 0 && p * (2 * n - p - 1) / 2 > pi) --p;
-        while ((p + 1) * (2 * n - p - 2) / 2 <= pi) ++p;
-        const int64_t q = pi - p * (2 * n - p - 1) / 2 + p + 1;
-        double a = 0.0, b = 0.0, g = 0.0;
-        for (int64_t i = lane; i < n; i += 32) {
-            const double x = __ldcg(X + i + p * n), y = __ldcg(X + i + q * n);
-            a = fma(x, x, a);
-            b = fma(y, y, b);
-            g = fma(x, y, g);
+    for (int64_t pi = gw; pi < total && !any; pi += Wn) {
+        int64_t lo = 0, hi = n - 1;  // pairs before row p: p (2n - p - 1) / 2
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (mid * (2 * n - mid - 1) / 2 <= pi) lo = mid;
+            else hi = mid;
         }
-        a = __shfl_sync(0xffffffffu, warp_sum(a), 0);
-        b = __shfl_sync(0xffffffffu, warp_sum(b), 0);
-        g = __shfl_sync(0xffffffffu, warp_sum(g), 0);
-        if (g != 0.0 && g * g > tol2 * a * b) {
-            any = 1;
-            break;
-        }
+        const int64_t p = lo, q = pi - p * (2 * n - p - 1) / 2 + p + 1;
+        double g = 0.0;
+        for (int64_t i = lane; i < n; i += 32) g = fma(__ldcg(X + i + p * n), __ldcg(X + i + q * n), g);
+        g = warp_sum(g);
+        if (g != 0.0 && g * g > tol2 * __ldcg(nrm + p) * __ldcg(nrm + q)) any = 1;
     }
     if (any && lane == 0) atomicAdd(flag, 1u);
     if (!grid_sync(bar)) return -1;
@@ -912,7 +919,7 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_coop_kernel(double *X, d
     for (int sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
         if (prev_rot < (unsigned int)kCheckBelow) {
             ++check_passes;
-            const int c = jacobi_check_pass(X, n, tol2, bar, checkflag + sweep);
+            const int c = jacobi_check_pass(X, n, tol2, bar, checkflag + sweep, sigma);
             if (c < 0) return;
             if (c == 1) {
                 converged = true;
@@ -1109,50 +1116,45 @@ struct RingSums {
 __device__ __forceinline__ int ring_lexp(float f, int E) { return (int)((__float_as_uint(f) >> 23) & 0xFF) - 127 + 2 * (E - 1023); }
 
 // The threshold test g^2 > tol2 alpha beta on the exponents and the leading 23
-// fraction bits: no FP64 instruction, and no overflow or underflow of the
-// products.  It can differ from the exact comparison only within a relative
-// 2^-20 of the threshold (plus the FP32 rounding of the norms).  A zero or
-// subnormal gamma, or a column whose entries are all zero or subnormal, is
-// below the threshold.
+// fraction bits: no FP64 instruction, no overflow or underflow of the
+// products, and no branch (it runs beside the angle on the scalar warp's
+// critical path).  It can differ from the exact comparison only within a
+// relative 2^-20 of the threshold (plus the FP32 rounding of the norms).  A
+// zero or subnormal gamma, or a column whose entries are all zero or
+// subnormal, is below the threshold; an infinite gamma is above it.
 __device__ __forceinline__ bool ring_above(const RingSums &r, double tol2) {
     const unsigned long long kg = (unsigned long long)__double_as_longlong(r.g) & 0x7FFFFFFFFFFFFFFFull;
     const unsigned long long kt = (unsigned long long)__double_as_longlong(tol2);
     const int eg = (int)(kg >> 52), et = (int)(kt >> 52);
-    if (eg == 0) return false;
-    if (eg == 0x7FF) return kg == 0x7FF0000000000000ull;  // infinite gamma: rotate; NaN: no
     const uint32_t ua = __float_as_uint(r.fa), ub = __float_as_uint(r.fb);
-    if (((ua >> 23) & 0xFF) == 0 || ((ub >> 23) & 0xFF) == 0) return false;
+    const bool special = eg == 0 || eg == 0x7FF || ((ua >> 23) & 0xFF) == 0 || ((ub >> 23) & 0xFF) == 0;
     // gamma^2 / (tol2 alpha beta) = 2^k mg^2 / (mt ma mb), mg^2 in [1, 4), mt ma mb in [1, 8)
     const int k = 2 * (eg - 1023) - ring_lexp(r.fa, r.Ea) - ring_lexp(r.fb, r.Eb) - (et - 1023);
-    if (k >= 3) return true;
-    if (k <= -2) return false;
     const float mg = lead_mant(kg), ma = __uint_as_float(0x3F800000u | (ua & 0x7FFFFFu)),
                 mb = __uint_as_float(0x3F800000u | (ub & 0x7FFFFFu));
-    return (mg * mg) * pow2f(k) > (lead_mant(kt) * ma) * mb;
+    const bool cmp = k >= 3 || (k > -2 && (mg * mg) * pow2f(min(k, 2)) > (lead_mant(kt) * ma) * mb);
+    return special ? kg == 0x7FF0000000000000ull : cmp;
 }
 
 // Jacobi angle of a pair held as scaled columns x = d x~ (ring kernel): the
 // sums are those of x~_p, x~_q; dp2, dq2, dpq the squares and product of the
 // scales (FP32).  The threshold test does not depend on the scales.
 // t = tan(theta) needs only modest accuracy (the applied rotation is
-// orthogonal whatever t is), so it comes from FP32 images of the scaled sums.
+// orthogonal whatever t is), so it comes from FP32 images of the scaled sums;
+// it is evaluated unconditionally, beside the threshold test.
 __device__ __forceinline__ bool ring_angle(const RingSums &r, double tol2, float dp2, float dq2, float dpq, double dp,
                                            double dq, double *t_out) {
-    if (!ring_above(r, tol2)) return false;
+    const bool above = ring_above(r, tol2);
     const int la = ring_lexp(r.fa, r.Ea), lb = ring_lexp(r.fb, r.Eb), shift = max(la, lb);
     const float a32 = r.fa * pow2f(2 * (r.Ea - 1023) - shift) * dp2;
     const float b32 = r.fb * pow2f(2 * (r.Eb - 1023) - shift) * dq2;
     const float g32 = f32_image(r.g, shift) * dpq;
+    const float z = __fdividef(b32 - a32, 2.0f * g32), az = fabsf(z);
+    const float w = fmaf(z, z, 1.0f);
+    const float tb = (az > 1e18f) ? __fdividef(0.5f, z) : copysignf(__fdividef(1.0f, az + w * rsqrtf(w)), z);
+    if (!above) return false;
     if (fabsf(g32) >= 1e-30f) {
-        const float z = __fdividef(b32 - a32, 2.0f * g32), az = fabsf(z);
-        float t32;
-        if (az > 1e18f) {
-            t32 = __fdividef(0.5f, z);
-        } else {
-            const float w = fmaf(z, z, 1.0f);
-            t32 = copysignf(__fdividef(1.0f, az + w * rsqrtf(w)), z);
-        }
-        *t_out = f64_of(t32);
+        *t_out = f64_of(tb);
         return true;
     }
     // tiny angle: t ~ gamma / (beta - alpha) with the true (scaled) sums (rare)
@@ -1318,7 +1320,7 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
     for (int sweep = 0; sweep < kMaxSweeps && !converged && ok; ++sweep) {
         if (prev_rot < (unsigned int)kCheckBelow) {
             ++check_passes;
-            const int c = jacobi_check_pass(X, n, tol2, bar, checkflag + sweep);
+            const int c = jacobi_check_pass(X, n, tol2, bar, checkflag + sweep, sigma);
             if (c < 0) {
                 ok = false;
                 break;
@@ -1434,15 +1436,12 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
                     double tn = 0.0;
                     const bool rot = ring_angle(rs, tol2, fP * fP, fQ * fQ, fP * fQ, dP, dQ, &tn);
                     const double mn = tn * rr;  // lane 0: mu (x~_p -= mu x~_q), lane 1: nu (x~_q += nu x~_p)
-                    const double nu = __shfl_sync(0xffffffffu, mn, 1);
-                    if (lane == 0) {
-                        par[j][0] = rot ? 1.0 : 0.0;
-                        par[j][1] = rot ? mn : 0.0;
-                        par[j][2] = rot ? nu : 0.0;
-                        asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(
-                                         shared_addr(&mbr[j]))
+                    if (lane < 2) par[j][1 + lane] = rot ? mn : 0.0;
+                    if (lane == 0) par[j][0] = rot ? 1.0 : 0.0;
+                    __syncwarp();
+                    if (lane == 0)
+                        asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(shared_addr(&mbr[j]))
                                      : "memory");
-                    }
                     xbar();  // par[j] is visible to the X row warps
                     if (rot) {  // new scales: d <- c d, e <- e / c, c = (1 + t^2)^(-1/2)
                         ++local;
