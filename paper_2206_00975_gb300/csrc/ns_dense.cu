@@ -59,7 +59,8 @@ DenseWork dense_carve(Carver &c, int64_t s, int64_t n) {
     w.X = c.take<double>((size_t)(n * n));
     w.V = c.take<double>((size_t)(n * n));
     w.sigma = c.take<double>((size_t)n);
-    w.L = c.take<double>((size_t)(n * n));
+    w.L = c.take<double>((size_t)(2 * n * n));
+    w.R2 = c.take<double>((size_t)(2 * n * n));
     w.U = c.take<double>((size_t)(s * n));
     w.perm = c.take<int32_t>((size_t)n);
     w.pivslot = c.take<unsigned long long>((size_t)n + 1);
@@ -661,14 +662,16 @@ __global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(const double *W,
         __syncthreads();
         if (++jm == G) jm = 0;
     }
-    // R (column order as stored in W)
+    // R: rows 0..steps-1 of every column (column order as stored in W),
+    // leading dimension steps; for cols > rows the columns past the last
+    // reflector come out as Q^T times their input
     for (int64_t o = 0; o < nown; ++o) {
         const int64_t c = me + o * G;
-        for (int64_t i = tid; i < cols; i += kPipeThreads) {
+        for (int64_t i = tid; i < steps; i += kPipeThreads) {
             double r = 0.0;
-            if (i < c && i < rows) r = own[o * rows + i];
-            else if (i == c) r = (c < steps) ? beta[o] : own[o * rows + c];
-            Rout[i + c * cols] = r;
+            if (i < c) r = own[o * rows + i];
+            else if (i == c) r = beta[o];
+            Rout[i + c * steps] = r;
         }
     }
 }
@@ -769,6 +772,21 @@ __global__ void r2t_kernel(const double *__restrict__ R2, int64_t n, double *__r
     if (idx >= n * n) return;
     const int64_t i = idx % n, j = idx / n;
     X[i + j * n] = (i >= j) ? R2[j + i * n] : 0.0;
+}
+
+// B (n x n) = I
+__global__ void identity_kernel(double *__restrict__ B, int64_t n) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < n * n) B[idx] = (idx % n == idx / n) ? 1.0 : 0.0;
+}
+
+// rows of V to the input column order: W[perm[i], c] = V[i, c]
+__global__ void permute_rows_kernel(const double *__restrict__ V, int64_t n, const int32_t *__restrict__ perm,
+                                    double *__restrict__ W) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    const int64_t i = idx % n, c = idx / n;
+    W[perm[i] + c * n] = V[idx];
 }
 
 // --------------------------------------------------------------- Jacobi ----
@@ -904,14 +922,15 @@ template <int RPT>
 __global__ void __launch_bounds__(kDenseThreads) jacobi_coop_kernel(double *X, double *V, int64_t n, double tol,
                                                                    GridBarrier bar, unsigned int *rotcount,
                                                                    unsigned int *checkflag, double *sigma,
-                                                                   int32_t *status) {
+                                                                   int32_t *status, int vinit) {
     __shared__ double red[32 * 3];
     __shared__ double par[3];
     const int64_t G = gridDim.x, me = blockIdx.x;
     const int tid = threadIdx.x;
     const double tol2 = tol * tol;
-    for (int64_t l = me; l < n; l += G)
-        for (int64_t i = tid; i < n; i += blockDim.x) V[i + l * n] = (i == l) ? 1.0 : 0.0;
+    if (!vinit)  // V = I, else V arrives holding Q2
+        for (int64_t l = me; l < n; l += G)
+            for (int64_t i = tid; i < n; i += blockDim.x) V[i + l * n] = (i == l) ? 1.0 : 0.0;
     const int64_t n2 = n + (n & 1), npairs = n2 / 2, steps = n2 - 1;
     bool converged = (n < 2);
     unsigned int prev_rot = 0xFFFFFFFFu;
@@ -1052,16 +1071,21 @@ __device__ __forceinline__ void cluster_sync_all() {
 }
 __device__ __forceinline__ uint32_t shared_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Waiting threads are suspended in hardware until the phase completes (or the
+// hint elapses) instead of re-polling: a polling loop of whole warps keeps the
+// shared-memory pipe busy and delays the scalar warp's loads.
+constexpr uint32_t kRingSuspendNs = 1000000;
+
 // bounded wait for phase `parity` of a local mbarrier that peers complete
 __device__ __forceinline__ bool ring_wait(uint32_t mbar, uint32_t parity) {
     const long long t0 = clock64();
     for (;;) {
         uint32_t done;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
-            : "r"(mbar), "r"(parity)
+            : "r"(mbar), "r"(parity), "r"(kRingSuspendNs)
             : "memory");
         if (done) return true;
         if (clock64() - t0 > (1ll << 32)) return false;  // ~2 s: a healthy ring waits microseconds
@@ -1084,10 +1108,10 @@ __device__ __forceinline__ bool ring_wait_cta(uint32_t mbar, uint32_t parity) {
     for (;;) {
         uint32_t done;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
-            : "r"(mbar), "r"(parity)
+            : "r"(mbar), "r"(parity), "r"(kRingSuspendNs)
             : "memory");
         if (done) return true;
         if (clock64() - t0 > (1ll << 32)) return false;
@@ -1243,7 +1267,7 @@ __device__ __forceinline__ void send_pair(uint32_t dst, double a, double b, uint
 __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
     jacobi_ring_kernel(double *X, double *V, int64_t n, int64_t G, double tol, GridBarrier bar,
                        unsigned int *rotcount, unsigned int *checkflag, double *sigma, unsigned int *colver,
-                       int32_t *status) {
+                       int32_t *status, int vinit) {
     // Slot j receives the Q column of round j: rows t and t + kRingT of X in
     // xbuf[j][t] and of V in vbuf[j][t], and its scale pair in sbuf[j], each
     // completed on its own mbarrier (mbx, mbv, mbs).  Columns are held scaled,
@@ -1299,8 +1323,9 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
     }
-    for (int64_t l = blockIdx.x; l < n; l += gridDim.x)
-        for (int64_t i = tid; i < n; i += blockDim.x) V[i + l * n] = (i == l) ? 1.0 : 0.0;
+    if (!vinit)  // V = I, else V arrives holding Q2
+        for (int64_t l = blockIdx.x; l < n; l += gridDim.x)
+            for (int64_t i = tid; i < n; i += blockDim.x) V[i + l * n] = (i == l) ? 1.0 : 0.0;
     cluster_sync_all();  // every mbarrier of the cluster is initialised before the first st.async
     const uint32_t peer = (ci + kRingC - 1) % kRingC;
     const uint32_t xb_peer = peer_addr(shared_addr(&xbuf[0][0]), peer);
@@ -1404,10 +1429,12 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
                     }
                     // before the sums arrive: d_Q e_P (lane 0, for mu), d_P e_Q
                     // (lane 1, for nu) and the FP32 images of the scales
-                    const double dP = __shfl_sync(0xffffffffu, sv, 0), dQ = __shfl_sync(0xffffffffu, sv, 1);
+                    double dP = __shfl_sync(0xffffffffu, sv, 0), dQ = __shfl_sync(0xffffffffu, sv, 1);
                     const double ee = __shfl_sync(0xffffffffu, sv, lane == 0 ? 2 : 3);
-                    const double rr = (lane == 0 ? dQ : dP) * ee;
-                    const float fP = f32_image(dP, 0), fQ = f32_image(dQ, 0);
+                    double rr = (lane == 0 ? dQ : dP) * ee;
+                    float fP = f32_image(dP, 0), fQ = f32_image(dQ, 0);
+                    // computed here, before the barrier, not after it on the critical path
+                    asm volatile("" : "+d"(rr), "+d"(dP), "+d"(dQ), "+f"(fP), "+f"(fQ));
                     xbar();  // the row warps' sums of round j are in rg, rab, rexp
                     // lanes 0-3 hold row warp w = lane; sums in the order (w0 + w1) + (w2 + w3)
                     RingSums rs;
@@ -1529,10 +1556,14 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
                             q1 = in.y;
                         }
                     }
-                    // the Q half first: it is what the neighbour waits for
+                    // the Q half first: it is what the neighbour waits for.  The V
+                    // warps start after the X warps have sent their Q rows, so the
+                    // X updates, on the critical path, do not queue behind the V
+                    // updates for the shared FP64 pipe.
                     const bool rj = par[j][0] != 0.0;
                     const double mu = par[j][1], nu = par[j][2];
                     const double oq0 = q0, oq1 = q1;
+                    if (!isx) asm volatile("bar.sync 2, %0;" ::"n"(2 * kRingT) : "memory");
                     if (rj) {
                         q0 = fma(nu, p0, q0);
                         q1 = fma(nu, p1, q1);
@@ -1542,6 +1573,7 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
                         if (isx) send_pair(xb_peer + off, q0, q1, mx_peer + (uint32_t)((j + 1) * 8));
                         else send_pair(vb_peer + off, q0, q1, mv_peer + (uint32_t)((j + 1) * 8));
                     }
+                    if (isx) asm volatile("bar.arrive 2, %0;" ::"n"(2 * kRingT) : "memory");
                     if (rj) {
                         p0 = fma(-mu, oq0, p0);
                         p1 = fma(-mu, oq1, p1);
@@ -1701,7 +1733,8 @@ static int sm_count() {
 }
 
 template <int RPT>
-static cudaError_t launch_jacobi(const DenseWork &w, int64_t n, GridBarrier bar, int32_t *status, cudaStream_t st) {
+static cudaError_t launch_jacobi(const DenseWork &w, int64_t n, GridBarrier bar, int32_t *status, int vinit,
+                                 cudaStream_t st) {
     const int64_t npairs = (n + (n & 1)) / 2;
     int64_t G = npairs < sm_count() ? npairs : sm_count();
     if (G < 1) G = 1;
@@ -1710,7 +1743,8 @@ static cudaError_t launch_jacobi(const DenseWork &w, int64_t n, GridBarrier bar,
     double tol = (double)n * std::ldexp(1.0, -53);
     unsigned int *rot = w.bar + 64, *chk = w.bar + 64 + 64;
     int32_t *status_ = status;
-    void *args[] = {&X, &V, &n_, &tol, &bar, &rot, &chk, &sigma, &status_};
+    int vinit_ = vinit;
+    void *args[] = {&X, &V, &n_, &tol, &bar, &rot, &chk, &sigma, &status_, &vinit_};
     return cudaLaunchCooperativeKernel((const void *)jacobi_coop_kernel<RPT>, (int)G, kDenseThreads, args, 0, st);
 }
 
@@ -1718,7 +1752,7 @@ static cudaError_t launch_jacobi(const DenseWork &w, int64_t n, GridBarrier bar,
 // 2 G kRingC >= n columns, resident at once: a cooperative launch.  Falls
 // back (sets *used = false) when the device cannot hold them or rejects the
 // launch.
-static cudaError_t launch_jacobi_ring(const DenseWork &w, int64_t n, GridBarrier bar, int32_t *status,
+static cudaError_t launch_jacobi_ring(const DenseWork &w, int64_t n, GridBarrier bar, int32_t *status, int vinit,
                                       cudaStream_t st, bool *used) {
     static int state[64] = {0};  // per device: 0 unknown, 1 usable, -1 not usable
     *used = false;
@@ -1749,7 +1783,7 @@ static cudaError_t launch_jacobi_ring(const DenseWork &w, int64_t n, GridBarrier
     unsigned int *colver = w.colver;
     cudaError_t e = cudaMemsetAsync(colver, 0, sizeof(unsigned int) * (size_t)(n + 16), st);
     if (e != cudaSuccess) return e;
-    e = cudaLaunchKernelEx(&cfg, jacobi_ring_kernel, X, V, n, G, tol, bar, rot, chk, sigma, colver, status);
+    e = cudaLaunchKernelEx(&cfg, jacobi_ring_kernel, X, V, n, G, tol, bar, rot, chk, sigma, colver, status, vinit);
     if (e != cudaSuccess) {
         cudaGetLastError();
         state[dev] = -1;
@@ -1793,7 +1827,8 @@ static bool launch_hqr_pipe(const double *W, double *U, int64_t rows, int64_t co
     if (!pipe_fits(rows, cols)) return false;
     *err = cudaMemsetAsync(flags, 0xFF, sizeof(unsigned long long) * (size_t)cols, st);  // kPipeEmpty
     if (*err != cudaSuccess) return true;
-    *err = cudaMemsetAsync(U, 0xFF, sizeof(double) * (size_t)(rows * cols), st);  // kPipeEmpty
+    const int64_t steps = rows < cols ? rows : cols;
+    *err = cudaMemsetAsync(U, 0xFF, sizeof(double) * (size_t)(rows * steps), st);  // kPipeEmpty
     if (*err != cudaSuccess) return true;
     *err = cudaFuncSetAttribute(hqr_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (*err != cudaSuccess) return true;
@@ -1863,36 +1898,54 @@ cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k
         e = launch_hqr(w.W, s, n, 1, u0a, cfa, w.perm, w.pivslot, w.X, bar, st);
     }
     if (e != cudaSuccess) return e;
-    // 2. L = R^T; QR of L without pivoting: reflectors stay in L, R2 lands in V (scratch)
-    {
-        dim3 tb(32, 8), grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
-        transpose_kernel<<<grid, tb, 0, st>>>(w.X, n, w.L);
+    // 2. QR of L = R^T without pivoting.  On the pipelined path L carries the
+    // identity as n more columns, [R^T | I]: the reflectors applied to them
+    // give Q2^T beside R2, so V starts as Q2 and the Jacobi rotations
+    // accumulate Q2 Vx directly.  Otherwise (barrier-separated QR) Q2 is
+    // applied to Vx afterwards.
+    const dim3 ttb(32, 8), tgrid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
+    const unsigned nn_blocks = (unsigned)((n * n + 255) / 256);
+    transpose_kernel<<<tgrid, ttb, 0, st>>>(w.X, n, w.L);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const bool q2_in_v = pipe_fits(n, 2 * n);
+    const double *Lq = w.L;  // reflectors of the second QR (barrier-separated path)
+    if (q2_in_v) {
+        identity_kernel<<<nn_blocks, 256, 0, st>>>(w.L + n * n, n);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        launch_hqr_pipe(w.L, w.U, n, 2 * n, u0b, cfb, flags, w.R2, status, st, &e);
+        if (e != cudaSuccess) return e;
+        // 3. X = R2^T, V = (Q2^T)^T
+        r2t_kernel<<<nn_blocks, 256, 0, st>>>(w.R2, n, w.X);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        transpose_kernel<<<tgrid, ttb, 0, st>>>(w.R2 + n * n, n, w.V);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else {
+        int32_t *perm2 = (int32_t *)w.sigma;  // identity permutation of the unpivoted QR (unused)
+        e = launch_hqr(w.L, n, n, 0, u0b, cfb, perm2, w.pivslot, w.V, bar, st);
+        if (e != cudaSuccess) return e;
+        // 3. X = R2^T (R2 landed in V)
+        r2t_kernel<<<nn_blocks, 256, 0, st>>>(w.V, n, w.X);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    int32_t *perm2 = (int32_t *)w.sigma;  // identity permutation of the unpivoted QR (unused)
-    const double *Lq = w.U;  // the reflectors of the second QR
-    if (!launch_hqr_pipe(w.L, w.U, n, n, u0b, cfb, flags, w.V, status, st, &e)) {
-        e = launch_hqr(w.L, n, n, 0, u0b, cfb, perm2, w.pivslot, w.V, bar, st);
-        Lq = w.L;
-    }
-    if (e != cudaSuccess) return e;
-    // 3. X = R2^T; Jacobi on X (V receives Vx)
-    r2t_kernel<<<(unsigned)((n * n + 255) / 256), 256, 0, st>>>(w.V, n, w.X);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // Jacobi on X; V receives Q2 Vx (pipelined path) or Vx
     e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * kBarWords, st);
     if (e != cudaSuccess) return e;
+    const int vinit = q2_in_v ? 1 : 0;
     bool ring = false;
     if (n <= kRingN) {
-        e = launch_jacobi_ring(w, n, bar, status, st, &ring);
+        e = launch_jacobi_ring(w, n, bar, status, vinit, st, &ring);
         if (e != cudaSuccess) return e;
     }
     if (ring) e = cudaSuccess;
-    else if (n <= 256) e = launch_jacobi<1>(w, n, bar, status, st);
-    else if (n <= 1024) e = launch_jacobi<4>(w, n, bar, status, st);
-    else e = launch_jacobi<16>(w, n, bar, status, st);
+    else if (n <= 256) e = launch_jacobi<1>(w, n, bar, status, vinit, st);
+    else if (n <= 1024) e = launch_jacobi<4>(w, n, bar, status, vinit, st);
+    else e = launch_jacobi<16>(w, n, bar, status, vinit, st);
     if (e != cudaSuccess) return e;
-    // 4. V = P Q2 Vx  (Vx is in w.V; the result goes to w.W, reused as n x n)
-    {
+    // 4. V = P Q2 Vx into w.W (reused as n x n)
+    if (q2_in_v) {
+        permute_rows_kernel<<<nn_blocks, 256, 0, st>>>(w.V, n, w.perm, w.W);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else {
         const size_t smem = sizeof(double) * (size_t)n;
         e = cudaFuncSetAttribute(apply_q2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -123,7 +123,8 @@ struct DenseWork {
     double *X;        // n x n: R, then X = R2^T rotated into U Sigma
     double *V;        // n x n: R2, then the accumulated rotations Vx
     double *sigma;    // n
-    double *L;        // n x n: R^T, then the reflectors of its QR (coop fallback)
+    double *L;        // n x 2n: [R^T | I] for the second QR (n x n R^T and its reflectors on the coop fallback)
+    double *R2;       // n x 2n: [R2 | Q2^T] from the pipelined second QR
     double *U;        // s x n: reflectors published by the pipelined QRs
     int32_t *perm;    // n: column pivots of the first QR
     unsigned long long *pivslot;  // n + 1: pivot candidates (atomic max)
