@@ -1099,6 +1099,7 @@ __device__ __forceinline__ bool ring_wait(uint32_t mbar, uint32_t parity) {
 // update of one round overlaps the X work of the next.
 constexpr int kRingCta = 32 + 2 * kRingT;
 constexpr int kRingBar = 32 + kRingT;  // scalar warp + X row warps (named barrier 1)
+constexpr int kRingXV = kRingCta;      // X rows arrive, V rows and the scalar warp wait (named barrier 2)
 
 __device__ __forceinline__ void xbar() { asm volatile("bar.sync 1, %0;" ::"n"(kRingBar) : "memory"); }
 
@@ -1470,6 +1471,8 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
                         asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(shared_addr(&mbr[j]))
                                      : "memory");
                     xbar();  // par[j] is visible to the X row warps
+                    // the scale update waits for the X rows' sends, like the V warps
+                    asm volatile("bar.sync 2, %0;" ::"n"(kRingXV) : "memory");
                     if (rot) {  // new scales: d <- c d, e <- e / c, c = (1 + t^2)^(-1/2)
                         ++local;
                         const double u = tn * tn;
@@ -1563,7 +1566,7 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
                     const bool rj = par[j][0] != 0.0;
                     const double mu = par[j][1], nu = par[j][2];
                     const double oq0 = q0, oq1 = q1;
-                    if (!isx) asm volatile("bar.sync 2, %0;" ::"n"(2 * kRingT) : "memory");
+                    if (!isx) asm volatile("bar.sync 2, %0;" ::"n"(kRingXV) : "memory");
                     if (rj) {
                         q0 = fma(nu, p0, q0);
                         q1 = fma(nu, p1, q1);
@@ -1573,7 +1576,7 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
                         if (isx) send_pair(xb_peer + off, q0, q1, mx_peer + (uint32_t)((j + 1) * 8));
                         else send_pair(vb_peer + off, q0, q1, mv_peer + (uint32_t)((j + 1) * 8));
                     }
-                    if (isx) asm volatile("bar.arrive 2, %0;" ::"n"(2 * kRingT) : "memory");
+                    if (isx) asm volatile("bar.arrive 2, %0;" ::"n"(kRingXV) : "memory");
                     if (rj) {
                         p0 = fma(-mu, oq0, p0);
                         p1 = fma(-mu, oq1, p1);
