@@ -239,6 +239,114 @@ __global__ void __launch_bounds__(64) srht_f32_chunk_kernel(const float *__restr
     if (nonfinite) set_status(status, NS_ERR_NONFINITE);
 }
 
+// Same transform with the sampled rows' sums in registers (s <= 64 RPT): each
+// thread owns the rows t + 64 q, so the per-block gather is one shared-memory
+// load and one add per owned row, in the same order as the kernel above (the
+// results are identical).  The next block is prefetched into L2 with one bulk
+// copy while the current one is transformed.
+template <int RPT>
+__global__ void __launch_bounds__(64) srht_f32_chunk_reg_kernel(const float *__restrict__ A, int64_t m, int64_t n,
+                                                                int64_t lda, int64_t s, int chunk, int64_t nchunk,
+                                                                const uint32_t *__restrict__ sign_words,
+                                                                const int32_t *__restrict__ rows,
+                                                                double *__restrict__ partial, int32_t *status,
+                                                                int vec_ok) {
+    __shared__ __align__(16) float Zs[kBlock];
+    __shared__ unsigned long long need[64];
+    __shared__ uint32_t sgn[128];
+    const int t = threadIdx.x;
+    const int64_t item = blockIdx.x;
+    const int64_t c = item / nchunk, ch = item - c * nchunk;
+    const float *Acol = A + c * lda;
+    int32_t pr[RPT];
+    float acc[RPT];
+    need[t] = 0ull;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        const int64_t i = t + 64 * q;
+        acc[q] = 0.0f;
+        pr[q] = -1;
+        if (i < s) {
+            const int32_t r = rows[i];
+            pr[q] = srht_pack_row(r);
+            const int lo = r & (kBlock - 1);
+            atomicOr(&need[(lo & 1) | ((lo >> 7) << 1)], 1ull << ((lo >> 1) & 63));
+        }
+    }
+    __syncthreads();
+    const unsigned long long myneed = need[t];
+    int nonfinite = 0;
+    float z[64];
+    for (int bl = 0; bl < chunk; ++bl) {
+        const int64_t b = ch * chunk + bl;
+        const int64_t base = b * kBlock;
+        sgn[t] = sign_words[(base >> 5) + t];
+        sgn[t + 64] = sign_words[(base >> 5) + 64 + t];
+        if (t == 0 && bl + 1 < chunk && vec_ok && base + 2 * kBlock <= m)  // the next block, into L2
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(Acol + base + kBlock),
+                         "r"((uint32_t)(kBlock * 4))
+                         : "memory");
+        if (vec_ok && base + kBlock <= m) {
+#pragma unroll
+            for (int kk = 0; kk < 32; ++kk) {
+                const float2 v = __ldcs((const float2 *)(Acol + base + 2 * t + 128 * kk));
+                z[2 * kk] = v.x;
+                z[2 * kk + 1] = v.y;
+            }
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < 32; ++kk) {
+                const int64_t i0 = base + 2 * t + 128 * kk;
+                z[2 * kk] = (i0 < m) ? __ldcs(Acol + i0) : 0.0f;
+                z[2 * kk + 1] = (i0 + 1 < m) ? __ldcs(Acol + i0 + 1) : 0.0f;
+            }
+        }
+        __syncthreads();  // publishes sgn[]
+#pragma unroll
+        for (int kk = 0; kk < 32; ++kk) {
+            const uint32_t sw = sgn[4 * kk + (t >> 4)] >> (2 * (t & 15));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t bits = __float_as_uint(z[2 * kk + h]);
+                if ((bits & 0x7F800000u) == 0x7F800000u) nonfinite = 1;
+                bits ^= ((sw >> h) & 1u) << 31;
+                z[2 * kk + h] = __uint_as_float(bits);
+            }
+        }
+        fwht64f(z);
+#pragma unroll
+        for (int kk = 0; kk < 32; ++kk) {
+            const int i = 2 * t + 128 * kk;
+            const int p = i ^ (((i >> 7) & 15) << 1);
+            *(float2 *)(Zs + p) = make_float2(z[2 * kk], z[2 * kk + 1]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 64; ++k) z[k] = Zs[swz(l2_elem(t, k))];
+        __syncthreads();
+        fwht64f(z);
+#pragma unroll
+        for (int k = 0; k < 64; ++k)
+            if ((myneed >> k) & 1ull) Zs[swz(l2_elem(t, k))] = z[k];
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            if (pr[q] >= 0) {
+                const float v = Zs[pr[q] & (kBlock - 1)];
+                const int neg = __popc((uint32_t)(pr[q] >> kBlockLog) & (uint32_t)b) & 1;
+                acc[q] += neg ? -v : v;
+            }
+        }
+        __syncthreads();
+    }
+    double *out = partial + (ch * n + c) * s;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+        if (t + 64 * q < s) out[t + 64 * q] = (double)acc[q];
+    if (nonfinite) set_status(status, NS_ERR_NONFINITE);
+}
+
 size_t srht_f32_smem(int64_t s) {
     return (size_t)kBlock * 4 + (size_t)((s + 1) & ~1ll) * 4 + 64 * 8 + 128 * 4 + (size_t)s * 4;
 }
@@ -246,14 +354,28 @@ size_t srht_f32_smem(int64_t s) {
 cudaError_t launch_srht_f32(const float *A, int64_t m, int64_t n, int64_t lda, int64_t s, const SrhtWork &w,
                             double *SA, int32_t *status, cudaStream_t st) {
     const SrhtGeom g = srht_geom(m, n);
-    const size_t smem = srht_f32_smem(s);
-    cudaError_t e = cudaFuncSetAttribute(srht_f32_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
     const int vec_ok = ((((uintptr_t)A) & 7) == 0 && (lda & 1) == 0) ? 1 : 0;
-    srht_f32_chunk_kernel<<<(unsigned)(n * g.nchunk), 64, smem, st>>>(A, m, n, lda, s, g.chunk, g.nchunk,
-                                                                      w.sign_words, w.rows, w.partial, status,
-                                                                      vec_ok);
+    const unsigned grid = (unsigned)(n * g.nchunk);
+    if (s <= 64 * 32) {  // sampled rows in registers
+        // the bulk L2 prefetch wants 16-byte aligned blocks
+        const int vec16 = (vec_ok && (((uintptr_t)A) & 15) == 0 && (lda & 3) == 0) ? 1 : 0;
+        if (s <= 64 * 8)
+            srht_f32_chunk_reg_kernel<8><<<grid, 64, 0, st>>>(A, m, n, lda, s, g.chunk, g.nchunk, w.sign_words,
+                                                               w.rows, w.partial, status, vec16);
+        else if (s <= 64 * 16)
+            srht_f32_chunk_reg_kernel<16><<<grid, 64, 0, st>>>(A, m, n, lda, s, g.chunk, g.nchunk, w.sign_words,
+                                                                w.rows, w.partial, status, vec16);
+        else
+            srht_f32_chunk_reg_kernel<32><<<grid, 64, 0, st>>>(A, m, n, lda, s, g.chunk, g.nchunk, w.sign_words,
+                                                                w.rows, w.partial, status, vec16);
+    } else {
+        const size_t smem = srht_f32_smem(s);
+        e = cudaFuncSetAttribute(srht_f32_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        srht_f32_chunk_kernel<<<grid, 64, smem, st>>>(A, m, n, lda, s, g.chunk, g.nchunk, w.sign_words, w.rows,
+                                                      w.partial, status, vec_ok);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     srht_reduce_kernel<<<(unsigned)((n * s + 255) / 256), 256, 0, st>>>(w.partial, n, s, g.nchunk,
                                                                         1.0 / std::sqrt((double)s), SA);

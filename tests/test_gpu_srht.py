@@ -202,8 +202,10 @@ def test_residual_gpu(api):
 
 
 # ------------------------------------------------------------- FP32 stream ----
-@pytest.mark.parametrize("m,n,s", [(4096, 3, 128), (5000, 4, 256), ((1 << 18) + 3, 2, 2048)])
+@pytest.mark.parametrize("m,n,s", [(4096, 3, 128), (5000, 4, 256), (9000, 3, 700), ((1 << 18) + 3, 2, 2048),
+                                   (8197, 2, 2100)])
 def test_srht_fp32_stream_parity(api, m, n, s):
+    # s <= 2048 keeps the sampled rows' sums in registers; larger s in shared memory
     # FP32 arithmetic: error bound u32 * (log2 m' + 2) * ||A||_F per entry
     rng = np.random.default_rng(m)
     A32 = rng.standard_normal((m, n)).astype(np.float32)
