@@ -1365,16 +1365,19 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
         for (int64_t ot = 0; ot < nouter; ++ot) {
             const int64_t P = rr_player(g, ot, nblk), Q = rr_player(nblk - 1 - g, ot, nblk);
             if (ot == 0) {  // pairs inside blocks P and Q
+                // Both blocks belong to this cluster alone at the first outer step
+                // (the grid barrier at the start of the sweep ordered their last
+                // writes), so a cluster barrier (release/acquire at cluster scope)
+                // separates the rounds.
                 const int half = kRingC / 2;
                 const int64_t B = ((int)ci < half) ? P : Q;
                 const int k = (int)ci % half;
-                for (int j = 0; j < kRingC - 1 && ok; ++j) {
+                for (int j = 0; j < kRingC - 1; ++j) {
                     const int64_t a = B * kRingC + rr_player(k, j, kRingC);
                     const int64_t b = B * kRingC + rr_player(kRingC - 1 - k, j, kRingC);
                     local += jacobi_pair_global(X, V, n, a, b, tol2, red, &par[0][0]);
-                    ok = grid_sync(bar);
+                    cluster_sync_all();
                 }
-                if (!ok) break;
             }
             if (ot > 0) {
                 // the two columns this CTA loads were stored at the previous outer
