@@ -480,7 +480,7 @@ def main():
                    "peak_source": peak_kind, "algorithmic_bytes": sketch_bytes}
     dense_roof = {"bound": "alu", "achieved": dense_tf, "peak": fp64_peak, "unit": "TFLOP/s",
                   "frac": dense_tf / fp64_peak, "traffic": None,
-                  "kernel": "FP64 dense stage (column order, hqr_pipe x2, jacobi_ring, apply_q2, extract) via ns_solve_sketched",
+                  "kernel": "FP64 dense stage (column order, hqr_pipe x2 with Q2 formed in the second, jacobi_ring from V = Q2, extract) via ns_solve_sketched",
                   "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x sampled SM clock",
                   "algorithmic_flops": dflops, "jacobi_sweeps_rotations_checks": stats[:3],
                   "jacobi_kernel": "cluster ring" if stats[3] == 1 else "barrier-separated"}
@@ -504,7 +504,7 @@ def main():
                 "h2d_bytes_per_step": M * N * 8, "d2h_bytes_per_step": (N * K_NULL + K_NULL) * 8,
                 "overlap": "copy of step i+1 overlaps the solve of step i (two device buffers)",
                 "results_finite": e2e_ok},
-        "gpu_launches": 15 * args.steps,
+        "gpu_launches": 17 * args.steps,
         "clocks": clocks,
     }
     if args.extra and rank == 0:

@@ -103,3 +103,30 @@ def test_dense_stage_wide_range(api):
     _, _, sigma = api.unpack_save(sv, s, n)
     np.testing.assert_allclose(np.sort(sigma.cpu().numpy()), np.sort(sig_or), rtol=1e-8, atol=0)
     np.testing.assert_allclose(sk.cpu().numpy(), sk_or, rtol=1e-8, atol=0)
+
+
+def test_dense_stage_near_repeated_column(api):
+    # Two columns parallel to ~1e-9: they sit next to each other in the
+    # decreasing-norm order, so when the owner of the second applies the
+    # first one's reflector, the downdated tail norm cancels to ~1e-18 of its
+    # terms and is recomputed from the updated column.
+    rng = np.random.default_rng(21)
+    s, n, k = 400, 100, 1
+    SA = rng.standard_normal((s, n))
+    SA[:, 7] = SA[:, 3] + 1e-9 * rng.standard_normal(s)
+    order = np.argsort(-np.sum(SA * SA, axis=0), kind="stable")
+    pos = sorted([int(np.where(order == 3)[0][0]), int(np.where(order == 7)[0][0])])
+    assert pos[1] == pos[0] + 1 and pos[0] >= 1  # adjacent, past the first reflector
+    SA = np.asfortranarray(SA)
+    d = api.desc(api.NS_SRHT, s=s, seed=0)
+    Vk, sk, sv, status = api.ns_solve_sketched(d, api.colmajor(SA, device="cuda"), k, save=True)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    Vk_or, sk_or, _, sig_or, _, st = O.solve_sketched(SA, k)
+    assert st == 0
+    _, V, sigma = api.unpack_save(sv, s, n)
+    V = V.cpu().numpy()
+    assert np.linalg.norm(V.T @ V - np.eye(n)) < 1e-13 * n
+    s1 = sig_or.max()
+    np.testing.assert_allclose(np.sort(sigma.cpu().numpy()), np.sort(sig_or), rtol=0, atol=1e-12 * s1)
+    assert sine(Vk_or, Vk.cpu().numpy()) < 1e-8
