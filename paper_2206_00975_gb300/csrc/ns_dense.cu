@@ -65,7 +65,7 @@ DenseWork dense_carve(Carver &c, int64_t s, int64_t n) {
     w.perm = c.take<int32_t>((size_t)n);
     w.pivslot = c.take<unsigned long long>((size_t)n + 1);
     w.bar = c.take<unsigned int>(kBarWords);
-    w.colver = c.take<unsigned int>((size_t)n + 16);
+    w.colver = c.take<unsigned int>((size_t)n + 32);
     return w;
 }
 
@@ -495,9 +495,10 @@ __device__ __forceinline__ void pipe_apply(int64_t rows, int64_t j, const double
 // updated column follows from sums over the old one (norm downdating):
 //   |y'_T|^2 = S_yy - 2 f S_uy + f^2 S_uu,   f = coef (u . y),   T = rows j+2..,
 // with S_uu = |u[j+1:]|^2 - u_{j+1}^2 (published with reflector j) and
-// S_uy = u . y - u_j y_j - u_{j+1} y_{j+1}.  Where the terms cancel (the
-// result below 1/16 of their magnitudes) or the norm would need rescaling, the
-// norm is recomputed from the updated column (pipe_form).
+// S_uy = u . y - u_j y_j - u_{j+1} y_{j+1}.  Where the result is below 1/16 of
+// the magnitudes it was formed from (the rounding of the cancellations is
+// bounded by u times those) or the norm would need rescaling, the norm is
+// recomputed from the updated column (pipe_form).
 __device__ double pipe_apply_form(double *U, int64_t rows, int64_t j, const double *ush, double coef, double unrm2,
                                   double *y, double *ushn, double *u0, double *cf, unsigned long long *flag,
                                   double *red, double *coef_sh, double *unrm_sh) {
@@ -532,10 +533,16 @@ __device__ double pipe_apply_form(double *U, int64_t rows, int64_t j, const doub
     }
     if (tid == 0) {
         const double x0 = fma(-f, un, yn);  // y'_{j+1}, as the update computes it
-        const double suy = (d - uj * yj) - un * yn, suu = unrm2 - un * un;
-        const double n2 = fma(f, fma(f, suu, -2.0 * suy), syy);
-        const double mag = syy + fabs(f) * fma(fabs(f), fabs(suu), 2.0 * fabs(suy));
-        bool ok = n2 >= 0.0625 * mag && mag <= 1e280 && (n2 == 0.0 || n2 >= 1e-280);
+        const double p1 = uj * yj, p2 = un * yn, u2 = un * un;
+        const double suy = (d - p1) - p2, suu = unrm2 - u2;
+        // With no rows below j + 1 the tail norm is exactly 0 (H = I).  Otherwise
+        // S_uy and S_uu come from cancellations whose rounding is bounded by u
+        // times the magnitudes they were formed from, so those set the guard.
+        const bool notail = jn + 1 >= rows;
+        const double n2 = notail ? 0.0 : fma(f, fma(f, suu, -2.0 * suy), syy);
+        const double af = fabs(f);
+        const double mag = syy + af * fma(af, unrm2 + u2, 2.0 * (fabs(d) + fabs(p1) + fabs(p2)));
+        bool ok = notail || (n2 >= 0.0625 * mag && mag <= 1e280 && (n2 == 0.0 || n2 >= 1e-280));
         double beta = x0, ua = 0.0, cfn = 0.0;  // n2 == 0: H = I
         if (ok && n2 != 0.0) ok = pipe_reflector(x0, n2, &beta, &ua, &cfn);
         if (ok) {
@@ -1031,7 +1038,9 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_coop_kernel(double *X, d
 // warps keep all four FP64 units of the SM busy while the reduction tree stays
 // short (FP64 runs at 2 operations per clock per SM here, so every add of a
 // reduction counts).
-constexpr int kRingC = 8;      // CTAs per cluster = columns per block
+// The cluster size C (CTAs per cluster = columns per block) is a template
+// parameter: 8 (portable), or 16 for n > 240, where 16 clusters of 8 would
+// not all find SMs of their own (the one that shares SMs paces every other).
 constexpr int kRingT = 128;    // threads per CTA
 constexpr int kRingR = 2;      // rows per thread: n <= kRingT * kRingR
 constexpr int kRingN = kRingT * kRingR;
@@ -1265,6 +1274,7 @@ __device__ __forceinline__ void send_pair(uint32_t dst, double a, double b, uint
                  : "memory");
 }
 
+template <int kRingC>
 __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
     jacobi_ring_kernel(double *X, double *V, int64_t n, int64_t G, double tol, GridBarrier bar,
                        unsigned int *rotcount, unsigned int *checkflag, double *sigma, unsigned int *colver,
@@ -1276,13 +1286,14 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
     //   x~_p <- x~_p - mu x~_q,  x~_q <- x~_q + nu x~_p,  mu = t d_q / d_p,
     //   nu = t d_p / d_q,  d_p, d_q <- c d_p, c d_q  (c = cos, t = tan of the angle),
     // the same first-order rounding as the plain rotation; the scales stay in
-    // [2^-4, 1] within an outer step (at most 8 rotations per column) and are
+    // [2^-kRingC/2, 1] within an outer step (at most kRingC rotations per column) and are
     // folded back into the columns when they are stored.  par[j] = (rotated,
     // mu, nu) of round j, announced to the V warps by mbr[j]; mbf announces
     // the final scales of the outer step to the row warps.
     static_assert(kRingR == 2, "one double2 per thread and slot");
-    __shared__ __align__(16) double2 xbuf[kRingC][kRingT];
-    __shared__ __align__(16) double2 vbuf[kRingC][kRingT];
+    extern __shared__ __align__(16) double2 ring_dyn[];  // 2 kRingC kRingT double2 (ring_smem)
+    double2(*xbuf)[kRingT] = reinterpret_cast<double2(*)[kRingT]>(ring_dyn);
+    double2(*vbuf)[kRingT] = reinterpret_cast<double2(*)[kRingT]>(ring_dyn + kRingC * kRingT);
     __shared__ __align__(16) double2 sbuf[kRingC];
     __shared__ __align__(8) unsigned long long mbx[kRingC], mbv[kRingC], mbs[kRingC], mbr[kRingC], mbf;
     __shared__ double red[16];
@@ -1754,23 +1765,35 @@ static cudaError_t launch_jacobi(const DenseWork &w, int64_t n, GridBarrier bar,
     return cudaLaunchCooperativeKernel((const void *)jacobi_coop_kernel<RPT>, (int)G, kDenseThreads, args, 0, st);
 }
 
-// The ring Jacobi (cluster size fixed at compile time) needs its G clusters,
-// 2 G kRingC >= n columns, resident at once: a cooperative launch.  Falls
-// back (sets *used = false) when the device cannot hold them or rejects the
+// The ring Jacobi (cluster size C fixed at compile time) needs its G clusters,
+// 2 G C >= n columns, resident at once: a cooperative launch.  Returns without
+// launching (*used = false) when the device cannot hold them or rejects the
 // launch.
-static cudaError_t launch_jacobi_ring(const DenseWork &w, int64_t n, GridBarrier bar, int32_t *status, int vinit,
-                                      cudaStream_t st, bool *used) {
+static size_t ring_smem(int C) { return (size_t)2 * C * kRingT * sizeof(double2); }
+
+template <int C>
+static cudaError_t launch_ring_c(const DenseWork &w, int64_t n, GridBarrier bar, int32_t *status, int vinit,
+                                 cudaStream_t st, bool *used) {
     static int state[64] = {0};  // per device: 0 unknown, 1 usable, -1 not usable
     *used = false;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaSuccess;
     if (state[dev] < 0) return cudaSuccess;
-    int64_t G = (n + 2 * kRingC - 1) / (2 * kRingC);
+    int64_t G = (n + 2 * C - 1) / (2 * C);
     if (G < 1) G = 1;
+    const size_t dyn = ring_smem(C);
+    if ((C > 8 && cudaFuncSetAttribute(jacobi_ring_kernel<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                      cudaSuccess) ||
+        cudaFuncSetAttribute(jacobi_ring_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        state[dev] = -1;
+        return cudaSuccess;
+    }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(G * kRingC), 1, 1);
+    cfg.gridDim = dim3((unsigned)(G * C), 1, 1);
     cfg.blockDim = dim3(kRingCta, 1, 1);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = dyn;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -1778,7 +1801,7 @@ static cudaError_t launch_jacobi_ring(const DenseWork &w, int64_t n, GridBarrier
     cfg.attrs = attr;
     cfg.numAttrs = 0;
     int maxc = 0;
-    if (cudaOccupancyMaxActiveClusters(&maxc, (void *)jacobi_ring_kernel, &cfg) != cudaSuccess || maxc < G) {
+    if (cudaOccupancyMaxActiveClusters(&maxc, (void *)jacobi_ring_kernel<C>, &cfg) != cudaSuccess || maxc < G) {
         cudaGetLastError();
         return cudaSuccess;
     }
@@ -1787,9 +1810,10 @@ static cudaError_t launch_jacobi_ring(const DenseWork &w, int64_t n, GridBarrier
     unsigned int *rot = w.bar + 64, *chk = w.bar + 64 + 64;
     const double tol = (double)n * std::ldexp(1.0, -53);
     unsigned int *colver = w.colver;
-    cudaError_t e = cudaMemsetAsync(colver, 0, sizeof(unsigned int) * (size_t)(n + 16), st);
+    cudaError_t e = cudaMemsetAsync(colver, 0, sizeof(unsigned int) * (size_t)(n + 32), st);
     if (e != cudaSuccess) return e;
-    e = cudaLaunchKernelEx(&cfg, jacobi_ring_kernel, X, V, n, G, tol, bar, rot, chk, sigma, colver, status, vinit);
+    e = cudaLaunchKernelEx(&cfg, jacobi_ring_kernel<C>, X, V, n, G, tol, bar, rot, chk, sigma, colver, status,
+                           vinit);
     if (e != cudaSuccess) {
         cudaGetLastError();
         state[dev] = -1;
@@ -1798,6 +1822,15 @@ static cudaError_t launch_jacobi_ring(const DenseWork &w, int64_t n, GridBarrier
     state[dev] = 1;
     *used = true;
     return cudaSuccess;
+}
+
+static cudaError_t launch_jacobi_ring(const DenseWork &w, int64_t n, GridBarrier bar, int32_t *status, int vinit,
+                                      cudaStream_t st, bool *used) {
+    if (n > 2 * 15 * 8) {  // 16 clusters of 8 would share SMs: try clusters of 16
+        const cudaError_t e = launch_ring_c<16>(w, n, bar, status, vinit, st, used);
+        if (e != cudaSuccess || *used) return e;
+    }
+    return launch_ring_c<8>(w, n, bar, status, vinit, st, used);
 }
 
 template <int NB>

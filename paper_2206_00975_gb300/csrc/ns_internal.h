@@ -129,7 +129,7 @@ struct DenseWork {
     int32_t *perm;    // n: column pivots of the first QR
     unsigned long long *pivslot;  // n + 1: pivot candidates (atomic max)
     unsigned int *bar;  // grid barrier words (2), rotation counters (64), check flags (64)
-    unsigned int *colver;  // n + 16: per-column write versions of the ring Jacobi
+    unsigned int *colver;  // n + 32: per-column write versions of the ring Jacobi
 };
 size_t dense_work_bytes(int64_t s, int64_t n);
 DenseWork dense_carve(Carver &c, int64_t s, int64_t n);
