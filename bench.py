@@ -483,7 +483,7 @@ def main():
                   "kernel": "FP64 dense stage (column order, hqr_pipe x2 with Q2 formed in the second, jacobi_ring from V = Q2, extract) via ns_solve_sketched",
                   "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x sampled SM clock",
                   "algorithmic_flops": dflops, "jacobi_sweeps_rotations_checks": stats[:3],
-                  "jacobi_kernel": "cluster ring" if stats[3] == 1 else "barrier-separated"}
+                  "jacobi_kernel": ("cluster ring, %d CTAs per cluster" % stats[3]) if stats[3] else "barrier-separated"}
     dominant = dense_roof if t_dense > t_sketch else sketch_roof
     line = {
         "metric": METRIC, "value": n_ranks * args.steps / (ms_solve / 1e3), "unit": "solves/s", "n_gpus": n_ranks,

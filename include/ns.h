@@ -144,8 +144,8 @@ ns_status ns_solve_sketched(const ns_sketch_desc *desc, const double *SA, int64_
  * the last ns_solve (ns_solve_sketched) that ran in workspace ws with the same
  * desc and shape: dev_out (device int64[4]) receives the number of full
  * sweeps, the number of rotations, the number of barrier-free check passes
- * and the kernel that ran (1: the cluster-ring Jacobi, 0: the
- * barrier-separated one).
+ * and the kernel that ran (the cluster size, 8 or 16, of the cluster-ring
+ * Jacobi, or 0: the barrier-separated one).
  * Enqueued on stream after that call.
  */
 ns_status ns_solve_stats(const ns_sketch_desc *desc, int64_t m, int64_t n, const void *ws, int64_t *dev_out,

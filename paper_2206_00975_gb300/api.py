@@ -252,7 +252,7 @@ def ns_solve_sketched(d, SA, k, save=False, status=None, ws=None, stream=None):
 
 
 def jacobi_stats(d, m, n, ws, sketched=False, stream=None):
-    """(full sweeps, rotations, check passes, ring kernel used) of the last solve in workspace ws."""
+    """(full sweeps, rotations, check passes, ring cluster size or 0) of the last solve in workspace ws."""
     out = torch.zeros(4, dtype=torch.int64, device=ws.device)
     lib = _lib.load()
     if sketched:

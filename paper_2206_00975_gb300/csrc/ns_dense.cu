@@ -912,7 +912,7 @@ __device__ void jacobi_sigma(const double *X, int64_t n, double *sigma) {
 }
 
 // statistics of the iteration: full sweeps, rotations, barrier-free checks,
-// and which kernel ran (1: cluster ring, 0: barrier-separated)
+// and which kernel ran (the cluster-ring size C, or 0: barrier-separated)
 __device__ __forceinline__ void jacobi_record_stats(unsigned int *rotcount, int full_sweeps, int check_passes,
                                                     int ring) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1634,7 +1634,7 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
     }
     if (ok) {
         if (!converged && blockIdx.x == 0 && tid == 0) set_status(status, NS_ERR_NOCONV);
-        jacobi_record_stats(rotcount, full_sweeps, check_passes, 1);
+        jacobi_record_stats(rotcount, full_sweeps, check_passes, kRingC);
         if (grid_sync(bar)) jacobi_sigma(X, n, sigma);
     }
     cluster_sync_all();  // no CTA leaves while a peer may still address its shared memory

@@ -48,7 +48,7 @@ def test_dense_stage_parity(api, s, n, k):
     torch.cuda.synchronize()
     assert int(status.item()) == 0
     stats = api.jacobi_stats(d, s, n, ws, sketched=True)
-    assert stats[3] == 1, "the cluster-ring Jacobi should run for n <= 256"
+    assert stats[3] in (8, 16), "the cluster-ring Jacobi should run for n <= 256"
     Vk_or, sk_or, V_or, sig_or, _, st = O.solve_sketched(SA, k)
     assert st == 0
     _, V, sigma = api.unpack_save(sv, s, n)
