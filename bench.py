@@ -29,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 M, N, S, K_NULL, SEED = 1 << 20, 256, 1024, 4, 0
+E2E_PARTS = 4   # concurrent host-to-device copies per step in the end-to-end leg
 METRIC = "null-space solves/s and sketch HBM GB/s (% of peak) at stated ||AV||_F accuracy"
 WORKLOAD = "at_scale: m=2^20 n=256 FP64 column-major, sigma log-spaced 1..1e-6 + 4 exact zeros, SRHT s=1024, k=4"
 FP64_FLOPS_PER_CLK_SM = 4.0   # 2 FP64 FMA per clock per SM (measured 597 GFMA/s at 1.99 GHz on 152 SMs)
@@ -410,15 +411,16 @@ def main():
 
     # end to end through the public API: every step copies its A (2 GiB) from
     # pinned host memory and reads V_k and sigma_k back.  The host copy is the
-    # contiguous (n, m) storage of the column-major A, so each step is one
-    # cudaMemcpyAsync; two device buffers and a copy stream let the copy of
-    # step i + 1 overlap the solve of step i.
+    # contiguous (n, m) storage of the column-major A, split into E2E_PARTS
+    # column ranges copied on as many streams (one copy engine each); two
+    # device buffers let the copy of step i + 1 overlap the solve of step i.
     H = A_host.t()  # (n, m) contiguous, pinned
     Dbuf = [torch.empty_like(H, device=dev), torch.empty_like(H, device=dev)]
     Vk_host = torch.empty((K_NULL, N), dtype=torch.float64).pin_memory()
     sk_host = torch.empty(K_NULL, dtype=torch.float64).pin_memory()
-    cstream = torch.cuda.Stream()
-    ready = [torch.cuda.Event(), torch.cuda.Event()]
+    parts = [(N * q) // E2E_PARTS for q in range(E2E_PARTS + 1)]
+    cstreams = [torch.cuda.Stream() for _ in range(E2E_PARTS)]
+    ready = [[torch.cuda.Event() for _ in range(E2E_PARTS)] for _ in range(2)]
     done = [torch.cuda.Event(), torch.cuda.Event()]
     e2e_steps = max(6, args.steps)
 
@@ -428,15 +430,18 @@ def main():
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        cstream.wait_stream(stream)
+        for cs in cstreams:
+            cs.wait_stream(stream)
         for i in range(steps):
             b = i & 1
-            with torch.cuda.stream(cstream):
-                if i >= 2:
-                    cstream.wait_event(done[b])
-                Dbuf[b].copy_(H, non_blocking=True)
-                ready[b].record(cstream)
-            stream.wait_event(ready[b])
+            for q, cs in enumerate(cstreams):
+                with torch.cuda.stream(cs):
+                    if i >= 2:
+                        cs.wait_event(done[b])
+                    Dbuf[b][parts[q]:parts[q + 1]].copy_(H[parts[q]:parts[q + 1]], non_blocking=True)
+                    ready[b][q].record(cs)
+            for q in range(E2E_PARTS):
+                stream.wait_event(ready[b][q])
             Vk, sk, _, _ = solve(Dbuf[b].t())
             Vk_host.copy_(Vk.t(), non_blocking=True)
             sk_host.copy_(sk, non_blocking=True)
@@ -502,7 +507,7 @@ def main():
                         "residual_AV_F": resid_sp},
         "e2e": {"value": n_ranks * e2e_steps / (ms_e2e / 1e3), "unit": "solves/s",
                 "h2d_bytes_per_step": M * N * 8, "d2h_bytes_per_step": (N * K_NULL + K_NULL) * 8,
-                "overlap": "copy of step i+1 overlaps the solve of step i (two device buffers)",
+                "overlap": "copy of step i+1 (E2E_PARTS streams) overlaps the solve of step i (two device buffers)",
                 "results_finite": e2e_ok},
         "gpu_launches": 17 * args.steps,
         "clocks": clocks,
