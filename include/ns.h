@@ -130,6 +130,25 @@ ns_status ns_solve(const ns_sketch_desc *desc, const void *A, int32_t dtype, int
                    size_t ws_bytes, void *stream);
 
 /*
+ * ns_solve_eps -- the tolerance version of Algorithm 1 (Section 2, the remark
+ * after Algorithm 1): instead of k, W is every right singular vector of SA
+ * whose singular value is below eps (eps = O(u) sigma_1 gives the numerical
+ * null space).
+ *   eps    absolute tolerance, eps >= 0 (the comparison is sigma_i < eps).
+ *   Vk     device, n x n FP64 output: columns 0..k-1 receive W, ordered and
+ *          signed as ns_solve (the last column belongs to the smallest
+ *          singular value); the other columns are left as they were.
+ *   sigk   device, n FP64 output: entries 0..k-1 receive the matching
+ *          singular values.
+ *   dev_k  device int32 output: k = #{i : sigma_i < eps}, 0 <= k <= n.
+ * Everything else as ns_solve (workspace: ns_workspace_size with any k).
+ * Errors: NS_ERR_INVALID_ARG as ns_solve, and for eps < 0 or NaN.
+ */
+ns_status ns_solve_eps(const ns_sketch_desc *desc, const void *A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                       double eps, double *Vk, double *sigk, int32_t *dev_k, double *save, int32_t *dev_status,
+                       void *ws, size_t ws_bytes, void *stream);
+
+/*
  * ns_solve_sketched -- Algorithm 1 lines 3-4 on a sketch the caller already
  * holds: SA (device, s x n FP64, ld s, s = desc->s) -> QR, Jacobi SVD, the k
  * trailing right singular vectors.  Outputs as ns_solve (save receives a copy

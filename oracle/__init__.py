@@ -57,6 +57,7 @@ def _load():
             "or_householder_qr": (i, [P, i64, i64, i64, P]),
             "or_jacobi": (i, [P, i64, P, P, dbl, i, P]),
             "or_extract": (None, [P, P, i64, i32, P, P, P]),
+            "or_count_below": (ctypes.c_int32, [P, i64, ctypes.c_double]),
             "or_sketch": (i, [i, u64, i64, i32, P, i64, i64, i64, P]),
             "or_solve_sketched": (i, [P, i64, i64, i32, P, P, P, P, P]),
             "or_solve": (i, [i, u64, i64, i32, P, i64, i64, i64, i32, P, P, P, P, P]),
@@ -254,6 +255,20 @@ def solve(kind, seed, s, A, k, zeta=8):
     st = _check(_load().or_solve(int(kind), ctypes.c_uint64(seed), s, zeta, _p(A), m, n, max(m, 1), k, _p(Vk),
                                  _p(sk), _p(SA), _p(V), _p(sig)), "solve")
     return {"Vk": Vk, "sigk": sk, "SA": SA, "V": V, "sigma": sig, "status": st}
+
+
+def solve_eps(kind, seed, s, A, eps, zeta=8):
+    """The tolerance version of Algorithm 1 (Section 2, after Algorithm 1): every right
+    singular vector of SA with sigma < eps.  Returns (Vk n x k, sigk k, k, full solve dict)."""
+    A = _f64(A)
+    n = A.shape[1]
+    full = solve(kind, seed, s, A, 1, zeta=zeta)
+    sig = np.ascontiguousarray(full["sigma"], dtype=np.float64)
+    k = int(_load().or_count_below(_p(sig), n, float(eps)))
+    if k == 0:
+        return np.zeros((n, 0), order="F"), np.zeros(0), 0, full
+    Vk, sk, _ = extract(sig, full["V"], k)
+    return Vk, sk, k, full
 
 
 def residual(A, W):

@@ -376,6 +376,16 @@ void or_extract(const double *sigma, const double *V, int64_t n, int32_t k, doub
     free(order);
 }
 
+/* The tolerance version of Algorithm 1 (Section 2, the remark after
+ * Algorithm 1): the number of singular values below eps.  W is then the
+ * trailing k = #{i : sigma_i < eps} columns in the order of or_extract. */
+int32_t or_count_below(const double *sigma, int64_t n, double eps) {
+    int32_t k = 0;
+    for (int64_t i = 0; i < n; i++)
+        if (sigma[i] < eps) k++;
+    return k;
+}
+
 /* Sketch kinds. */
 #define OR_SRHT 0
 #define OR_SPARSE_SIGN 1

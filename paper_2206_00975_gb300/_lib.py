@@ -21,7 +21,7 @@ EXPORTS = [
     "ns_status_string", "ns_version", "ns_workspace_size", "ns_save_size", "ns_sketch", "ns_solve",
     "ns_backward", "ns_residual", "ns_srht_meta", "ns_sparse_meta", "ns_sketch_static",
     "ns_batched_workspace_size", "ns_solve_batched", "ns_aaa_workspace_size", "ns_aaa_real",
-    "ns_solve_sketched", "ns_solve_stats", "ns_sketched_stats",
+    "ns_solve_sketched", "ns_solve_stats", "ns_sketched_stats", "ns_solve_eps",
 ]
 
 
@@ -76,6 +76,7 @@ def load():
         "ns_solve_sketched": (ctypes.c_int, [D, P, i64, i32, P, P, P, P, P, sz, P]),
         "ns_solve_stats": (ctypes.c_int, [D, i64, i64, P, P, P]),
         "ns_sketched_stats": (ctypes.c_int, [D, i64, P, P, P]),
+        "ns_solve_eps": (ctypes.c_int, [D, P, i32, i64, i64, i64, ctypes.c_double, P, P, P, P, P, P, sz, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

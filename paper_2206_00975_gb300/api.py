@@ -106,6 +106,29 @@ def ns_solve(d, A, k, save=True, status=None, ws=None, stream=None):
     return Vk, sigk, sv, status
 
 
+def ns_solve_eps(d, A, eps, save=True, status=None, ws=None, stream=None):
+    """Tolerance version of Algorithm 1: returns (Vk n x n, sigk n, k int32 tensor, save or None,
+    status); columns 0..k-1 of Vk hold the right singular vectors with sigma < eps."""
+    m, n = A.shape
+    dev = A.device
+    Vk = _empty_cm(n, n, dev)
+    sigk = torch.empty(n, dtype=torch.float64, device=dev)
+    kt = torch.zeros(1, dtype=torch.int32, device=dev)
+    sv = None
+    if save is True:
+        sv = torch.empty(save_size(d.s, n), dtype=torch.float64, device=dev)
+    elif isinstance(save, torch.Tensor):
+        sv = save
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+    if ws is None:
+        ws = workspace(d, m, n, 1, dev)
+    st = _lib.load().ns_solve_eps(ctypes.byref(d), _p(A), _dtype_code(A), m, n, _ld(A), float(eps), _p(Vk),
+                                  _p(sigk), _p(kt), _p(sv), _p(status), _p(ws), ws.numel(), _stream(stream))
+    _lib.check(st, "ns_solve_eps")
+    return Vk, sigk, kt, sv, status
+
+
 def unpack_save(sv, s, n):
     """Views (SA s x n, V n x n, sigma n) of a save buffer."""
     SA = sv[: s * n].view(n, s).t()

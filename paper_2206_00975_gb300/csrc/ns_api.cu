@@ -216,6 +216,28 @@ ns_status ns_solve(const ns_sketch_desc *d, const void *A, int32_t dtype, int64_
     return cuda_status(launch_dense_solve(SA, d->s, n, k, L.dense, Vk, sigk, save_V, save_sigma, status, st));
 }
 
+ns_status ns_solve_eps(const ns_sketch_desc *d, const void *A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                       double eps, double *Vk, double *sigk, int32_t *dev_k, double *save, int32_t *dev_status,
+                       void *ws, size_t ws_bytes, void *stream) {
+    if (!desc_ok(d) || !A || !Vk || !sigk || !dev_k || !ws) return NS_ERR_INVALID_ARG;
+    if (!path_ok(d, dtype) || !shape_ok(d, m, n, lda)) return NS_ERR_INVALID_ARG;
+    if (m < n || n > d->s || n > kMaxN || !(eps >= 0.0)) return NS_ERR_INVALID_ARG;
+    if ((((uintptr_t)ws) & 255) != 0 || (((uintptr_t)A) & (dtype == NS_F32 ? 3 : 7)) != 0) return NS_ERR_INVALID_ARG;
+    SolveLayout L = solve_layout(ws, d, m, n, save == nullptr);
+    if (L.bytes > ws_bytes) return NS_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *status = dev_status ? dev_status : L.status_word;
+    if (cudaMemsetAsync(status, 0, sizeof(int32_t), st) != cudaSuccess) return NS_ERR_CUDA;
+    double *SA = save ? save : L.SA;
+    ns_status r = run_sketch(d, A, m, n, lda, SA, L, status, st);
+    if (r != NS_OK) return r;
+    double *save_V = save ? save + d->s * n : nullptr;
+    double *save_sigma = save ? save + d->s * n + n * n : nullptr;
+    cudaError_t e = launch_dense_solve(SA, d->s, n, 0, L.dense, nullptr, nullptr, save_V, save_sigma, status, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    return cuda_status(launch_dense_select_eps(L.dense, n, eps, Vk, sigk, dev_k, st));
+}
+
 ns_status ns_solve_sketched(const ns_sketch_desc *d, const double *SA, int64_t n, int32_t k, double *Vk, double *sigk,
                            double *save, int32_t *dev_status, void *ws, size_t ws_bytes, void *stream) {
     if (!desc_ok(d) || !SA || !Vk || !sigk || !ws) return NS_ERR_INVALID_ARG;

@@ -1737,6 +1737,32 @@ __global__ void __launch_bounds__(kDenseThreads) extract_kernel(const double *V,
     if (tid == 0) sigk[col] = sigma[src];
 }
 
+// The tolerance version of Algorithm 1 (Section 2, after Algorithm 1): W =
+// the right singular vectors whose singular values are below eps.  Vs, ss
+// hold all n extracted columns (extract_kernel with k = n: non-increasing
+// sigma, signed), so those are the last k = #{sigma < eps}; they go to
+// columns 0..k-1 of Vk in the same order, and k to *dev_k.
+__global__ void __launch_bounds__(kDenseThreads) eps_select_kernel(const double *__restrict__ Vs,
+                                                                  const double *__restrict__ ss, int64_t n,
+                                                                  double eps, double *__restrict__ Vk,
+                                                                  double *__restrict__ sigk, int32_t *dev_k) {
+    __shared__ int s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    int c = 0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) c += (ss[i] < eps) ? 1 : 0;
+    atomicAdd(&s_cnt, c);  // an integer count: the order of the adds does not matter
+    __syncthreads();
+    const int64_t k = s_cnt;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *dev_k = (int32_t)k;
+    for (int64_t col = blockIdx.x; col < k; col += gridDim.x) {
+        const int64_t src = n - k + col;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Vk[i + col * n] = Vs[i + src * n];
+        if (threadIdx.x == 0) sigk[col] = ss[src];
+    }
+}
+
+
 __global__ void copy_kernel(const double *__restrict__ a, int64_t len, double *__restrict__ b) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
         b[i] = a[i];
@@ -1747,6 +1773,17 @@ static int sm_count() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return sms > 0 ? sms : 1;
+}
+
+cudaError_t launch_dense_select_eps(const DenseWork &w, int64_t n, double eps, double *Vk, double *sigk,
+                                    int32_t *dev_k, cudaStream_t st) {
+    // all n columns in order into X (free after the iteration), their sigma into L
+    extract_kernel<<<(unsigned)n, kDenseThreads, 0, st>>>(w.W, w.sigma, n, (int32_t)n, w.X, w.L);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = n < sm_count() * 4 ? n : sm_count() * 4;
+    eps_select_kernel<<<(unsigned)blocks, kDenseThreads, 0, st>>>(w.X, w.L, n, eps, Vk, sigk, dev_k);
+    return cudaGetLastError();
 }
 
 template <int RPT>
@@ -1992,9 +2029,11 @@ cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k
         apply_q2_kernel<<<(unsigned)blocks, kDenseThreads, smem, st>>>(Lq, u0b, cfb, w.perm, w.V, n, w.W);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    // 5. extraction (and the save buffers)
-    extract_kernel<<<(unsigned)k, kDenseThreads, 0, st>>>(w.W, w.sigma, n, k, Vk, sigk);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // 5. extraction (k = 0: left to the caller, V in w.W and sigma in w.sigma)
+    if (k > 0) {
+        extract_kernel<<<(unsigned)k, kDenseThreads, 0, st>>>(w.W, w.sigma, n, k, Vk, sigk);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     if (save_V) {
         copy_kernel<<<64, 256, 0, st>>>(w.W, n * n, save_V);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

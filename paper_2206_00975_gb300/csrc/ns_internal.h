@@ -134,6 +134,9 @@ struct DenseWork {
 size_t dense_work_bytes(int64_t s, int64_t n);
 DenseWork dense_carve(Carver &c, int64_t s, int64_t n);
 cudaError_t launch_dense_stats(const DenseWork &w, int64_t *out, cudaStream_t st);
+// after launch_dense_solve with k = 0: the tolerance selection (Vk n x n, sigk n, k in *dev_k)
+cudaError_t launch_dense_select_eps(const DenseWork &w, int64_t n, double eps, double *Vk, double *sigk,
+                                    int32_t *dev_k, cudaStream_t st);
 cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k, const DenseWork &w, double *Vk,
                                double *sigk, double *save_V, double *save_sigma, int32_t *status, cudaStream_t st);
 

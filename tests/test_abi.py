@@ -94,3 +94,15 @@ def test_null_pointers_rejected(lib):
     assert lib.ns_sketch(ctypes.byref(d), None, _lib.NS_F64, 100, 4, 100, FAKE, FAKE, 1 << 30, None) == \
         _lib.NS_ERR_INVALID_ARG
     assert lib.ns_sketch(None, FAKE, _lib.NS_F64, 100, 4, 100, FAKE, FAKE, 1 << 30, None) == _lib.NS_ERR_INVALID_ARG
+
+
+def test_solve_eps_rejects_bad_tolerance(lib):
+    d = _desc(s=64)
+    for eps in (-1.0, float("nan")):
+        st = lib.ns_solve_eps(ctypes.byref(d), FAKE, _lib.NS_F64, 100, 4, 100, eps, FAKE, FAKE, FAKE, None, None,
+                              FAKE, 1 << 30, None)
+        assert st == _lib.NS_ERR_INVALID_ARG
+    # a missing k output
+    st = lib.ns_solve_eps(ctypes.byref(d), FAKE, _lib.NS_F64, 100, 4, 100, 1e-8, FAKE, FAKE, None, None, None,
+                          FAKE, 1 << 30, None)
+    assert st == _lib.NS_ERR_INVALID_ARG

@@ -497,3 +497,35 @@ def test_backward_gauge_invariance():
     flip = np.array([1.0, -1.0])
     dA3 = O.backward_srht(1, s, m, out["SA"], out["V"], out["sigma"], out["Vk"] * flip, dV * flip)
     assert np.linalg.norm(dA1 - dA3) <= 1e-12 * np.linalg.norm(dA1)
+
+
+# --------------------------------------------------- tolerance version ----
+def test_solve_eps_finds_the_exact_null_space():
+    # Section 2, after Algorithm 1: with sigma(A) = (1 .. 1e-3, 0, 0, 0) the
+    # sketch keeps the three exact zeros (SA x = 0 whenever A x = 0) and the
+    # nonzero values within a constant factor, so eps = 1e-8 selects exactly 3
+    # vectors, and they annihilate A.
+    w = workloads.at_scale(seed=3, m=2048, n=24, null_dim=3)
+    A = w["A"]
+    Vk, sk, k, full = O.solve_eps(O.SRHT, 0, 96, A, 1e-8)
+    assert k == 3
+    assert np.all(sk < 1e-8)
+    assert np.linalg.norm(A @ Vk) <= 1e-13 * np.linalg.norm(A)
+    assert sine(w["V"][:, -3:], Vk) < 1e-10
+    # the same vectors, order and signs as the fixed-k solve
+    ref = O.solve(O.SRHT, 0, 96, A, 3)
+    np.testing.assert_array_equal(Vk, ref["Vk"])
+    np.testing.assert_array_equal(sk, ref["sigk"])
+
+
+def test_solve_eps_limits():
+    # eps = 0 selects nothing (singular values are >= 0); eps above sigma_1
+    # selects everything: W is then all of V, orthonormal
+    w = workloads.plain(seed=1, m=512, n=12)
+    A = w["A"]
+    _, _, k0, _ = O.solve_eps(O.SRHT, 0, 48, A, 0.0)
+    assert k0 == 0
+    Vk, sk, kn, full = O.solve_eps(O.SRHT, 0, 48, A, 2.0 * np.linalg.norm(A, 2) * 2)
+    assert kn == 12
+    assert np.all(np.diff(sk) <= 0)  # non-increasing, the smallest last
+    np.testing.assert_allclose(Vk.T @ Vk, np.eye(12), atol=1e-13)
