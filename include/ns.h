@@ -149,6 +149,32 @@ ns_status ns_solve_eps(const ns_sketch_desc *desc, const void *A, int32_t dtype,
                        void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * ns_sketch_update -- keep a sketch SA current when A gains or loses a row
+ * (Section 5: Algorithms 2 and 3, and the rule for non-Gaussian sketches).
+ *   m0    the row count SA was sketched with (sets m' and which columns of S
+ *         are SRHT or sparse-sign columns).
+ *   op    NS_ROW_APPEND: A gains the row `row` with index j >= m0 (appended
+ *         rows are numbered m0, m0 + 1, ...); S gains the column g / sqrt(s),
+ *         g the Gaussian sketch's column j for desc->seed (Philox stream 3),
+ *         and SA += g row / sqrt(s).
+ *         NS_ROW_REMOVE: A loses row j, whose entries are `row`; SA -= (S e_j)
+ *         row, with S e_j regenerated from desc: the SRHT column
+ *         d_j (-1)^popcount(r_t & j) / sqrt(s) or the sparse-sign column for
+ *         j < m0, the Gaussian column j for a row appended earlier (j >= m0) and
+ *         for the Gaussian kind.
+ *   row   device, n FP64 (the row's entries).
+ *   SA    device, s x n FP64, leading dimension s, updated in place.
+ * O(s n) work, enqueued on stream.  A column of A is added by sketching it
+ * with ns_sketch (n = 1, the same desc and m0) and appending it to SA; a column
+ * is removed by dropping it from SA.
+ * Errors: NS_ERR_INVALID_ARG for a bad desc or op, j < 0, an append with
+ * j < m0, m0 < 1, n < 1, an SRHT s > m', or a NULL pointer.
+ */
+enum { NS_ROW_APPEND = 0, NS_ROW_REMOVE = 1 };
+ns_status ns_sketch_update(const ns_sketch_desc *desc, int64_t m0, int32_t op, int64_t j, const double *row,
+                           int64_t n, double *SA, void *stream);
+
+/*
  * ns_solve_sketched -- Algorithm 1 lines 3-4 on a sketch the caller already
  * holds: SA (device, s x n FP64, ld s, s = desc->s) -> QR, Jacobi SVD, the k
  * trailing right singular vectors.  Outputs as ns_solve (save receives a copy

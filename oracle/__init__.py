@@ -58,6 +58,8 @@ def _load():
             "or_jacobi": (i, [P, i64, P, P, dbl, i, P]),
             "or_extract": (None, [P, P, i64, i32, P, P, P]),
             "or_count_below": (ctypes.c_int32, [P, i64, ctypes.c_double]),
+            "or_sketch_update": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, i64, i32, i64, ctypes.c_int, i64, P,
+                                                i64, P]),
             "or_sketch": (i, [i, u64, i64, i32, P, i64, i64, i64, P]),
             "or_solve_sketched": (i, [P, i64, i64, i32, P, P, P, P, P]),
             "or_solve": (i, [i, u64, i64, i32, P, i64, i64, i64, i32, P, P, P, P, P]),
@@ -269,6 +271,16 @@ def solve_eps(kind, seed, s, A, eps, zeta=8):
         return np.zeros((n, 0), order="F"), np.zeros(0), 0, full
     Vk, sk, _ = extract(sig, full["V"], k)
     return Vk, sk, k, full
+
+
+def sketch_update(kind, seed, s, SA, m0, op, j, row, zeta=8):
+    """Section 5 row update of a sketch (op 0: Algorithm 2, append row j >= m0; op 1:
+    Algorithm 3, remove row j).  Returns the updated copy of SA."""
+    SA = _f64(SA).copy(order="F")
+    row = np.ascontiguousarray(row, dtype=np.float64)
+    _check(_load().or_sketch_update(int(kind), ctypes.c_uint64(seed), int(s), int(zeta), int(m0), int(op), int(j),
+                                    _p(row), row.size, _p(SA)), "sketch_update")
+    return SA
 
 
 def residual(A, W):

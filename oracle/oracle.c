@@ -399,6 +399,35 @@ int or_sketch(int kind, uint64_t seed, int64_t s, int32_t zeta, const double *A,
     return OR_ERR_INVALID_ARG;
 }
 
+/* Section 5, row updates of a sketch SA (s x n) of an m0-row A.
+ * op 0 (Algorithm 2): A gains `row` as row j >= m0; S gains the column
+ *   g / sqrt(s), g_r = G(r, j) (the Gaussian sketch's column j), and
+ *   SA += g row / sqrt(s).
+ * op 1 (Algorithm 3 and the non-Gaussian rule): A loses row j; SA -= (S e_j)
+ *   row, where S e_j is the sketch of the unit vector e_j of length m0 for
+ *   j < m0 (the SRHT or sparse-sign column), the Gaussian column j otherwise. */
+int or_sketch_update(int kind, uint64_t seed, int64_t s, int32_t zeta, int64_t m0, int op, int64_t j,
+                     const double *row, int64_t n, double *SA) {
+    if (s < 1 || m0 < 1 || n < 1 || j < 0 || (op != 0 && op != 1) || (op == 0 && j < m0))
+        return OR_ERR_INVALID_ARG;
+    double *col = (double *)calloc((size_t)s, sizeof(double));
+    int st = OR_OK;
+    if (op == 0 || j >= m0 || kind == OR_GAUSSIAN) {
+        for (int64_t r = 0; r < s; r++) col[r] = or_gaussian_entry(seed, r, j) / sqrt((double)s);
+    } else {
+        double *e = (double *)calloc((size_t)m0, sizeof(double));
+        e[j] = 1.0;
+        st = or_sketch(kind, seed, s, zeta, e, m0, 1, m0, col);
+        free(e);
+    }
+    const double sign = (op == 0) ? 1.0 : -1.0;
+    if (st == OR_OK)
+        for (int64_t c = 0; c < n; c++)
+            for (int64_t r = 0; r < s; r++) SA[r + c * s] += sign * col[r] * row[c];
+    free(col);
+    return st;
+}
+
 /* Algorithm 1 on an already-formed sketch SA (s x n, leading dimension s):
  * QR, Jacobi SVD of R, extraction.  V_full (n x n) and sigma_full (n) receive
  * the Jacobi result (may be NULL). */

@@ -15,13 +15,14 @@ NS_ERR_NOCONV, NS_ERR_TLS_NOSOLUTION, NS_ERR_TIMEOUT, NS_ERR_CUDA = 4, 5, 6, 7
 NS_SRHT, NS_SPARSE_SIGN, NS_GAUSSIAN = 0, 1, 2
 NS_F64, NS_F32 = 0, 1
 NS_PREC_FP64, NS_PREC_FP32_STREAM, NS_PREC_BF16X3 = 0, 1, 2
+NS_ROW_APPEND, NS_ROW_REMOVE = 0, 1
 
 # every symbol include/ns.h declares
 EXPORTS = [
     "ns_status_string", "ns_version", "ns_workspace_size", "ns_save_size", "ns_sketch", "ns_solve",
     "ns_backward", "ns_residual", "ns_srht_meta", "ns_sparse_meta", "ns_sketch_static",
     "ns_batched_workspace_size", "ns_solve_batched", "ns_aaa_workspace_size", "ns_aaa_real",
-    "ns_solve_sketched", "ns_solve_stats", "ns_sketched_stats", "ns_solve_eps",
+    "ns_solve_sketched", "ns_solve_stats", "ns_sketched_stats", "ns_solve_eps", "ns_sketch_update",
 ]
 
 
@@ -77,6 +78,7 @@ def load():
         "ns_solve_stats": (ctypes.c_int, [D, i64, i64, P, P, P]),
         "ns_sketched_stats": (ctypes.c_int, [D, i64, P, P, P]),
         "ns_solve_eps": (ctypes.c_int, [D, P, i32, i64, i64, i64, ctypes.c_double, P, P, P, P, P, P, sz, P]),
+        "ns_sketch_update": (ctypes.c_int, [D, i64, i32, i64, P, i64, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -13,7 +13,7 @@ import torch
 from . import _lib
 from ._lib import Problem  # noqa: F401
 from ._lib import (NS_F32, NS_F64, NS_GAUSSIAN, NS_PREC_BF16X3, NS_PREC_FP32_STREAM, NS_PREC_FP64,  # noqa: F401
-                   NS_SPARSE_SIGN, NS_SRHT, NSError, SketchDesc)
+                   NS_ROW_APPEND, NS_ROW_REMOVE, NS_SPARSE_SIGN, NS_SRHT, NSError, SketchDesc)
 
 
 def desc(kind=NS_SRHT, s=0, seed=0, zeta=8, prec=NS_PREC_FP64):
@@ -127,6 +127,17 @@ def ns_solve_eps(d, A, eps, save=True, status=None, ws=None, stream=None):
                                   _p(sigk), _p(kt), _p(sv), _p(status), _p(ws), ws.numel(), _stream(stream))
     _lib.check(st, "ns_solve_eps")
     return Vk, sigk, kt, sv, status
+
+
+def ns_sketch_update(d, m0, op, j, row, SA, stream=None):
+    """Section 5 row update of a sketch in place: op NS_ROW_APPEND (row index j >= m0) or
+    NS_ROW_REMOVE (row j); row is the row's n entries (device FP64), SA s x n column-major."""
+    n = SA.shape[1]
+    row = row.contiguous()
+    st = _lib.load().ns_sketch_update(ctypes.byref(d), int(m0), int(op), int(j), _p(row), n, _p(SA),
+                                      _stream(stream))
+    _lib.check(st, "ns_sketch_update")
+    return SA
 
 
 def unpack_save(sv, s, n):

@@ -238,6 +238,17 @@ ns_status ns_solve_eps(const ns_sketch_desc *d, const void *A, int32_t dtype, in
     return cuda_status(launch_dense_select_eps(L.dense, n, eps, Vk, sigk, dev_k, st));
 }
 
+ns_status ns_sketch_update(const ns_sketch_desc *d, int64_t m0, int32_t op, int64_t j, const double *row, int64_t n,
+                           double *SA, void *stream) {
+    if (!desc_ok(d) || !row || !SA) return NS_ERR_INVALID_ARG;
+    if (m0 < 1 || n < 1 || j < 0 || (op != NS_ROW_APPEND && op != NS_ROW_REMOVE)) return NS_ERR_INVALID_ARG;
+    if (op == NS_ROW_APPEND && j < m0) return NS_ERR_INVALID_ARG;
+    if (d->kind == NS_SRHT && d->s > ((int64_t)1 << ceil_log2(m0 > kBlock ? m0 : kBlock))) return NS_ERR_INVALID_ARG;
+    if (n > kMaxN * 64) return NS_ERR_INVALID_ARG;
+    return cuda_status(launch_sketch_update(d->kind, d->seed, d->s, d->zeta, m0, op, j, row, n, SA,
+                                            (cudaStream_t)stream));
+}
+
 ns_status ns_solve_sketched(const ns_sketch_desc *d, const double *SA, int64_t n, int32_t k, double *Vk, double *sigk,
                            double *save, int32_t *dev_status, void *ws, size_t ws_bytes, void *stream) {
     if (!desc_ok(d) || !SA || !Vk || !sigk || !ws) return NS_ERR_INVALID_ARG;

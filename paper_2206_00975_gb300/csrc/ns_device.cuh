@@ -64,6 +64,30 @@ __device__ __forceinline__ uint32_t sample_perm(uint64_t seed, int lg, uint32_t 
     return (uint32_t)((hi << nlo) | lo);
 }
 
+// Floyd's sampling of zeta distinct rows of [0, s) for column j of S.
+__device__ __forceinline__ void sparse_column(uint64_t seed, int64_t s, int zeta, int64_t j, int32_t *rows,
+                                              int8_t *signs) {
+    uint64_t w[64];
+    for (int q = 0; q < (zeta + 3) / 4; ++q) {
+        const u64x4 b = draw(seed, (uint64_t)j, (uint64_t)q, 2);
+        w[4 * q + 0] = b.w[0];
+        w[4 * q + 1] = b.w[1];
+        w[4 * q + 2] = b.w[2];
+        w[4 * q + 3] = b.w[3];
+    }
+    for (int i = 0; i < zeta; ++i) {
+        const int64_t bound = s - zeta + i;
+        int64_t t = (int64_t)__umul64hi(w[i], (uint64_t)(bound + 1));
+        for (int u = 0; u < i; ++u)
+            if (rows[u] == t) {
+                t = bound;
+                break;
+            }
+        rows[i] = (int32_t)t;
+        signs[i] = (w[i] & 1ull) ? -1 : 1;
+    }
+}
+
 // ------------------------------------------------------------ reductions ----
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {

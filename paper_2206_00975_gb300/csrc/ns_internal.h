@@ -134,6 +134,9 @@ struct DenseWork {
 size_t dense_work_bytes(int64_t s, int64_t n);
 DenseWork dense_carve(Carver &c, int64_t s, int64_t n);
 cudaError_t launch_dense_stats(const DenseWork &w, int64_t *out, cudaStream_t st);
+// Section 5 row updates of a sketch (op 0: append row index j, 1: remove row j)
+cudaError_t launch_sketch_update(int kind, uint64_t seed, int64_t s, int zeta, int64_t m0, int op, int64_t j,
+                                 const double *row, int64_t n, double *SA, cudaStream_t st);
 // after launch_dense_solve with k = 0: the tolerance selection (Vk n x n, sigk n, k in *dev_k)
 cudaError_t launch_dense_select_eps(const DenseWork &w, int64_t n, double eps, double *Vk, double *sigk,
                                     int32_t *dev_k, cudaStream_t st);

@@ -106,3 +106,10 @@ def test_solve_eps_rejects_bad_tolerance(lib):
     st = lib.ns_solve_eps(ctypes.byref(d), FAKE, _lib.NS_F64, 100, 4, 100, 1e-8, FAKE, FAKE, None, None, None,
                           FAKE, 1 << 30, None)
     assert st == _lib.NS_ERR_INVALID_ARG
+
+
+def test_sketch_update_rejects_bad_arguments(lib):
+    d = _desc(s=64)
+    for m0, op, j in ((100, 2, 5), (100, 0, 50), (0, 1, 0), (100, 1, -1)):
+        assert lib.ns_sketch_update(ctypes.byref(d), m0, op, j, FAKE, 4, FAKE, None) == _lib.NS_ERR_INVALID_ARG
+    assert lib.ns_sketch_update(ctypes.byref(d), 100, 1, 5, None, 4, FAKE, None) == _lib.NS_ERR_INVALID_ARG

@@ -529,3 +529,46 @@ def test_solve_eps_limits():
     assert kn == 12
     assert np.all(np.diff(sk) <= 0)  # non-increasing, the smallest last
     np.testing.assert_allclose(Vk.T @ Vk, np.eye(12), atol=1e-13)
+
+
+# ------------------------------------------------------ row updates (Section 5) ----
+@pytest.mark.parametrize("kind", [O.SRHT, O.SPARSE_SIGN, O.GAUSSIAN])
+def test_row_remove_equals_sketch_with_row_zeroed(kind):
+    # Removing row j from the sketch is sketching A with row j set to zero
+    # (Section 5: removing column j of S zeroes row j's contribution).  This
+    # pins the regenerated column S e_j against the full sketch.
+    rng = np.random.default_rng(kind + 7)
+    m, n, s, j = 700, 5, 64, 333
+    A = np.asfortranarray(rng.standard_normal((m, n)))
+    SA = O.sketch(kind, 5, s, A, zeta=8)
+    upd = O.sketch_update(kind, 5, s, SA, m, 1, j, A[j, :], zeta=8)
+    A0 = A.copy(order="F")
+    A0[j, :] = 0.0
+    ref = O.sketch(kind, 5, s, A0, zeta=8)
+    np.testing.assert_allclose(upd, ref, rtol=0, atol=1e-13 * np.linalg.norm(SA))
+
+
+def test_gaussian_row_append_equals_sketch_of_grown_matrix():
+    # Algorithm 2: [G | g_{m+1}] is the Gaussian sketch of m + 1 rows, so the
+    # updated sketch equals the Gaussian sketch of [A; a].
+    rng = np.random.default_rng(3)
+    m, n, s = 301, 4, 32
+    A = np.asfortranarray(rng.standard_normal((m, n)))
+    a = rng.standard_normal(n)
+    SA = O.sketch(O.GAUSSIAN, 11, s, A)
+    upd = O.sketch_update(O.GAUSSIAN, 11, s, SA, m, 0, m, a)
+    ref = O.sketch(O.GAUSSIAN, 11, s, np.asfortranarray(np.vstack([A, a[None, :]])))
+    np.testing.assert_allclose(upd, ref, rtol=0, atol=1e-13 * np.linalg.norm(ref))
+
+
+@pytest.mark.parametrize("kind", [O.SRHT, O.SPARSE_SIGN])
+def test_row_append_then_remove_restores(kind):
+    rng = np.random.default_rng(kind + 20)
+    m, n, s = 900, 3, 48
+    A = np.asfortranarray(rng.standard_normal((m, n)))
+    SA = O.sketch(kind, 2, s, A, zeta=8)
+    a = rng.standard_normal(n)
+    up = O.sketch_update(kind, 2, s, SA, m, 0, m + 4, a, zeta=8)
+    assert np.linalg.norm(up - SA) > 0.1 * np.linalg.norm(a)
+    back = O.sketch_update(kind, 2, s, up, m, 1, m + 4, a, zeta=8)
+    np.testing.assert_allclose(back, SA, rtol=0, atol=1e-13 * np.linalg.norm(SA))
