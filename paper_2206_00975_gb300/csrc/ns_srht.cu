@@ -117,6 +117,42 @@ __global__ void __launch_bounds__(64) srht_f64_chunk_kernel(const double *__rest
     if (nonfinite) set_status(status, NS_ERR_NONFINITE);
 }
 
+__global__ void __launch_bounds__(128, 4) srht_f64_chunk128_kernel(const double *__restrict__ A, int64_t m, int64_t n,
+                                                            int64_t lda, int64_t s, int chunk, int64_t nchunk,
+                                                            int P, const uint32_t *__restrict__ sign_words,
+                                                            const int32_t *__restrict__ rows,
+                                                            double *__restrict__ partial, int32_t *status,
+                                                            int vec_ok) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    long long *Zs = (long long *)smem_raw;                       // 4096
+    long long *acc = Zs + kBlock;                                // s
+    uint32_t *sgn = (uint32_t *)(acc + s);                       // 128
+    int *red = (int *)(sgn + 128);                               // 4
+    int32_t *rows_s = (int32_t *)(red + 4);                      // s
+
+    const int t = threadIdx.x;
+    const int64_t item = blockIdx.x;
+    const int64_t c = item / nchunk, ch = item - c * nchunk;
+    const double *Acol = A + c * lda;
+
+    for (int64_t i = t; i < s; i += 128) {
+        rows_s[i] = srht_pack_row(rows[i]);
+        acc[i] = 0;
+    }
+    __syncthreads();
+
+    int Erun = 0;  // running biased exponent of the chunk (0: none yet)
+    int nonfinite = 0;
+    for (int bl = 0; bl < chunk; ++bl)
+        srht_f64_block128(Acol, m, s, ch * chunk + bl, P, sign_words, rows_s, Zs, acc, sgn, red, vec_ok, Erun,
+                       nonfinite, bl + 1 < chunk);
+    // chunk partial in FP64: value = acc * 2^(E - 1022 - P)
+    const double scale = ldexp(1.0, Erun - 1022 - P);
+    double *out = partial + (ch * n + c) * s;
+    for (int64_t i = t; i < s; i += 128) out[i] = (double)acc[i] * scale;
+    if (nonfinite) set_status(status, NS_ERR_NONFINITE);
+}
+
 // SA[t, c] = (1/sqrt s) * sum over chunks, in chunk order (deterministic)
 __global__ void srht_reduce_kernel(const double *__restrict__ partial, int64_t n, int64_t s, int64_t nchunk,
                                    double scale, double *__restrict__ SA) {
@@ -388,13 +424,13 @@ cudaError_t launch_srht_f64(const double *A, int64_t m, int64_t n, int64_t lda, 
                             double *SA, int32_t *status, cudaStream_t st) {
     const SrhtGeom g = srht_geom(m, n);
     const size_t smem = srht_f64_smem(s);
-    cudaError_t e = cudaFuncSetAttribute(srht_f64_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(srht_f64_chunk128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const int vec_ok = ((((uintptr_t)A) & 15) == 0 && (lda & 1) == 0) ? 1 : 0;
     const int64_t items = n * g.nchunk;
-    srht_f64_chunk_kernel<<<(unsigned)items, 64, smem, st>>>(A, m, n, lda, s, g.chunk, g.nchunk, g.fx_bits,
-                                                             w.sign_words, w.rows, w.partial, status, vec_ok);
+    srht_f64_chunk128_kernel<<<(unsigned)items, 128, smem, st>>>(A, m, n, lda, s, g.chunk, g.nchunk, g.fx_bits,
+                                                                 w.sign_words, w.rows, w.partial, status, vec_ok);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int threads = 256;

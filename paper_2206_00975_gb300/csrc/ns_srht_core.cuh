@@ -129,6 +129,129 @@ __device__ __forceinline__ void srht_f64_block(const double *__restrict__ Acol, 
     __syncthreads();
 }
 
+// in-register Walsh-Hadamard transform of 32 values (Sylvester order on the
+// register index)
+__device__ __forceinline__ void fwht32(long long (&z)[32]) {
+#pragma unroll
+    for (int h = 1; h < 32; h <<= 1) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            if ((k & h) == 0) {
+                const long long a = z[k], b = z[k + h];
+                z[k] = a + b;
+                z[k + h] = a - b;
+            }
+        }
+    }
+}
+
+// The same block pipeline with 128 threads of 32 values (twice the warps per
+// SM of the 64-thread form, for the same shared memory):
+//   layout A: thread t, register k holds element (k & 1) | (t << 1) | ((k >> 1) << 8);
+//     registers carry index bits 0, 8..11 and lanes bits 1..5, so H over bits
+//     0, 8..11 runs in registers and over bits 1, 2 by two lane butterflies;
+//   layout B: thread t, register k holds element (t & 7) | (k << 3) | ((t >> 3) << 8);
+//     registers carry bits 3..7, the remaining five.
+// One swizzled transpose separates them; the lanes of a warp reading one
+// register of layout B differ in index bits 0-2, 8, 9, which swz spreads over
+// all banks.  Exact integer adds: the result is the 64-thread form's, bit for bit.
+__device__ __forceinline__ void srht_f64_block128(const double *__restrict__ Acol, int64_t m, int64_t s, int64_t b,
+                                                  int P, const uint32_t *__restrict__ sign_words,
+                                                  const int32_t *rows_s, long long *Zs, long long *acc,
+                                                  uint32_t *sgn, int *red, int vec_ok, int &Erun, int &nonfinite,
+                                                  bool prefetch_next) {
+    const int t = threadIdx.x, lane = t & 31;
+    const int64_t base = b * kBlock;
+    sgn[t] = sign_words[(base >> 5) + t];
+    if (t == 0 && prefetch_next && vec_ok && base + 2 * kBlock <= m)  // the next block, into L2
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(Acol + base + kBlock),
+                     "r"((uint32_t)(kBlock * 8))
+                     : "memory");
+    long long z[32];
+    if (vec_ok && base + kBlock <= m) {
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            const double2 v = __ldcs((const double2 *)(Acol + base + 2 * t + 256 * kk));
+            z[2 * kk] = __double_as_longlong(v.x);
+            z[2 * kk + 1] = __double_as_longlong(v.y);
+        }
+    } else {
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            const int64_t i0 = base + 2 * t + 256 * kk;
+            z[2 * kk] = (i0 < m) ? __double_as_longlong(__ldcs(Acol + i0)) : 0;
+            z[2 * kk + 1] = (i0 + 1 < m) ? __double_as_longlong(__ldcs(Acol + i0 + 1)) : 0;
+        }
+    }
+    unsigned int hmax = 0x00100000u;  // biased exponent 1
+#pragma unroll
+    for (int k = 0; k < 32; ++k) hmax = max(hmax, (unsigned int)((unsigned long long)z[k] >> 32) & 0x7FF00000u);
+    hmax = warp_max(hmax);
+    if (lane == 0) red[t >> 5] = (int)(hmax >> 20);
+    __syncthreads();  // also publishes sgn[]
+    const int emax = max(max(red[0], red[1]), max(red[2], red[3]));
+    if (emax == 0x7FF) nonfinite = 1;
+    if (emax > Erun) {
+        if (Erun > 0) {
+            const int d = emax - Erun;
+            for (int64_t i = t; i < s; i += 128) acc[i] = (d >= 63) ? (acc[i] >> 63) : (acc[i] >> d);
+        }
+        Erun = emax;
+    }
+    const int sh1b = Erun + 52 - P;
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+        const uint32_t sw = sgn[8 * kk + (t >> 4)] >> (2 * (t & 15));
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const unsigned long long raw = (unsigned long long)z[2 * kk + h];
+            const uint32_t hi = (uint32_t)(raw >> 32);
+            const int e = (int)((hi >> 20) & 0x7FF), e1 = max(e, 1);
+            const uint32_t sh1 = (uint32_t)(sh1b - e1);
+            const uint32_t mhi = (hi & 0x000FFFFFu) | ((uint32_t)(1 - (e1 - e)) << 20);
+            const unsigned long long mant = ((unsigned long long)mhi << 32) | (uint32_t)raw;
+            unsigned long long q1;
+            asm("shr.b64 %0, %1, %2;" : "=l"(q1) : "l"(mant), "r"(sh1));
+            const unsigned long long q = (q1 + 1ull) >> 1;
+            const long long msk = (long long)(int)((hi ^ (sw << (31 - h))) & 0x80000000u) >> 31;
+            z[2 * kk + h] = ((long long)q ^ msk) - msk;
+        }
+    }
+    fwht32(z);  // index bits 0, 8..11
+#pragma unroll
+    for (int lv = 1; lv <= 2; lv <<= 1) {  // index bits 1, 2: lanes t ^ 1, t ^ 2
+        const bool upper = (lane & lv) != 0;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const long long o = __shfl_xor_sync(0xffffffffu, z[k], lv);
+            z[k] = upper ? o - z[k] : z[k] + o;
+        }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+        const int i = 2 * t + 256 * kk;
+        longlong2 v;
+        v.x = z[2 * kk];
+        v.y = z[2 * kk + 1];
+        *(longlong2 *)(Zs + swz(i)) = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 32; ++k) z[k] = Zs[swz((t & 7) | (k << 3) | ((t >> 3) << 8))];
+    __syncthreads();
+    fwht32(z);  // index bits 3..7
+#pragma unroll
+    for (int k = 0; k < 32; ++k) Zs[swz((t & 7) | (k << 3) | ((t >> 3) << 8))] = z[k];
+    __syncthreads();
+    for (int64_t i = t; i < s; i += 128) {
+        const uint32_t pr = (uint32_t)rows_s[i];  // srht_pack_row: (hi(r) << 12) | swz(lo(r))
+        const long long v = Zs[pr & (kBlock - 1)];
+        const long long msk = -(long long)(__popc(pr >> kBlockLog & (uint32_t)b) & 1);
+        acc[i] += (v ^ msk) - msk;
+    }
+    __syncthreads();
+}
+
 // sample row r as the gather uses it: (hi(r) << 12) | swz(lo(r)) (r < 2^31)
 __device__ __forceinline__ int32_t srht_pack_row(int32_t r) {
     return (int32_t)(((uint32_t)r >> kBlockLog << kBlockLog) | (uint32_t)swz(r & (kBlock - 1)));
