@@ -146,15 +146,16 @@ __device__ __forceinline__ void fwht32(long long (&z)[32]) {
 }
 
 // The same block pipeline with 128 threads of 32 values (twice the warps per
-// SM of the 64-thread form, for the same shared memory):
-//   layout A: thread t, register k holds element (k & 1) | (t << 1) | ((k >> 1) << 8);
-//     registers carry index bits 0, 8..11 and lanes bits 1..5, so H over bits
-//     0, 8..11 runs in registers and over bits 1, 2 by two lane butterflies;
-//   layout B: thread t, register k holds element (t & 7) | (k << 3) | ((t >> 3) << 8);
-//     registers carry bits 3..7, the remaining five.
-// One swizzled transpose separates them; the lanes of a warp reading one
-// register of layout B differ in index bits 0-2, 8, 9, which swz spreads over
-// all banks.  Exact integer adds: the result is the 64-thread form's, bit for bit.
+// SM of the 64-thread form, for the same shared memory), H in three register
+// phases around two swizzled transposes:
+//   layout A: thread t, register k holds element (k & 1) | (t << 1) | ((k >> 1) << 8)
+//     (H over index bits 0, 8..11);
+//   layout B: (t & 1) | (k << 1) | ((t >> 1) << 6)  (bits 1..5);
+//   layout C: (t & 63) | (k << 6) | ((t >> 6) << 11)  (bits 6, 7: the first
+//     two register bits only; bits 8..10 are done).
+// The lanes of a warp reading one register of layout B (C) differ in index
+// bits 0, 6..9 (0..4), which swz spreads over all banks.  Exact integer adds:
+// the result is the 64-thread form's, bit for bit.
 __device__ __forceinline__ void srht_f64_block128(const double *__restrict__ Acol, int64_t m, int64_t s, int64_t b,
                                                   int P, const uint32_t *__restrict__ sign_words,
                                                   const int32_t *rows_s, long long *Zs, long long *acc,
@@ -219,15 +220,6 @@ __device__ __forceinline__ void srht_f64_block128(const double *__restrict__ Aco
     }
     fwht32(z);  // index bits 0, 8..11
 #pragma unroll
-    for (int lv = 1; lv <= 2; lv <<= 1) {  // index bits 1, 2: lanes t ^ 1, t ^ 2
-        const bool upper = (lane & lv) != 0;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            const long long o = __shfl_xor_sync(0xffffffffu, z[k], lv);
-            z[k] = upper ? o - z[k] : z[k] + o;
-        }
-    }
-#pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
         const int i = 2 * t + 256 * kk;
         longlong2 v;
@@ -237,11 +229,28 @@ __device__ __forceinline__ void srht_f64_block128(const double *__restrict__ Aco
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < 32; ++k) z[k] = Zs[swz((t & 7) | (k << 3) | ((t >> 3) << 8))];
+    for (int k = 0; k < 32; ++k) z[k] = Zs[swz((t & 1) | (k << 1) | ((t >> 1) << 6))];
     __syncthreads();
-    fwht32(z);  // index bits 3..7
+    fwht32(z);  // index bits 1..5
 #pragma unroll
-    for (int k = 0; k < 32; ++k) Zs[swz((t & 7) | (k << 3) | ((t >> 3) << 8))] = z[k];
+    for (int k = 0; k < 32; ++k) Zs[swz((t & 1) | (k << 1) | ((t >> 1) << 6))] = z[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 32; ++k) z[k] = Zs[swz((t & 63) | (k << 6) | ((t >> 6) << 11))];
+    __syncthreads();
+#pragma unroll
+    for (int h = 1; h <= 2; h <<= 1) {  // index bits 6, 7
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            if ((k & h) == 0) {
+                const long long a = z[k], c = z[k + h];
+                z[k] = a + c;
+                z[k + h] = a - c;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 32; ++k) Zs[swz((t & 63) | (k << 6) | ((t >> 6) << 11))] = z[k];
     __syncthreads();
     for (int64_t i = t; i < s; i += 128) {
         const uint32_t pr = (uint32_t)rows_s[i];  // srht_pack_row: (hi(r) << 12) | swz(lo(r))
