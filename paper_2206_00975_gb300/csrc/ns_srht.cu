@@ -81,42 +81,6 @@ cudaError_t launch_srht_meta(uint64_t seed, int lg, int64_t nsign_words, int64_t
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(64) srht_f64_chunk_kernel(const double *__restrict__ A, int64_t m, int64_t n,
-                                                            int64_t lda, int64_t s, int chunk, int64_t nchunk,
-                                                            int P, const uint32_t *__restrict__ sign_words,
-                                                            const int32_t *__restrict__ rows,
-                                                            double *__restrict__ partial, int32_t *status,
-                                                            int vec_ok) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    long long *Zs = (long long *)smem_raw;                       // 4096
-    long long *acc = Zs + kBlock;                                // s
-    uint32_t *sgn = (uint32_t *)(acc + s);                       // 128
-    int *red = (int *)(sgn + 128);                               // 4
-    int32_t *rows_s = (int32_t *)(red + 4);                      // s
-
-    const int t = threadIdx.x;
-    const int64_t item = blockIdx.x;
-    const int64_t c = item / nchunk, ch = item - c * nchunk;
-    const double *Acol = A + c * lda;
-
-    for (int64_t i = t; i < s; i += 64) {
-        rows_s[i] = srht_pack_row(rows[i]);
-        acc[i] = 0;
-    }
-    __syncthreads();
-
-    int Erun = 0;  // running biased exponent of the chunk (0: none yet)
-    int nonfinite = 0;
-    for (int bl = 0; bl < chunk; ++bl)
-        srht_f64_block(Acol, m, s, ch * chunk + bl, P, sign_words, rows_s, Zs, acc, sgn, red, vec_ok, Erun,
-                       nonfinite, bl + 1 < chunk);
-    // chunk partial in FP64: value = acc * 2^(E - 1022 - P)
-    const double scale = ldexp(1.0, Erun - 1022 - P);
-    double *out = partial + (ch * n + c) * s;
-    for (int64_t i = t; i < s; i += 64) out[i] = (double)acc[i] * scale;
-    if (nonfinite) set_status(status, NS_ERR_NONFINITE);
-}
-
 __global__ void __launch_bounds__(128, 4) srht_f64_chunk128_kernel(const double *__restrict__ A, int64_t m, int64_t n,
                                                             int64_t lda, int64_t s, int chunk, int64_t nchunk,
                                                             int P, const uint32_t *__restrict__ sign_words,
