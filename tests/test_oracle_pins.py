@@ -306,6 +306,41 @@ def test_theorem_3_2_bound_deterministic(kind):
     assert O.residual(A, out["Vk"]) <= su.max() / su.min() * sig[-1] * (1 + 1e-6)
 
 
+@pytest.mark.parametrize("kind", [O.SRHT, O.GAUSSIAN, O.SPARSE_SIGN])
+def test_theorem_3_4_bounds_deterministic(kind):
+    # Subspaces of different dimensions (Theorem 3.4): the trailing k = 4 singular
+    # values of A are 1e-2 .. 1e-3 with no gap among them, so the trailing l = 2
+    # alone are not determined, but the theorem still places
+    #   case 1: the sketched trailing l inside A's trailing k,
+    #   case 2: A's trailing l inside the sketched trailing k,
+    # both within ||R - R^{-T}||_2 / chi(alpha^2, (alpha + delta)^2), R from S U.
+    rng = np.random.default_rng(40 + kind)
+    m, n, s, k, l = 1000, 100, 400, 4, 2
+    U = workloads.orthonormal(rng, m, n)
+    V = workloads.orthonormal(rng, n, n)
+    sig = np.concatenate([np.ones(n - k), np.logspace(-2, -3, k)])
+    A = workloads.from_svd(U, sig, V)
+    out = O.solve(kind, 23, s, A, k)
+    assert np.all(np.diff(out["sigk"]) <= 0)  # tilde sigma_{n-k+1} >= ... >= tilde sigma_n
+    st = np.sort(out["sigma"])[::-1]         # tilde sigma_1 >= ... >= tilde sigma_n
+    R = np.linalg.qr(O.sketch(kind, 23, s, U), mode="r")
+    Mnorm = np.linalg.norm(R - np.linalg.inv(R).T, 2)
+    Vl = out["Vk"][:, k - l:]                # the trailing l sketched vectors
+    # case 1: alpha = tilde sigma_{n-l+1}, alpha + delta = sigma_{n-k}
+    alpha, ad = st[n - l], sig[n - k - 1]
+    assert ad > alpha
+    b1 = Mnorm / chi(alpha ** 2, ad ** 2)
+    assert sine(V[:, n - k:], Vl) <= b1 * (1 + 1e-8) + 1e-15
+    # case 2: alpha = sigma_{n-l+1}, alpha + delta = tilde sigma_{n-k}
+    alpha, ad = sig[n - l], st[n - k - 1]
+    assert ad > alpha
+    b2 = Mnorm / chi(alpha ** 2, ad ** 2)
+    assert sine(out["Vk"], V[:, n - l:]) <= b2 * (1 + 1e-8) + 1e-15
+    # the bounds are informative here (sigma_{n-k} / sigma_{n-l+1} ~ 300), so a
+    # window shifted onto a sigma = 1 direction fails them
+    assert max(b1, b2) < 0.05
+
+
 def test_exact_null_space_preserved():
     # sigma_{n-k+1..n} = 0: the sketched trailing subspace is the null space (Section 3.1.1)
     rng = np.random.default_rng(6)
