@@ -22,7 +22,7 @@ _SO = os.path.join(_HERE, "_oracle.so")
 _lib = None
 
 OK, ERR_INVALID_ARG, ERR_NOCONV, ERR_TLS_NOSOLUTION = 0, 1, 4, 5
-SRHT, SPARSE_SIGN, GAUSSIAN = 0, 1, 2
+SRHT, SPARSE_SIGN, GAUSSIAN, HRHT = 0, 1, 2, 3
 
 
 def build(force=False):
@@ -50,6 +50,9 @@ def _load():
             "or_fwht": (None, [P, i64]),
             "or_srht": (i, [u64, i64, P, i64, i64, i64, i, P]),
             "or_srht_explicit": (i, [u64, i64, i64, P]),
+            "or_hash_rows": (None, [u64, i64, i64, P, P]),
+            "or_hrht": (i, [u64, i64, P, i64, i64, i64, i, P]),
+            "or_hrht_explicit": (i, [u64, i64, i64, P]),
             "or_sparse_sign_cols": (None, [u64, i64, i32, i64, P, P]),
             "or_sparse_sign": (i, [u64, i64, i32, P, i64, i64, i64, i, P]),
             "or_gaussian_entry": (dbl, [u64, i64, i64]),
@@ -148,6 +151,31 @@ def srht_explicit(seed, s, m):
     """Explicit unscaled SRHT matrix S[t, j] = d_j (-1)^popcount(r_t & j), s x m."""
     S = np.zeros((s, m), dtype=np.float64, order="F")
     _check(_load().or_srht_explicit(ctypes.c_uint64(seed), s, m, _p(S)), "srht_explicit")
+    return S
+
+
+def hash_rows(seed, s, mp):
+    """The 1-hashing matrix of the H-RHT (Section 2): row h[i] (int64) and sign
+    sg[i] (int8) of coordinate i < mp."""
+    h = np.zeros(int(mp), dtype=np.int64)
+    sg = np.zeros(int(mp), dtype=np.int8)
+    _load().or_hash_rows(ctypes.c_uint64(seed), int(s), int(mp), _p(h), _p(sg))
+    return h, sg
+
+
+def hrht(seed, s, A, scaled=True):
+    """SA = S_h (1/sqrt m') H D [A; 0], the H-RHT of Section 2."""
+    A = _f64(A)
+    m, n = A.shape
+    SA = np.zeros((s, n), dtype=np.float64, order="F")
+    _check(_load().or_hrht(ctypes.c_uint64(seed), s, _p(A), m, n, max(m, 1), int(scaled), _p(SA)), "hrht")
+    return SA
+
+
+def hrht_explicit(seed, s, m):
+    """Explicit unscaled H-RHT matrix, s x m: S[t, j] = d_j sum_{h[i]=t} sg[i] (-1)^popcount(i & j)."""
+    S = np.zeros((s, m), dtype=np.float64, order="F")
+    _check(_load().or_hrht_explicit(ctypes.c_uint64(seed), s, m, _p(S)), "hrht_explicit")
     return S
 
 

@@ -21,6 +21,9 @@
  *  - the sparse-sign sketch has zeta distinct rows per column of S, chosen
  *    by Floyd's sampling algorithm, with values +-1/sqrt(zeta);
  *  - the Gaussian sketch is G/sqrt(s) with G from Box-Muller on Philox words;
+ *  - the H-RHT (Section 2) is S_h (1/sqrt m') H D with the 1-hashing S_h:
+ *    coordinate i goes to row floor(s (w mod 2^32) / 2^32) with the sign of
+ *    bit 63 of w, w a stream-4 Philox word;
  *  - random numbers come from Philox4x64-10 (Salmon et al., SC'11) with
  *    key = (seed, 0) and counter = (index, aux, stream, 0).
  */
@@ -165,6 +168,71 @@ int or_srht_explicit(uint64_t seed, int64_t s, int64_t m, double *S) {
         for (int64_t t = 0; t < s; t++)
             S[t + j * s] = d[j] * ((__builtin_popcountll((uint64_t)(r[t] & j)) & 1) ? -1.0 : 1.0);
     free(d); free(r);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* H-RHT (Section 2, after Theorem 2.2): the SRFT with its restriction R     */
+/* replaced by a random 1-hashing matrix, S = S_h (1/sqrt m') H D.  Column i */
+/* of S_h has one nonzero, sg[i] = +-1, in row h[i].                         */
+/* ------------------------------------------------------------------------ */
+
+/* h[i], sg[i] for i < mp: word w = word (i mod 4) of stream-4 block i/4;
+ * h[i] = floor(s (w mod 2^32) / 2^32), sg[i] = -1 if bit 63 of w is set. */
+void or_hash_rows(uint64_t seed, int64_t s, int64_t mp, int64_t *h, int8_t *sg) {
+    uint64_t w[4];
+    for (int64_t i = 0; i < mp; i++) {
+        draw(seed, (uint64_t)(i / 4), 0, 4, w);
+        uint64_t word = w[i % 4];
+        h[i] = (int64_t)(((word & 0xFFFFFFFFULL) * (uint64_t)s) >> 32);
+        sg[i] = (word >> 63) ? -1 : +1;
+    }
+}
+
+/* SA = S_h (1/sqrt m') H D [A; 0]: per column, the sign flip, the full
+ * recursive transform of length m', then each coordinate i added with its
+ * sign into row h[i], in i order.  With scaled = 0 the 1/sqrt(m') factor is
+ * left out (integer inputs then give integer outputs). */
+int or_hrht(uint64_t seed, int64_t s, const double *A, int64_t m, int64_t n, int64_t lda, int scaled,
+            double *SA) {
+    int lg = or_ceil_log2(m);
+    int64_t mp = (int64_t)1 << lg;
+    if (s < 1 || s > mp || lda < m) return OR_ERR_INVALID_ARG;
+    int8_t *d = (int8_t *)malloc((size_t)mp);
+    int8_t *sg = (int8_t *)malloc((size_t)mp);
+    int64_t *h = (int64_t *)malloc(sizeof(int64_t) * (size_t)mp);
+    double *buf = (double *)malloc(sizeof(double) * (size_t)mp);
+    or_signs(seed, mp, d);
+    or_hash_rows(seed, s, mp, h, sg);
+    double scale = scaled ? 1.0 / sqrt((double)mp) : 1.0;
+    for (int64_t j = 0; j < n; j++) {
+        for (int64_t i = 0; i < mp; i++) buf[i] = (i < m) ? d[i] * A[i + j * lda] : 0.0;
+        fwht_rec(buf, mp);
+        for (int64_t t = 0; t < s; t++) SA[t + j * s] = 0.0;
+        for (int64_t i = 0; i < mp; i++) SA[h[i] + j * s] += sg[i] * buf[i];
+        for (int64_t t = 0; t < s; t++) SA[t + j * s] *= scale;
+    }
+    free(d); free(sg); free(h); free(buf);
+    return OR_OK;
+}
+
+/* The explicit unscaled H-RHT matrix for small m:
+ * S[t, j] = d_j sum over i with h[i] = t of sg[i] (-1)^popcount(i & j), j < m. */
+int or_hrht_explicit(uint64_t seed, int64_t s, int64_t m, double *S) {
+    int lg = or_ceil_log2(m);
+    int64_t mp = (int64_t)1 << lg;
+    if (s < 1 || s > mp) return OR_ERR_INVALID_ARG;
+    int8_t *d = (int8_t *)malloc((size_t)mp);
+    int8_t *sg = (int8_t *)malloc((size_t)mp);
+    int64_t *h = (int64_t *)malloc(sizeof(int64_t) * (size_t)mp);
+    or_signs(seed, mp, d);
+    or_hash_rows(seed, s, mp, h, sg);
+    for (int64_t j = 0; j < m; j++) {
+        for (int64_t t = 0; t < s; t++) S[t + j * s] = 0.0;
+        for (int64_t i = 0; i < mp; i++)
+            S[h[i] + j * s] += d[j] * sg[i] * ((__builtin_popcountll((uint64_t)(i & j)) & 1) ? -1.0 : 1.0);
+    }
+    free(d); free(sg); free(h);
     return OR_OK;
 }
 
@@ -390,12 +458,14 @@ int32_t or_count_below(const double *sigma, int64_t n, double eps) {
 #define OR_SRHT 0
 #define OR_SPARSE_SIGN 1
 #define OR_GAUSSIAN 2
+#define OR_HRHT 3
 
 int or_sketch(int kind, uint64_t seed, int64_t s, int32_t zeta, const double *A, int64_t m, int64_t n,
               int64_t lda, double *SA) {
     if (kind == OR_SRHT) return or_srht(seed, s, A, m, n, lda, 1, SA);
     if (kind == OR_SPARSE_SIGN) return or_sparse_sign(seed, s, zeta, A, m, n, lda, 1, SA);
     if (kind == OR_GAUSSIAN) return or_gaussian(seed, s, A, m, n, lda, NULL, n, SA);
+    if (kind == OR_HRHT) return or_hrht(seed, s, A, m, n, lda, 1, SA);
     return OR_ERR_INVALID_ARG;
 }
 

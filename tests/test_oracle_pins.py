@@ -122,6 +122,90 @@ def test_srht_exact_null_vector():
     assert np.all(SA2 @ x == 0)
 
 
+# ---------------------------------------------- H-RHT (Section 2) ----
+def test_hash_rows_from_numpy_philox():
+    # h[i], sg[i] from word (i mod 4) of stream-4 block i/4, drawn here with
+    # numpy's Philox (counter (i/4, 0, 4, 0), key (seed, 0)) as a black box
+    seed, s, mp = 77, 300, 64
+    h, sg = O.hash_rows(seed, s, mp)
+    for i in range(mp):
+        ctr = np.array([i // 4 - 1 if i >= 4 else 2 ** 64 - 1, 0 if i >= 4 else 2 ** 64 - 1, 4 if i >= 4 else 3, 0],
+                       dtype=np.uint64)
+        w = int(np.random.Philox(counter=ctr, key=np.array([seed, 0], dtype=np.uint64)).random_raw(4)[i % 4])
+        assert h[i] == ((w & 0xFFFFFFFF) * s) >> 32
+        assert sg[i] == (-1 if w >> 63 else 1)
+
+
+def test_hash_rows_uniform_and_balanced():
+    s, mp = 64, 1 << 14
+    h, sg = O.hash_rows(5, s, mp)
+    assert h.min() >= 0 and h.max() < s
+    assert scipy.stats.chisquare(np.bincount(h, minlength=s)).pvalue > 1e-4
+    assert abs(sg.astype(np.int64).sum()) < 5 * np.sqrt(mp)
+    assert not np.array_equal(h, O.hash_rows(6, s, mp)[0])
+
+
+def test_hrht_is_hashing_times_scipy_hadamard():
+    # S = S_h (1/sqrt m') H D with H from scipy and S_h one +-1 per column
+    seed, m, s = 12, 45, 20
+    lg = O.ceil_log2(m)
+    mp = 1 << lg
+    H = scipy.linalg.hadamard(mp).astype(np.float64)
+    D = np.diag(O.signs(seed, mp).astype(np.float64))
+    h, sg = O.hash_rows(seed, s, mp)
+    Sh = np.zeros((s, mp))
+    Sh[h, np.arange(mp)] = sg
+    assert np.all(np.count_nonzero(Sh, axis=0) == 1)
+    S_ref = (Sh @ H @ D)[:, :m]
+    assert np.array_equal(O.hrht_explicit(seed, s, m), S_ref)
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((m, 4))
+    np.testing.assert_allclose(O.hrht(seed, s, A), S_ref @ A / np.sqrt(mp), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("m,n,s", [(64, 7, 32), (37, 5, 16), (1, 1, 1), (300, 3, 100), (4096, 2, 512)])
+def test_hrht_matches_explicit_S_bitexact(m, n, s):
+    rng = np.random.default_rng(m * 17 + n)
+    A = rng.integers(-50, 51, size=(m, n)).astype(np.float64)
+    S = O.hrht_explicit(8, s, m)
+    assert np.array_equal(O.hrht(8, s, A, scaled=False), S @ A)
+
+
+def test_hrht_exact_null_vector():
+    rng = np.random.default_rng(4)
+    m, n = 300, 6
+    B = rng.integers(-20, 21, size=(m, n - 1)).astype(np.float64)
+    z = rng.integers(-3, 4, size=n - 1).astype(np.float64)
+    A = np.column_stack([B, B @ z])
+    x = np.concatenate([z, [-1.0]])
+    assert np.all(O.hrht(4, 64, A, scaled=False) @ x == 0)
+
+
+def test_hrht_embeds_coherent_subspace_where_srht_fails():
+    # Figure 1's difficult example: U = [I_n; 0], m = 1000, n = 100, s = 2n.
+    # The Sylvester SRHT at s = 2n is no subspace embedding of span(U)
+    # (sigma_min(S U) = 0: the sampled rows of H[:, :n] repeat), so Algorithm 1
+    # returns a vector unrelated to the null vector; with the 1-hashing in place
+    # of R, sigma(S U) lies in the Gaussian range and the solve succeeds, within
+    # Theorem 3.2's bound.
+    m, n, s = 1000, 100, 200
+    U = np.zeros((m, n))
+    U[:n, :n] = np.eye(n)
+    V = workloads.orthonormal(np.random.default_rng(3), n, n)
+    sig = np.concatenate([np.ones(n - 2), [0.1, 1e-6]])
+    A = workloads.from_svd(U, sig, V)
+    su_s = np.linalg.svd(O.srht(1, s, U), compute_uv=False)
+    su_h = np.linalg.svd(O.hrht(1, s, U), compute_uv=False)
+    assert su_s.min() < 1e-8
+    assert 0.2 < su_h.min() and su_h.max() < 1.8
+    bad = O.solve(O.SRHT, 1, s, A, 1)
+    good = O.solve(O.HRHT, 1, s, A, 1)
+    assert sine(V[:, -1:], bad["Vk"]) > 0.5
+    R = np.linalg.qr(O.hrht(1, s, U), mode="r")
+    bound = np.linalg.norm(R - np.linalg.inv(R).T, 2) / chi(good["sigk"][0] ** 2, sig[n - 2] ** 2)
+    assert sine(V[:, -1:], good["Vk"]) <= bound * (1 + 1e-8) < 1e-4
+
+
 # ------------------------------------------------------------ sparse sign ----
 def test_sparse_sign_columns_structure():
     s, zeta, m = 50, 8, 4000
