@@ -295,6 +295,20 @@ def extra_workloads(torch, api, dev, timer, hbm_peak, bf16_peak):
     return out
 
 
+def hrht_moved_bytes(m, n, s):
+    """DRAM bytes the two-pass H-RHT moves per sketch: A read once, the
+    transformed blocks (int64, m' x n) written by pass 1 and read by pass 2,
+    the hash table written once (pass 2 reads it from L2), the segment
+    partials written and read, SA written."""
+    mp = 1 << (m - 1).bit_length()
+    blocks = max(mp // 4096, 1)
+    want, nseg = max(16, -(-2048 // n)), 1
+    while nseg < want and nseg < 64:
+        nseg *= 2
+    nseg = min(nseg, blocks)
+    return 8 * m * n + 2 * 8 * max(mp, 4096) * n + 4 * mp + 2 * 8 * nseg * n * s + 8 * s * n
+
+
 def profile_case(args, torch, api, dev):
     """One kernel family on a small case (a few GB at most), for ncu captures."""
     g = torch.Generator(device=dev).manual_seed(1)
@@ -306,6 +320,10 @@ def profile_case(args, torch, api, dev):
         m, n, s = 1 << 19, 64, 1024
         A = torch.randn((n, m), generator=g, device=dev, dtype=torch.float64).t()
         d = api.desc(api.NS_SPARSE_SIGN, s=s, seed=0, zeta=8)
+    elif args.case == "hrht":
+        m, n, s = 1 << 19, 64, 1024
+        A = torch.randn((n, m), generator=g, device=dev, dtype=torch.float64).t()
+        d = api.desc(api.NS_HRHT, s=s, seed=0)
     elif args.case == "srht32":
         m, n, s = 1 << 20, 64, 2048
         A = torch.randn((n, m), generator=g, device=dev, dtype=torch.float32).t()
@@ -343,7 +361,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--extra", action="store_true", help="also time the other workloads")
-    ap.add_argument("--case", default=None, help="profiling case: srht, sparse, srht32, gauss, dense")
+    ap.add_argument("--case", default=None, help="profiling case: srht, sparse, hrht, srht32, gauss, dense")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -406,12 +424,27 @@ def main():
         api.ns_sketch(dsp, A, SA=SA, ws=ws_sp, stream=stream)
     torch.cuda.synchronize()
 
+    # and with the H-RHT (the 1-hashing in place of the row sample, s = 1024)
+    dh = api.desc(api.NS_HRHT, s=S, seed=SEED)
+    ws_h = api.workspace(dh, M, N, K_NULL, dev)
+    status_h = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def solve_hrht():
+        return api.ns_solve(dh, A, K_NULL, save=False, status=status_h, ws=ws_h, stream=stream)
+
+    for _ in range(args.warmup):
+        solve_hrht()
+        api.ns_sketch(dh, A, SA=SA, ws=ws_h, stream=stream)
+    torch.cuda.synchronize()
+
     with ClockSampler(local) as clk:
         ms_solve = timer(lambda: solve(A), args.steps)
         ms_sketch = timer(lambda: api.ns_sketch(d, A, SA=SA, ws=ws, stream=stream), args.steps)
         ms_dense = timer(lambda: api.ns_solve_sketched(d, SA, K_NULL, ws=ws_dense, stream=stream), args.steps)
         ms_solve_sp = timer(solve_sparse, args.steps)
         ms_sketch_sp = timer(lambda: api.ns_sketch(dsp, A, SA=SA, ws=ws_sp, stream=stream), args.steps)
+        ms_solve_h = timer(solve_hrht, args.steps)
+        ms_sketch_h = timer(lambda: api.ns_sketch(dh, A, SA=SA, ws=ws_h, stream=stream), args.steps)
     clocks = clk.summary()
     stats = api.jacobi_stats(d, M, N, ws_dense, sketched=True)
 
@@ -475,6 +508,11 @@ def main():
     torch.cuda.synchronize()
     if int(status_sp.item()) != 0:
         raise SystemExit("sparse-sign solve status %d" % int(status_sp.item()))
+    Vk_h, _, _, _ = solve_hrht()
+    resid_h = float(api.ns_residual(A, Vk_h).item())
+    torch.cuda.synchronize()
+    if int(status_h.item()) != 0:
+        raise SystemExit("H-RHT solve status %d" % int(status_h.item()))
 
     n_ranks = world
     hbm_peak, bf16_peak, peak_kind = peaks()
@@ -512,6 +550,13 @@ def main():
                         "sketch_gbs": sketch_bytes / (ms_sketch_sp / args.steps / 1e3) / 1e9,
                         "sketch_frac": sketch_bytes / (ms_sketch_sp / args.steps / 1e3) / 1e9 / hbm_peak,
                         "residual_AV_F": resid_sp},
+        "hrht": {"s": S, "solves_per_s": n_ranks * args.steps / (ms_solve_h / 1e3),
+                 "sketch_ms": ms_sketch_h / args.steps,
+                 "sketch_gbs": sketch_bytes / (ms_sketch_h / args.steps / 1e3) / 1e9,
+                 "sketch_frac": sketch_bytes / (ms_sketch_h / args.steps / 1e3) / 1e9 / hbm_peak,
+                 "moved_bytes_per_sketch": hrht_moved_bytes(M, N, S),
+                 "moved_gbs": hrht_moved_bytes(M, N, S) / (ms_sketch_h / args.steps / 1e3) / 1e9,
+                 "residual_AV_F": resid_h},
         "e2e": {"value": n_ranks * e2e_steps / (ms_e2e / 1e3), "unit": "solves/s",
                 "h2d_bytes_per_step": M * N * 8, "d2h_bytes_per_step": (N * K_NULL + K_NULL) * 8,
                 "overlap": "copy of step i+1 (E2E_PARTS streams) overlaps the solve of step i (two device buffers)",

@@ -57,7 +57,11 @@ typedef enum {
                            Sylvester Walsh-Hadamard matrix H on m' = 2^ceil(log2 m) */
     NS_SPARSE_SIGN = 1, /* zeta entries +-1/sqrt(zeta) per column of S (sparse
                            sketch of the kind Section 1 names, CountSketch-like) */
-    NS_GAUSSIAN = 2     /* S = G/sqrt(s), G standard Gaussian (Theorem 2.1) */
+    NS_GAUSSIAN = 2,    /* S = G/sqrt(s), G standard Gaussian (Theorem 2.1) */
+    NS_HRHT = 3         /* S = S_h (1/sqrt m') H D: the SRFT with R replaced by a
+                           1-hashing matrix S_h (Section 2, after Theorem 2.2), one
+                           +-1 per column of S_h; an embedding at s = O(n) also for
+                           coherent A, where the SRHT needs s = O(n log n) */
 } ns_sketch_kind;
 
 typedef enum { NS_F64 = 0, NS_F32 = 1 } ns_dtype;
@@ -104,7 +108,16 @@ int64_t ns_save_size(int64_t s, int64_t n);
  * SRHT (Section 2, with H in place of F): SA = (1/sqrt s) R H_{m'} D [A; 0].
  * Sparse sign: SA = sum_j S(:, j) A(j, :), zeta entries per column of S.
  * Gaussian: SA = G A / sqrt(s).
- * Errors: NS_ERR_INVALID_ARG for m < 1, n < 1, s < 1, lda < m, SRHT s > m',
+ * H-RHT: SA = S_h (1/sqrt m') H_{m'} D [A; 0]; coordinate i of the transform
+ *   goes to row h(i) = floor(s (w mod 2^32) / 2^32) with the sign of bit 63 of
+ *   w, w = word (i mod 4) of the stream-4 Philox block i/4.  Exact fixed-point
+ *   arithmetic with two roundings (the input onto 2^-50 of its 4096-row
+ *   block's largest magnitude; the block transforms onto 2^-P of the column's
+ *   largest, P = 62 - log2(m'/4096) - ceil(log2(largest count of rows one
+ *   pass-2 segment sends to one bucket)), about 47 at m' = 2^20, s = 1024).
+ *   Its workspace holds the m' x n transformed blocks (8 m' n bytes).
+ * Errors: NS_ERR_INVALID_ARG for m < 1, n < 1, s < 1, lda < m, SRHT or H-RHT
+ * s > m', H-RHT m' > 2^24,
  * zeta outside 1..min(64, s), an unsupported (kind, prec, dtype) triple, or a
  * NULL pointer; NS_ERR_WORKSPACE for a short workspace.
  */
@@ -168,7 +181,8 @@ ns_status ns_solve_eps(const ns_sketch_desc *desc, const void *A, int32_t dtype,
  * with ns_sketch (n = 1, the same desc and m0) and appending it to SA; a column
  * is removed by dropping it from SA.
  * Errors: NS_ERR_INVALID_ARG for a bad desc or op, j < 0, an append with
- * j < m0, m0 < 1, n < 1, an SRHT s > m', or a NULL pointer.
+ * j < m0, m0 < 1, n < 1, an SRHT s > m', the H-RHT kind (its column S e_j
+ * takes all m' coordinates, not O(s) work), or a NULL pointer.
  */
 enum { NS_ROW_APPEND = 0, NS_ROW_REMOVE = 1 };
 ns_status ns_sketch_update(const ns_sketch_desc *desc, int64_t m0, int32_t op, int64_t j, const double *row,

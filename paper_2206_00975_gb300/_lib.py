@@ -12,7 +12,7 @@ LIB_PATH = os.path.join(HERE, "libns.so")
 
 NS_OK, NS_ERR_INVALID_ARG, NS_ERR_WORKSPACE, NS_ERR_NONFINITE = 0, 1, 2, 3
 NS_ERR_NOCONV, NS_ERR_TLS_NOSOLUTION, NS_ERR_TIMEOUT, NS_ERR_CUDA = 4, 5, 6, 7
-NS_SRHT, NS_SPARSE_SIGN, NS_GAUSSIAN = 0, 1, 2
+NS_SRHT, NS_SPARSE_SIGN, NS_GAUSSIAN, NS_HRHT = 0, 1, 2, 3
 NS_F64, NS_F32 = 0, 1
 NS_PREC_FP64, NS_PREC_FP32_STREAM, NS_PREC_BF16X3 = 0, 1, 2
 NS_ROW_APPEND, NS_ROW_REMOVE = 0, 1

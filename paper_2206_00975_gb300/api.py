@@ -12,7 +12,7 @@ import torch
 
 from . import _lib
 from ._lib import Problem  # noqa: F401
-from ._lib import (NS_F32, NS_F64, NS_GAUSSIAN, NS_PREC_BF16X3, NS_PREC_FP32_STREAM, NS_PREC_FP64,  # noqa: F401
+from ._lib import (NS_F32, NS_F64, NS_GAUSSIAN, NS_HRHT, NS_PREC_BF16X3, NS_PREC_FP32_STREAM, NS_PREC_FP64,  # noqa: F401
                    NS_ROW_APPEND, NS_ROW_REMOVE, NS_SPARSE_SIGN, NS_SRHT, NSError, SketchDesc)
 
 

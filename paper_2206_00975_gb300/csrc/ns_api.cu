@@ -15,7 +15,7 @@ constexpr int64_t kMaxN = 4096;    // columns handled by the dense kernels
 
 static bool desc_ok(const ns_sketch_desc *d) {
     if (!d) return false;
-    if (d->kind < NS_SRHT || d->kind > NS_GAUSSIAN) return false;
+    if (d->kind < NS_SRHT || d->kind > NS_HRHT) return false;
     if (d->prec < NS_PREC_FP64 || d->prec > NS_PREC_BF16X3) return false;
     if (d->s < 1 || d->s > kMaxS) return false;
     if (d->kind == NS_SPARSE_SIGN && (d->zeta < 1 || d->zeta > 64 || d->zeta > d->s)) return false;
@@ -28,13 +28,15 @@ static bool path_ok(const ns_sketch_desc *d, int32_t dtype) {
         return (d->prec == NS_PREC_FP64 && dtype == NS_F64) || (d->prec == NS_PREC_FP32_STREAM && dtype == NS_F32);
     if (d->kind == NS_SPARSE_SIGN) return d->prec == NS_PREC_FP64 && dtype == NS_F64;
     if (d->kind == NS_GAUSSIAN) return d->prec == NS_PREC_BF16X3 && dtype == NS_F32;
+    if (d->kind == NS_HRHT) return d->prec == NS_PREC_FP64 && dtype == NS_F64;
     return false;
 }
 
 static bool shape_ok(const ns_sketch_desc *d, int64_t m, int64_t n, int64_t lda) {
     if (m < 1 || n < 1 || lda < m) return false;
     if (d->kind == NS_GAUSSIAN && n > 512) return false;
-    if (d->kind == NS_SRHT && d->s > ((int64_t)1 << ceil_log2(m))) return false;
+    if ((d->kind == NS_SRHT || d->kind == NS_HRHT) && d->s > ((int64_t)1 << ceil_log2(m))) return false;
+    if (d->kind == NS_HRHT && ceil_log2(m) > 24) return false;  // at most 4096 blocks across
     return true;
 }
 
@@ -42,6 +44,7 @@ struct SolveLayout {
     int32_t *status_word;
     SrhtWork srht;
     SparseWork sparse;
+    HrhtWork hrht;
     float *gauss_partial;
     double *SA;
     DenseWork dense;
@@ -56,6 +59,8 @@ static SolveLayout solve_layout(void *ws, const ns_sketch_desc *d, int64_t m, in
     L.sparse = SparseWork{nullptr, nullptr, nullptr};
     if (d->kind == NS_SRHT) L.srht = srht_carve(c, m, n, d->s);
     if (d->kind == NS_SPARSE_SIGN) L.sparse = sparse_carve(c, m, n, d->s, d->zeta);
+    L.hrht = HrhtWork{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (d->kind == NS_HRHT) L.hrht = hrht_carve(c, m, n, d->s);
     L.gauss_partial = nullptr;
     if (d->kind == NS_GAUSSIAN) {
         const GaussGeom g = gauss_geom(m, n, d->s);
@@ -74,6 +79,8 @@ static ns_status run_sketch(const ns_sketch_desc *d, const void *A, int64_t m, i
     if (d->kind == NS_GAUSSIAN)
         return cuda_status(launch_gauss_bf16x3(d->seed, (const float *)A, m, n, lda, d->s, L.gauss_partial, SA, status,
                                                st));
+    if (d->kind == NS_HRHT)
+        return cuda_status(launch_hrht_f64(d->seed, (const double *)A, m, n, lda, d->s, L.hrht, SA, status, st));
     if (d->kind == NS_SPARSE_SIGN)
         return cuda_status(launch_sparse_f64(d->seed, (const double *)A, m, n, lda, d->s, d->zeta, L.sparse, SA,
                                              status, st));
@@ -243,6 +250,7 @@ ns_status ns_sketch_update(const ns_sketch_desc *d, int64_t m0, int32_t op, int6
     if (!desc_ok(d) || !row || !SA) return NS_ERR_INVALID_ARG;
     if (m0 < 1 || n < 1 || j < 0 || (op != NS_ROW_APPEND && op != NS_ROW_REMOVE)) return NS_ERR_INVALID_ARG;
     if (op == NS_ROW_APPEND && j < m0) return NS_ERR_INVALID_ARG;
+    if (d->kind == NS_HRHT) return NS_ERR_INVALID_ARG;
     if (d->kind == NS_SRHT && d->s > ((int64_t)1 << ceil_log2(m0 > kBlock ? m0 : kBlock))) return NS_ERR_INVALID_ARG;
     if (n > kMaxN * 64) return NS_ERR_INVALID_ARG;
     return cuda_status(launch_sketch_update(d->kind, d->seed, d->s, d->zeta, m0, op, j, row, n, SA,

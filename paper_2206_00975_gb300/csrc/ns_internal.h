@@ -59,6 +59,35 @@ cudaError_t launch_srht_f64(const double *A, int64_t m, int64_t n, int64_t lda, 
                             double *SA, int32_t *status, cudaStream_t st);
 cudaError_t launch_srht_f32(const float *A, int64_t m, int64_t n, int64_t lda, int64_t s, const SrhtWork &w,
                             double *SA, int32_t *status, cudaStream_t st);
+// SA[t, c] = scale * sum over nchunk partials (chunk-major, s x n each), in chunk order
+cudaError_t launch_srht_reduce(const double *partial, int64_t n, int64_t s, int64_t nchunk, double scale, double *SA,
+                               cudaStream_t st);
+
+// H-RHT geometry: B = m'/4096 blocks per column (1 when m' <= 4096), slabs of
+// W = 2^lw consecutive lo across all blocks, nseg segments of sps slabs per
+// column, one pass-2 CTA and one FP64 partial per (column, segment).
+struct HrhtGeom {
+    int lg;              // m' = 2^lg
+    int64_t mp;
+    int64_t B;           // blocks per column
+    int LB;              // log2 B
+    int lw;              // log2 W = 12 - LB
+    int nseg;            // segments per column
+    int64_t sps;         // slabs per segment (B / nseg)
+    int64_t sign_words;  // uint32 words of sign bits
+};
+struct HrhtWork {
+    uint32_t *sign_words;
+    uint32_t *hash;      // m': h(i) | (sign < 0) << 31
+    unsigned int *cmax;  // largest bucket count of any segment
+    int2 *blk;           // n * B: (quantum exponent, top exponent) of each Z_b
+    long long *Z;        // n * B * 4096: pass-1 blocks
+    double *partial;     // nseg * n * s
+};
+HrhtGeom hrht_geom(int64_t m, int64_t n);
+HrhtWork hrht_carve(Carver &c, int64_t m, int64_t n, int64_t s);
+cudaError_t launch_hrht_f64(uint64_t seed, const double *A, int64_t m, int64_t n, int64_t lda, int64_t s,
+                            const HrhtWork &w, double *SA, int32_t *status, cudaStream_t st);
 
 struct SparseGeom {
     int64_t ntile;        // 128-row tiles of A

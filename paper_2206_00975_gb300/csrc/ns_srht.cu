@@ -128,6 +128,14 @@ __global__ void srht_reduce_kernel(const double *__restrict__ partial, int64_t n
     SA[t + c * s] = a * scale;
 }
 
+cudaError_t launch_srht_reduce(const double *partial, int64_t n, int64_t s, int64_t nchunk, double scale, double *SA,
+                               cudaStream_t st) {
+    const int threads = 256;
+    const int64_t blocks = (n * s + threads - 1) / threads;
+    srht_reduce_kernel<<<(unsigned)blocks, threads, 0, st>>>(partial, n, s, nchunk, scale, SA);
+    return cudaGetLastError();
+}
+
 // --------------------------------------------------------- FP32 stream ----
 // Precision variant: A stored in FP32 is streamed through the same blocked
 // transform in FP32 arithmetic.  The signs of D are applied exactly (sign-bit

@@ -156,11 +156,16 @@ __device__ __forceinline__ void fwht32(long long (&z)[32]) {
 // The lanes of a warp reading one register of layout B (C) differ in index
 // bits 0, 6..9 (0..4), which swz spreads over all banks.  Exact integer adds:
 // the result is the 64-thread form's, bit for bit.
-__device__ __forceinline__ void srht_f64_block128(const double *__restrict__ Acol, int64_t m, int64_t s, int64_t b,
-                                                  int P, const uint32_t *__restrict__ sign_words,
-                                                  const int32_t *rows_s, long long *Zs, long long *acc,
-                                                  uint32_t *sgn, int *red, int vec_ok, int &Erun, int &nonfinite,
-                                                  bool prefetch_next) {
+//
+// srht_block128_core runs the load, the quantisation at Erun (rescaling
+// acc[0..s) when Erun grows) and all 12 levels, and returns Z_b in registers
+// in layout C; the shared-memory reads are complete on return.
+__device__ __forceinline__ int layout_c(int t, int k) { return (t & 63) | (k << 6) | ((t >> 6) << 11); }
+
+__device__ __forceinline__ void srht_block128_core(const double *__restrict__ Acol, int64_t m, int64_t s, int64_t b,
+                                                   int P, const uint32_t *__restrict__ sign_words, long long *Zs,
+                                                   long long *acc, uint32_t *sgn, int *red, int vec_ok, int &Erun,
+                                                   int &nonfinite, bool prefetch_next, long long (&z)[32]) {
     const int t = threadIdx.x, lane = t & 31;
     const int64_t base = b * kBlock;
     sgn[t] = sign_words[(base >> 5) + t];
@@ -168,7 +173,6 @@ __device__ __forceinline__ void srht_f64_block128(const double *__restrict__ Aco
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(Acol + base + kBlock),
                      "r"((uint32_t)(kBlock * 8))
                      : "memory");
-    long long z[32];
     if (vec_ok && base + kBlock <= m) {
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
@@ -249,8 +253,21 @@ __device__ __forceinline__ void srht_f64_block128(const double *__restrict__ Aco
             }
         }
     }
+}
+
+// One 4096-row block of the SRHT with 128 threads: srht_block128_core, then
+// the signed gather of the sampled rows (rows_s packed by srht_pack_row) into
+// acc[0..s).  Ends with __syncthreads().
+__device__ __forceinline__ void srht_f64_block128(const double *__restrict__ Acol, int64_t m, int64_t s, int64_t b,
+                                                  int P, const uint32_t *__restrict__ sign_words,
+                                                  const int32_t *rows_s, long long *Zs, long long *acc,
+                                                  uint32_t *sgn, int *red, int vec_ok, int &Erun, int &nonfinite,
+                                                  bool prefetch_next) {
+    const int t = threadIdx.x;
+    long long z[32];
+    srht_block128_core(Acol, m, s, b, P, sign_words, Zs, acc, sgn, red, vec_ok, Erun, nonfinite, prefetch_next, z);
 #pragma unroll
-    for (int k = 0; k < 32; ++k) Zs[swz((t & 63) | (k << 6) | ((t >> 6) << 11))] = z[k];
+    for (int k = 0; k < 32; ++k) Zs[swz(layout_c(t, k))] = z[k];
     __syncthreads();
     for (int64_t i = t; i < s; i += 128) {
         const uint32_t pr = (uint32_t)rows_s[i];  // srht_pack_row: (hi(r) << 12) | swz(lo(r))

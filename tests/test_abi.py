@@ -113,3 +113,23 @@ def test_sketch_update_rejects_bad_arguments(lib):
     for m0, op, j in ((100, 2, 5), (100, 0, 50), (0, 1, 0), (100, 1, -1)):
         assert lib.ns_sketch_update(ctypes.byref(d), m0, op, j, FAKE, 4, FAKE, None) == _lib.NS_ERR_INVALID_ARG
     assert lib.ns_sketch_update(ctypes.byref(d), 100, 1, 5, None, 4, FAKE, None) == _lib.NS_ERR_INVALID_ARG
+
+
+def test_hrht_rejections(lib):
+    d = _desc(kind=_lib.NS_HRHT, s=256)
+    # s > m' = 128
+    assert lib.ns_sketch(ctypes.byref(d), FAKE, _lib.NS_F64, 100, 4, 100, FAKE, FAKE, 1 << 30, None) == \
+        _lib.NS_ERR_INVALID_ARG
+    d = _desc(kind=_lib.NS_HRHT, s=64)
+    # m' > 2^24, FP32 input, FP32-stream precision
+    assert lib.ns_sketch(ctypes.byref(d), FAKE, _lib.NS_F64, (1 << 24) + 1, 1, (1 << 24) + 1, FAKE, FAKE, 1 << 40,
+                         None) == _lib.NS_ERR_INVALID_ARG
+    assert lib.ns_sketch(ctypes.byref(d), FAKE, _lib.NS_F32, 100, 4, 100, FAKE, FAKE, 1 << 30, None) == \
+        _lib.NS_ERR_INVALID_ARG
+    d32 = _desc(kind=_lib.NS_HRHT, s=64, prec=_lib.NS_PREC_FP32_STREAM)
+    assert lib.ns_sketch(ctypes.byref(d32), FAKE, _lib.NS_F32, 100, 4, 100, FAKE, FAKE, 1 << 30, None) == \
+        _lib.NS_ERR_INVALID_ARG
+    # row updates take O(s) columns of S; the H-RHT's takes all m' coordinates
+    assert lib.ns_sketch_update(ctypes.byref(d), 100, 1, 5, FAKE, 4, FAKE, None) == _lib.NS_ERR_INVALID_ARG
+    # the workspace holds the transformed blocks: at least 8 m' n bytes
+    assert lib.ns_workspace_size(ctypes.byref(d), 1 << 20, 256, 4) >= 8 * (1 << 20) * 256
