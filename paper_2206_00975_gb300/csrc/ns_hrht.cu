@@ -10,7 +10,9 @@
 //     own largest exponent), written to workspace as int64 with the block's
 //     quantum exponent and the exponent just above its largest |Z|;
 //   pass 2 (hrht_cross_kernel): for a slab of W = 4096/B consecutive lo and
-//     all B blocks, each Z_b[lo] is rounded once onto the column's common
+//     all B blocks (staged into shared memory by cp.async, the next slab's
+//     copies in flight while this one is transformed), each Z_b[lo] is
+//     rounded once onto the column's common
 //     quantum (so that the column's largest |Z| sits at 2^P2), H_B runs across
 //     the blocks in 4-bit register phases around a shared-memory transpose,
 //     and each result y[(hi << 12) | lo] is added with its sign into the
@@ -52,7 +54,7 @@ HrhtWork hrht_carve(Carver &c, int64_t m, int64_t n, int64_t s) {
     const HrhtGeom g = hrht_geom(m, n);
     HrhtWork w;
     w.sign_words = c.take<uint32_t>((size_t)g.sign_words);
-    w.hash = c.take<uint32_t>((size_t)g.mp);
+    w.hash = c.take<uint32_t>((size_t)(g.mp > kBlock ? g.mp : kBlock));  // the staged tiles read whole slabs
     w.cmax = c.take<unsigned int>(1);
     w.blk = c.take<int2>((size_t)(n * g.B));
     w.Z = c.take<long long>((size_t)(n * g.B * kBlock));
@@ -172,20 +174,70 @@ __device__ __forceinline__ long long hrht_align(long long q, int sh) {
     return (q + (1ll << (sh - 1))) >> sh;
 }
 
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Stage the slab at lo0 of a column: the B x W tile of Z (element (b, w) at
+// index (b << lw) | w) and the matching B x W tile of hash words (rows
+// (b << 12) | (lo0 + w)).  16-byte copies where a row of the tile allows.
+__device__ __forceinline__ void hrht_stage(long long *zt, uint32_t *ht, const long long *Zc,
+                                           const uint32_t *__restrict__ hash, int lw, int64_t lo0) {
+    const int t = threadIdx.x;
+    if (lw >= 1) {
+        for (int q = t; q < kBlock / 2; q += 256) {
+            const int e = 2 * q, b = e >> lw, w = e & ((1 << lw) - 1);
+            cp_async16(zt + e, Zc + ((int64_t)b << kBlockLog) + lo0 + w);
+        }
+    } else {
+        for (int e = t; e < kBlock; e += 256) cp_async8(zt + e, Zc + ((int64_t)e << kBlockLog) + lo0);
+    }
+    if (lw >= 2) {
+        for (int q = t; q < kBlock / 4; q += 256) {
+            const int e = 4 * q, b = e >> lw, w = e & ((1 << lw) - 1);
+            cp_async16(ht + e, hash + ((int64_t)b << kBlockLog) + lo0 + w);
+        }
+    } else {
+        for (int e = t; e < kBlock; e += 256) {
+            const int b = e >> lw, w = e & ((1 << lw) - 1);
+            cp_async4(ht + e, hash + ((int64_t)b << kBlockLog) + lo0 + w);
+        }
+    }
+    cp_async_commit();
+}
+
+// STAGES = 2: the copies of slab k + 1 run while slab k is transformed.
+template <int STAGES>
 __global__ void __launch_bounds__(256) hrht_cross_kernel(const long long *__restrict__ Z,
                                                          const int2 *__restrict__ blk, int64_t n, int LB, int lw,
                                                          int nseg, int64_t sps, int64_t mp, int64_t s,
                                                          const uint32_t *__restrict__ hash,
                                                          const unsigned int *cmax, double *__restrict__ partial) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    long long *acc = (long long *)smem_raw;                       // s
-    long long *tile = acc + s;                                    // 4096 (two or more phases)
-    int *shb = (int *)(tile + (LB > 4 ? kBlock : 0));             // B
+    long long *zst = (long long *)smem_raw;                       // STAGES x 4096
+    uint32_t *hst = (uint32_t *)(zst + STAGES * kBlock);          // STAGES x 4096
+    long long *acc = (long long *)(hst + STAGES * kBlock);        // s
+    int *shb = (int *)(acc + s);                                  // B
     __shared__ int red[8];
     const int t = threadIdx.x;
     const int64_t B = (int64_t)1 << LB;
     const int64_t c = blockIdx.x / nseg, g = blockIdx.x - c * nseg;
     const int2 *bc = blk + c * B;
+    const long long *Zc = Z + ((c * B) << kBlockLog);
+    const int64_t slab0 = g * sps, slab1 = (g + 1) * sps;
+    hrht_stage(zst, hst, Zc, hash, lw, slab0 << lw);
 
     // the column's top exponent and each block's alignment shift
     int top = INT_MIN;
@@ -205,11 +257,24 @@ __global__ void __launch_bounds__(256) hrht_cross_kernel(const long long *__rest
         const int2 e = bc[b];
         shb[b] = (e.y == INT_MIN || top == INT_MIN) ? 64 : qx2 - e.x;
     }
-    __syncthreads();
 
     const int nph = LB > 0 ? (LB + 3) / 4 : 1;
-    const long long *Zc = Z + ((c * B) << kBlockLog);
-    for (int64_t slab = g * sps; slab < (g + 1) * sps; ++slab) {
+    for (int64_t slab = slab0; slab < slab1; ++slab) {
+        const int cur = STAGES == 2 ? (int)((slab - slab0) & 1) : 0;
+        if (STAGES == 2) {
+            if (slab + 1 < slab1) {
+                hrht_stage(zst + (cur ^ 1) * kBlock, hst + (cur ^ 1) * kBlock, Zc, hash, lw, (slab + 1) << lw);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+        } else {
+            if (slab > slab0) hrht_stage(zst, hst, Zc, hash, lw, slab << lw);  // the single stage is free again
+            cp_async_wait<0>();
+        }
+        __syncthreads();  // slab's tiles (and shb) visible to all
+        long long *tile = zst + cur * kBlock;
+        const uint32_t *htile = hst + cur * kBlock;
         const int64_t lo0 = slab << lw;
         long long z[16];
         int nb = LB < 4 ? LB : 4;
@@ -217,11 +282,12 @@ __global__ void __launch_bounds__(256) hrht_cross_kernel(const long long *__rest
         for (int j = 0; j < 16; ++j) {
             int b, w;
             hrht_coord(t, j, 0, nb, lw, b, w);
-            z[j] = hrht_align(Zc[((int64_t)b << kBlockLog) + lo0 + w], shb[b]);
+            z[j] = hrht_align(tile[(b << lw) | w], shb[b]);
         }
         fwht16_bits(z, nb);
         int p = 0;
         for (int pn = 1; pn < nph; ++pn) {
+            // in place: each element is read and written by its owner only
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 int b, w;
@@ -243,22 +309,20 @@ __global__ void __launch_bounds__(256) hrht_cross_kernel(const long long *__rest
         for (int j = 0; j < 16; ++j) {
             int b, w;
             hrht_coord(t, j, p, nb, lw, b, w);
-            const int64_t i = ((int64_t)b << kBlockLog) | (lo0 + w);
-            if (i < mp) {
-                const uint32_t hv = hash[i];
+            if ((((int64_t)b << kBlockLog) | (lo0 + w)) < mp) {
+                const uint32_t hv = htile[(b << lw) | w];
                 const long long v = (hv >> 31) ? -z[j] : z[j];
                 atomicAdd((unsigned long long *)&acc[hv & 0x7FFFFFFFu], (unsigned long long)v);
             }
         }
-        if (nph > 1) __syncthreads();  // the next slab rewrites the tile
+        __syncthreads();  // this stage is refilled two slabs on
     }
-    __syncthreads();
     double *out = partial + (g * n + c) * s;
     for (int64_t r = t; r < s; r += 256) out[r] = ldexp((double)acc[r], qx2);
 }
 
-size_t hrht_cross_smem(const HrhtGeom &g, int64_t s) {
-    return (size_t)s * 8 + (g.LB > 4 ? (size_t)kBlock * 8 : 0) + (size_t)g.B * 4;
+size_t hrht_cross_smem(const HrhtGeom &g, int64_t s, int stages) {
+    return (size_t)stages * kBlock * (8 + 4) + (size_t)s * 8 + (size_t)g.B * 4;
 }
 
 cudaError_t launch_hrht_f64(uint64_t seed, const double *A, int64_t m, int64_t n, int64_t lda, int64_t s,
@@ -277,11 +341,20 @@ cudaError_t launch_hrht_f64(uint64_t seed, const double *A, int64_t m, int64_t n
     const int vec_ok = ((((uintptr_t)A) & 15) == 0 && (lda & 1) == 0) ? 1 : 0;
     hrht_block_kernel<<<(unsigned)(n * g.B), 128, 0, st>>>(A, m, lda, g.B, w.sign_words, w.Z, w.blk, status, vec_ok);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t csmem = hrht_cross_smem(g, s);
-    e = cudaFuncSetAttribute(hrht_cross_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
-    if (e != cudaSuccess) return e;
-    hrht_cross_kernel<<<(unsigned)(n * g.nseg), 256, csmem, st>>>(w.Z, w.blk, n, g.LB, g.lw, g.nseg, g.sps, g.mp, s,
-                                                                  w.hash, w.cmax, w.partial);
+    // two stages where shared memory allows (s up to ~9000 with B = 4096)
+    const bool two = hrht_cross_smem(g, s, 2) <= (size_t)200 * 1024;
+    const size_t csmem = hrht_cross_smem(g, s, two ? 2 : 1);
+    if (two) {
+        e = cudaFuncSetAttribute(hrht_cross_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
+        if (e != cudaSuccess) return e;
+        hrht_cross_kernel<2><<<(unsigned)(n * g.nseg), 256, csmem, st>>>(w.Z, w.blk, n, g.LB, g.lw, g.nseg, g.sps,
+                                                                         g.mp, s, w.hash, w.cmax, w.partial);
+    } else {
+        e = cudaFuncSetAttribute(hrht_cross_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
+        if (e != cudaSuccess) return e;
+        hrht_cross_kernel<1><<<(unsigned)(n * g.nseg), 256, csmem, st>>>(w.Z, w.blk, n, g.LB, g.lw, g.nseg, g.sps,
+                                                                         g.mp, s, w.hash, w.cmax, w.partial);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return launch_srht_reduce(w.partial, n, s, g.nseg, 1.0 / std::sqrt((double)g.mp), SA, st);
 }

@@ -51,8 +51,10 @@ def test_hrht_integer_inputs_bitexact(api, m, n, s):
 
 
 @pytest.mark.parametrize("m,n,s", [(37, 3, 16), (1000, 16, 128), (4097, 6, 640), ((1 << 14) + 3, 8, 500),
-                                   (1 << 17, 4, 1000), (3 * 4096 + 17, 3, 4096)])
+                                   (1 << 17, 4, 1000), (3 * 4096 + 17, 3, 4096), (20000, 2, 16000)])
 def test_hrht_sketch_parity(api, m, n, s):
+    # (the last case, s = 16000, takes the single-stage pass 2: two stages of
+    # staged tiles and the s accumulators would not fit in shared memory)
     rng = np.random.default_rng(m * 7 + n)
     A = rng.standard_normal((m, n)) * np.exp(rng.uniform(-3, 3, size=(1, n)))
     got = sketch(api, A, s, 4)
