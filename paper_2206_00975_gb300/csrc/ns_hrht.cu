@@ -165,13 +165,21 @@ __device__ __forceinline__ void fwht16_bits(long long (&z)[16], int nb) {
     }
 }
 
-// q rounded (half up) from its block's quantum onto the column's: a right
-// shift by sh > 0, an exact left shift by -sh otherwise (the bound on the
-// block's top exponent keeps the result within 2^P2).
-__device__ __forceinline__ long long hrht_align(long long q, int sh) {
-    if (sh <= 0) return sh < -62 ? 0 : (long long)((unsigned long long)q << (-sh));
-    if (sh >= 63) return 0;
-    return (q + (1ll << (sh - 1))) >> sh;
+// q rounded (half up) from its block's quantum onto the column's, given the
+// block's shift sh packed by hrht_pack_shift: an exact left shift by -sh when
+// sh <= 0 (the bound on the block's top exponent keeps the result within
+// 2^P2), else ((q >> (sh - 1)) + 1) >> 1, with shr.s64 clamping shifts past 63
+// (a block far below the column's top rounds to 0).
+__device__ __forceinline__ uint32_t hrht_pack_shift(int sh) {
+    const int ls = sh < 0 ? (sh < -62 ? 62 : -sh) : 0;
+    const int rs = sh > 0 ? (sh > 64 ? 64 : sh) : 0;
+    return (uint32_t)ls | ((uint32_t)(rs > 0 ? rs - 1 : 0) << 8) | ((uint32_t)(rs > 0) << 16);
+}
+__device__ __forceinline__ long long hrht_align(long long q, uint32_t pk) {
+    const long long v = (long long)((unsigned long long)q << (pk & 0xFF));
+    long long r;
+    asm("shr.s64 %0, %1, %2;" : "=l"(r) : "l"(v), "r"((pk >> 8) & 0xFF));
+    return (pk >> 16) ? (r + 1) >> 1 : r;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -219,17 +227,22 @@ __device__ __forceinline__ void hrht_stage(long long *zt, uint32_t *ht, const lo
 }
 
 // STAGES = 2: the copies of slab k + 1 run while slab k is transformed.
-template <int STAGES>
+// LB = log2 B is a template parameter, so every tile coordinate below folds to
+// a per-thread base plus a constant.  nst = 2: the copies of slab k + 1 run
+// while slab k is transformed; nst = 1 where shared memory is short.
+template <int LB>
 __global__ void __launch_bounds__(256) hrht_cross_kernel(const long long *__restrict__ Z,
-                                                         const int2 *__restrict__ blk, int64_t n, int LB, int lw,
+                                                         const int2 *__restrict__ blk, int64_t n, int nst,
                                                          int nseg, int64_t sps, int64_t mp, int64_t s,
                                                          const uint32_t *__restrict__ hash,
                                                          const unsigned int *cmax, double *__restrict__ partial) {
+    constexpr int lw = kBlockLog - LB;
+    constexpr int nph = LB > 0 ? (LB + 3) / 4 : 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    long long *zst = (long long *)smem_raw;                       // STAGES x 4096
-    uint32_t *hst = (uint32_t *)(zst + STAGES * kBlock);          // STAGES x 4096
-    long long *acc = (long long *)(hst + STAGES * kBlock);        // s
-    int *shb = (int *)(acc + s);                                  // B
+    long long *zst = (long long *)smem_raw;                       // nst x 4096
+    uint32_t *hst = (uint32_t *)(zst + nst * kBlock);             // nst x 4096
+    long long *acc = (long long *)(hst + nst * kBlock);           // s
+    uint32_t *shb = (uint32_t *)(acc + s);                        // B
     __shared__ int red[8];
     const int t = threadIdx.x;
     const int64_t B = (int64_t)1 << LB;
@@ -255,13 +268,12 @@ __global__ void __launch_bounds__(256) hrht_cross_kernel(const long long *__rest
     const int qx2 = (top == INT_MIN) ? 0 : top - P2;
     for (int64_t b = t; b < B; b += 256) {
         const int2 e = bc[b];
-        shb[b] = (e.y == INT_MIN || top == INT_MIN) ? 64 : qx2 - e.x;
+        shb[b] = hrht_pack_shift((e.y == INT_MIN || top == INT_MIN) ? 64 : qx2 - e.x);
     }
 
-    const int nph = LB > 0 ? (LB + 3) / 4 : 1;
     for (int64_t slab = slab0; slab < slab1; ++slab) {
-        const int cur = STAGES == 2 ? (int)((slab - slab0) & 1) : 0;
-        if (STAGES == 2) {
+        const int cur = nst == 2 ? (int)((slab - slab0) & 1) : 0;
+        if (nst == 2) {
             if (slab + 1 < slab1) {
                 hrht_stage(zst + (cur ^ 1) * kBlock, hst + (cur ^ 1) * kBlock, Zc, hash, lw, (slab + 1) << lw);
                 cp_async_wait<1>();
@@ -286,6 +298,7 @@ __global__ void __launch_bounds__(256) hrht_cross_kernel(const long long *__rest
         }
         fwht16_bits(z, nb);
         int p = 0;
+#pragma unroll
         for (int pn = 1; pn < nph; ++pn) {
             // in place: each element is read and written by its owner only
 #pragma unroll
@@ -321,6 +334,16 @@ __global__ void __launch_bounds__(256) hrht_cross_kernel(const long long *__rest
     for (int64_t r = t; r < s; r += 256) out[r] = ldexp((double)acc[r], qx2);
 }
 
+template <int LB>
+static void launch_cross(const HrhtGeom &g, const HrhtWork &w, int64_t n, int64_t s, int nst, size_t smem,
+                         cudaStream_t st, cudaError_t *e) {
+    *e = cudaFuncSetAttribute(hrht_cross_kernel<LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (*e != cudaSuccess) return;
+    hrht_cross_kernel<LB><<<(unsigned)(n * g.nseg), 256, smem, st>>>(w.Z, w.blk, n, nst, g.nseg, g.sps, g.mp, s,
+                                                                      w.hash, w.cmax, w.partial);
+    *e = cudaGetLastError();
+}
+
 size_t hrht_cross_smem(const HrhtGeom &g, int64_t s, int stages) {
     return (size_t)stages * kBlock * (8 + 4) + (size_t)s * 8 + (size_t)g.B * 4;
 }
@@ -344,18 +367,24 @@ cudaError_t launch_hrht_f64(uint64_t seed, const double *A, int64_t m, int64_t n
     // two stages where shared memory allows (s up to ~9000 with B = 4096)
     const bool two = hrht_cross_smem(g, s, 2) <= (size_t)200 * 1024;
     const size_t csmem = hrht_cross_smem(g, s, two ? 2 : 1);
-    if (two) {
-        e = cudaFuncSetAttribute(hrht_cross_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
-        if (e != cudaSuccess) return e;
-        hrht_cross_kernel<2><<<(unsigned)(n * g.nseg), 256, csmem, st>>>(w.Z, w.blk, n, g.LB, g.lw, g.nseg, g.sps,
-                                                                         g.mp, s, w.hash, w.cmax, w.partial);
-    } else {
-        e = cudaFuncSetAttribute(hrht_cross_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
-        if (e != cudaSuccess) return e;
-        hrht_cross_kernel<1><<<(unsigned)(n * g.nseg), 256, csmem, st>>>(w.Z, w.blk, n, g.LB, g.lw, g.nseg, g.sps,
-                                                                         g.mp, s, w.hash, w.cmax, w.partial);
+    const int nst = two ? 2 : 1;
+    switch (g.LB) {
+        case 0: launch_cross<0>(g, w, n, s, nst, csmem, st, &e); break;
+        case 1: launch_cross<1>(g, w, n, s, nst, csmem, st, &e); break;
+        case 2: launch_cross<2>(g, w, n, s, nst, csmem, st, &e); break;
+        case 3: launch_cross<3>(g, w, n, s, nst, csmem, st, &e); break;
+        case 4: launch_cross<4>(g, w, n, s, nst, csmem, st, &e); break;
+        case 5: launch_cross<5>(g, w, n, s, nst, csmem, st, &e); break;
+        case 6: launch_cross<6>(g, w, n, s, nst, csmem, st, &e); break;
+        case 7: launch_cross<7>(g, w, n, s, nst, csmem, st, &e); break;
+        case 8: launch_cross<8>(g, w, n, s, nst, csmem, st, &e); break;
+        case 9: launch_cross<9>(g, w, n, s, nst, csmem, st, &e); break;
+        case 10: launch_cross<10>(g, w, n, s, nst, csmem, st, &e); break;
+        case 11: launch_cross<11>(g, w, n, s, nst, csmem, st, &e); break;
+        case 12: launch_cross<12>(g, w, n, s, nst, csmem, st, &e); break;
+        default: return cudaErrorInvalidValue;
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e != cudaSuccess) return e;
     return launch_srht_reduce(w.partial, n, s, g.nseg, 1.0 / std::sqrt((double)g.mp), SA, st);
 }
 
