@@ -16,7 +16,8 @@
 //     quantum (so that the column's largest |Z| sits at 2^P2), H_B runs across
 //     the blocks in 4-bit register phases around a shared-memory transpose,
 //     and each result y[(hi << 12) | lo] is added with its sign into the
-//     int64 accumulator of row h(i) (red.shared.add.u64);
+//     accumulator of row h(i): three 21-bit limbs in 32-bit words while a
+//     bucket takes at most 2^11 values of a segment, else one int64;
 //   the segment partials go to FP64 and are summed in segment order.
 // All adds after the two roundings (input quantisation, alignment) are exact
 // integer adds, so the result does not depend on the order of the atomics.
@@ -233,7 +234,7 @@ __device__ __forceinline__ void hrht_stage(long long *zt, uint32_t *ht, const lo
 template <int LB>
 __global__ void __launch_bounds__(256) hrht_cross_kernel(const long long *__restrict__ Z,
                                                          const int2 *__restrict__ blk, int64_t n, int nst,
-                                                         int nseg, int64_t sps, int64_t mp, int64_t s,
+                                                         int limbs_ok, int nseg, int64_t sps, int64_t mp, int64_t s,
                                                          const uint32_t *__restrict__ hash,
                                                          const unsigned int *cmax, double *__restrict__ partial) {
     constexpr int lw = kBlockLog - LB;
@@ -241,8 +242,8 @@ __global__ void __launch_bounds__(256) hrht_cross_kernel(const long long *__rest
     extern __shared__ __align__(16) unsigned char smem_raw[];
     long long *zst = (long long *)smem_raw;                       // nst x 4096
     uint32_t *hst = (uint32_t *)(zst + nst * kBlock);             // nst x 4096
-    long long *acc = (long long *)(hst + nst * kBlock);           // s
-    uint32_t *shb = (uint32_t *)(acc + s);                        // B
+    long long *acc = (long long *)(hst + nst * kBlock);           // s int64, or 3 x s uint32 limbs
+    uint32_t *shb = (uint32_t *)((uint32_t *)acc + (limbs_ok ? 3 : 2) * s);  // B
     __shared__ int red[8];
     const int t = threadIdx.x;
     const int64_t B = (int64_t)1 << LB;
@@ -257,7 +258,8 @@ __global__ void __launch_bounds__(256) hrht_cross_kernel(const long long *__rest
     for (int64_t b = t; b < B; b += 256) top = max(top, bc[b].y);
     top = warp_max(top);
     if ((t & 31) == 0) red[t >> 5] = top;
-    for (int64_t r = t; r < s; r += 256) acc[r] = 0;
+    uint32_t *acc32 = (uint32_t *)acc;
+    for (int64_t r = t; r < (limbs_ok ? 3 : 2) * s; r += 256) acc32[r] = 0;
     __syncthreads();
     top = red[0];
 #pragma unroll
@@ -265,6 +267,10 @@ __global__ void __launch_bounds__(256) hrht_cross_kernel(const long long *__rest
     const unsigned int cm = *cmax;
     const int cb = cm > 1 ? 32 - __clz(cm - 1) : 0;
     const int P2 = 62 - LB - cb;
+    // Bucket sums on three 21-bit limbs in 32-bit words (32-bit shared atomics
+    // run several times faster than 64-bit ones): exact while a bucket takes
+    // at most 2^11 values, since |value| <= 2^(62 - cb).
+    const bool limbs = limbs_ok && cb <= 11;
     const int qx2 = (top == INT_MIN) ? 0 : top - P2;
     for (int64_t b = t; b < B; b += 256) {
         const int2 e = bc[b];
@@ -325,27 +331,39 @@ __global__ void __launch_bounds__(256) hrht_cross_kernel(const long long *__rest
             if ((((int64_t)b << kBlockLog) | (lo0 + w)) < mp) {
                 const uint32_t hv = htile[(b << lw) | w];
                 const long long v = (hv >> 31) ? -z[j] : z[j];
-                atomicAdd((unsigned long long *)&acc[hv & 0x7FFFFFFFu], (unsigned long long)v);
+                const uint32_t bk = hv & 0x7FFFFFFFu;
+                if (limbs) {
+                    atomicAdd(&acc32[bk], (uint32_t)v & 0x1FFFFFu);
+                    atomicAdd(&acc32[s + bk], (uint32_t)(v >> 21) & 0x1FFFFFu);
+                    atomicAdd(&acc32[2 * s + bk], (uint32_t)(int32_t)(v >> 42));
+                } else {
+                    atomicAdd((unsigned long long *)&acc[bk], (unsigned long long)v);
+                }
             }
         }
         __syncthreads();  // this stage is refilled two slabs on
     }
     double *out = partial + (g * n + c) * s;
-    for (int64_t r = t; r < s; r += 256) out[r] = ldexp((double)acc[r], qx2);
+    for (int64_t r = t; r < s; r += 256) {
+        const long long a = limbs ? (long long)acc32[r] + ((long long)acc32[s + r] << 21) +
+                                        ((long long)(int32_t)acc32[2 * s + r] << 42)
+                                  : acc[r];
+        out[r] = ldexp((double)a, qx2);
+    }
 }
 
 template <int LB>
-static void launch_cross(const HrhtGeom &g, const HrhtWork &w, int64_t n, int64_t s, int nst, size_t smem,
-                         cudaStream_t st, cudaError_t *e) {
+static void launch_cross(const HrhtGeom &g, const HrhtWork &w, int64_t n, int64_t s, int nst, int limbs_ok,
+                         size_t smem, cudaStream_t st, cudaError_t *e) {
     *e = cudaFuncSetAttribute(hrht_cross_kernel<LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (*e != cudaSuccess) return;
-    hrht_cross_kernel<LB><<<(unsigned)(n * g.nseg), 256, smem, st>>>(w.Z, w.blk, n, nst, g.nseg, g.sps, g.mp, s,
-                                                                      w.hash, w.cmax, w.partial);
+    hrht_cross_kernel<LB><<<(unsigned)(n * g.nseg), 256, smem, st>>>(w.Z, w.blk, n, nst, limbs_ok, g.nseg, g.sps,
+                                                                      g.mp, s, w.hash, w.cmax, w.partial);
     *e = cudaGetLastError();
 }
 
-size_t hrht_cross_smem(const HrhtGeom &g, int64_t s, int stages) {
-    return (size_t)stages * kBlock * (8 + 4) + (size_t)s * 8 + (size_t)g.B * 4;
+size_t hrht_cross_smem(const HrhtGeom &g, int64_t s, int stages, int limbs) {
+    return (size_t)stages * kBlock * (8 + 4) + (size_t)s * (limbs ? 12 : 8) + (size_t)g.B * 4;
 }
 
 cudaError_t launch_hrht_f64(uint64_t seed, const double *A, int64_t m, int64_t n, int64_t lda, int64_t s,
@@ -365,23 +383,25 @@ cudaError_t launch_hrht_f64(uint64_t seed, const double *A, int64_t m, int64_t n
     hrht_block_kernel<<<(unsigned)(n * g.B), 128, 0, st>>>(A, m, lda, g.B, w.sign_words, w.Z, w.blk, status, vec_ok);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // two stages where shared memory allows (s up to ~9000 with B = 4096)
-    const bool two = hrht_cross_smem(g, s, 2) <= (size_t)200 * 1024;
-    const size_t csmem = hrht_cross_smem(g, s, two ? 2 : 1);
+    const size_t cap = (size_t)200 * 1024;
+    const bool two = hrht_cross_smem(g, s, 2, 0) <= cap;
     const int nst = two ? 2 : 1;
+    const int limbs_ok = hrht_cross_smem(g, s, nst, 1) <= cap ? 1 : 0;
+    const size_t csmem = hrht_cross_smem(g, s, nst, limbs_ok);
     switch (g.LB) {
-        case 0: launch_cross<0>(g, w, n, s, nst, csmem, st, &e); break;
-        case 1: launch_cross<1>(g, w, n, s, nst, csmem, st, &e); break;
-        case 2: launch_cross<2>(g, w, n, s, nst, csmem, st, &e); break;
-        case 3: launch_cross<3>(g, w, n, s, nst, csmem, st, &e); break;
-        case 4: launch_cross<4>(g, w, n, s, nst, csmem, st, &e); break;
-        case 5: launch_cross<5>(g, w, n, s, nst, csmem, st, &e); break;
-        case 6: launch_cross<6>(g, w, n, s, nst, csmem, st, &e); break;
-        case 7: launch_cross<7>(g, w, n, s, nst, csmem, st, &e); break;
-        case 8: launch_cross<8>(g, w, n, s, nst, csmem, st, &e); break;
-        case 9: launch_cross<9>(g, w, n, s, nst, csmem, st, &e); break;
-        case 10: launch_cross<10>(g, w, n, s, nst, csmem, st, &e); break;
-        case 11: launch_cross<11>(g, w, n, s, nst, csmem, st, &e); break;
-        case 12: launch_cross<12>(g, w, n, s, nst, csmem, st, &e); break;
+        case 0: launch_cross<0>(g, w, n, s, nst, limbs_ok, csmem, st, &e); break;
+        case 1: launch_cross<1>(g, w, n, s, nst, limbs_ok, csmem, st, &e); break;
+        case 2: launch_cross<2>(g, w, n, s, nst, limbs_ok, csmem, st, &e); break;
+        case 3: launch_cross<3>(g, w, n, s, nst, limbs_ok, csmem, st, &e); break;
+        case 4: launch_cross<4>(g, w, n, s, nst, limbs_ok, csmem, st, &e); break;
+        case 5: launch_cross<5>(g, w, n, s, nst, limbs_ok, csmem, st, &e); break;
+        case 6: launch_cross<6>(g, w, n, s, nst, limbs_ok, csmem, st, &e); break;
+        case 7: launch_cross<7>(g, w, n, s, nst, limbs_ok, csmem, st, &e); break;
+        case 8: launch_cross<8>(g, w, n, s, nst, limbs_ok, csmem, st, &e); break;
+        case 9: launch_cross<9>(g, w, n, s, nst, limbs_ok, csmem, st, &e); break;
+        case 10: launch_cross<10>(g, w, n, s, nst, limbs_ok, csmem, st, &e); break;
+        case 11: launch_cross<11>(g, w, n, s, nst, limbs_ok, csmem, st, &e); break;
+        case 12: launch_cross<12>(g, w, n, s, nst, limbs_ok, csmem, st, &e); break;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
