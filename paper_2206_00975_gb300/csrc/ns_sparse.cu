@@ -14,9 +14,11 @@
 //      memory as 64-bit fixed point (per-column running exponent, as for the
 //      SRHT), quantises each 128 x 16 tile of A into shared memory (each entry
 //      with both signs, so the key indexes the signed value), and half
-//      warp h of warp w (lane = column) applies the entries of owner 2w + h:
-//      the two halves of a warp never touch the same target row, and one
-//      half walks its entries in order, so no update races;
+//      warp h of warp w (lane = column) applies the entries of owner 2w + h,
+//      two per step: the two halves of a warp never touch the same target
+//      row, and one half walks its entries in order, so no update races.
+//      The next tile's A values, offsets and entries are loaded while this
+//      tile is applied;
 //   3. one FP64 partial per chunk is summed over chunks in a fixed order.
 // Integer addition is exact and associative, so the result does not depend on
 // the order of the updates.
@@ -148,31 +150,38 @@ __global__ void __launch_bounds__(kSpThreads, 1) sparse_acc_kernel(
     int nonfinite = 0;
     const int64_t t0 = ch * chunk_tiles, t1 = (t0 + chunk_tiles < ntile) ? t0 + chunk_tiles : ntile;
     __syncthreads();
-    for (int64_t t = t0; t < t1; ++t) {
-        // ---- tile: warp w loads column lcol, rows lane + 32 q (coalesced)
-        long long raw[4];
-        int emax = 1;
+    // Software pipeline: tile t + 1's values of A, bucket offsets and entries
+    // are loaded while tile t is applied.
+    long long raw[4];
+    uint32_t pre[EPT];
+    int32_t e0 = 0, e1 = 0, myoff = 0;
+    auto load_tile = [&](int64_t t, long long (&rv)[4], uint32_t (&pv)[EPT], int32_t &f0, int32_t &f1,
+                         int32_t &fo) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int64_t j = t * kSpTile + lane + 32 * q;
-            long long v = 0;
-            if (lcol < n && j < m) v = __double_as_longlong(__ldcs(A + j + lcol * lda));
-            raw[q] = v;
-            const int e = (int)((unsigned long long)v >> 52) & 0x7FF;
+            rv[q] = (lcol < n && j < m) ? __double_as_longlong(__ldcs(A + j + lcol * lda)) : 0;
+        }
+        const int32_t *off = offsets + t * (nbucket + 1) + tg * kSpOwners;
+        f0 = __ldg(off);
+        f1 = __ldg(off + kSpOwners);
+        fo = (tid <= kSpOwners) ? __ldg(off + tid) : 0;
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const int32_t e = f0 + tid + q * kSpThreads;
+            pv[q] = (e < f1) ? __ldg(entries + t * nent + e) : 0u;
+        }
+    };
+    if (t0 < t1) load_tile(t0, raw, pre, e0, e1, myoff);
+    for (int64_t t = t0; t < t1; ++t) {
+        int emax = 1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = (int)((unsigned long long)raw[q] >> 52) & 0x7FF;
             emax = (e == 0x7FF) ? emax : max(emax, e);
             nonfinite |= (e == 0x7FF);
         }
         emax = warp_max(emax);
-        // ---- this tile's entries of the target group, into registers
-        const int32_t *off = offsets + t * (nbucket + 1) + tg * kSpOwners;
-        const int32_t e0 = __ldg(off), e1 = __ldg(off + kSpOwners);
-        uint32_t pre[EPT];
-#pragma unroll
-        for (int q = 0; q < EPT; ++q) {
-            const int32_t e = e0 + tid + q * kSpThreads;
-            pre[q] = (e < e1) ? __ldg(entries + t * nent + e) : 0u;
-        }
-        const int32_t myoff = (tid <= kSpOwners) ? __ldg(off + tid) : 0;
         __syncthreads();  // the previous tile is fully applied
         if (tid <= kSpOwners) boff[tid] = myoff;
 #pragma unroll
@@ -211,6 +220,7 @@ __global__ void __launch_bounds__(kSpThreads, 1) sparse_acc_kernel(
         }
         if (lane == 0) Ecol[w] = E;
         __syncthreads();  // tile, entries, offsets and exponents in place
+        if (t + 1 < t1) load_tile(t + 1, raw, pre, e0, e1, myoff);  // lands while this tile is applied
         // ---- half warp h of warp w applies the entries of owner 2w + h
         const int o = 2 * w + h;
         const int32_t b0 = boff[o] - boff[0], cntme = boff[o + 1] - boff[o];
@@ -218,10 +228,24 @@ __global__ void __launch_bounds__(kSpThreads, 1) sparse_acc_kernel(
         const int steps = max(cntme, cnt_other);
         const long long *tqc = tq + c * kSpTileStride;  // +v at 2 jl, -v at 2 jl + 1
         long long *accc = acc + c;
-        for (int i = 0; i < steps; ++i) {
-            if (i < cntme) {
-                const uint32_t key = ents[b0 + i];
-                accc[((key >> 8) & (kSpGroup - 1)) * kSpCols] += tqc[key & (2 * kSpTile - 1)];
+        // two entries per step: both accumulators are read before either is
+        // written (their updates overlap), and two entries for the same target
+        // row are summed first; an inactive slot writes nothing
+        for (int i = 0; i < steps; i += 2) {
+            const bool a0 = i < cntme, a1 = i + 1 < cntme;
+            const uint32_t k0 = a0 ? ents[b0 + i] : 0u, k1 = a1 ? ents[b0 + i + 1] : 0u;
+            const int r0 = (int)((k0 >> 8) & (kSpGroup - 1)) * kSpCols, r1 = (int)((k1 >> 8) & (kSpGroup - 1)) * kSpCols;
+            const long long v0 = tqc[k0 & (2 * kSpTile - 1)], v1 = tqc[k1 & (2 * kSpTile - 1)];
+            if (a1) {
+                if (r0 == r1) {
+                    accc[r0] += v0 + v1;
+                } else {
+                    const long long x0 = accc[r0], x1 = accc[r1];
+                    accc[r0] = x0 + v0;
+                    accc[r1] = x1 + v1;
+                }
+            } else if (a0) {
+                accc[r0] += v0;
             }
         }
     }
