@@ -63,6 +63,35 @@ def test_hrht_sketch_parity(api, m, n, s):
         assert np.max(np.abs(got[:, c] - ref[:, c])) <= 2.0 ** -40 * np.max(np.abs(ref[:, c]))
 
 
+@pytest.mark.parametrize("m,n,s,ld", [(5000, 4, 300, 5003), (3 * 4096 + 17, 3, 512, 3 * 4096 + 18)])
+def test_hrht_strided_columns(api, m, n, s, ld):
+    # leading dimension above m (odd: the 16-byte load path is off)
+    rng = np.random.default_rng(m + ld)
+    A = rng.standard_normal((m, n))
+    buf = torch.zeros((n, ld), dtype=torch.float64, device="cuda")
+    buf[:, :m] = torch.as_tensor(A.T.copy(), device="cuda")
+    d = api.desc(api.NS_HRHT, s=s, seed=2)
+    got = api.ns_sketch(d, buf.t()[:m, :]).cpu().numpy()
+    ref = O.hrht(2, s, A)
+    for c in range(n):
+        assert np.max(np.abs(got[:, c] - ref[:, c])) <= 2.0 ** -40 * np.max(np.abs(ref[:, c]))
+
+
+def test_hrht_solve_exact_null_space(api):
+    # Algorithm 1 with the H-RHT on an exact 4-dimensional null space
+    w = workloads.at_scale(seed=4, m=1 << 14, n=64, null_dim=4)
+    A = w["A"]
+    d = api.desc(api.NS_HRHT, s=256, seed=3)
+    Vk, sk, _, status = api.ns_solve(d, api.colmajor(A, device="cuda"), 4, save=False)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    Vk = Vk.cpu().numpy()
+    ref = O.solve(O.HRHT, 3, 256, A, 4)
+    assert sine(ref["Vk"], Vk) < 1e-8
+    assert sine(w["V"][:, -4:], Vk) < 1e-9
+    assert O.residual(A, Vk) <= 1e-12 * np.linalg.norm(A)
+
+
 def test_hrht_wide_dynamic_range_and_zero_column(api):
     # columns from 1e-200 to 1e200, a column of zeros, and one large entry in
     # an otherwise tiny column (its block sets the column quantum)
