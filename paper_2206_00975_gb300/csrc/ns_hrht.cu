@@ -227,7 +227,6 @@ __device__ __forceinline__ void hrht_stage(long long *zt, uint32_t *ht, const lo
     cp_async_commit();
 }
 
-// STAGES = 2: the copies of slab k + 1 run while slab k is transformed.
 // LB = log2 B is a template parameter, so every tile coordinate below folds to
 // a per-thread base plus a constant.  nst = 2: the copies of slab k + 1 run
 // while slab k is transformed; nst = 1 where shared memory is short.
@@ -362,7 +361,7 @@ static void launch_cross(const HrhtGeom &g, const HrhtWork &w, int64_t n, int64_
     *e = cudaGetLastError();
 }
 
-size_t hrht_cross_smem(const HrhtGeom &g, int64_t s, int stages, int limbs) {
+static size_t hrht_cross_smem(const HrhtGeom &g, int64_t s, int stages, int limbs) {
     return (size_t)stages * kBlock * (8 + 4) + (size_t)s * (limbs ? 12 : 8) + (size_t)g.B * 4;
 }
 
