@@ -42,12 +42,22 @@ def sketch(api, A, s, seed):
     return SA.cpu().numpy()
 
 
-@pytest.mark.parametrize("m,n,s", [(1, 1, 1), (1000, 3, 200), (4096, 5, 512), (5000, 4, 300), (70000, 3, 700),
-                                   ((1 << 18) + 3, 2, 2048)])
+@pytest.mark.parametrize("m,n,s", [(1, 1, 1), (2, 1, 2), (3, 2, 3), (1000, 3, 200), (4095, 2, 100), (4096, 5, 512),
+                                   (5000, 4, 300), (70000, 3, 700), ((1 << 18) + 3, 2, 2048)])
 def test_hrht_integer_inputs_bitexact(api, m, n, s):
     rng = np.random.default_rng(m + 3 * n)
     A = rng.integers(-50, 51, size=(m, n)).astype(np.float64)
     assert np.array_equal(sketch(api, A, s, 9), O.hrht(9, s, A))
+
+
+@pytest.mark.parametrize("m", [(1 << 20) + 1, (1 << 21) + 1, (1 << 22) + 1, (1 << 23) + 1])
+def test_hrht_three_phase_geometries_bitexact(api, m):
+    # m' = 2^21 .. 2^24: 512 .. 4096 blocks across, so the cross-block
+    # transform takes three register phases, and at 2048 and 4096 blocks the
+    # slab is 2 and 1 values wide (8- and 4-byte staged copies)
+    rng = np.random.default_rng(m)
+    A = rng.integers(-50, 51, size=(m, 1)).astype(np.float64)
+    assert np.array_equal(sketch(api, A, 1000, 13), O.hrht(13, 1000, A))
 
 
 @pytest.mark.parametrize("m,n,s", [(37, 3, 16), (1000, 16, 128), (4097, 6, 640), ((1 << 14) + 3, 8, 500),
