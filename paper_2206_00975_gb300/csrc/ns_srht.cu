@@ -13,10 +13,11 @@
 //
 // Structure (Kronecker split H_{m'} = H_{m'/4096} (x) H_{4096}):
 //   y[r] = sum_b (-1)^popcount(hi(r) & b) Z_b[lo(r)],   Z_b = H_4096 (D a)_b,
-// with hi(r) = r >> 12, lo(r) = r & 4095.  A CTA of 64 threads holds a block in
-// registers (64 values per thread), runs 6 butterfly stages in registers, one
-// swizzled shared-memory transpose, 6 more stages, and adds the s sampled
-// values Z_b[lo(r_t)] into its accumulator.  For m' <= 4096 the column is one
+// with hi(r) = r >> 12, lo(r) = r & 4095.  A CTA of 128 threads holds a block
+// in registers (32 values per thread), takes the 12 butterfly levels in three
+// register phases around two swizzled shared-memory transposes
+// (srht_block128_core in ns_srht_core.cuh), and adds the s sampled values
+// Z_b[lo(r_t)] into its accumulator.  For m' <= 4096 the column is one
 // zero-padded block: H's entries depend only on popcount(i & j), so padding to
 // 4096 leaves the sampled rows unchanged.
 #include <cmath>

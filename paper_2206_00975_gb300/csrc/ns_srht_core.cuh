@@ -1,5 +1,7 @@
-// ns_srht_core.cuh -- the per-block pipeline of the FP64 SRHT (see ns_srht.cu),
-// shared by the single-problem chunk kernel and the batched kernel.
+// ns_srht_core.cuh -- the per-block pipelines of the FP64 SRHT (see ns_srht.cu):
+// the 64-thread form (srht_f64_block, used by the batched kernel) and the
+// 128-thread form (srht_block128_core + srht_f64_block128, used by the
+// single-problem chunk kernel and by pass 1 of the H-RHT).
 #pragma once
 #include "ns_device.cuh"
 #include "ns_internal.h"
