@@ -349,13 +349,15 @@ def test_residual_against_numpy():
 
 
 # ------------------------------------------- whole solve (Algorithm 1) ----
-def test_ostrowski_bracket_srht():
+@pytest.mark.parametrize("kind", [O.SRHT, O.HRHT, O.SPARSE_SIGN, O.GAUSSIAN])
+def test_ostrowski_bracket(kind):
     # proof of Theorem 2.3: sigma_min(S U_A) sigma_i(A) <= sigma_i(SA) <= sigma_max(S U_A) sigma_i(A)
+    # for the realized S of every sketch kind
     w = workloads.plain(seed=3, m=1024, n=16)
     A, s = w["A"], 64
-    SA = O.srht(5, s, A)
+    SA = O.sketch(kind, 5, s, A)
     UA, sa, _ = np.linalg.svd(A, full_matrices=False)
-    SU = O.srht(5, s, UA)
+    SU = O.sketch(kind, 5, s, UA)
     su = np.linalg.svd(SU, compute_uv=False)
     ssa = np.linalg.svd(SA, compute_uv=False)
     slack = 1e-12
@@ -365,7 +367,7 @@ def test_ostrowski_bracket_srht():
     assert np.all(ssa[big] >= su.min() * sa[big] * (1 - slack))
 
 
-@pytest.mark.parametrize("kind", [O.SRHT, O.GAUSSIAN, O.SPARSE_SIGN])
+@pytest.mark.parametrize("kind", [O.SRHT, O.GAUSSIAN, O.SPARSE_SIGN, O.HRHT])
 def test_theorem_3_2_bound_deterministic(kind):
     # Figure-1 style input: m=1000, n=100, k=1, sigma = (1,...,1, 0.1, sigma_n)
     rng = np.random.default_rng(10 + kind)
@@ -390,7 +392,7 @@ def test_theorem_3_2_bound_deterministic(kind):
     assert O.residual(A, out["Vk"]) <= su.max() / su.min() * sig[-1] * (1 + 1e-6)
 
 
-@pytest.mark.parametrize("kind", [O.SRHT, O.GAUSSIAN, O.SPARSE_SIGN])
+@pytest.mark.parametrize("kind", [O.SRHT, O.GAUSSIAN, O.SPARSE_SIGN, O.HRHT])
 def test_theorem_3_4_bounds_deterministic(kind):
     # Subspaces of different dimensions (Theorem 3.4): the trailing k = 4 singular
     # values of A are 1e-2 .. 1e-3 with no gap among them, so the trailing l = 2
@@ -433,7 +435,7 @@ def test_exact_null_space_preserved():
     Z = rng.standard_normal((n - k, k))
     A = np.asfortranarray(np.column_stack([B, B @ Z]))
     N = np.vstack([Z, -np.eye(k)])            # A N = 0 up to rounding of B @ Z
-    for kind in (O.SRHT, O.SPARSE_SIGN, O.GAUSSIAN):
+    for kind in (O.SRHT, O.SPARSE_SIGN, O.GAUSSIAN, O.HRHT):
         out = O.solve(kind, 1, 4 * n, A, k)
         assert sine(N, out["Vk"]) < 1e-12
         assert O.residual(A, out["Vk"]) < 1e-13 * np.linalg.norm(A)
