@@ -133,3 +133,103 @@ def test_hrht_rejections(lib):
     assert lib.ns_sketch_update(ctypes.byref(d), 100, 1, 5, FAKE, 4, FAKE, None) == _lib.NS_ERR_INVALID_ARG
     # the workspace holds the transformed blocks: at least 8 m' n bytes
     assert lib.ns_workspace_size(ctypes.byref(d), 1 << 20, 256, 4) >= 8 * (1 << 20) * 256
+
+
+INV, WSP = _lib.NS_ERR_INVALID_ARG, 2  # NS_ERR_WORKSPACE
+MIS = ctypes.c_void_p(0x100008)        # not 256-byte aligned
+
+
+def test_solve_sketched_and_stats_rejections(lib):
+    d = _desc(s=64)
+    for n, k in ((4, 0), (4, 5), (65, 1), (0, 1)):  # k outside 1..n, n > s, n < 1
+        assert lib.ns_solve_sketched(ctypes.byref(d), FAKE, n, k, FAKE, FAKE, None, None, FAKE, 1 << 30,
+                                     None) == INV
+    assert lib.ns_solve_sketched(ctypes.byref(d), None, 4, 1, FAKE, FAKE, None, None, FAKE, 1 << 30, None) == INV
+    assert lib.ns_solve_sketched(ctypes.byref(d), FAKE, 4, 1, FAKE, FAKE, None, None, MIS, 1 << 30, None) == INV
+    assert lib.ns_solve_sketched(ctypes.byref(d), FAKE, 4, 1, FAKE, FAKE, None, None, FAKE, 16, None) == WSP
+    assert lib.ns_solve_stats(ctypes.byref(d), 0, 4, FAKE, FAKE, None) == INV
+    assert lib.ns_solve_stats(ctypes.byref(d), 100, 5000, FAKE, FAKE, None) == INV
+    assert lib.ns_solve_stats(ctypes.byref(d), 100, 4, None, FAKE, None) == INV
+    assert lib.ns_sketched_stats(ctypes.byref(d), 0, FAKE, FAKE, None) == INV
+    assert lib.ns_sketched_stats(ctypes.byref(d), 4, FAKE, None, None) == INV
+
+
+def test_backward_rejections(lib):
+    d = _desc(s=64)
+    bw = lambda dd, m, n, k, ldd, ws=FAKE, nb=1 << 30: lib.ns_backward(  # noqa: E731
+        ctypes.byref(dd), m, n, k, FAKE, FAKE, FAKE, FAKE, ldd, ws, nb, None)
+    assert bw(_desc(s=64, kind=_lib.NS_SPARSE_SIGN), 100, 4, 1, 100) == INV  # SRHT only
+    assert bw(_desc(s=64, kind=_lib.NS_HRHT), 100, 4, 1, 100) == INV
+    assert bw(d, 100, 4, 4, 100) == INV      # k >= n (the projector has no complement)
+    assert bw(d, 100, 1, 1, 100) == INV      # n < 2
+    assert bw(d, 100, 4, 1, 99) == INV       # ldd < m
+    assert bw(_desc(s=256), 100, 4, 1, 100) == INV  # s > m'
+    assert bw(d, 100, 4, 1, 100, ws=MIS) == INV
+    assert bw(d, 100, 4, 1, 100, nb=16) == WSP
+
+
+def _problem(**kw):
+    base = dict(A=0x100000, m=1000, n=8, lda=1000, s=32, k=1, tls=0, seed=1, Vk=0x100000, sigk=0x100000, x=0)
+    base.update(kw)
+    return _lib.Problem(**base)
+
+
+def test_batched_rejections(lib):
+    d = _desc()
+    ok = (_lib.Problem * 1)(_problem())
+    assert lib.ns_batched_workspace_size(ctypes.byref(d), 1, ok) > 0
+    for bad in (dict(s=4), dict(s=2048), dict(m=4), dict(lda=999), dict(k=0), dict(k=9), dict(tls=1),
+                dict(tls=1, k=1, x=0), dict(A=0x100004), dict(A=0), dict(Vk=0)):
+        arr = (_lib.Problem * 2)(_problem(), _problem(**bad))
+        assert lib.ns_batched_workspace_size(ctypes.byref(d), 2, arr) == 0, bad
+        assert lib.ns_solve_batched(ctypes.byref(d), 2, arr, FAKE, FAKE, FAKE, 1 << 30, None) == INV, bad
+    dsp = _desc(kind=_lib.NS_SPARSE_SIGN)
+    assert lib.ns_batched_workspace_size(ctypes.byref(dsp), 1, ok) == 0
+    assert lib.ns_solve_batched(ctypes.byref(dsp), 1, ok, FAKE, FAKE, FAKE, 1 << 30, None) == INV
+    assert lib.ns_solve_batched(ctypes.byref(d), 0, ok, FAKE, FAKE, FAKE, 1 << 30, None) == INV
+    assert lib.ns_solve_batched(ctypes.byref(d), 1, ok, FAKE, FAKE, MIS, 1 << 30, None) == INV
+    assert lib.ns_solve_batched(ctypes.byref(d), 1, ok, FAKE, FAKE, FAKE, 16, None) == WSP
+
+
+def test_aaa_rejections(lib):
+    d = _desc(s=400)
+    assert lib.ns_aaa_workspace_size(ctypes.byref(d), 1 << 17, 100) > 0
+    assert lib.ns_aaa_workspace_size(ctypes.byref(d), 1, 100) == 0          # m < 2
+    assert lib.ns_aaa_workspace_size(ctypes.byref(d), 1 << 17, 401) == 0    # K > s
+    assert lib.ns_aaa_workspace_size(ctypes.byref(d), 200, 100) == 0        # s > m' = 256
+    assert lib.ns_aaa_workspace_size(ctypes.byref(_desc(s=400, kind=_lib.NS_HRHT)), 1 << 17, 100) == 0
+    aaa = lambda x=FAKE, ws=FAKE, nb=1 << 30: lib.ns_aaa_real(  # noqa: E731
+        ctypes.byref(d), x, FAKE, 1 << 17, 100, None, FAKE, FAKE, FAKE, None, FAKE, ws, nb, None)
+    assert aaa(x=None) == INV
+    assert aaa(ws=MIS) == INV
+    assert aaa(nb=16) == WSP
+
+
+def test_residual_and_meta_rejections(lib):
+    res = lambda dtype=_lib.NS_F64, m=100, n=4, lda=100, k=1, nb=1 << 20: lib.ns_residual(  # noqa: E731
+        FAKE, dtype, m, n, lda, FAKE, k, FAKE, FAKE, nb, None)
+    assert res(dtype=_lib.NS_F32) == INV
+    for k in (0, 17):
+        assert res(k=k) == INV
+    assert res(lda=99) == INV
+    assert res(nb=16) == WSP
+    assert res(n=4096, k=16) == INV          # W would not fit in shared memory
+    d = _desc(s=64)
+    assert lib.ns_srht_meta(ctypes.byref(_desc(s=64, kind=_lib.NS_SPARSE_SIGN)), 100, FAKE, FAKE, None) == INV
+    assert lib.ns_srht_meta(ctypes.byref(_desc(s=256)), 100, FAKE, FAKE, None) == INV
+    assert lib.ns_srht_meta(ctypes.byref(d), 0, FAKE, FAKE, None) == INV
+    assert lib.ns_sparse_meta(ctypes.byref(d), 100, FAKE, FAKE, None) == INV   # not sparse-sign
+    dsp = _desc(s=64, kind=_lib.NS_SPARSE_SIGN)
+    assert lib.ns_sparse_meta(ctypes.byref(dsp), 100, None, FAKE, None) == INV
+
+
+def test_sketch_static_rejections(lib):
+    st = lambda dd, dtype=_lib.NS_F64, m=100, lda=100, A=FAKE: lib.ns_sketch_static(  # noqa: E731
+        ctypes.byref(dd), A, dtype, m, 4, lda, FAKE, None)
+    assert st(_desc(kind=_lib.NS_HRHT)) == INV
+    assert st(_desc(kind=_lib.NS_SPARSE_SIGN)) == INV
+    assert st(_desc(), dtype=_lib.NS_F32) == INV
+    assert st(_desc(s=256)) == INV            # s > m'
+    assert st(_desc(), lda=99) == INV
+    assert st(_desc(), A=ctypes.c_void_p(0x100004)) == INV
+    assert st(_desc(s=1024), m=1 << 24, lda=1 << 24) == WSP  # scratch above the static 16 MiB
