@@ -83,7 +83,10 @@ typedef struct {
     int64_t s;       /* sketch size, n <= s; SRHT also needs s <= m' */
     uint64_t seed;
     int32_t prec;    /* ns_prec */
-    int32_t reserved;
+    int32_t max_sweeps; /* Jacobi sweep limit of the solves, 0 = the default 30;
+                           a limit the iteration reaches makes the solve report
+                           NS_ERR_NOCONV with its partial result written (the
+                           failure-detection tests force this with 1) */
 } ns_sketch_desc;
 
 /* Human-readable name of a status code (static storage). */
@@ -318,13 +321,13 @@ ns_status ns_sparse_meta(const ns_sketch_desc *desc, int64_t m, int32_t *rows, i
 
 /*
  * ns_sketch_static -- the SRHT sketch of ns_sketch (FP64 input, NS_SRHT with
- * NS_PREC_FP64 only, same result) without a caller-supplied workspace.  The
- * paper has no counterpart of this call; it exists for callers that cannot
- * allocate device memory: code embedded in a host application whose device
- * memory is owned by the application's own pool allocator, or a service that
- * must not allocate after start-up because an allocation can fail, block or
- * fragment memory at an unpredictable moment.  Such callers still pass A and
- * SA, but need no scratch of their own.
+ * NS_PREC_FP64 only, bit-identical result) without a caller-supplied
+ * workspace.  The paper has no counterpart of this call; it exists for
+ * callers that cannot allocate device memory: code embedded in a host
+ * application whose device memory is owned by the application's own pool
+ * allocator, or a service that must not allocate after start-up because an
+ * allocation can fail, block or fragment memory at an unpredictable moment.
+ * Such callers still pass A and SA, but need no scratch of their own.
  *
  * The scratch lives in one fixed device array of 16 MiB inside libns; every
  * GPU on which the library is used holds those 16 MiB until the process
@@ -334,14 +337,43 @@ ns_status ns_sparse_meta(const ns_sketch_desc *desc, int64_t m, int32_t *rows, i
  * call allocates nothing (no cudaMalloc, no cudaFree, no allocating library
  * routine).
  *
- * The first call on each device looks up the array's device address (with
- * that device current) and caches it; make that first call before any stream
- * capture.  Every call shares the one array and leaves its contents behind:
- * calls whose work overlaps on the GPU (two streams, or two threads) race on
- * it and must be serialised by the caller.
+ *   dev_status  device int32 owned by the caller, or NULL: receives 0, or
+ *               NS_ERR_NONFINITE when A holds an Inf or a NaN (SA is then not
+ *               meaningful).  With NULL the word inside the library's array
+ *               is used and non-finite input is NOT reported to the caller.
+ *
+ * The first call in each CUDA context looks up the array's device address
+ * (with the device current) and caches it under the context's id, so a call
+ * after cudaDeviceReset (a new context, possibly another address) looks it up
+ * again; make the first call in a context before any stream capture.  Every
+ * call shares the one array and leaves its contents behind: calls whose work
+ * overlaps on the GPU (two streams, or two threads) race on it and must be
+ * serialised by the caller.
  */
 ns_status ns_sketch_static(const ns_sketch_desc *desc, const void *A, int32_t dtype, int64_t m, int64_t n,
-                           int64_t lda, double *SA, void *stream);
+                           int64_t lda, double *SA, int32_t *dev_status, void *stream);
+
+/*
+ * ns_test_bounded_wait -- failure-detection test hook; the paper has no
+ * counterpart.  Every spin wait in the library's kernels is bounded; this call
+ * launches one of those waits on something nothing completes, with a short
+ * limit, so the wait runs out, the kernel writes NS_ERR_TIMEOUT to
+ * *dev_status and returns, and the stream stays usable.  Nothing faults or
+ * hangs.
+ *   which   0: the grid barrier of the cooperative kernels (two CTAs, the
+ *              second leaves without arriving; limit = polls of the barrier
+ *              word; ws: 256 bytes of device scratch, 256-byte aligned);
+ *           1: the cluster-peer mbarrier wait of the ring Jacobi (a cluster
+ *              of two CTAs, the first waits for a phase the second never
+ *              completes; limit = clock cycles; ws unused), after which both
+ *              CTAs meet at the final cluster barrier.
+ *   limit   1 .. 2^24.
+ *   dev_status  device int32, set to NS_ERR_TIMEOUT (callers zero it first).
+ * Errors: NS_ERR_INVALID_ARG for another `which`, a limit out of range, a
+ * NULL dev_status, or (which 0) a missing or short workspace.
+ */
+ns_status ns_test_bounded_wait(int32_t which, int64_t limit, int32_t *dev_status, void *ws, size_t ws_bytes,
+                               void *stream);
 
 #ifdef __cplusplus
 }

@@ -57,6 +57,7 @@ def _load():
             "or_sparse_sign": (i, [u64, i64, i32, P, i64, i64, i64, i, P]),
             "or_gaussian_entry": (dbl, [u64, i64, i64]),
             "or_gaussian": (i, [u64, i64, P, i64, i64, i64, P, i64, P]),
+            "or_gaussian_rows": (i, [u64, i64, P, i64, i64, i64, P, i64, P, P]),
             "or_householder_qr": (i, [P, i64, i64, i64, P]),
             "or_jacobi": (i, [P, i64, P, P, dbl, i, P]),
             "or_extract": (None, [P, P, i64, i32, P, P, P]),
@@ -212,6 +213,20 @@ def gaussian(seed, s, A, cols=None):
         _check(_load().or_gaussian(ctypes.c_uint64(seed), s, _p(A), m, n, max(m, 1), _p(c), c.size, _p(SA)),
                "gaussian")
     return SA
+
+
+def gaussian_rows(seed, s, A, rows):
+    """Rows `rows` of SA = G A / sqrt(s) (every column), and the size of their
+    terms sqrt(sum_j (G(r, j) A(j, c))^2) / sqrt(s): returns (out, mag), both
+    len(rows) x n."""
+    A = _f64(A)
+    m, n = A.shape
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.zeros((r.size, n), dtype=np.float64, order="F")
+    mag = np.zeros((r.size, n), dtype=np.float64, order="F")
+    _check(_load().or_gaussian_rows(ctypes.c_uint64(seed), s, _p(A), m, n, max(m, 1), _p(r), r.size, _p(out),
+                                    _p(mag)), "gaussian_rows")
+    return out, mag
 
 
 def sketch(kind, seed, s, A, zeta=8):

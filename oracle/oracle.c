@@ -317,6 +317,38 @@ int or_gaussian(uint64_t seed, int64_t s, const double *A, int64_t m, int64_t n,
     return OR_OK;
 }
 
+/* Rows rows[0..nrows) of SA = G A / sqrt(s) (Theorem 2.1 scaling), every
+ * column: out[i + c*nrows] = sum_j G(rows[i], j) A(j, c) / sqrt(s), summed over
+ * j in increasing order as or_gaussian does (so the two agree bit for bit).
+ * mag[i + c*nrows] (if not NULL) receives sqrt(sum_j (G(rows[i], j) A(j, c))^2)
+ * / sqrt(s): the size of the terms, the scale against which the rounding
+ * error of any evaluation of that entry is judged. */
+int or_gaussian_rows(uint64_t seed, int64_t s, const double *A, int64_t m, int64_t n, int64_t lda,
+                     const int64_t *rows, int64_t nrows, double *out, double *mag) {
+    if (s < 1 || lda < m || nrows < 0) return OR_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < nrows; i++)
+        if (rows[i] < 0 || rows[i] >= s) return OR_ERR_INVALID_ARG;
+    double scale = 1.0 / sqrt((double)s);
+    double *acc = (double *)calloc((size_t)(nrows * n), sizeof(double));
+    double *sq = (double *)calloc((size_t)(nrows * n), sizeof(double));
+    for (int64_t j = 0; j < m; j++) {
+        for (int64_t i = 0; i < nrows; i++) {
+            double g = or_gaussian_entry(seed, rows[i], j);
+            for (int64_t c = 0; c < n; c++) {
+                double t = g * A[j + c * lda];
+                acc[i + c * nrows] += t;
+                sq[i + c * nrows] += t * t;
+            }
+        }
+    }
+    for (int64_t q = 0; q < nrows * n; q++) {
+        out[q] = scale * acc[q];
+        if (mag) mag[q] = scale * sqrt(sq[q]);
+    }
+    free(acc); free(sq);
+    return OR_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Algorithm 1 line 3: SVD of SA, taken as Householder QR SA = QR followed   */
 /* by a one-sided (Hestenes) Jacobi SVD of R; SA and R share singular values */

@@ -23,12 +23,13 @@ EXPORTS = [
     "ns_backward", "ns_residual", "ns_srht_meta", "ns_sparse_meta", "ns_sketch_static",
     "ns_batched_workspace_size", "ns_solve_batched", "ns_aaa_workspace_size", "ns_aaa_real",
     "ns_solve_sketched", "ns_solve_stats", "ns_sketched_stats", "ns_solve_eps", "ns_sketch_update",
+    "ns_test_bounded_wait",
 ]
 
 
 class SketchDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("zeta", ctypes.c_int32), ("s", ctypes.c_int64),
-                ("seed", ctypes.c_uint64), ("prec", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("prec", ctypes.c_int32), ("max_sweeps", ctypes.c_int32)]
 
 
 class Problem(ctypes.Structure):
@@ -69,7 +70,7 @@ def load():
         "ns_residual": (ctypes.c_int, [P, i32, i64, i64, i64, P, i32, P, P, sz, P]),
         "ns_srht_meta": (ctypes.c_int, [D, i64, P, P, P]),
         "ns_sparse_meta": (ctypes.c_int, [D, i64, P, P, P]),
-        "ns_sketch_static": (ctypes.c_int, [D, P, i32, i64, i64, i64, P, P]),
+        "ns_sketch_static": (ctypes.c_int, [D, P, i32, i64, i64, i64, P, P, P]),
         "ns_batched_workspace_size": (sz, [D, i32, P]),
         "ns_solve_batched": (ctypes.c_int, [D, i32, P, P, P, P, sz, P]),
         "ns_aaa_workspace_size": (sz, [D, i64, i32]),
@@ -79,6 +80,7 @@ def load():
         "ns_sketched_stats": (ctypes.c_int, [D, i64, P, P, P]),
         "ns_solve_eps": (ctypes.c_int, [D, P, i32, i64, i64, i64, ctypes.c_double, P, P, P, P, P, P, sz, P]),
         "ns_sketch_update": (ctypes.c_int, [D, i64, i32, i64, P, i64, P, P]),
+        "ns_test_bounded_wait": (ctypes.c_int, [i32, i64, P, P, sz, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

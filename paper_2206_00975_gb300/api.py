@@ -16,8 +16,8 @@ from ._lib import (NS_F32, NS_F64, NS_GAUSSIAN, NS_HRHT, NS_PREC_BF16X3, NS_PREC
                    NS_ROW_APPEND, NS_ROW_REMOVE, NS_SPARSE_SIGN, NS_SRHT, NSError, SketchDesc)
 
 
-def desc(kind=NS_SRHT, s=0, seed=0, zeta=8, prec=NS_PREC_FP64):
-    return SketchDesc(int(kind), int(zeta), int(s), int(seed) & ((1 << 64) - 1), int(prec), 0)
+def desc(kind=NS_SRHT, s=0, seed=0, zeta=8, prec=NS_PREC_FP64, max_sweeps=0):
+    return SketchDesc(int(kind), int(zeta), int(s), int(seed) & ((1 << 64) - 1), int(prec), int(max_sweeps))
 
 
 def colmajor(x, dtype=None, device=None):
@@ -193,16 +193,19 @@ def ns_sparse_meta(d, m, stream=None, device="cuda"):
     return rows, signs
 
 
-def ns_sketch_static(d, A, SA=None, stream=None):
+def ns_sketch_static(d, A, SA=None, status=None, stream=None):
     """SRHT sketch using the library's own fixed scratch array: no workspace is
-    passed and nothing is allocated by the call (the output SA is allocated
-    here only if the caller did not pass one)."""
+    passed and nothing is allocated by the call (the output SA and the status
+    word are allocated here only if the caller did not pass them)."""
     m, n = A.shape
     if SA is None:
         SA = _empty_cm(d.s, n, A.device)
-    st = _lib.load().ns_sketch_static(ctypes.byref(d), _p(A), _dtype_code(A), m, n, _ld(A), _p(SA), _stream(stream))
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    st = _lib.load().ns_sketch_static(ctypes.byref(d), _p(A), _dtype_code(A), m, n, _ld(A), _p(SA), _p(status),
+                                      _stream(stream))
     _lib.check(st, "ns_sketch_static")
-    return SA
+    return SA, status
 
 
 def ns_solve_batched(problems, stream=None, ws=None, device="cuda"):

@@ -10,8 +10,24 @@
 
 namespace ns {
 
-constexpr int64_t kMaxS = 16384;   // sketch rows held in one CTA's shared memory
 constexpr int64_t kMaxN = 4096;    // columns handled by the dense kernels
+
+int device_sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (cached[dev] > 0) return cached[dev];
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    cached[dev] = sms;
+    return sms;
+}
 
 static bool desc_ok(const ns_sketch_desc *d) {
     if (!d) return false;
@@ -19,6 +35,7 @@ static bool desc_ok(const ns_sketch_desc *d) {
     if (d->prec < NS_PREC_FP64 || d->prec > NS_PREC_BF16X3) return false;
     if (d->s < 1 || d->s > kMaxS) return false;
     if (d->kind == NS_SPARSE_SIGN && (d->zeta < 1 || d->zeta > 64 || d->zeta > d->s)) return false;
+    if (d->max_sweeps < 0 || d->max_sweeps > 30) return false;
     return true;
 }
 
@@ -220,7 +237,8 @@ ns_status ns_solve(const ns_sketch_desc *d, const void *A, int32_t dtype, int64_
     if (r != NS_OK) return r;
     double *save_V = save ? save + d->s * n : nullptr;
     double *save_sigma = save ? save + d->s * n + n * n : nullptr;
-    return cuda_status(launch_dense_solve(SA, d->s, n, k, L.dense, Vk, sigk, save_V, save_sigma, status, st));
+    return cuda_status(
+        launch_dense_solve(SA, d->s, n, k, L.dense, Vk, sigk, save_V, save_sigma, status, st, d->max_sweeps));
 }
 
 ns_status ns_solve_eps(const ns_sketch_desc *d, const void *A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
@@ -240,7 +258,8 @@ ns_status ns_solve_eps(const ns_sketch_desc *d, const void *A, int32_t dtype, in
     if (r != NS_OK) return r;
     double *save_V = save ? save + d->s * n : nullptr;
     double *save_sigma = save ? save + d->s * n + n * n : nullptr;
-    cudaError_t e = launch_dense_solve(SA, d->s, n, 0, L.dense, nullptr, nullptr, save_V, save_sigma, status, st);
+    cudaError_t e =
+        launch_dense_solve(SA, d->s, n, 0, L.dense, nullptr, nullptr, save_V, save_sigma, status, st, d->max_sweeps);
     if (e != cudaSuccess) return cuda_status(e);
     return cuda_status(launch_dense_select_eps(L.dense, n, eps, Vk, sigk, dev_k, st));
 }
@@ -277,7 +296,7 @@ ns_status ns_solve_sketched(const ns_sketch_desc *d, const double *SA, int64_t n
         save_V = save + d->s * n;
         save_sigma = save + d->s * n + n * n;
     }
-    return cuda_status(launch_dense_solve(SA, d->s, n, k, w, Vk, sigk, save_V, save_sigma, status, st));
+    return cuda_status(launch_dense_solve(SA, d->s, n, k, w, Vk, sigk, save_V, save_sigma, status, st, d->max_sweeps));
 }
 
 ns_status ns_solve_stats(const ns_sketch_desc *d, int64_t m, int64_t n, const void *ws, int64_t *dev_out,
@@ -393,6 +412,13 @@ ns_status ns_srht_meta(const ns_sketch_desc *d, int64_t m, uint32_t *sign_words,
 ns_status ns_sparse_meta(const ns_sketch_desc *d, int64_t m, int32_t *rows, int8_t *signs, void *stream) {
     if (!desc_ok(d) || d->kind != NS_SPARSE_SIGN || m < 1 || !rows || !signs) return NS_ERR_INVALID_ARG;
     return cuda_status(launch_sparse_meta(d->seed, d->s, d->zeta, m, rows, signs, (cudaStream_t)stream));
+}
+
+ns_status ns_test_bounded_wait(int32_t which, int64_t limit, int32_t *dev_status, void *ws, size_t ws_bytes,
+                               void *stream) {
+    if ((which != 0 && which != 1) || limit < 1 || limit > ((int64_t)1 << 24) || !dev_status) return NS_ERR_INVALID_ARG;
+    if (which == 0 && (!ws || ws_bytes < 256 || (((uintptr_t)ws) & 255) != 0)) return NS_ERR_INVALID_ARG;
+    return cuda_status(launch_test_wait(which, (long long)limit, dev_status, (unsigned int *)ws, (cudaStream_t)stream));
 }
 
 }  // extern "C"

@@ -223,12 +223,7 @@ __global__ void __launch_bounds__(kBatchThreads) batched_dense_kernel(const ns_p
     }
 }
 
-static int sm_count_b() {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms > 0 ? sms : 1;
-}
+static int sm_count_b() { return device_sm_count(); }
 
 size_t batched_work_bytes(int32_t batch, const ns_problem *host) {
     int64_t total = (int64_t)batched_head_bytes(batch);

@@ -929,7 +929,7 @@ template <int RPT>
 __global__ void __launch_bounds__(kDenseThreads) jacobi_coop_kernel(double *X, double *V, int64_t n, double tol,
                                                                    GridBarrier bar, unsigned int *rotcount,
                                                                    unsigned int *checkflag, double *sigma,
-                                                                   int32_t *status, int vinit) {
+                                                                   int32_t *status, int vinit, int max_sweeps) {
     __shared__ double red[32 * 3];
     __shared__ double par[3];
     const int64_t G = gridDim.x, me = blockIdx.x;
@@ -942,7 +942,7 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_coop_kernel(double *X, d
     bool converged = (n < 2);
     unsigned int prev_rot = 0xFFFFFFFFu;
     int full_sweeps = 0, check_passes = 0;
-    for (int sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
+    for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
         if (prev_rot < (unsigned int)kCheckBelow) {
             ++check_passes;
             const int c = jacobi_check_pass(X, n, tol2, bar, checkflag + sweep, sigma);
@@ -1086,7 +1086,8 @@ __device__ __forceinline__ uint32_t shared_addr(const void *p) { return (uint32_
 constexpr uint32_t kRingSuspendNs = 1000000;
 
 // bounded wait for phase `parity` of a local mbarrier that peers complete
-__device__ __forceinline__ bool ring_wait(uint32_t mbar, uint32_t parity) {
+// (limit in clock cycles: ~2 s by default; a healthy ring waits microseconds)
+__device__ __forceinline__ bool ring_wait(uint32_t mbar, uint32_t parity, long long limit = 1ll << 32) {
     const long long t0 = clock64();
     for (;;) {
         uint32_t done;
@@ -1097,7 +1098,7 @@ __device__ __forceinline__ bool ring_wait(uint32_t mbar, uint32_t parity) {
             : "r"(mbar), "r"(parity), "r"(kRingSuspendNs)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > (1ll << 32)) return false;  // ~2 s: a healthy ring waits microseconds
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -1278,7 +1279,7 @@ template <int kRingC>
 __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
     jacobi_ring_kernel(double *X, double *V, int64_t n, int64_t G, double tol, GridBarrier bar,
                        unsigned int *rotcount, unsigned int *checkflag, double *sigma, unsigned int *colver,
-                       int32_t *status, int vinit) {
+                       int32_t *status, int vinit, int max_sweeps) {
     // Slot j receives the Q column of round j: rows t and t + kRingT of X in
     // xbuf[j][t] and of V in vbuf[j][t], and its scale pair in sbuf[j], each
     // completed on its own mbarrier (mbx, mbv, mbs).  Columns are held scaled,
@@ -1354,7 +1355,7 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
     unsigned int prev_rot = 0xFFFFFFFFu;
     int full_sweeps = 0, check_passes = 0;
     uint32_t ostep = 0;  // outer steps so far: phase parity of the slot mbarriers
-    for (int sweep = 0; sweep < kMaxSweeps && !converged && ok; ++sweep) {
+    for (int sweep = 0; sweep < max_sweeps && !converged && ok; ++sweep) {
         if (prev_rot < (unsigned int)kCheckBelow) {
             ++check_passes;
             const int c = jacobi_check_pass(X, n, tol2, bar, checkflag + sweep, sigma);
@@ -1768,11 +1769,48 @@ __global__ void copy_kernel(const double *__restrict__ a, int64_t len, double *_
         b[i] = a[i];
 }
 
-static int sm_count() {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms > 0 ? sms : 1;
+static int sm_count() { return device_sm_count(); }
+
+// ------------------------------------------- failure-detection test hook ----
+// Runs one of the library's bounded waits on something nothing completes, so
+// the wait runs out: the kernel writes NS_ERR_TIMEOUT and returns, and the
+// stream stays usable.  Used by the tests only (ns_test_bounded_wait).
+//
+// Grid barrier: two CTAs; CTA 1 leaves without arriving, CTA 0 polls the
+// barrier word `limit` times.
+__global__ void test_grid_wait_kernel(GridBarrier bar) {
+    if (blockIdx.x != 0) return;
+    grid_sync(bar);
+}
+
+// Cluster-peer wait: a cluster of two CTAs; CTA 0 waits for phase 0 of a local
+// mbarrier that only CTA 1 could complete (as a ring neighbour completes a
+// slot), for `limit` clock cycles.  Both CTAs then meet at the final cluster
+// barrier, as the ring kernel's CTAs do after an abandoned wait.
+__global__ void __cluster_dims__(2, 1, 1) test_cluster_wait_kernel(int32_t *status, long long limit) {
+    __shared__ __align__(8) unsigned long long mb;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(shared_addr(&mb)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cluster_sync_all();
+    if (cluster_rank() == 0 && threadIdx.x == 0) {
+        if (!ring_wait(shared_addr(&mb), 0u, limit)) set_status(status, NS_ERR_TIMEOUT);
+    }
+    __syncwarp();
+    cluster_sync_all();
+}
+
+cudaError_t launch_test_wait(int which, long long limit, int32_t *status, unsigned int *word, cudaStream_t st) {
+    if (which == 0) {
+        cudaError_t e = cudaMemsetAsync(word, 0, sizeof(unsigned int), st);
+        if (e != cudaSuccess) return e;
+        GridBarrier bar{word, status, limit};
+        test_grid_wait_kernel<<<2, 32, 0, st>>>(bar);
+        return cudaGetLastError();
+    }
+    test_cluster_wait_kernel<<<2, 32, 0, st>>>(status, limit);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dense_select_eps(const DenseWork &w, int64_t n, double eps, double *Vk, double *sigk,
@@ -1788,7 +1826,7 @@ cudaError_t launch_dense_select_eps(const DenseWork &w, int64_t n, double eps, d
 
 template <int RPT>
 static cudaError_t launch_jacobi(const DenseWork &w, int64_t n, GridBarrier bar, int32_t *status, int vinit,
-                                 cudaStream_t st) {
+                                 int max_sweeps, cudaStream_t st) {
     const int64_t npairs = (n + (n & 1)) / 2;
     int64_t G = npairs < sm_count() ? npairs : sm_count();
     if (G < 1) G = 1;
@@ -1797,8 +1835,8 @@ static cudaError_t launch_jacobi(const DenseWork &w, int64_t n, GridBarrier bar,
     double tol = (double)n * std::ldexp(1.0, -53);
     unsigned int *rot = w.bar + 64, *chk = w.bar + 64 + 64;
     int32_t *status_ = status;
-    int vinit_ = vinit;
-    void *args[] = {&X, &V, &n_, &tol, &bar, &rot, &chk, &sigma, &status_, &vinit_};
+    int vinit_ = vinit, ms_ = max_sweeps;
+    void *args[] = {&X, &V, &n_, &tol, &bar, &rot, &chk, &sigma, &status_, &vinit_, &ms_};
     return cudaLaunchCooperativeKernel((const void *)jacobi_coop_kernel<RPT>, (int)G, kDenseThreads, args, 0, st);
 }
 
@@ -1810,7 +1848,7 @@ static size_t ring_smem(int C) { return (size_t)2 * C * kRingT * sizeof(double2)
 
 template <int C>
 static cudaError_t launch_ring_c(const DenseWork &w, int64_t n, GridBarrier bar, int32_t *status, int vinit,
-                                 cudaStream_t st, bool *used) {
+                                 int max_sweeps, cudaStream_t st, bool *used) {
     static int state[64] = {0};  // per device: 0 unknown, 1 usable, -1 not usable
     *used = false;
     int dev = 0;
@@ -1850,7 +1888,7 @@ static cudaError_t launch_ring_c(const DenseWork &w, int64_t n, GridBarrier bar,
     cudaError_t e = cudaMemsetAsync(colver, 0, sizeof(unsigned int) * (size_t)(n + 32), st);
     if (e != cudaSuccess) return e;
     e = cudaLaunchKernelEx(&cfg, jacobi_ring_kernel<C>, X, V, n, G, tol, bar, rot, chk, sigma, colver, status,
-                           vinit);
+                           vinit, max_sweeps);
     if (e != cudaSuccess) {
         cudaGetLastError();
         state[dev] = -1;
@@ -1862,12 +1900,12 @@ static cudaError_t launch_ring_c(const DenseWork &w, int64_t n, GridBarrier bar,
 }
 
 static cudaError_t launch_jacobi_ring(const DenseWork &w, int64_t n, GridBarrier bar, int32_t *status, int vinit,
-                                      cudaStream_t st, bool *used) {
+                                      int max_sweeps, cudaStream_t st, bool *used) {
     if (n > 2 * 15 * 8) {  // 16 clusters of 8 would share SMs: try clusters of 16
-        const cudaError_t e = launch_ring_c<16>(w, n, bar, status, vinit, st, used);
+        const cudaError_t e = launch_ring_c<16>(w, n, bar, status, vinit, max_sweeps, st, used);
         if (e != cudaSuccess || *used) return e;
     }
-    return launch_ring_c<8>(w, n, bar, status, vinit, st, used);
+    return launch_ring_c<8>(w, n, bar, status, vinit, max_sweeps, st, used);
 }
 
 template <int NB>
@@ -1945,8 +1983,10 @@ cudaError_t launch_dense_stats(const DenseWork &w, int64_t *out, cudaStream_t st
 }
 
 cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k, const DenseWork &w, double *Vk,
-                               double *sigk, double *save_V, double *save_sigma, int32_t *status, cudaStream_t st) {
+                               double *sigk, double *save_V, double *save_sigma, int32_t *status, cudaStream_t st,
+                               int max_sweeps) {
     cudaError_t e = cudaSuccess;
+    if (max_sweeps <= 0 || max_sweeps > kMaxSweeps) max_sweeps = kMaxSweeps;
     GridBarrier bar{w.bar, status};
     double *u0a = w.tau, *cfa = w.tau + n, *u0b = w.tau + 2 * n, *cfb = w.tau + 3 * n;
     // 1. SA P = Q1 R; R (n x n) lands in X.  Pipelined after a static ordering
@@ -2009,13 +2049,13 @@ cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k
     const int vinit = q2_in_v ? 1 : 0;
     bool ring = false;
     if (n <= kRingN) {
-        e = launch_jacobi_ring(w, n, bar, status, vinit, st, &ring);
+        e = launch_jacobi_ring(w, n, bar, status, vinit, max_sweeps, st, &ring);
         if (e != cudaSuccess) return e;
     }
     if (ring) e = cudaSuccess;
-    else if (n <= 256) e = launch_jacobi<1>(w, n, bar, status, vinit, st);
-    else if (n <= 1024) e = launch_jacobi<4>(w, n, bar, status, vinit, st);
-    else e = launch_jacobi<16>(w, n, bar, status, vinit, st);
+    else if (n <= 256) e = launch_jacobi<1>(w, n, bar, status, vinit, max_sweeps, st);
+    else if (n <= 1024) e = launch_jacobi<4>(w, n, bar, status, vinit, max_sweeps, st);
+    else e = launch_jacobi<16>(w, n, bar, status, vinit, max_sweeps, st);
     if (e != cudaSuccess) return e;
     // 4. V = P Q2 Vx into w.W (reused as n x n)
     if (q2_in_v) {

@@ -141,11 +141,13 @@ __device__ __forceinline__ double block_max(double v, double *scratch) {
 // arrives and its low bits return to their previous value.  Every block waits
 // (acquire loads) until the top bit differs from the one in the value its own
 // add returned.  The host zeroes the word before the launch.  The wait is
-// bounded: after `limit` polls the barrier records NS_ERR_TIMEOUT in *status
-// and returns false; callers then leave the kernel.
+// bounded: after `limit` polls (2^24 unless a test hook sets it) the barrier
+// records NS_ERR_TIMEOUT in *status and returns false; callers then leave the
+// kernel.
 struct GridBarrier {
     unsigned int *word;
     int32_t *status;
+    long long limit = 1ll << 24;  // polls; a healthy barrier needs a few hundred at most
 };
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
@@ -169,9 +171,8 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier &b) {
         const unsigned int old = atom_add_release_u32(b.word, inc);
         int ok = 1;
         long long polls = 0;
-        const long long limit = 1ll << 24;  // a healthy barrier needs a few hundred polls at most
         while (((ld_acquire_u32(b.word) ^ old) & 0x80000000u) == 0u) {
-            if (++polls > limit) {
+            if (++polls > b.limit) {
                 atomicMax(b.status, (int32_t)NS_ERR_TIMEOUT);
                 ok = 0;
                 break;

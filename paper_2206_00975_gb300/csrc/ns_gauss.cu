@@ -276,10 +276,7 @@ GaussGeom gauss_geom(int64_t m, int64_t n, int64_t s) {
     GaussGeom g;
     g.mtiles = (s + kGM - 1) / kGM;
     g.NP = (int)(((n + 15) / 16) * 16);
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms < 1) sms = 148;
+    const int sms = device_sm_count();
     int64_t nsplit = sms / (g.mtiles > 0 ? g.mtiles : 1);
     if (nsplit < 1) nsplit = 1;
     const int64_t kchunks = (m + kGK - 1) / kGK;

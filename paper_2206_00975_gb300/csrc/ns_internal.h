@@ -10,6 +10,7 @@ namespace ns {
 constexpr int kBlockLog = 12;                 // FWHT block: 4096 rows of one column
 constexpr int64_t kBlock = 1 << kBlockLog;
 constexpr int kMaxChunkBlocks = 16;           // blocks summed per fixed-point accumulator
+constexpr int64_t kMaxS = 16384;              // sketch rows held in one CTA's shared memory
 
 inline int ceil_log2(int64_t m) {
     int lg = 0;
@@ -17,6 +18,12 @@ inline int ceil_log2(int64_t m) {
     return lg;
 }
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Streaming multiprocessors of the current device (queried once per device;
+// 1 if no device can be queried, e.g. when only workspace sizes are asked for
+// on a machine without a GPU: geometries derived from it then stay valid, they
+// only spread work less widely).
+int device_sm_count();
 
 // Carves consecutive 256-byte-aligned pieces out of the caller's workspace.
 struct Carver {
@@ -163,13 +170,19 @@ struct DenseWork {
 size_t dense_work_bytes(int64_t s, int64_t n);
 DenseWork dense_carve(Carver &c, int64_t s, int64_t n);
 cudaError_t launch_dense_stats(const DenseWork &w, int64_t *out, cudaStream_t st);
+// failure-detection test hook: which 0 = grid barrier (limit in polls), 1 = cluster-peer mbarrier wait (limit
+// in clock cycles); word: one device word of scratch for the barrier
+cudaError_t launch_test_wait(int which, long long limit, int32_t *status, unsigned int *word, cudaStream_t st);
 // Section 5 row updates of a sketch (op 0: append row index j, 1: remove row j)
 cudaError_t launch_sketch_update(int kind, uint64_t seed, int64_t s, int zeta, int64_t m0, int op, int64_t j,
                                  const double *row, int64_t n, double *SA, cudaStream_t st);
 // after launch_dense_solve with k = 0: the tolerance selection (Vk n x n, sigk n, k in *dev_k)
 cudaError_t launch_dense_select_eps(const DenseWork &w, int64_t n, double eps, double *Vk, double *sigk,
                                     int32_t *dev_k, cudaStream_t st);
+// max_sweeps: Jacobi sweep limit (30 when 0 or out of range); the solve reports
+// NS_ERR_NOCONV, with the partial result written, when the limit is reached
 cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k, const DenseWork &w, double *Vk,
-                               double *sigk, double *save_V, double *save_sigma, int32_t *status, cudaStream_t st);
+                               double *sigk, double *save_V, double *save_sigma, int32_t *status, cudaStream_t st,
+                               int max_sweeps = 0);
 
 }  // namespace ns

@@ -46,7 +46,7 @@ SparseGeom sparse_geom(int64_t m, int64_t n, int64_t s, int zeta) {
     g.ncolgrp = (n + kSpCols - 1) / kSpCols;
     // about two CTAs per SM over (column group, target group, chunk)
     const int64_t per = g.ncolgrp * g.ntgrp;
-    int64_t want = (2 * 152 + per - 1) / per;
+    int64_t want = (2 * (int64_t)device_sm_count() + per - 1) / per;
     if (want < 1) want = 1;
     if (want > g.ntile) want = g.ntile;
     g.chunk_tiles = (g.ntile + want - 1) / want;

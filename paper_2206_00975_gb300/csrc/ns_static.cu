@@ -7,8 +7,12 @@
 // kStaticScratchBytes: every GPU that loads libns holds it until the process
 // exits.  Host code may not pass the array's name to a kernel (on the host it
 // is only a stand-in symbol), so the device address is looked up with
-// cudaGetSymbolAddress once per device, with that device current, and cached.
+// cudaGetSymbolAddress, with the device current, and cached per CUDA context:
+// a context created after a cudaDeviceReset loads the module again, and the
+// array may then sit at another address, so the cache entry is keyed on the
+// context's unique id rather than on the device ordinal.
 #include <mutex>
+#include <cuda.h>
 #include "ns_device.cuh"
 #include "ns_internal.h"
 
@@ -20,20 +24,56 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 static std::mutex g_static_mu;
-static void *g_static_ptr[kMaxDevices] = {nullptr};
+struct StaticSlot {
+    unsigned long long ctx_id;  // id of the context the address belongs to (0: none)
+    void *ptr;
+};
+static StaticSlot g_static_slot[kMaxDevices] = {};
 
-// Device address of g_static_scratch on the current device (set up on the
-// first call per device).  Returns nullptr if the lookup fails.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current context (0 if it cannot be read).
+// The driver entry points are resolved through the runtime, so libns needs no
+// link against libcuda.
+static unsigned long long current_ctx_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool resolved = false;
+    if (!resolved) {
+        void *f0 = nullptr, *f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) == cudaSuccess &&
+            q0 == cudaDriverEntryPointSuccess)
+            get_current = (CtxGetCurrentFn)f0;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetIdFn)f1;
+        resolved = true;
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of g_static_scratch in the current context (looked up on
+// the first call in each context).  Returns nullptr if the lookup fails.
 static void *static_scratch_address() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    const unsigned long long id = current_ctx_id();  // 0 before the runtime has made a context current
+    StaticSlot &slot = g_static_slot[dev];
+    if (!slot.ptr || id == 0 || slot.ctx_id != id) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return nullptr;
-        g_static_ptr[dev] = p;
+        slot.ptr = p;
+        slot.ctx_id = current_ctx_id();  // the lookup has made the device's context current
     }
-    return g_static_ptr[dev];
+    return slot.ptr;
 }
 
 }  // namespace ns
@@ -41,10 +81,10 @@ static void *static_scratch_address() {
 using namespace ns;
 
 extern "C" ns_status ns_sketch_static(const ns_sketch_desc *d, const void *A, int32_t dtype, int64_t m, int64_t n,
-                                      int64_t lda, double *SA, void *stream) {
+                                      int64_t lda, double *SA, int32_t *dev_status, void *stream) {
     if (!d || !A || !SA) return NS_ERR_INVALID_ARG;
     if (d->kind != NS_SRHT || d->prec != NS_PREC_FP64 || dtype != NS_F64) return NS_ERR_INVALID_ARG;
-    if (d->s < 1 || d->s > 16384 || m < 1 || n < 1 || lda < m) return NS_ERR_INVALID_ARG;
+    if (d->s < 1 || d->s > kMaxS || m < 1 || n < 1 || lda < m) return NS_ERR_INVALID_ARG;
     if (d->s > ((int64_t)1 << ceil_log2(m))) return NS_ERR_INVALID_ARG;
     if ((((uintptr_t)A) & 7) != 0) return NS_ERR_INVALID_ARG;
     // scratch needed: one status word, then the sketch's signs, rows and partial sums
@@ -55,8 +95,9 @@ extern "C" ns_status ns_sketch_static(const ns_sketch_desc *d, const void *A, in
     void *base = static_scratch_address();
     if (!base) return NS_ERR_CUDA;
     Carver c(base);
-    int32_t *status = c.take<int32_t>(1);
+    int32_t *own_status = c.take<int32_t>(1);
     SrhtWork w = srht_carve(c, m, n, d->s);
+    int32_t *status = dev_status ? dev_status : own_status;
     cudaStream_t st = (cudaStream_t)stream;
     // the status word is the only scratch that must start at zero; the
     // kernels overwrite signs, rows and partial sums before reading them

@@ -225,7 +225,7 @@ def test_residual_and_meta_rejections(lib):
 
 def test_sketch_static_rejections(lib):
     st = lambda dd, dtype=_lib.NS_F64, m=100, lda=100, A=FAKE: lib.ns_sketch_static(  # noqa: E731
-        ctypes.byref(dd), A, dtype, m, 4, lda, FAKE, None)
+        ctypes.byref(dd), A, dtype, m, 4, lda, FAKE, None, None)
     assert st(_desc(kind=_lib.NS_HRHT)) == INV
     assert st(_desc(kind=_lib.NS_SPARSE_SIGN)) == INV
     assert st(_desc(), dtype=_lib.NS_F32) == INV
@@ -233,3 +233,27 @@ def test_sketch_static_rejections(lib):
     assert st(_desc(), lda=99) == INV
     assert st(_desc(), A=ctypes.c_void_p(0x100004)) == INV
     assert st(_desc(s=1024), m=1 << 24, lda=1 << 24) == WSP  # scratch above the static 16 MiB
+
+
+def test_bounded_wait_hook_rejections(lib):
+    hook = lambda which=0, limit=100, status=FAKE, ws=ctypes.c_void_p(0x100000), nb=256: \
+        lib.ns_test_bounded_wait(which, limit, status, ws, nb, None)  # noqa: E731
+    assert hook(which=2) == INV
+    assert hook(limit=0) == INV
+    assert hook(limit=(1 << 24) + 1) == INV
+    assert hook(status=None) == INV
+    assert hook(ws=None) == INV            # the grid-barrier form needs a word of scratch
+    assert hook(ws=MIS) == INV
+    assert hook(nb=128) == INV
+
+
+def test_sweep_limit_range(lib):
+    # the descriptor's Jacobi sweep limit: 0 (default 30) .. 30
+    for bad in (-1, 31):
+        d = _lib.SketchDesc(_lib.NS_SRHT, 8, 64, 1, _lib.NS_PREC_FP64, bad)
+        assert lib.ns_workspace_size(ctypes.byref(d), 100, 4, 1) == 0
+        st = lib.ns_solve(ctypes.byref(d), FAKE, _lib.NS_F64, 100, 4, 100, 1, FAKE, FAKE, None, None, FAKE,
+                          1 << 30, None)
+        assert st == INV
+    d = _lib.SketchDesc(_lib.NS_SRHT, 8, 64, 1, _lib.NS_PREC_FP64, 1)
+    assert lib.ns_workspace_size(ctypes.byref(d), 100, 4, 1) > 0

@@ -47,6 +47,37 @@ def test_batched_tls_matches_oracle(api):
         assert sine(v_or[:, None], Vk.cpu().numpy()) < 1e-8
 
 
+def test_batched_tls_benchmark_shapes(api):
+    # a seeded subset of the batched workload's 4096 shapes (m uniform in
+    # [2^11, 2^16], n uniform in [8, 128]), with its largest-n and largest-m
+    # problems, all in one persistent launch, against the oracle per problem
+    ms, ns = workloads.tls_batch_shapes(seed=0, batch=4096)
+    pick = sorted(set(np.random.default_rng(8).choice(4096, 14, replace=False).tolist() +
+                      [int(np.argmax(ns)), int(np.argmax(ms))]))
+    rng = np.random.default_rng(13)
+    probs, host = [], []
+    for i in pick:
+        m, n = int(ms[i]), int(ns[i])
+        Xb, _ = workloads.tls_problem(rng, m, n)
+        s = 2 * (n + 1)
+        host.append((Xb, s, i))
+        probs.append({"A": api.colmajor(Xb, device="cuda"), "s": s, "k": 1, "seed": i, "tls": True})
+    assert max(p["A"].shape[1] for p in probs) == 129 and max(p["A"].shape[0] for p in probs) >= 65000
+    outs, status, keep = api.ns_solve_batched(probs)
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    for (Xb, s, seed), (Vk, sk, x) in zip(host, outs):
+        x_or, v_or, st = O.tls(seed, s, Xb)
+        assert st == O.OK
+        v = Vk.cpu().numpy()[:, 0]
+        # the gap sigma_n(X) / sigma_{n+1}([X b]) of these problems is ~1e2..1e3 at
+        # s = 2(n + 1): the TLS solution is determined to ~u * 1e3 relative
+        assert np.linalg.norm(x.cpu().numpy() - x_or) <= 1e-8 * np.linalg.norm(x_or)
+        assert sine(v_or[:, None], v[:, None]) < 1e-8
+        r_gpu, r_or = O.residual(Xb, v[:, None]), O.residual(Xb, v_or[:, None])
+        assert r_gpu <= (1 + 1e-10) * r_or + 10 * U53 * np.sqrt(Xb.shape[1]) * np.linalg.norm(Xb)
+
+
 def test_batched_general_problems(api):
     rng = np.random.default_rng(9)
     shapes = [(5000, 24, 96, 2), (300, 3, 8, 1), (4096, 32, 128, 4), (9000, 17, 40, 17), (70000, 40, 200, 3)]

@@ -1,0 +1,97 @@
+"""The precision workload: A stored in FP32 with a graded spectrum (sigma_1..510
+log-spaced from 1 to 1e-6, sigma_511 = sigma_512 = 1e-9), n = 512, k = 2,
+sketched with s = 2048 by the FP32-stream SRHT and by the 3 x BF16 tensor-core
+Gaussian sketch, then solved in FP64.  Both results are compared with the FP64
+oracle's on the same (FP32-stored) A.
+
+m is 2^17 for the SRHT (2^13 for the Gaussian) rather than the benchmark's
+2^22: the oracle's QR and Jacobi of the 2048 x 512 sketch, its FP64 sketch and
+the QR that gives range(A) must finish in seconds on the host (the Gaussian
+oracle costs s m n multiply-adds).  The sketch geometry (s, n and the number
+of 4096-row blocks per split or chunk) is the benchmark's.
+
+The FP32 sketch noise (about 2^-24 ||A||) lies far above sigma_511 = 1e-9, so
+the trailing subspace is not resolved and no 1e-8 sine can be asked for.  What
+holds whatever the noise is the deterministic residual bound: with
+E = SA_gpu - SA_oracle (measured), W_gpu minimising ||SA_gpu W||_F and
+Q an orthonormal basis of range(A),
+  ||A W_gpu||_F <= (||SA_or W_or||_F + 2 sqrt(k) ||E||_2 + slack) / sigma_min(S Q),
+since ||S x|| >= sigma_min(S Q) ||x|| on range(A) (the argument of Theorem 2.3),
+slack = 10 u sqrt(n) ||SA||_F covering the FP64 dense stage.  The test asserts
+it, reports the sine and residuals, and checks the sketches entry by entry.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2206_00975_gb300 import workloads
+from tests.helpers import sine
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U53 = 2.0 ** -53
+N, S_ROWS, K = 512, 2048, 2
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_00975_gb300 import build
+    build.build()
+    from paper_2206_00975_gb300 import api as a
+    return a
+
+
+def precision_input(m, seed):
+    w = workloads.graded(seed=seed, m=m, n=N, k=K, tail=1e-9, dtype=np.float32)
+    A64 = w["A"].astype(np.float64)            # the FP32 data, upcast exactly
+    Q, _ = np.linalg.qr(A64)
+    return w["A"], A64, np.asfortranarray(Q)
+
+
+def residual_bound_check(A64, Q, SA_gpu, SA_or, W_gpu, sketch_fn, label):
+    W_or = O.solve_sketched(SA_or, K)[0]
+    E = SA_gpu - SA_or
+    smin = np.linalg.svd(sketch_fn(Q), compute_uv=False).min()
+    slack = 10 * U53 * np.sqrt(N) * np.linalg.norm(SA_or)
+    bound = (np.linalg.norm(SA_or @ W_or) + 2 * np.sqrt(K) * np.linalg.norm(E, 2) + slack) / smin
+    r_gpu, r_or = O.residual(A64, W_gpu), O.residual(A64, W_or)
+    print("%s: ||A W||_F gpu %.3e oracle %.3e bound %.3e; sine(W_gpu, W_or) %.3e; ||E||_2 %.3e" %
+          (label, r_gpu, r_or, bound, sine(W_or, W_gpu), np.linalg.norm(E, 2)))
+    assert r_gpu <= bound
+    return r_gpu, r_or
+
+
+def test_precision_fp32_stream_srht(api):
+    m = 1 << 17
+    A32, A64, Q = precision_input(m, seed=22)
+    d = api.desc(api.NS_SRHT, s=S_ROWS, seed=5, prec=api.NS_PREC_FP32_STREAM)
+    Ad = api.colmajor(A32, device="cuda")
+    Vk, sk, sv, status = api.ns_solve(d, Ad, K, save=True)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    SA_gpu = api.unpack_save(sv, S_ROWS, N)[0].cpu().numpy()
+    # the sketch entry by entry: FP32 butterflies, error <= u32 (log2 m' + 2) ||A||_F
+    SA_or = O.srht(5, S_ROWS, A64)
+    assert np.max(np.abs(SA_gpu - SA_or)) <= 2.0 ** -24 * (O.ceil_log2(m) + 2) * np.linalg.norm(A64)
+    residual_bound_check(A64, Q, SA_gpu, SA_or, Vk.cpu().numpy(), lambda X: O.srht(5, S_ROWS, X),
+                         "fp32-stream SRHT")
+
+
+def test_precision_bf16x3_gaussian(api):
+    m = 1 << 13
+    A32, A64, Q = precision_input(m, seed=23)
+    d = api.desc(api.NS_GAUSSIAN, s=S_ROWS, seed=6, prec=api.NS_PREC_BF16X3)
+    Ad = api.colmajor(A32, device="cuda")
+    Vk, sk, sv, status = api.ns_solve(d, Ad, K, save=True)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    SA_gpu = api.unpack_save(sv, S_ROWS, N)[0].cpu().numpy()
+    SA_or = O.gaussian(6, S_ROWS, A64)
+    rows = list(range(0, S_ROWS, 97))
+    _, mag = O.gaussian_rows(6, S_ROWS, A64, rows)
+    assert np.all(np.abs(SA_gpu[rows] - SA_or[rows]) <= 2.0 ** -12 * mag + 1e-300)
+    residual_bound_check(A64, Q, SA_gpu, SA_or, Vk.cpu().numpy(), lambda X: O.gaussian(6, S_ROWS, X),
+                         "bf16x3 Gaussian")

@@ -260,6 +260,22 @@ def test_gaussian_sketch_equals_explicit():
     np.testing.assert_allclose(part[:, 2], (G @ A / np.sqrt(s))[:, 2], rtol=1e-13, atol=1e-14)
 
 
+def test_gaussian_rows_equal_explicit_product_and_full_sketch():
+    # the sampled-rows routine against an explicit G A (brute force) and the
+    # full sketch (same summation order: bit for bit); the term sizes against
+    # their definition
+    s, m, n = 24, 57, 4
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((m, n))
+    G = np.array([[O.gaussian_entry(5, r, j) for j in range(m)] for r in range(s)])
+    rows = [0, 7, 23, 7]
+    out, mag = O.gaussian_rows(5, s, A, rows)
+    np.testing.assert_allclose(out, (G @ A / np.sqrt(s))[rows], rtol=1e-13, atol=1e-14)
+    assert np.array_equal(out, O.gaussian(5, s, A)[rows])
+    want = np.sqrt(((G[rows][:, :, None] * A[None, :, :]) ** 2).sum(axis=1)) / np.sqrt(s)
+    np.testing.assert_allclose(mag, want, rtol=1e-13)
+
+
 # -------------------------------------------------------- QR and Jacobi ----
 @pytest.mark.parametrize("s,n", [(40, 8), (128, 32), (9, 9), (5, 1)])
 def test_householder_qr_against_lapack(s, n):
