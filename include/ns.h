@@ -204,10 +204,12 @@ ns_status ns_solve_sketched(const ns_sketch_desc *desc, const double *SA, int64_
 /*
  * ns_solve_stats / ns_sketched_stats -- statistics of the Jacobi iteration of
  * the last ns_solve (ns_solve_sketched) that ran in workspace ws with the same
- * desc and shape: dev_out (device int64[4]) receives the number of full
- * sweeps, the number of rotations, the number of barrier-free check passes
- * and the kernel that ran (the cluster size, 8 or 16, of the cluster-ring
- * Jacobi, or 0: the barrier-separated one).
+ * desc and shape: dev_out (device int64[6]) receives the number of full FP64
+ * sweeps, the number of FP64 rotations, the number of barrier-free check
+ * passes, the kernel that ran (the cluster size, 8 or 16, of the cluster-ring
+ * Jacobi, or 0: the barrier-separated one), and the sweeps and rotations of
+ * the FP32 linear phase that precedes the FP64 iteration for 64 <= n <= 256
+ * (0 and 0 when it did not run).
  * Enqueued on stream after that call.
  */
 ns_status ns_solve_stats(const ns_sketch_desc *desc, int64_t m, int64_t n, const void *ws, int64_t *dev_out,

@@ -44,7 +44,9 @@ namespace ns {
 constexpr int kDenseThreads = 256;
 constexpr int kMaxSweeps = 30;
 constexpr int kCheckBelow = 4096;        // run the barrier-free check after a sweep with fewer rotations
-constexpr int kBarWords = 64 + 2 * 64 + 8;  // barrier word (padded), rotation counts, check flags, stats
+constexpr int kBarWords = 64 + 2 * 64 + 16;  // barrier word (padded), rotation counts, check flags, stats,
+                                             // FP32-phase control (bar[196..198])
+constexpr int kJ32Ctl = 196;                 // word of bar: 1 if the FP32 phase ran, then its sweeps, rotations
 
 size_t dense_work_bytes(int64_t s, int64_t n) {
     Carver c(nullptr);
@@ -1065,20 +1067,6 @@ __device__ __forceinline__ double warp_sum3(double v0, double v1, double v2) {
     return k;
 }
 
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ uint32_t peer_addr(uint32_t local, uint32_t rank) {
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
-    return r;
-}
-__device__ __forceinline__ void cluster_sync_all() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ uint32_t shared_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Waiting threads are suspended in hardware until the phase completes (or the
 // hint elapses) instead of re-polling: a polling loop of whole warps keeps the
@@ -1279,7 +1267,7 @@ template <int kRingC>
 __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
     jacobi_ring_kernel(double *X, double *V, int64_t n, int64_t G, double tol, GridBarrier bar,
                        unsigned int *rotcount, unsigned int *checkflag, double *sigma, unsigned int *colver,
-                       int32_t *status, int vinit, int max_sweeps) {
+                       int32_t *status, int vinit, int max_sweeps, const unsigned int *fp32_ran) {
     // Slot j receives the Q column of round j: rows t and t + kRingT of X in
     // xbuf[j][t] and of V in vbuf[j][t], and its scale pair in sbuf[j], each
     // completed on its own mbarrier (mbx, mbv, mbs).  Columns are held scaled,
@@ -1355,8 +1343,12 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
     unsigned int prev_rot = 0xFFFFFFFFu;
     int full_sweeps = 0, check_passes = 0;
     uint32_t ostep = 0;  // outer steps so far: phase parity of the slot mbarriers
+    // After the FP32 phase the columns start nearly orthogonal (cosines ~2^-17):
+    // two sweeps reach FP64 convergence, so the barrier-free check runs from
+    // the third sweep on whatever the rotation count was.
+    const int check_from = (fp32_ran && *(volatile const unsigned int *)fp32_ran != 0u) ? 2 : max_sweeps + 1;
     for (int sweep = 0; sweep < max_sweeps && !converged && ok; ++sweep) {
-        if (prev_rot < (unsigned int)kCheckBelow) {
+        if (prev_rot < (unsigned int)kCheckBelow || sweep >= check_from) {
             ++check_passes;
             const int c = jacobi_check_pass(X, n, tol2, bar, checkflag + sweep, sigma);
             if (c < 0) {
@@ -1848,7 +1840,7 @@ static size_t ring_smem(int C) { return (size_t)2 * C * kRingT * sizeof(double2)
 
 template <int C>
 static cudaError_t launch_ring_c(const DenseWork &w, int64_t n, GridBarrier bar, int32_t *status, int vinit,
-                                 int max_sweeps, cudaStream_t st, bool *used) {
+                                 int max_sweeps, const unsigned int *fp32_ran, cudaStream_t st, bool *used) {
     static int state[64] = {0};  // per device: 0 unknown, 1 usable, -1 not usable
     *used = false;
     int dev = 0;
@@ -1888,7 +1880,7 @@ static cudaError_t launch_ring_c(const DenseWork &w, int64_t n, GridBarrier bar,
     cudaError_t e = cudaMemsetAsync(colver, 0, sizeof(unsigned int) * (size_t)(n + 32), st);
     if (e != cudaSuccess) return e;
     e = cudaLaunchKernelEx(&cfg, jacobi_ring_kernel<C>, X, V, n, G, tol, bar, rot, chk, sigma, colver, status,
-                           vinit, max_sweeps);
+                           vinit, max_sweeps, fp32_ran);
     if (e != cudaSuccess) {
         cudaGetLastError();
         state[dev] = -1;
@@ -1900,12 +1892,12 @@ static cudaError_t launch_ring_c(const DenseWork &w, int64_t n, GridBarrier bar,
 }
 
 static cudaError_t launch_jacobi_ring(const DenseWork &w, int64_t n, GridBarrier bar, int32_t *status, int vinit,
-                                      int max_sweeps, cudaStream_t st, bool *used) {
+                                      int max_sweeps, const unsigned int *fp32_ran, cudaStream_t st, bool *used) {
     if (n > 2 * 15 * 8) {  // 16 clusters of 8 would share SMs: try clusters of 16
-        const cudaError_t e = launch_ring_c<16>(w, n, bar, status, vinit, max_sweeps, st, used);
+        const cudaError_t e = launch_ring_c<16>(w, n, bar, status, vinit, max_sweeps, fp32_ran, st, used);
         if (e != cudaSuccess || *used) return e;
     }
-    return launch_ring_c<8>(w, n, bar, status, vinit, max_sweeps, st, used);
+    return launch_ring_c<8>(w, n, bar, status, vinit, max_sweeps, fp32_ran, st, used);
 }
 
 template <int NB>
@@ -1974,6 +1966,8 @@ __global__ void dense_stats_kernel(const unsigned int *bar, int64_t *out) {
         out[1] = bar[64 + 129];
         out[2] = bar[64 + 130];
         out[3] = bar[64 + 131];
+        out[4] = bar[kJ32Ctl] ? bar[kJ32Ctl + 1] : 0;  // FP32-phase sweeps (0: the phase did not run)
+        out[5] = bar[kJ32Ctl] ? bar[kJ32Ctl + 2] : 0;  // FP32-phase rotations
     }
 }
 
@@ -1984,7 +1978,7 @@ cudaError_t launch_dense_stats(const DenseWork &w, int64_t *out, cudaStream_t st
 
 cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k, const DenseWork &w, double *Vk,
                                double *sigk, double *save_V, double *save_sigma, int32_t *status, cudaStream_t st,
-                               int max_sweeps) {
+                               int max_sweeps, bool fp32_phase) {
     cudaError_t e = cudaSuccess;
     if (max_sweeps <= 0 || max_sweeps > kMaxSweeps) max_sweeps = kMaxSweeps;
     GridBarrier bar{w.bar, status};
@@ -2048,8 +2042,15 @@ cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k
     if (e != cudaSuccess) return e;
     const int vinit = q2_in_v ? 1 : 0;
     bool ring = false;
+    unsigned int *fp32_ran = nullptr;
+    if (q2_in_v && n <= kRingN && jacobi32_applicable(n) && fp32_phase) {
+        // the linear phase of the Jacobi iteration in FP32 (X = X0 V0, V = Q2 V0)
+        fp32_ran = w.bar + kJ32Ctl;
+        e = launch_jacobi32_precondition(w, n, fp32_ran, st);
+        if (e != cudaSuccess) return e;
+    }
     if (n <= kRingN) {
-        e = launch_jacobi_ring(w, n, bar, status, vinit, max_sweeps, st, &ring);
+        e = launch_jacobi_ring(w, n, bar, status, vinit, max_sweeps, fp32_ran, st, &ring);
         if (e != cudaSuccess) return e;
     }
     if (ring) e = cudaSuccess;

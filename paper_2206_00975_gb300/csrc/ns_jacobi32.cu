@@ -1,0 +1,397 @@
+// ns_jacobi32.cu -- the linear phase of the one-sided Jacobi SVD in FP32, as a
+// preconditioner for the FP64 iteration of ns_dense.cu (Algorithm 1 line 3:
+// the SVD of SA, through R and X = R2^T).
+//
+// One-sided Jacobi converges linearly over its first sweeps and quadratically
+// once the columns are nearly orthogonal.  On this part FP32 arithmetic runs
+// at 64 times the FP64 rate and an FP32 column takes half the bytes, so the
+// linear phase runs in FP32 and the FP64 ring only finishes the job:
+//
+//   1. Y = X0 in FP32 (columns of X0 = R2^T scaled by one power of two);
+//      columns whose norm is below 2^-30 of the largest are left out (zero in
+//      Y, identity in W): their relative accuracy is not touched, see below.
+//   2. One-sided Jacobi sweeps on Y in FP32, the rotations accumulated in W
+//      (FP32, from I), with the rotation threshold |y_a . y_b| > tau |y_a||y_b|,
+//      tau = 2^-17, until a sweep rotates nothing or 8 sweeps.
+//   3. V0 = W made orthogonal in FP64: E = I - W^T W (about 1e-6), and
+//      V0 = W (I + E/2 + 3 E^2 / 8), the series of (W^T W)^(-1/2) to second
+//      order (the remainder is of order E^3).
+//   4. X1 = X0 V0 and V = Q2 V0 in FP64; the FP64 ring Jacobi then starts from
+//      nearly orthogonal columns (cosines ~ tau) and needs two sweeps and a
+//      check instead of seven sweeps and a check.
+//
+// Step 2 runs on one cluster of 8 CTAs (n <= 256): the 256 columns of Y and W
+// are 16 blocks of 16 columns, two blocks per CTA in shared memory.  A sweep is
+// one round-robin tournament of the blocks (15 outer steps, block pairs; the
+// pairs inside each block at the first); inside an outer step the 256 pairs
+// between the CTA's two blocks take 16 rounds of 16 disjoint pairs, one warp
+// per pair, separated by CTA barriers only.  Between outer steps each CTA pulls
+// its next blocks from its neighbours' shared memory (distributed shared
+// memory loads, one cluster barrier per exchange, two slot parities).
+//
+// Accuracy.  Rounding in step 4 puts an absolute error of about u |X0| into the
+// columns of X1.  V0 is the product of FP32 rotations: an entry V0[i, j] that
+// couples columns of norms d_i >> d_j is ~ d_j/d_i (one-sided Jacobi angles are
+// small between columns of very different size), up to the FP32 rounding of W
+// (absolute ~1e-7), so column j of X1 gains at most ~u (1 + 1e-7 d_max/d_j)
+// relative error; with d_j >= 2^-30 d_max that is below 1e3 u.  Columns below
+// 2^-30 d_max keep their X0 column unchanged.  The FP64 iteration is then the
+// usual one and fixes the final accuracy.
+#include <cmath>
+#include "ns_device.cuh"
+#include "ns_internal.h"
+
+namespace ns {
+
+constexpr int kJ32Cta = 8;                     // CTAs per cluster
+constexpr int kJ32B = 16;                      // columns per block
+constexpr int kJ32Blocks = 2 * kJ32Cta;        // 16 blocks
+constexpr int kJ32N = kJ32B * kJ32Blocks;      // 256 columns (n <= 256)
+constexpr int kJ32Rows = 256;                  // rows of Y and of W
+constexpr int kJ32Col = 2 * kJ32Rows;          // floats per column: y (256), then w (256)
+constexpr int kJ32Slot = kJ32B * kJ32Col;      // floats per block slot (32 KB)
+constexpr int kJ32Threads = kJ32B * 32;        // one warp per pair of a round
+constexpr int kJ32Steps = kJ32Blocks - 1;      // outer steps per sweep
+constexpr int kJ32MaxSweeps = 8;
+constexpr float kJ32Tau = 1.0f / 131072.0f;    // 2^-17
+constexpr double kJ32Keep = 8.673617379884035e-19;  // 2^-60: kept columns have |x|^2 >= 2^-60 max |x|^2
+constexpr size_t kJ32Smem = (size_t)4 * kJ32Slot * sizeof(float);
+
+// slot index in the per-CTA array of four block slots: parity p holds
+// top (2 p) and bottom (2 p + 1)
+__device__ __forceinline__ float *j32_slot(float *base, int idx) { return base + (size_t)idx * kJ32Slot; }
+
+// player of tournament position `pos` at step `step` (16 players, player 0 fixed)
+__device__ __forceinline__ int j32_rr(int pos, int step) { return pos == 0 ? 0 : 1 + (pos - 1 + step) % 15; }
+
+// One pair (columns a, b: pointers to their y rows; w follows at +kJ32Rows),
+// one warp; returns 1 (in every lane) if the pair was rotated.
+__device__ __forceinline__ unsigned int j32_pair(float *a, float *b, float tau2) {
+    const int lane = threadIdx.x & 31;
+    // lane l holds rows 4l..4l+3 and 128+4l..128+4l+3: each float4 access of the
+    // warp covers 512 contiguous bytes (no bank conflicts)
+    const float4 a0 = *(const float4 *)(a + 4 * lane), a1 = *(const float4 *)(a + 128 + 4 * lane);
+    const float4 b0 = *(const float4 *)(b + 4 * lane), b1 = *(const float4 *)(b + 128 + 4 * lane);
+    float al = a0.x * a0.x, be = b0.x * b0.x, ga = a0.x * b0.x;
+    al = fmaf(a0.y, a0.y, al); be = fmaf(b0.y, b0.y, be); ga = fmaf(a0.y, b0.y, ga);
+    al = fmaf(a0.z, a0.z, al); be = fmaf(b0.z, b0.z, be); ga = fmaf(a0.z, b0.z, ga);
+    al = fmaf(a0.w, a0.w, al); be = fmaf(b0.w, b0.w, be); ga = fmaf(a0.w, b0.w, ga);
+    al = fmaf(a1.x, a1.x, al); be = fmaf(b1.x, b1.x, be); ga = fmaf(a1.x, b1.x, ga);
+    al = fmaf(a1.y, a1.y, al); be = fmaf(b1.y, b1.y, be); ga = fmaf(a1.y, b1.y, ga);
+    al = fmaf(a1.z, a1.z, al); be = fmaf(b1.z, b1.z, be); ga = fmaf(a1.z, b1.z, ga);
+    al = fmaf(a1.w, a1.w, al); be = fmaf(b1.w, b1.w, be); ga = fmaf(a1.w, b1.w, ga);
+    // butterfly sums: every lane ends with the same totals (addition commutes)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        al += __shfl_xor_sync(0xffffffffu, al, o);
+        be += __shfl_xor_sync(0xffffffffu, be, o);
+        ga += __shfl_xor_sync(0xffffffffu, ga, o);
+    }
+    if (!(ga != 0.0f && ga * ga > tau2 * (al * be))) return 0u;
+    // the rotation of the FP64 kernel: zeta = (beta - alpha) / (2 gamma),
+    // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t;
+    // a <- c a - s b, b <- s a + c b
+    const float z = (be - al) / (2.0f * ga), az = fabsf(z);
+    const float t = (az > 1e18f) ? 0.5f / z : copysignf(1.0f / (az + sqrtf(fmaf(z, z, 1.0f))), z);
+    const float c = rsqrtf(fmaf(t, t, 1.0f)), s = c * t;
+    float4 na0, na1, nb0, nb1;
+    na0.x = c * a0.x - s * b0.x; nb0.x = s * a0.x + c * b0.x;
+    na0.y = c * a0.y - s * b0.y; nb0.y = s * a0.y + c * b0.y;
+    na0.z = c * a0.z - s * b0.z; nb0.z = s * a0.z + c * b0.z;
+    na0.w = c * a0.w - s * b0.w; nb0.w = s * a0.w + c * b0.w;
+    na1.x = c * a1.x - s * b1.x; nb1.x = s * a1.x + c * b1.x;
+    na1.y = c * a1.y - s * b1.y; nb1.y = s * a1.y + c * b1.y;
+    na1.z = c * a1.z - s * b1.z; nb1.z = s * a1.z + c * b1.z;
+    na1.w = c * a1.w - s * b1.w; nb1.w = s * a1.w + c * b1.w;
+    *(float4 *)(a + 4 * lane) = na0;
+    *(float4 *)(a + 128 + 4 * lane) = na1;
+    *(float4 *)(b + 4 * lane) = nb0;
+    *(float4 *)(b + 128 + 4 * lane) = nb1;
+    float *aw = a + kJ32Rows, *bw = b + kJ32Rows;
+    const float4 p0 = *(const float4 *)(aw + 4 * lane), p1 = *(const float4 *)(aw + 128 + 4 * lane);
+    const float4 q0 = *(const float4 *)(bw + 4 * lane), q1 = *(const float4 *)(bw + 128 + 4 * lane);
+    na0.x = c * p0.x - s * q0.x; nb0.x = s * p0.x + c * q0.x;
+    na0.y = c * p0.y - s * q0.y; nb0.y = s * p0.y + c * q0.y;
+    na0.z = c * p0.z - s * q0.z; nb0.z = s * p0.z + c * q0.z;
+    na0.w = c * p0.w - s * q0.w; nb0.w = s * p0.w + c * q0.w;
+    na1.x = c * p1.x - s * q1.x; nb1.x = s * p1.x + c * q1.x;
+    na1.y = c * p1.y - s * q1.y; nb1.y = s * p1.y + c * q1.y;
+    na1.z = c * p1.z - s * q1.z; nb1.z = s * p1.z + c * q1.z;
+    na1.w = c * p1.w - s * q1.w; nb1.w = s * p1.w + c * q1.w;
+    *(float4 *)(aw + 4 * lane) = na0;
+    *(float4 *)(aw + 128 + 4 * lane) = na1;
+    *(float4 *)(bw + 4 * lane) = nb0;
+    *(float4 *)(bw + 128 + 4 * lane) = nb1;
+    return 1u;
+}
+
+__device__ __forceinline__ float4 ld_peer_f4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_peer_u32(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_peer_f64(uint32_t addr, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+
+// X (n x n FP64, column-major) -> V0 (n x n FP64: the accumulated FP32
+// rotations W, exactly), ctl[0] = 1 if the phase ran (0: it was skipped and V0
+// is not written), ctl[1] = sweeps, ctl[2] = rotations.
+__global__ void __cluster_dims__(kJ32Cta, 1, 1) __launch_bounds__(kJ32Threads, 1)
+    jacobi32_phase_kernel(const double *__restrict__ X, int64_t n, double *__restrict__ V0, unsigned int *ctl) {
+    extern __shared__ __align__(16) float j32_smem[];
+    __shared__ double s_nrm[2 * kJ32B];
+    __shared__ double s_max[kJ32Cta];
+    __shared__ unsigned int s_cnt[kJ32Cta];
+    __shared__ unsigned int s_rot[kJ32Cta];
+    __shared__ unsigned int s_local;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int c = (int)cluster_rank();
+    const int btop = c, bbot = kJ32Blocks - 1 - c;  // blocks held at the start of every sweep
+    cluster_sync_all();  // every CTA of the cluster has started before any distributed access
+    // ---- column norms of this CTA's 32 columns (FP64), cluster-wide maximum
+    for (int q = w; q < 2 * kJ32B; q += kJ32Threads / 32) {
+        const int64_t j = (int64_t)(q < kJ32B ? btop : bbot) * kJ32B + (q % kJ32B);
+        double a = 0.0;
+        if (j < n)
+            for (int64_t r = lane; r < n; r += 32) {
+                const double x = X[r + j * n];
+                a = fma(x, x, a);
+            }
+        a = warp_sum(a);
+        if (lane == 0) s_nrm[q] = a;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double mx = 0.0;
+        for (int q = 0; q < 2 * kJ32B; ++q) mx = fmax(mx, s_nrm[q]);
+        for (int r = 0; r < kJ32Cta; ++r) st_peer_f64(peer_addr(shared_addr(&s_max[c]), r), mx);
+    }
+    __syncthreads();
+    cluster_sync_all();
+    double gmax = 0.0;
+    for (int r = 0; r < kJ32Cta; ++r) gmax = fmax(gmax, s_max[r]);
+    const double keep = gmax * kJ32Keep;
+    if (tid == 0) {
+        unsigned int cnt = 0;
+        for (int q = 0; q < 2 * kJ32B; ++q) cnt += (s_nrm[q] > 0.0 && s_nrm[q] >= keep) ? 1u : 0u;
+        for (int r = 0; r < kJ32Cta; ++r) st_peer_u32(peer_addr(shared_addr(&s_cnt[c]), r), cnt);
+    }
+    __syncthreads();
+    cluster_sync_all();
+    unsigned int kept = 0;
+    for (int r = 0; r < kJ32Cta; ++r) kept += s_cnt[r];
+    if (!(gmax > 0.0) || !(gmax < 1e300) || 2 * (int64_t)kept < n) {  // nothing to gain (or nothing finite)
+        if (c == 0 && tid == 0) ctl[0] = 0u;
+        return;  // no CTA touched a peer after the last cluster barrier
+    }
+    // scale: the largest column norm lands in [0.5, 1)
+    int e2 = 0;
+    frexp(sqrt(gmax), &e2);
+    const double sc = ldexp(1.0, -e2);
+    // ---- Y and W = I into the parity-0 slots
+    for (int sl = 0; sl < 2; ++sl) {
+        float *S = j32_slot(j32_smem, sl);
+        const int blk = sl == 0 ? btop : bbot;
+        for (int idx = tid; idx < kJ32Slot; idx += kJ32Threads) {
+            const int i = idx / kJ32Col, e = idx % kJ32Col;
+            const int64_t j = (int64_t)blk * kJ32B + i;
+            const bool inc = j < n && s_nrm[sl * kJ32B + i] > 0.0 && s_nrm[sl * kJ32B + i] >= keep;
+            float v;
+            if (e < kJ32Rows) v = (inc && e < n) ? (float)(X[e + j * n] * sc) : 0.0f;
+            else v = (e - kJ32Rows == j) ? 1.0f : 0.0f;
+            S[idx] = v;
+        }
+    }
+    if (tid == 0) s_local = 0u;
+    __syncthreads();
+    const float tau2 = kJ32Tau * kJ32Tau;
+    int par = 0, sweeps = 0;
+    unsigned int rot_total = 0;
+    for (int sweep = 0; sweep < kJ32MaxSweeps; ++sweep) {
+        ++sweeps;
+        unsigned int mine = 0;  // rotations of this warp (lane values agree)
+        for (int step = 0; step < kJ32Steps; ++step) {
+            float *T = j32_slot(j32_smem, 2 * par), *B = j32_slot(j32_smem, 2 * par + 1);
+            if (step == 0) {  // pairs inside each block: warps 0-7 the top block, 8-15 the bottom
+                float *M = w < 8 ? T : B;
+                const int q = w & 7;
+                for (int r = 0; r < kJ32B - 1; ++r) {
+                    const int pa = j32_rr(q, r), pb = j32_rr(kJ32B - 1 - q, r);
+                    mine += j32_pair(M + pa * kJ32Col, M + pb * kJ32Col, tau2);
+                    __syncthreads();
+                }
+            }
+            for (int r = 0; r < kJ32B; ++r) {  // the 256 pairs between the two blocks
+                mine += j32_pair(T + w * kJ32Col, B + ((w + r) & (kJ32B - 1)) * kJ32Col, tau2);
+                __syncthreads();
+            }
+            if (step == kJ32Steps - 1) {  // publish this CTA's rotation count of the sweep
+                if (lane == 0) atomicAdd(&s_local, mine);
+                __syncthreads();
+                if (tid == 0) {
+                    for (int r = 0; r < kJ32Cta; ++r) st_peer_u32(peer_addr(shared_addr(&s_rot[c]), r), s_local);
+                    s_local = 0u;
+                }
+                __syncthreads();
+            }
+            // ---- exchange: position p takes the block of position p - 1 (1 after 15; 0 stays)
+            cluster_sync_all();
+            const int np = par ^ 1;
+            float *dT = j32_slot(j32_smem, 2 * np), *dB = j32_slot(j32_smem, 2 * np + 1);
+            // sources: new top <- (c == 0: own top; c == 1: CTA 0's bottom; else CTA c-1's top)
+            //          new bottom <- (c == 7: own top; else CTA c+1's bottom)
+            const int st_rank = c == 0 ? 0 : (c == 1 ? 0 : c - 1);
+            const int st_slot = c == 0 ? 2 * par : (c == 1 ? 2 * par + 1 : 2 * par);
+            const int sb_rank = c == kJ32Cta - 1 ? c : c + 1;
+            const int sb_slot = c == kJ32Cta - 1 ? 2 * par : 2 * par + 1;
+            const uint32_t srcT = peer_addr(shared_addr(j32_slot(j32_smem, st_slot)), (uint32_t)st_rank);
+            const uint32_t srcB = peer_addr(shared_addr(j32_slot(j32_smem, sb_slot)), (uint32_t)sb_rank);
+#pragma unroll 4
+            for (int v = tid; v < kJ32Slot / 4; v += kJ32Threads) {
+                const float4 x = ld_peer_f4(srcT + 16u * (uint32_t)v);
+                const float4 y = ld_peer_f4(srcB + 16u * (uint32_t)v);
+                ((float4 *)dT)[v] = x;
+                ((float4 *)dB)[v] = y;
+            }
+            __syncthreads();
+            par = np;
+        }
+        // every CTA reads the same counts (published before the last cluster barrier)
+        unsigned int tot = 0;
+        for (int r = 0; r < kJ32Cta; ++r) tot += s_rot[r];
+        rot_total += tot;
+        if (tot == 0u) break;
+    }
+    // ---- blocks are back where they started: W columns -> V0 (FP64, exact)
+    for (int sl = 0; sl < 2; ++sl) {
+        const float *S = j32_slot(j32_smem, 2 * par + sl);
+        const int blk = sl == 0 ? btop : bbot;
+        for (int idx = tid; idx < kJ32B * kJ32Rows; idx += kJ32Threads) {
+            const int i = idx / kJ32Rows, r = idx % kJ32Rows;
+            const int64_t j = (int64_t)blk * kJ32B + i;
+            if (j < n && r < n) V0[r + j * n] = (double)S[i * kJ32Col + kJ32Rows + r];
+        }
+    }
+    if (c == 0 && tid == 0) {
+        ctl[0] = 1u;
+        ctl[1] = (unsigned int)sweeps;
+        ctl[2] = rot_total;
+    }
+    __syncthreads();
+    cluster_sync_all();  // no CTA leaves while a peer may still read its shared memory
+}
+
+// ----------------------------------------------------- small FP64 GEMMs ----
+// C (M x N) = op(A) B with op(A) = A (M x K) or A^T (A: K x M); column-major,
+// leading dimensions lda, ldb, ldc.  Epilogues: 0: C = AB; 1: C = I - A^T B;
+// 2: C = I + E/2 + (3/8) A B (E: M x N, ld ldc).  One 16 x 16 tile per CTA,
+// one output per thread, K in chunks of 16 through shared memory.  Skipped
+// when *ctl == 0 (the FP32 phase did not run).
+constexpr int kG64T = 16;
+
+template <bool TA, int EPI>
+__global__ void __launch_bounds__(kG64T * kG64T) gemm64_kernel(const double *__restrict__ A, int64_t lda,
+                                                              const double *__restrict__ B, int64_t ldb,
+                                                              double *__restrict__ C, int64_t ldc,
+                                                              const double *__restrict__ E, int64_t M, int64_t N,
+                                                              int64_t K, const unsigned int *ctl) {
+    if (ctl && *(volatile const unsigned int *)ctl == 0u) return;
+    __shared__ double As[kG64T][kG64T + 1];  // As[k][i] = op(A)[i, k]
+    __shared__ double Bs[kG64T][kG64T + 1];  // Bs[k][j] = B[k, j]
+    const int tx = threadIdx.x % kG64T, ty = threadIdx.x / kG64T;
+    const int64_t i = (int64_t)blockIdx.x * kG64T + tx, j = (int64_t)blockIdx.y * kG64T + ty;
+    double acc = 0.0;
+    for (int64_t k0 = 0; k0 < K; k0 += kG64T) {
+        {   // thread (tx, ty) loads op(A)[blockIdx.x*16 + ?, k0 + ?] and B[k0 + ?, blockIdx.y*16 + ?]
+            const int64_t ai = (int64_t)blockIdx.x * kG64T + (TA ? ty : tx), ak = k0 + (TA ? tx : ty);
+            double av = 0.0;
+            if (ai < M && ak < K) av = TA ? A[ak + ai * lda] : A[ai + ak * lda];
+            if (TA) As[tx][ty] = av;
+            else As[ty][tx] = av;
+            const int64_t bk = k0 + tx, bj = (int64_t)blockIdx.y * kG64T + ty;
+            Bs[tx][ty] = (bk < K && bj < N) ? B[bk + bj * ldb] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kG64T; ++kk) acc = fma(As[kk][tx], Bs[kk][ty], acc);
+        __syncthreads();
+    }
+    if (i < M && j < N) {
+        double v = acc;
+        if (EPI == 1) v = (i == j ? 1.0 : 0.0) - acc;
+        if (EPI == 2) v = (i == j ? 1.0 : 0.0) + 0.5 * E[i + j * ldc] + 0.375 * acc;
+        C[i + j * ldc] = v;
+    }
+}
+
+__global__ void copy_if_kernel(const double *__restrict__ a, int64_t len, double *__restrict__ b,
+                               const unsigned int *ctl) {
+    if (*(volatile const unsigned int *)ctl == 0u) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = a[i];
+}
+
+template <bool TA, int EPI>
+static cudaError_t gemm64(const double *A, int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc,
+                          const double *E, int64_t M, int64_t N, int64_t K, const unsigned int *ctl,
+                          cudaStream_t st) {
+    dim3 grid((unsigned)((M + kG64T - 1) / kG64T), (unsigned)((N + kG64T - 1) / kG64T));
+    gemm64_kernel<TA, EPI><<<grid, kG64T * kG64T, 0, st>>>(A, lda, B, ldb, C, ldc, E, M, N, K, ctl);
+    return cudaGetLastError();
+}
+
+bool jacobi32_applicable(int64_t n) { return n >= 64 && n <= kJ32N; }
+
+cudaError_t launch_jacobi32_precondition(const DenseWork &w, int64_t n, unsigned int *ctl, cudaStream_t st) {
+    // the phase is an optimisation: if the cluster cannot be placed, the FP64
+    // iteration runs alone (ctl[0] stays 0, the products below are skipped)
+    static int state[64] = {0};  // per device: 0 unknown, 1 usable, -1 not usable
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaSuccess;
+    if (state[dev] < 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (state[dev] == 0) {
+        if (cudaFuncSetAttribute(jacobi32_phase_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kJ32Smem) != cudaSuccess) {
+            cudaGetLastError();
+            state[dev] = -1;
+            return cudaSuccess;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(kJ32Cta, 1, 1);
+        cfg.blockDim = dim3(kJ32Threads, 1, 1);
+        cfg.dynamicSmemBytes = kJ32Smem;
+        cfg.stream = st;
+        int maxc = 0;
+        if (cudaOccupancyMaxActiveClusters(&maxc, (void *)jacobi32_phase_kernel, &cfg) != cudaSuccess || maxc < 1) {
+            cudaGetLastError();
+            state[dev] = -1;
+            return cudaSuccess;
+        }
+        state[dev] = 1;
+    }
+    double *V0 = w.L, *Em = w.L + n * n, *Mm = w.U, *V0p = w.W, *X1 = w.U, *V1 = w.L;
+    jacobi32_phase_kernel<<<kJ32Cta, kJ32Threads, kJ32Smem, st>>>(w.X, n, V0, ctl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // E = I - V0^T V0;  M = I + E/2 + (3/8) E^2;  V0' = V0 M
+    if ((e = gemm64<true, 1>(V0, n, V0, n, Em, n, nullptr, n, n, n, ctl, st)) != cudaSuccess) return e;
+    if ((e = gemm64<false, 2>(Em, n, Em, n, Mm, n, Em, n, n, n, ctl, st)) != cudaSuccess) return e;
+    if ((e = gemm64<false, 0>(V0, n, Mm, n, V0p, n, nullptr, n, n, n, ctl, st)) != cudaSuccess) return e;
+    // X1 = X0 V0' (into U, then X);  V = Q2 V0' (into L, then V)
+    if ((e = gemm64<false, 0>(w.X, n, V0p, n, X1, n, nullptr, n, n, n, ctl, st)) != cudaSuccess) return e;
+    if ((e = gemm64<false, 0>(w.V, n, V0p, n, V1, n, nullptr, n, n, n, ctl, st)) != cudaSuccess) return e;
+    copy_if_kernel<<<64, 256, 0, st>>>(X1, n * n, w.X, ctl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    copy_if_kernel<<<64, 256, 0, st>>>(V1, n * n, w.V, ctl);
+    return cudaGetLastError();
+}
+
+}  // namespace ns

@@ -49,6 +49,9 @@ def test_dense_stage_parity(api, s, n, k):
     assert int(status.item()) == 0
     stats = api.jacobi_stats(d, s, n, ws, sketched=True)
     assert stats[3] in (8, 16), "the cluster-ring Jacobi should run for n <= 256"
+    if n >= 64:   # the FP32 linear phase ran, and the FP64 iteration only finished it
+        assert stats[4] >= 1 and stats[5] > 0, stats
+        assert stats[0] <= 3, stats
     Vk_or, sk_or, V_or, sig_or, _, st = O.solve_sketched(SA, k)
     assert st == 0
     _, V, sigma = api.unpack_save(sv, s, n)
@@ -130,3 +133,62 @@ def test_dense_stage_near_repeated_column(api):
     s1 = sig_or.max()
     np.testing.assert_allclose(np.sort(sigma.cpu().numpy()), np.sort(sig_or), rtol=0, atol=1e-12 * s1)
     assert sine(Vk_or, Vk.cpu().numpy()) < 1e-8
+
+
+def test_dense_stage_fp32_phase_guard(api):
+    # 100 columns graded over 1 .. 1e-8 take part in the FP32 phase; 28 more,
+    # graded from 1e-20 down to 1e-60 (not null: sigma of high relative accuracy),
+    # are left out of it (below 2^-30 of the largest norm).  Every singular
+    # value must keep one-sided Jacobi's relative accuracy.
+    rng = np.random.default_rng(19)
+    s, n, k = 512, 128, 2
+    Q = workloads.orthonormal(rng, s, n)
+    V = workloads.orthonormal(rng, n, n)
+    SA = workloads.from_svd(Q, np.logspace(0, -3, n), V)
+    D = np.concatenate([np.logspace(0, -8, 100), np.logspace(-20, -60, 28)])
+    SAs = np.asfortranarray(SA * D[None, :])
+    d = api.desc(api.NS_SRHT, s=s, seed=0)
+    ws = api.workspace(d, s, n, k, "cuda")
+    Vk, sk, sv, status = api.ns_solve_sketched(d, api.colmajor(SAs, device="cuda"), k, save=True, ws=ws)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    stats = api.jacobi_stats(d, s, n, ws, sketched=True)
+    assert stats[4] >= 1, stats   # the phase ran on the 100 leading columns
+    Vk_or, sk_or, _, sig_or, _, st = O.solve_sketched(SAs, k)
+    assert st == 0
+    _, V, sigma = api.unpack_save(sv, s, n)
+    V = V.cpu().numpy()
+    assert np.linalg.norm(V.T @ V - np.eye(n)) < 1e-13 * n
+    np.testing.assert_allclose(np.sort(sigma.cpu().numpy()), np.sort(sig_or), rtol=1e-8, atol=0)
+    np.testing.assert_allclose(sk.cpu().numpy(), sk_or, rtol=1e-8, atol=0)
+
+
+def test_dense_stage_benchmark_spectrum(api):
+    # the benchmark's dense problem (sigma log-spaced 1 .. 1e-6 and a 4-dimensional
+    # exact null space, n = 256, s = 1024), which runs the FP32 phase: it must
+    # not cost accuracy against the oracle (relative 1e-9 down to 1e-6 sigma_1)
+    rng = np.random.default_rng(23)
+    s, n, k = 1024, 256, 4
+    Q = workloads.orthonormal(rng, s, n)
+    Vt = workloads.orthonormal(rng, n, n)
+    sig = np.concatenate([np.logspace(0, -6, n - k), np.zeros(k)])
+    SA = np.asfortranarray(workloads.from_svd(Q, sig, Vt))
+    d = api.desc(api.NS_SRHT, s=s, seed=0)
+    ws = api.workspace(d, s, n, k, "cuda")
+    Vk, sk, sv, status = api.ns_solve_sketched(d, api.colmajor(SA, device="cuda"), k, save=True, ws=ws)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    stats = api.jacobi_stats(d, s, n, ws, sketched=True)
+    print("benchmark spectrum: FP64 sweeps %d rotations %d checks %d; FP32 sweeps %d rotations %d" %
+          (stats[0], stats[1], stats[2], stats[4], stats[5]))
+    Vk_or, sk_or, _, sig_or, _, st = O.solve_sketched(SA, k)
+    _, V, sigma = api.unpack_save(sv, s, n)
+    V = V.cpu().numpy()
+    assert np.linalg.norm(V.T @ V - np.eye(n)) < 1e-13 * n
+    ref = np.sort(sig_or)[::-1]
+    got = np.sort(sigma.cpu().numpy())[::-1]
+    assert np.max(np.abs(got - ref)) <= 1e-12 * ref[0]
+    big = ref > 1e-6 * ref[0] * 0.999
+    assert np.max(np.abs(got[big] - ref[big]) / ref[big]) <= 1e-9
+    assert sine(Vk_or, Vk.cpu().numpy()) < 1e-8
+    assert sine(Vt[:, -k:], Vk.cpu().numpy()) < 1e-8

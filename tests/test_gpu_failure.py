@@ -125,7 +125,9 @@ def test_other_entry_points_ignore_workspace_contents(api):
 
     def run(nan):
         out = list(api.ns_solve_sketched(d, SA, k, save=True, ws=_poison(ws, nan)))
-        out += list(api.ns_solve_eps(d, A, 0.5, save=True, ws=_poison(ws, nan)))
+        Ve, se, ke, sve, ste = api.ns_solve_eps(d, A, 0.5, save=True, ws=_poison(ws, nan))
+        kk = int(ke.item())   # columns past k of Ve (entries past k of se) are not written
+        out += [Ve[:, :kk], se[:kk], ke, sve, ste]
         out.append(api.ns_backward(d, m, n, k, sv, Vk, dV, ws=_poison(ws, nan)))
         return out
     a, b = _twice(run)
