@@ -12,7 +12,13 @@
 //      Y, identity in W): their relative accuracy is not touched, see below.
 //   2. One-sided Jacobi sweeps on Y in FP32, the rotations accumulated in W
 //      (FP32, from I), with the rotation threshold |y_a . y_b| > tau |y_a||y_b|,
-//      tau = 2^-17, until a sweep rotates nothing or 8 sweeps.
+//      tau = 2^-17, until a sweep rotates nothing or 8 sweeps.  W is held
+//      graded, W~[i, j] = W[i, j] d_i / d_j with d the column norms of X0 (a
+//      rotation (c, s) of columns a, b then uses s d_b/d_a and s d_a/d_b, see
+//      j32_pair): one-sided Jacobi keeps W[i, j] ~ d_j/d_i between columns of
+//      very different size, so W~ is O(1) and its FP32 rounding is relative to
+//      the column it lands in (plain FP32 W would carry an absolute ~1e-7 that
+//      X0 W spreads from the largest columns over the smallest).
 //   3. V0 = W made orthogonal in FP64: E = I - W^T W (about 1e-6), and
 //      V0 = W (I + E/2 + 3 E^2 / 8), the series of (W^T W)^(-1/2) to second
 //      order (the remainder is of order E^3).
@@ -29,12 +35,11 @@
 // its next blocks from its neighbours' shared memory (distributed shared
 // memory loads, one cluster barrier per exchange, two slot parities).
 //
-// Accuracy.  Rounding in step 4 puts an absolute error of about u |X0| into the
-// columns of X1.  V0 is the product of FP32 rotations: an entry V0[i, j] that
-// couples columns of norms d_i >> d_j is ~ d_j/d_i (one-sided Jacobi angles are
-// small between columns of very different size), up to the FP32 rounding of W
-// (absolute ~1e-7), so column j of X1 gains at most ~u (1 + 1e-7 d_max/d_j)
-// relative error; with d_j >= 2^-30 d_max that is below 1e3 u.  Columns below
+// Accuracy.  W~ carries FP32 rounding relative to its O(1) entries, so
+// W[i, j] is off by ~2^-24 d_j/d_i and column j of X0 W by ~2^-24 sqrt(n) d_j:
+// the columns of X1 are orthogonal to ~1e-6 relative to their own sizes, and
+// the FP64 corrections of step 3 (E[a, b] ~ 2^-24 d_b/d_a) keep that grading.
+// Rounding in the FP64 products adds ~n u d_j to column j.  Columns below
 // 2^-30 d_max keep their X0 column unchanged.  The FP64 iteration is then the
 // usual one and fixes the final accuracy.
 #include <cmath>
@@ -64,9 +69,10 @@ __device__ __forceinline__ float *j32_slot(float *base, int idx) { return base +
 // player of tournament position `pos` at step `step` (16 players, player 0 fixed)
 __device__ __forceinline__ int j32_rr(int pos, int step) { return pos == 0 ? 0 : 1 + (pos - 1 + step) % 15; }
 
-// One pair (columns a, b: pointers to their y rows; w follows at +kJ32Rows),
-// one warp; returns 1 (in every lane) if the pair was rotated.
-__device__ __forceinline__ unsigned int j32_pair(float *a, float *b, float tau2) {
+// One pair (columns a, b: pointers to their y rows; w~ follows at +kJ32Rows;
+// da, db their scales d), one warp; returns 1 (in every lane) if the pair was
+// rotated.
+__device__ __forceinline__ unsigned int j32_pair(float *a, float *b, float da, float db, float tau2) {
     const int lane = threadIdx.x & 31;
     // lane l holds rows 4l..4l+3 and 128+4l..128+4l+3: each float4 access of the
     // warp covers 512 contiguous bytes (no bank conflicts)
@@ -91,9 +97,14 @@ __device__ __forceinline__ unsigned int j32_pair(float *a, float *b, float tau2)
     // the rotation of the FP64 kernel: zeta = (beta - alpha) / (2 gamma),
     // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t;
     // a <- c a - s b, b <- s a + c b
-    const float z = (be - al) / (2.0f * ga), az = fabsf(z);
-    const float t = (az > 1e18f) ? 0.5f / z : copysignf(1.0f / (az + sqrtf(fmaf(z, z, 1.0f))), z);
+    // (fast division and square root: the angle needs modest accuracy only; the
+    // applied (c, s) satisfy c^2 + s^2 = 1 to FP32 rounding whatever t is)
+    const float z = __fdividef(be - al, 2.0f * ga), az = fabsf(z);
+    const float w1 = fmaf(z, z, 1.0f);
+    const float t = (az > 1e18f) ? __fdividef(0.5f, z) : copysignf(__fdividef(1.0f, az + w1 * rsqrtf(w1)), z);
     const float c = rsqrtf(fmaf(t, t, 1.0f)), s = c * t;
+    // graded W~: w~_a <- c w~_a - (s d_b/d_a) w~_b,  w~_b <- (s d_a/d_b) w~_a + c w~_b
+    const float sab = s * __fdividef(db, da), sba = s * __fdividef(da, db);
     float4 na0, na1, nb0, nb1;
     na0.x = c * a0.x - s * b0.x; nb0.x = s * a0.x + c * b0.x;
     na0.y = c * a0.y - s * b0.y; nb0.y = s * a0.y + c * b0.y;
@@ -110,14 +121,14 @@ __device__ __forceinline__ unsigned int j32_pair(float *a, float *b, float tau2)
     float *aw = a + kJ32Rows, *bw = b + kJ32Rows;
     const float4 p0 = *(const float4 *)(aw + 4 * lane), p1 = *(const float4 *)(aw + 128 + 4 * lane);
     const float4 q0 = *(const float4 *)(bw + 4 * lane), q1 = *(const float4 *)(bw + 128 + 4 * lane);
-    na0.x = c * p0.x - s * q0.x; nb0.x = s * p0.x + c * q0.x;
-    na0.y = c * p0.y - s * q0.y; nb0.y = s * p0.y + c * q0.y;
-    na0.z = c * p0.z - s * q0.z; nb0.z = s * p0.z + c * q0.z;
-    na0.w = c * p0.w - s * q0.w; nb0.w = s * p0.w + c * q0.w;
-    na1.x = c * p1.x - s * q1.x; nb1.x = s * p1.x + c * q1.x;
-    na1.y = c * p1.y - s * q1.y; nb1.y = s * p1.y + c * q1.y;
-    na1.z = c * p1.z - s * q1.z; nb1.z = s * p1.z + c * q1.z;
-    na1.w = c * p1.w - s * q1.w; nb1.w = s * p1.w + c * q1.w;
+    na0.x = c * p0.x - sab * q0.x; nb0.x = sba * p0.x + c * q0.x;
+    na0.y = c * p0.y - sab * q0.y; nb0.y = sba * p0.y + c * q0.y;
+    na0.z = c * p0.z - sab * q0.z; nb0.z = sba * p0.z + c * q0.z;
+    na0.w = c * p0.w - sab * q0.w; nb0.w = sba * p0.w + c * q0.w;
+    na1.x = c * p1.x - sab * q1.x; nb1.x = sba * p1.x + c * q1.x;
+    na1.y = c * p1.y - sab * q1.y; nb1.y = sba * p1.y + c * q1.y;
+    na1.z = c * p1.z - sab * q1.z; nb1.z = sba * p1.z + c * q1.z;
+    na1.w = c * p1.w - sab * q1.w; nb1.w = sba * p1.w + c * q1.w;
     *(float4 *)(aw + 4 * lane) = na0;
     *(float4 *)(aw + 128 + 4 * lane) = na1;
     *(float4 *)(bw + 4 * lane) = nb0;
@@ -137,6 +148,9 @@ __device__ __forceinline__ float4 ld_peer_f4(uint32_t addr) {
 __device__ __forceinline__ void st_peer_u32(uint32_t addr, uint32_t v) {
     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
+__device__ __forceinline__ void st_peer_f32(uint32_t addr, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
 __device__ __forceinline__ void st_peer_f64(uint32_t addr, double v) {
     asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
 }
@@ -152,6 +166,8 @@ __global__ void __cluster_dims__(kJ32Cta, 1, 1) __launch_bounds__(kJ32Threads, 1
     __shared__ unsigned int s_cnt[kJ32Cta];
     __shared__ unsigned int s_rot[kJ32Cta];
     __shared__ unsigned int s_local;
+    __shared__ float s_d[4][kJ32B];  // column scales d of the four block slots (moved with the blocks)
+    __shared__ float d_all[kJ32N];   // column scales d of every column (rows of W)
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int c = (int)cluster_rank();
     const int btop = c, bbot = kJ32Blocks - 1 - c;  // blocks held at the start of every sweep
@@ -179,6 +195,20 @@ __global__ void __cluster_dims__(kJ32Cta, 1, 1) __launch_bounds__(kJ32Threads, 1
     double gmax = 0.0;
     for (int r = 0; r < kJ32Cta; ++r) gmax = fmax(gmax, s_max[r]);
     const double keep = gmax * kJ32Keep;
+    // scale: the largest column norm lands in [0.5, 1)
+    int e2 = 0;
+    frexp(sqrt(gmax), &e2);
+    const double sc = ldexp(1.0, -e2);
+    // column scales d (1 for the columns left out) into this CTA's two slots and
+    // into every CTA's d_all; the kept count into every CTA's s_cnt
+    if (tid < 2 * kJ32B) {
+        const int sl = tid / kJ32B, i = tid % kJ32B;
+        const int64_t j = (int64_t)(sl == 0 ? btop : bbot) * kJ32B + i;
+        const double nr = s_nrm[tid];
+        const float dv = (nr > 0.0 && nr >= keep && gmax < 1e300) ? (float)(sqrt(nr) * sc) : 1.0f;
+        s_d[sl][i] = dv;
+        for (int r = 0; r < kJ32Cta; ++r) st_peer_f32(peer_addr(shared_addr(&d_all[j]), r), dv);
+    }
     if (tid == 0) {
         unsigned int cnt = 0;
         for (int q = 0; q < 2 * kJ32B; ++q) cnt += (s_nrm[q] > 0.0 && s_nrm[q] >= keep) ? 1u : 0u;
@@ -192,11 +222,7 @@ __global__ void __cluster_dims__(kJ32Cta, 1, 1) __launch_bounds__(kJ32Threads, 1
         if (c == 0 && tid == 0) ctl[0] = 0u;
         return;  // no CTA touched a peer after the last cluster barrier
     }
-    // scale: the largest column norm lands in [0.5, 1)
-    int e2 = 0;
-    frexp(sqrt(gmax), &e2);
-    const double sc = ldexp(1.0, -e2);
-    // ---- Y and W = I into the parity-0 slots
+    // ---- Y and W~ = I into the parity-0 slots
     for (int sl = 0; sl < 2; ++sl) {
         float *S = j32_slot(j32_smem, sl);
         const int blk = sl == 0 ? btop : bbot;
@@ -222,15 +248,18 @@ __global__ void __cluster_dims__(kJ32Cta, 1, 1) __launch_bounds__(kJ32Threads, 1
             float *T = j32_slot(j32_smem, 2 * par), *B = j32_slot(j32_smem, 2 * par + 1);
             if (step == 0) {  // pairs inside each block: warps 0-7 the top block, 8-15 the bottom
                 float *M = w < 8 ? T : B;
+                const float *dM = s_d[w < 8 ? 2 * par : 2 * par + 1];
                 const int q = w & 7;
                 for (int r = 0; r < kJ32B - 1; ++r) {
                     const int pa = j32_rr(q, r), pb = j32_rr(kJ32B - 1 - q, r);
-                    mine += j32_pair(M + pa * kJ32Col, M + pb * kJ32Col, tau2);
+                    mine += j32_pair(M + pa * kJ32Col, M + pb * kJ32Col, dM[pa], dM[pb], tau2);
                     __syncthreads();
                 }
             }
+            const float *dT0 = s_d[2 * par], *dB0 = s_d[2 * par + 1];
             for (int r = 0; r < kJ32B; ++r) {  // the 256 pairs between the two blocks
-                mine += j32_pair(T + w * kJ32Col, B + ((w + r) & (kJ32B - 1)) * kJ32Col, tau2);
+                const int bq = (w + r) & (kJ32B - 1);
+                mine += j32_pair(T + w * kJ32Col, B + bq * kJ32Col, dT0[w], dB0[bq], tau2);
                 __syncthreads();
             }
             if (step == kJ32Steps - 1) {  // publish this CTA's rotation count of the sweep
@@ -254,6 +283,14 @@ __global__ void __cluster_dims__(kJ32Cta, 1, 1) __launch_bounds__(kJ32Threads, 1
             const int sb_slot = c == kJ32Cta - 1 ? 2 * par : 2 * par + 1;
             const uint32_t srcT = peer_addr(shared_addr(j32_slot(j32_smem, st_slot)), (uint32_t)st_rank);
             const uint32_t srcB = peer_addr(shared_addr(j32_slot(j32_smem, sb_slot)), (uint32_t)sb_rank);
+            if (tid < 2 * kJ32B) {  // the blocks' column scales travel with them
+                const int h = tid / kJ32B, i = tid % kJ32B;
+                const uint32_t src = peer_addr(shared_addr(&s_d[h ? sb_slot : st_slot][i]),
+                                               (uint32_t)(h ? sb_rank : st_rank));
+                float v;
+                asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(src) : "memory");
+                s_d[2 * np + h][i] = v;
+            }
 #pragma unroll 4
             for (int v = tid; v < kJ32Slot / 4; v += kJ32Threads) {
                 const float4 x = ld_peer_f4(srcT + 16u * (uint32_t)v);
@@ -270,14 +307,18 @@ __global__ void __cluster_dims__(kJ32Cta, 1, 1) __launch_bounds__(kJ32Threads, 1
         rot_total += tot;
         if (tot == 0u) break;
     }
-    // ---- blocks are back where they started: W columns -> V0 (FP64, exact)
+    // ---- blocks are back where they started: W = D^-1 W~ D -> V0 (FP64); the
+    // scale of row r (column r of X0) is read from the slot that holds it
     for (int sl = 0; sl < 2; ++sl) {
         const float *S = j32_slot(j32_smem, 2 * par + sl);
         const int blk = sl == 0 ? btop : bbot;
         for (int idx = tid; idx < kJ32B * kJ32Rows; idx += kJ32Threads) {
             const int i = idx / kJ32Rows, r = idx % kJ32Rows;
             const int64_t j = (int64_t)blk * kJ32B + i;
-            if (j < n && r < n) V0[r + j * n] = (double)S[i * kJ32Col + kJ32Rows + r];
+            if (j < n && r < n) {
+                const double wv = (double)S[i * kJ32Col + kJ32Rows + r];
+                V0[r + j * n] = wv == 0.0 ? 0.0 : wv * ((double)s_d[2 * par + sl][i] / (double)d_all[r]);
+            }
         }
     }
     if (c == 0 && tid == 0) {

@@ -1,17 +1,32 @@
 """GPU Gaussian sketch on the tensor cores (3-term BF16 split, FP32 accumulation)
 against the oracle's FP64 Gaussian sketch, entry by entry.
 
-Error model of one entry SA[r, c] = sum_j g_rj a_jc / sqrt(s).  Each operand
-x is split as hi = bf16(x) (|x - hi| <= 2^-8 |x|) and lo = bf16(x - hi)
-(|x - hi - lo| <= 2^-16 |x|); the three kept products hi hi + hi lo + lo hi
-miss lo lo and the two split residuals, at most 3 * 2^-16 |g a| per term,
-with signs that vary from term to term.  G is generated in FP32 (the oracle
-evaluates Box-Muller in FP64), a relative ~2^-20 per entry, and the split-K
-partials accumulate in FP32 (2^-24 per addition of a running sum).  The terms'
-errors add like a random walk, so the error of the entry is a small multiple
-of 2^-17 * mag with mag = sqrt(sum_j (g_rj a_jc)^2) / sqrt(s), the size of its
-terms (computed by the oracle).  The bound asserted per entry is
-2^-12 * mag: about 6 standard deviations over the entries checked.
+Error model of one entry SA[r, c] = sum_j T_j / sqrt(s), T_j = g_rj a_jc,
+with mag = sqrt(sum_j T_j^2) / sqrt(s) the size of its terms (computed by the
+oracle):
+
+* Split.  Each operand x is split as hi = bf16(x) (|x - hi| <= 2^-8 |x|) and
+  lo = bf16(x - hi) (|x - hi - lo| <= 2^-16 |x|); the three kept products
+  hi hi + hi lo + lo hi miss lo lo and the two split residuals, at most
+  3 * 2^-16 |T_j| per term, with signs that vary from term to term, so their
+  sum is a random walk: a few times 2^-17 mag.  (G itself is generated in FP32,
+  a relative ~2^-20 per entry: smaller.)
+* Accumulation.  Each CTA accumulates one split of K = kper rows of A in FP32
+  in tensor memory, 16 rows per step and three products per step.  If every
+  such addition loses up to one unit in the last place of the running sum
+  S_k (2^-23 |S_k|, alignment without rounding), the losses add up to
+  3 * 2^-23 sum_k |S_k|; S_k is a random walk of step 4 sigma_T
+  (sigma_T = mag sqrt(s / m) / sqrt(s) per term), so the expected sum is
+  sqrt(2/pi) 4 (2/3) (kper/16)^(3/2) sigma_T.  The nsplit splits are summed
+  in FP64.  This term grows like m at fixed s: measured on the GPU, the median
+  of |err| / mag went 5e-6, 1.8e-5, 6.8e-5 for m = 2^14, 2^16, 2^18 at s = 2048,
+  n = 512, which is the scaling of this model (a random-walk rounding error
+  would grow like sqrt(m)).
+
+The bound asserted per entry is
+  mag * (2^-13 + 2 * 3 * 2^-23 * E(kper) * sqrt(nsplit) / sqrt(m)),
+E(K) = sqrt(2/pi) 4 (2/3) (K/16)^(3/2): the split part at ~8 standard
+deviations and twice the expected accumulation loss.
 """
 import numpy as np
 import pytest
@@ -39,15 +54,32 @@ def gauss_gpu(api, A32, s, seed):
     return api.ns_sketch(d, api.colmajor(A32, device="cuda")).cpu().numpy()
 
 
-ENTRY_TOL = 2.0 ** -12
+def split_geometry(m, s):
+    """(kper, nsplit) of the tensor-core sketch: one CTA per (128-row tile of
+    SA, split of the rows of A), about one CTA per SM, splits in 32-row steps."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mtiles = -(-s // 128)
+    nsplit = max(sms // mtiles, 1)
+    kchunks = -(-m // 32)
+    nsplit = min(nsplit, kchunks)
+    kper = -(-kchunks // nsplit) * 32
+    return kper, -(-m // kper)
+
+
+def entry_tol(m, s):
+    kper, nsplit = split_geometry(m, s)
+    e_sum = np.sqrt(2 / np.pi) * 4 * (2 / 3) * (kper / 16) ** 1.5
+    return 2.0 ** -13 + 2 * 3 * 2.0 ** -23 * e_sum * np.sqrt(nsplit) / np.sqrt(m)
 
 
 def check_rows(SA, A64, s, seed, rows):
+    m = A64.shape[0]
     ref, mag = O.gaussian_rows(seed, s, A64, rows)
     err = np.abs(SA[rows] - ref)
+    tol = entry_tol(m, s)
     worst = float(np.max(err / np.maximum(mag, 1e-300)))
-    assert np.all(err <= ENTRY_TOL * mag + 1e-300), worst
-    return worst
+    assert np.all(err <= tol * mag + 1e-300), (worst, tol)
+    return worst, tol
 
 
 @pytest.mark.parametrize("m,n,s", [(1000, 16, 128), (5000, 37, 200), (3001, 300, 256), (20000, 512, 128),
@@ -69,8 +101,8 @@ def test_gaussian_sketch_parity_precision_geometry(api):
     A32 = rng.standard_normal((m, n)).astype(np.float32)
     SA = gauss_gpu(api, A32, s, 11)
     rows = sorted(set([128 * t + int(rng.integers(0, 128)) for t in range(16)] + [0, 1, s - 1]))
-    worst = check_rows(SA, A32.astype(np.float64), s, 11, rows)
-    print("gaussian s=2048 n=512 m=2^18: worst |err| / mag = %.3e (bound %.3e)" % (worst, ENTRY_TOL))
+    worst, tol = check_rows(SA, A32.astype(np.float64), s, 11, rows)
+    print("gaussian s=2048 n=512 m=2^18: worst |err| / mag = %.3e (bound %.3e)" % (worst, tol))
 
 
 def test_gaussian_is_deterministic_and_seeded(api):
