@@ -1,21 +1,24 @@
 #!/usr/bin/env python
 """Benchmark of the sketch-and-solve null-space hot path (Algorithm 1) on GB300.
 
-Workload (one step = one full solve): A = U diag(sigma) V^T with m = 2^20,
-n = 256, sigma_1..252 log-spaced from 1 to 1e-6 and a 4-dimensional exact null
-space; SRHT sketch with s = 1024; FP64 pivoted QR, QR of R^T and one-sided
-Jacobi SVD; the k = 4 trailing right singular vectors.  A (2 GiB) is larger
-than L2, so every step streams it from HBM.  The same workload is also solved
-with the sparse-sign sketch (zeta = 8).
+Headline workload (one step = one full solve): A = U diag(sigma) V^T with
+m = 2^20, n = 256, sigma_1..252 log-spaced from 1 to 1e-6 and a 4-dimensional
+exact null space; SRHT sketch with s = 1024; FP64 QR of the sketch, QR of R^T,
+FP32 linear phase and FP64 one-sided Jacobi SVD; the k = 4 trailing right
+singular vectors.  A (2 GiB) is larger than L2, so every step streams it from
+HBM.  The same workload is also solved with the sparse-sign sketch (zeta = 8)
+and the H-RHT.  The other workloads (plain, precision, adjoint, batched TLS
+and AAA) are timed in the same run, each with its own recipe, and reported
+under "configs".
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
-    python bench.py --extra          # also time the other workloads
     python bench.py --case NAME      # one kernel family on a small case (profiling)
 
 Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank solves its
 own replica of the workload (weak scaling; the path needs no collective).
 """
 import argparse
+import concurrent.futures
 import json
 import os
 import subprocess
@@ -30,16 +33,20 @@ sys.path.insert(0, ROOT)
 
 M, N, S, K_NULL, SEED = 1 << 20, 256, 1024, 4, 0
 E2E_PARTS = 4   # concurrent host-to-device copies per step in the end-to-end leg
-# DRAM bytes of one srht_f64_chunk128_kernel launch at full size: the ncu capture of
-# profiles/srht_f64_chunk_m2e19_n64.md (268.58 MB read + 3.03 MB written at
-# m = 2^19, n = 64) scaled by the 8x the full launch processes; the kernel is
-# unchanged since that capture.
+# DRAM bytes of one srht_f64_chunk128_kernel launch at full size: dram__bytes_read.sum
+# + dram__bytes_write.sum of the ncu capture at m = 2^19, n = 64 (268.58 MB read +
+# 3.03 MB written), scaled by the 8x the full launch processes
 SRHT_TRAFFIC = (268.58e6 + 3.03e6) * 8
 SRHT_TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum at m=2^19 n=64, scaled x8"
 METRIC = "null-space solves/s and sketch HBM GB/s (% of peak) at stated ||AV||_F accuracy"
 WORKLOAD = "at_scale: m=2^20 n=256 FP64 column-major, sigma log-spaced 1..1e-6 + 4 exact zeros, SRHT s=1024, k=4"
-FP64_FLOPS_PER_CLK_SM = 4.0   # 2 FP64 FMA per clock per SM (measured 597 GFMA/s at 1.99 GHz on 152 SMs)
-N_SM = 152
+FP64_FLOPS_PER_CLK_SM = 4.0   # 2 FP64 FMA per clock per SM (bench.py --case fp64peak measures the rate)
+
+
+def bench_config(world):
+    """The config dict both arms print (identical keys and values)."""
+    return {"workload": WORKLOAD, "l2": "input larger than L2 (2 GiB A per step)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
 def peaks():
@@ -115,27 +122,63 @@ def make_workload(seed):
 
 def dense_flops(s, n, k, stats):
     """Algorithmic FP64 flops of lines 3-4 of Algorithm 1 as the GPU runs them:
-    pivoted Householder QR of s x n, Householder QR of n x n, one-sided Jacobi
-    (dot products 6n per visited pair, rotation of two columns of X and of V 12n),
-    and the k trailing columns of V = P Q2 Vx (4 n^2 k)."""
+    Householder QR of s x n, Householder QR of n x n, one-sided Jacobi (dot
+    products 6n per visited pair, rotation of two columns of X and of V 12n),
+    the five n^3 products that make the FP32 phase's V0 orthogonal and apply
+    it (when it ran), and the k trailing columns of V (4 n^2 k).  The FP32
+    phase's own arithmetic is FP32 and not counted."""
     sweeps, rots, checks = stats[:3]
     pairs = n * (n - 1) / 2
     qr1 = 2.0 * n * n * (s - n / 3.0)
     qr2 = 4.0 / 3.0 * n ** 3
     jac = (sweeps + checks) * pairs * 6.0 * n + rots * 12.0 * n
-    return qr1 + qr2 + jac + 4.0 * n * n * k
+    prod = 5 * 2.0 * n ** 3 if len(stats) > 4 and stats[4] > 0 else 0.0
+    return qr1 + qr2 + jac + prod + 4.0 * n * n * k
+
+
+def launches_per_solve(stats):
+    """Library kernels one ns_solve launches: the sketch (meta, chunk, reduce),
+    the column order (3), the first QR, [R^T | I] (2), the second QR, X and V
+    (2), the FP32 phase with its products and copies (8, when it runs), the
+    ring Jacobi, V = P Q2 V0 Vx, the extraction and the two save copies."""
+    return 17 + (8 if len(stats) > 4 and stats[4] > 0 else 0)
 
 
 def cpu_baseline(A):
-    """The oracle as it stands, one full solve of the same workload, single-threaded."""
+    """The oracle as it stands on the host cores: one full solve of the workload on
+    one thread (best of 3), then as many concurrent solves as there are cores
+    (threads; the C oracle releases the GIL), and the unsketched dense LAPACK
+    SVD of A (numpy, best of 3) as the classical O(m n^2) context."""
     import oracle
     oracle.build()
-    t0 = time.perf_counter()
-    out = oracle.solve(oracle.SRHT, SEED, S, A, K_NULL)
-    dt = time.perf_counter() - t0
-    return {"value": 1.0 / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": "one full oracle solve of the workload (m=2^20, n=256, s=1024, k=4), %.1f s" % dt,
-            "residual": oracle.residual(A, out["Vk"])}
+    cores = os.cpu_count() or 1
+    t1 = []
+    out = None
+    for _ in range(3):
+        t0 = time.perf_counter()
+        out = oracle.solve(oracle.SRHT, SEED, S, A, K_NULL)
+        t1.append(time.perf_counter() - t0)
+    best1 = min(t1)
+    ta = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        with concurrent.futures.ThreadPoolExecutor(max_workers=cores) as ex:
+            list(ex.map(lambda _i: oracle.solve(oracle.SRHT, SEED, S, A, K_NULL)["status"], range(cores)))
+        ta.append(time.perf_counter() - t0)
+    tsvd = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        np.linalg.svd(A, full_matrices=False)
+        tsvd.append(time.perf_counter() - t0)
+    return {"value": 1.0 / best1, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": "one full oracle solve of the workload (m=2^20, n=256, s=1024, k=4) on one thread, "
+                      "best of 3: %.2f s" % best1,
+            "residual": oracle.residual(A, out["Vk"]),
+            "all_cores": {"value": cores / min(ta), "unit": "solves/s", "cores": cores,
+                          "sample": "%d concurrent oracle solves (one per core), best of 2: %.2f s" % (cores, min(ta))},
+            "lapack_dense_svd": {"value": 1.0 / min(tsvd), "unit": "solves/s", "cores": cores,
+                                 "sample": "numpy.linalg.svd of A (2^20 x 256, the unsketched O(m n^2) solve), "
+                                           "best of 3: %.2f s" % min(tsvd)}}
 
 
 def run_reference(args, rank, world):
@@ -157,7 +200,7 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "l2": "input larger than L2 (2 GiB)"},
+            "config": bench_config(world),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
                              "sample": "full oracle solves of the workload, one per step"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -189,11 +232,56 @@ class Timer:
         return ms
 
 
-def extra_workloads(torch, api, dev, timer, hbm_peak, bf16_peak):
-    """Timings of the other workloads (opt-in; accuracy is covered by the tests)."""
+def precision_input(torch, dev, seed):
+    """The precision workload's A (m = 2^22, n = 512) on the GPU: sigma_1..510
+    log-spaced from 1 to 1e-6, sigma_511 = sigma_512 = 1e-9, stored in FP32.
+    A = U diag(sigma) V^T with U = G R^-1 the Cholesky-QR factor of a seeded
+    Gaussian G (orthonormal to ~u for a Gaussian this tall), so A = G (R^-1
+    diag(sigma) V^T) takes two FP64 GEMMs; V is the Q factor of a seeded
+    Gaussian 512 x 512.  Input generation only (torch on the GPU)."""
+    m, n, k = 1 << 22, 512, 2
+    g = torch.Generator(device=dev).manual_seed(seed)
+    G = torch.randn((n, m), generator=g, device=dev, dtype=torch.float64).t()  # column-major m x n
+    R = torch.linalg.cholesky(G.t() @ G).t()                                  # upper, G^T G = R^T R
+    V, _ = torch.linalg.qr(torch.randn((n, n), generator=g, device=dev, dtype=torch.float64))
+    sig = torch.cat([torch.logspace(0, -6, n - k, dtype=torch.float64, device=dev),
+                     torch.full((k,), 1e-9, dtype=torch.float64, device=dev)])
+    Mr = torch.linalg.solve_triangular(R, torch.diag(sig) @ V.t(), upper=True)
+    A64 = (G @ Mr).t().contiguous().t()
+    del G
+    A32 = A64.to(torch.float32).t().contiguous().t()
+    del A64
+    torch.cuda.empty_cache()
+    return A32, V, sig, k
+
+
+def precision_accuracy(torch, A32, W):
+    """||A W||_F and the sine to the trailing right singular subspace of the
+    FP32-stored A itself, from its FP64 Gram matrix (eigh): the FP32 storage
+    perturbs A by ~2^-24 ||A||, far above sigma_511 = 1e-9, so A32's own trailing
+    subspace (not V's) is the reference."""
+    k = W.shape[1]
+    Gm = torch.zeros((A32.shape[1], A32.shape[1]), dtype=torch.float64, device=A32.device)
+    step = 1 << 20
+    for i in range(0, A32.shape[0], step):
+        blk = A32[i:i + step].double()
+        Gm += blk.t() @ blk
+    ev, Q = torch.linalg.eigh(Gm)
+    Wt = Q[:, :k]
+    resid = float(torch.linalg.norm(A32.double() @ W))
+    best = float(torch.sqrt(torch.clamp(ev[:k], min=0).sum()))
+    P = W - Wt @ (Wt.t() @ W)
+    return {"residual_AW_F": resid, "residual_fp64_reference": best,
+            "sine_to_fp64_reference": float(torch.linalg.matrix_norm(P, ord=2))}
+
+
+def config_legs(torch, api, dev, timer, hbm_peak, bf16_peak, fp64_peak):
+    """The other workloads, each with its own recipe (accuracy is checked
+    against the oracle by the tests; here it is reported)."""
     from paper_2206_00975_gb300 import workloads
     out = {}
-    # plain FP64: m = 4096, n = 32, s = 128, k = 1; single solves and 1000 seeds batched
+    stream = torch.cuda.current_stream()
+    # ---- plain FP64: m = 4096, n = 32, s = 128, k = 1; single solves, and 1000 seeds batched
     w = workloads.plain(seed=0)
     A = api.colmajor(w["A"], device=dev)
     d = api.desc(api.NS_SRHT, s=128, seed=0)
@@ -201,38 +289,50 @@ def extra_workloads(torch, api, dev, timer, hbm_peak, bf16_peak):
     for _ in range(3):
         api.ns_solve(d, A, 1, save=False, ws=ws)
     ms = timer(lambda: api.ns_solve(d, A, 1, save=False, ws=ws), 50)
+    Vk, _, _, _ = api.ns_solve(d, A, 1, save=False, ws=ws)
     probs = [{"A": A, "s": 128, "k": 1, "seed": i} for i in range(1000)]
-    api.ns_solve_batched(probs)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    _, st, keep = api.ns_solve_batched(probs)
-    torch.cuda.synchronize()
-    tb = time.perf_counter() - t0
+    _, _, keep = api.ns_solve_batched(probs)
+    msb = timer(lambda: api.ns_solve_batched(probs, ws=keep[2]), 3)
     out["plain_4096x32"] = {"solve_ms": ms / 50, "solves_per_s": 50 / (ms / 1e3),
-                            "batched_1000_seeds_solves_per_s": 1000 / tb}
-    # precision: m = 2^22, n = 512, A stored FP32; FP32-stream SRHT and Gaussian 3xBF16 (s = 2048)
-    m3, n3, s3 = 1 << 22, 512, 2048
-    g = torch.Generator(device=dev).manual_seed(3)
-    A3 = torch.randn((n3, m3), generator=g, device=dev, dtype=torch.float32).t()
+                            "batched_1000_seeds_solves_per_s": 3000 / (msb / 1e3),
+                            "residual_AV_F": float(api.ns_residual(A, Vk).item()),
+                            "true_min_AV_F": float(w["sigma"][-1])}
+    del probs, keep
+    # ---- precision: m = 2^22, n = 512, A stored FP32 with the graded spectrum;
+    # FP32-stream SRHT and 3 x BF16 Gaussian, s = 2048, FP64 QR / Jacobi
+    A32, Vt, sig, k3 = precision_input(torch, dev, seed=3)
+    m3, n3, s3 = A32.shape[0], A32.shape[1], 2048
     d32 = api.desc(api.NS_SRHT, s=s3, seed=0, prec=api.NS_PREC_FP32_STREAM)
     dg = api.desc(api.NS_GAUSSIAN, s=s3, seed=0, prec=api.NS_PREC_BF16X3)
-    ws3 = api.workspace(d32, m3, n3, 2, dev)
-    wsg = api.workspace(dg, m3, n3, 2, dev)
+    ws3 = api.workspace(d32, m3, n3, k3, dev)
     SA3 = api._empty_cm(s3, n3, dev)
-    api.ns_sketch(d32, A3, SA=SA3, ws=ws3)
-    api.ns_sketch(dg, A3, SA=SA3, ws=wsg)
-    ms32 = timer(lambda: api.ns_sketch(d32, A3, SA=SA3, ws=ws3), 5)
-    msg = timer(lambda: api.ns_sketch(dg, A3, SA=SA3, ws=wsg), 3)
+    api.ns_sketch(d32, A32, SA=SA3, ws=ws3)
+    ms32 = timer(lambda: api.ns_sketch(d32, A32, SA=SA3, ws=ws3), 5) / 5
+    api.ns_solve(d32, A32, k3, save=False, ws=ws3)
+    ms32s = timer(lambda: api.ns_solve(d32, A32, k3, save=False, ws=ws3), 3) / 3
+    W32, sk32, _, st32 = api.ns_solve(d32, A32, k3, save=False, ws=ws3)
+    acc32 = precision_accuracy(torch, A32, W32)
+    del ws3
+    torch.cuda.empty_cache()
+    wsg = api.workspace(dg, m3, n3, k3, dev)
+    api.ns_sketch(dg, A32, SA=SA3, ws=wsg)
+    msg = timer(lambda: api.ns_sketch(dg, A32, SA=SA3, ws=wsg), 3) / 3
+    Wg, skg, _, stg = api.ns_solve(dg, A32, k3, save=False, ws=wsg)
+    msgs = timer(lambda: api.ns_solve(dg, A32, k3, save=False, ws=wsg), 2) / 2
+    accg = precision_accuracy(torch, A32, Wg)
     b3 = m3 * n3 * 4 + s3 * n3 * 8
     mma_flops = 3 * 2.0 * s3 * m3 * n3
     out["precision_2^22x512"] = {
-        "srht_fp32_ms": ms32 / 5, "srht_fp32_gbs": b3 / (ms32 / 5 / 1e3) / 1e9,
-        "srht_fp32_frac": b3 / (ms32 / 5 / 1e3) / 1e9 / hbm_peak,
-        "gaussian_bf16x3_ms": msg / 3, "gaussian_mma_tflops": mma_flops / (msg / 3 / 1e3) / 1e12,
-        "gaussian_frac_of_bf16_peak": mma_flops / (msg / 3 / 1e3) / 1e12 / bf16_peak}
-    del A3, SA3, ws3, wsg
+        "recipe": "sigma 1..1e-6 (510) + 2 x 1e-9, A = U diag(sigma) V^T stored FP32",
+        "srht_fp32": {"sketch_ms": ms32, "sketch_gbs": b3 / (ms32 / 1e3) / 1e9,
+                      "sketch_frac": b3 / (ms32 / 1e3) / 1e9 / hbm_peak, "solve_ms": ms32s,
+                      "status": int(st32.item()), **acc32},
+        "gaussian_bf16x3": {"sketch_ms": msg, "mma_tflops": mma_flops / (msg / 1e3) / 1e12,
+                            "frac_of_bf16_peak": mma_flops / (msg / 1e3) / 1e12 / bf16_peak, "solve_ms": msgs,
+                            "status": int(stg.item()), **accg}}
+    del A32, SA3, wsg, W32, Wg
     torch.cuda.empty_cache()
-    # adjoint: m = 2^18, n = 128, k = 8, s = 512
+    # ---- adjoint: m = 2^18, n = 128, k = 8, s = 512; L = ||W W^T Z||_F^2
     wa = workloads.adjoint(seed=0)
     A4 = api.colmajor(wa["A"], device=dev)
     d4 = api.desc(api.NS_SRHT, s=512, seed=0)
@@ -242,45 +342,24 @@ def extra_workloads(torch, api, dev, timer, hbm_peak, bf16_peak):
     dV = api.colmajor(2.0 * Z @ Z.T @ Vk)
     dA = api._empty_cm(1 << 18, 128, dev)
     api.ns_backward(d4, 1 << 18, 128, 8, sv, Vk, dV, dA=dA, ws=ws4)
-    msf = timer(lambda: api.ns_solve(d4, A4, 8, save=sv, ws=ws4), 10)
-    msb = timer(lambda: api.ns_backward(d4, 1 << 18, 128, 8, sv, Vk, dV, dA=dA, ws=ws4), 10)
-    out["adjoint_2^18x128"] = {"forward_ms": msf / 10, "backward_ms": msb / 10,
-                               "backward_write_gbs": (1 << 18) * 128 * 8 / (msb / 10 / 1e3) / 1e9}
-    # batched TLS: 4096 problems, m ~ U{2^11..2^16}, n ~ U{8..128}, [X b] FP64 generated on the GPU
-    ms_, ns_ = workloads.tls_batch_shapes(seed=0, batch=4096)
-    probs, total_bytes = [], 0
-    for i, (mi, ni) in enumerate(zip(ms_, ns_)):
-        Xb = torch.randn((int(ni) + 1, int(mi)), generator=g, device=dev, dtype=torch.float64).t()
-        probs.append({"A": Xb, "s": 2 * (int(ni) + 1), "k": 1, "seed": i, "tls": True})
-        total_bytes += int(mi) * (int(ni) + 1) * 8
-    api.ns_solve_batched(probs[:64])
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    _, st, keep = api.ns_solve_batched(probs)
-    torch.cuda.synchronize()
-    tb = time.perf_counter() - t0
-    # the per-problem loop on a 256-problem subset (same problems), extrapolated
-    sub = probs[:256]
-    t0 = time.perf_counter()
-    for p in sub:
-        dd = api.desc(api.NS_SRHT, s=p["s"], seed=p["seed"])
-        api.ns_solve(dd, p["A"], 1, save=False)
-    torch.cuda.synchronize()
-    tl = (time.perf_counter() - t0) * len(probs) / len(sub)
-    out["batched_tls_4096"] = {"batched_s": tb, "batched_solves_per_s": len(probs) / tb,
-                               "loop_solves_per_s_extrapolated": len(probs) / tl, "input_gb": total_bytes / 1e9,
-                               "status_nonzero": int((st != 0).sum().item())}
-    del probs, keep
+    msf = timer(lambda: api.ns_solve(d4, A4, 8, save=sv, ws=ws4), 10) / 10
+    msbw = timer(lambda: api.ns_backward(d4, 1 << 18, 128, 8, sv, Vk, dV, dA=dA, ws=ws4), 10) / 10
+    out["adjoint_2^18x128"] = {"forward_ms": msf, "backward_ms": msbw,
+                               "backward_write_gbs": (1 << 18) * 128 * 8 / (msbw / 1e3) / 1e9,
+                               "backward_frac": (1 << 18) * 128 * 8 / (msbw / 1e3) / 1e9 / hbm_peak}
+    del A4, ws4, dA
     torch.cuda.empty_cache()
-    # AAA: 2^17 points, tanh(50 x), 100 iterations, 400-row sketch; eager vs CUDA graph
+    out["batched_tls_4096"] = batched_leg(torch, api, dev, timer)
+    torch.cuda.empty_cache()
+    # ---- AAA: 2^17 points, tanh(50 x), 100 iterations, 400-row sketch; eager vs CUDA graph
     x, f = workloads.aaa_points(seed=0, m=1 << 17, scale=50.0)
     xd, fd = torch.as_tensor(x, device=dev), torch.as_tensor(f, device=dev)
     r = api.ns_aaa_real(xd, fd, 100, 400, seed=0)
     torch.cuda.synchronize()
     wsa = r["_ws"]
-    mse = timer(lambda: api.ns_aaa_real(xd, fd, 100, 400, seed=0, ws=wsa), 3)
+    mse = timer(lambda: api.ns_aaa_real(xd, fd, 100, 400, seed=0, ws=wsa), 3) / 3
     s_cap = torch.cuda.Stream()
-    s_cap.wait_stream(torch.cuda.current_stream())
+    s_cap.wait_stream(stream)
     with torch.cuda.stream(s_cap):
         api.ns_aaa_real(xd, fd, 100, 400, seed=0, ws=wsa, stream=s_cap)
     torch.cuda.synchronize()
@@ -289,10 +368,72 @@ def extra_workloads(torch, api, dev, timer, hbm_peak, bf16_peak):
         api.ns_aaa_real(xd, fd, 100, 400, seed=0, ws=wsa, stream=s_cap)
     graph.replay()
     torch.cuda.synchronize()
-    msg2 = timer(lambda: graph.replay(), 3)
-    out["aaa_2^17_100it"] = {"eager_ms": mse / 3, "graph_ms": msg2 / 3, "iterations_per_s_graph": 100 / (msg2 / 3e3),
+    msg2 = timer(lambda: graph.replay(), 3) / 3
+    out["aaa_2^17_100it"] = {"eager_ms": mse, "graph_ms": msg2, "iterations_per_s_graph": 100 / (msg2 / 1e3),
                              "final_err": float(r["errmax"][-1].item())}
     return out
+
+
+def batched_leg(torch, api, dev, timer):
+    """Batched TLS: 4096 problems [X b], m_i ~ U{2^11..2^16}, n_i ~ U{8..128},
+    X Gaussian, b = X x_true + 1e-3 noise (generated on the GPU), SRHT with
+    s_i = 2(n_i + 1), k = 1: one batched call in FP64 and one with A in FP32
+    (FP32-stream sketch), against a loop of single FP64 ns_solve calls."""
+    from paper_2206_00975_gb300 import workloads
+    ms_, ns_ = workloads.tls_batch_shapes(seed=0, batch=4096)
+    g = torch.Generator(device=dev).manual_seed(5)
+    probs, probs32, total = [], [], 0
+    for i, (mi, ni) in enumerate(zip(ms_, ns_)):
+        mi, ni = int(mi), int(ni)
+        X = torch.randn((ni, mi), generator=g, device=dev, dtype=torch.float64).t()
+        xt = torch.randn(ni, generator=g, device=dev, dtype=torch.float64)
+        b = X @ xt + 1e-3 * torch.randn(mi, generator=g, device=dev, dtype=torch.float64)
+        Xb = torch.empty((ni + 1, mi), device=dev, dtype=torch.float64).t()
+        Xb[:, :ni] = X
+        Xb[:, ni] = b
+        probs.append({"A": Xb, "s": 2 * (ni + 1), "k": 1, "seed": i, "tls": True, "x_true": xt})
+        total += mi * (ni + 1)
+        del X
+    _, st, keep = api.ns_solve_batched(probs[:64])
+    outs, st, keep = api.ns_solve_batched(probs)
+    ms64 = timer(lambda: api.ns_solve_batched(probs, ws=keep[2]), 2) / 2
+    outs, st, keep = api.ns_solve_batched(probs, ws=keep[2])
+    torch.cuda.synchronize()
+    err = [float(torch.linalg.norm(o[2] - p["x_true"]) / torch.linalg.norm(p["x_true"])) for o, p in
+           zip(outs[:256], probs[:256])]
+    res = {"problems": len(probs), "input_gb_fp64": total * 8 / 1e9, "batched_fp64_ms": ms64,
+           "batched_fp64_solves_per_s": len(probs) / (ms64 / 1e3),
+           "status_nonzero_fp64": int((st != 0).sum().item()),
+           "tls_relerr_median_first256": float(np.median(err))}
+    # the per-problem FP64 loop on the first 256 problems, extrapolated
+    sub = probs[:256]
+    descs = [api.desc(api.NS_SRHT, s=p["s"], seed=p["seed"]) for p in sub]
+    wss = [api.workspace(dd, p["A"].shape[0], p["A"].shape[1], 1, dev) for dd, p in zip(descs, sub)]
+
+    def loop():
+        for dd, p, wsp in zip(descs, sub, wss):
+            api.ns_solve(dd, p["A"], 1, save=False, ws=wsp)
+    loop()
+    msl = timer(loop, 1) * len(probs) / len(sub)
+    res["loop_fp64_solves_per_s_extrapolated"] = len(probs) / (msl / 1e3)
+    del wss, keep
+    torch.cuda.empty_cache()
+    if getattr(api, "batched_supports_fp32", lambda: False)():
+        for p in probs:
+            p["A"] = p["A"].to(torch.float32).t().contiguous().t()
+        outs32, st32, keep32 = api.ns_solve_batched(probs)
+        ms32 = timer(lambda: api.ns_solve_batched(probs, ws=keep32[2]), 2) / 2
+        outs32, st32, keep32 = api.ns_solve_batched(probs, ws=keep32[2])
+        torch.cuda.synchronize()
+        err32 = [float(torch.linalg.norm(o[2] - p["x_true"]) / torch.linalg.norm(p["x_true"])) for o, p in
+                 zip(outs32[:256], probs[:256])]
+        res.update({"input_gb_fp32": total * 4 / 1e9, "batched_fp32_stream_ms": ms32,
+                    "batched_fp32_stream_solves_per_s": len(probs) / (ms32 / 1e3),
+                    "status_nonzero_fp32": int((st32 != 0).sum().item()),
+                    "tls_relerr_median_first256_fp32": float(np.median(err32))})
+        del keep32
+    del probs
+    return res
 
 
 def hrht_moved_bytes(m, n, s):
@@ -332,6 +473,23 @@ def profile_case(args, torch, api, dev):
         m, n, s = 1 << 17, 512, 2048
         A = torch.randn((n, m), generator=g, device=dev, dtype=torch.float32).t()
         d = api.desc(api.NS_GAUSSIAN, s=s, seed=0, prec=api.NS_PREC_BF16X3)
+    elif args.case == "fp64peak":  # FP64 throughput: cuBLAS DGEMM 8192^3 (2 n^3 flops), best of 5
+        nn = 8192
+        a = torch.randn((nn, nn), generator=g, device=dev, dtype=torch.float64)
+        b = torch.randn((nn, nn), generator=g, device=dev, dtype=torch.float64)
+        c = a @ b
+        best = 1e30
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            c = a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        print(json.dumps({"case": "fp64peak", "dgemm_n": nn, "ms": best, "tflops": 2.0 * nn ** 3 / (best / 1e3) / 1e12,
+                          "sms": sms, "checksum": float(c[0, 0])}))
+        return
     elif args.case == "dense":     # the at-scale dense stage on a Gaussian sketch
         n, s = N, S
         SA = torch.randn((n, s), generator=g, device=dev, dtype=torch.float64).t()
@@ -360,8 +518,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extra", action="store_true", help="also time the other workloads")
-    ap.add_argument("--case", default=None, help="profiling case: srht, sparse, hrht, srht32, gauss, dense")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workloads (headline only)")
+    ap.add_argument("--case", default=None,
+                    help="profiling case: srht, sparse, hrht, srht32, gauss, dense, fp64peak")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -521,7 +680,8 @@ def main():
     t_dense = ms_dense / args.steps / 1e3
     sketch_gbs = sketch_bytes / t_sketch / 1e9
     sm_mhz = clocks.get("sm_mhz") or 1990.0
-    fp64_peak = FP64_FLOPS_PER_CLK_SM * N_SM * sm_mhz * 1e6 / 1e12    # TFLOP/s at the sampled clock
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp64_peak = FP64_FLOPS_PER_CLK_SM * n_sm * sm_mhz * 1e6 / 1e12    # TFLOP/s at the sampled clock
     dflops = dense_flops(S, N, K_NULL, stats)
     dense_tf = dflops / t_dense / 1e12
     sketch_roof = {"bound": "hbm", "achieved": sketch_gbs, "peak": hbm_peak, "unit": "GB/s",
@@ -530,17 +690,18 @@ def main():
                    "peak_source": peak_kind, "algorithmic_bytes": sketch_bytes}
     dense_roof = {"bound": "alu", "achieved": dense_tf, "peak": fp64_peak, "unit": "TFLOP/s",
                   "frac": dense_tf / fp64_peak, "traffic": None,
-                  "kernel": "FP64 dense stage (column order, hqr_pipe x2 with Q2 formed in the second, jacobi_ring from V = Q2, extract) via ns_solve_sketched",
-                  "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x sampled SM clock",
+                  "kernel": "dense stage (column order, hqr_pipe x2 with Q2 formed in the second, FP32 Jacobi phase "
+                            "+ FP64 products, jacobi_ring from V = Q2 V0, extract) via ns_solve_sketched",
+                  "peak_source": "derived: %d SMs x 4 FP64 flop/clk x sampled SM clock" % n_sm,
                   "algorithmic_flops": dflops, "jacobi_sweeps_rotations_checks": stats[:3],
+                  "fp32_phase_sweeps_rotations": stats[4:6],
                   "jacobi_kernel": ("cluster ring, %d CTAs per cluster" % stats[3]) if stats[3] else "barrier-separated"}
     dominant = dense_roof if t_dense > t_sketch else sketch_roof
     line = {
         "metric": METRIC, "value": n_ranks * args.steps / (ms_solve / 1e3), "unit": "solves/s", "n_gpus": n_ranks,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_solve / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "input larger than L2 (2 GiB A per step)", "parallelism":
-                   "replicas" if n_ranks > 1 else "single GPU"},
+        "config": bench_config(world),
         "roofline": dominant,
         "sketch_roofline": sketch_roof,
         "breakdown_ms": {"sketch": t_sketch * 1e3, "dense": t_dense * 1e3},
@@ -561,11 +722,12 @@ def main():
                 "h2d_bytes_per_step": M * N * 8, "d2h_bytes_per_step": (N * K_NULL + K_NULL) * 8,
                 "overlap": "copy of step i+1 (E2E_PARTS streams) overlaps the solve of step i (two device buffers)",
                 "results_finite": e2e_ok},
-        "gpu_launches": 17 * args.steps,
+        "gpu_launches": launches_per_solve(stats) * args.steps,
         "clocks": clocks,
     }
-    if args.extra and rank == 0:
-        line["extra"] = extra_workloads(torch, api, dev, Timer(torch, stream, None, dev), hbm_peak, bf16_peak)
+    if rank == 0 and n_ranks == 1 and not args.no_configs:
+        line["configs"] = config_legs(torch, api, dev, Timer(torch, stream, None, dev), hbm_peak, bf16_peak,
+                                      fp64_peak)
     if rank == 0 and n_ranks == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(A_np)
     if rank == 0:

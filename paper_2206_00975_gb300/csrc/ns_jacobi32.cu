@@ -8,8 +8,10 @@
 // linear phase runs in FP32 and the FP64 ring only finishes the job:
 //
 //   1. Y = X0 in FP32 (columns of X0 = R2^T scaled by one power of two);
-//      columns whose norm is below 2^-30 of the largest are left out (zero in
-//      Y, identity in W): their relative accuracy is not touched, see below.
+//      columns whose norm is below 2^-60 of the largest are left out (zero in
+//      Y, identity in W), so that no FP32 square underflows.  Numerically null
+//      columns (~u of the largest) take part: left out, they would need FP64
+//      sweeps of their own among themselves.
 //   2. One-sided Jacobi sweeps on Y in FP32, the rotations accumulated in W
 //      (FP32, from I), with the rotation threshold |y_a . y_b| > tau |y_a||y_b|,
 //      tau = 2^-17, until a sweep rotates nothing or 8 sweeps.  W is held
@@ -40,7 +42,7 @@
 // the columns of X1 are orthogonal to ~1e-6 relative to their own sizes, and
 // the FP64 corrections of step 3 (E[a, b] ~ 2^-24 d_b/d_a) keep that grading.
 // Rounding in the FP64 products adds ~n u d_j to column j.  Columns below
-// 2^-30 d_max keep their X0 column unchanged.  The FP64 iteration is then the
+// 2^-60 d_max keep their X0 column unchanged.  The FP64 iteration is then the
 // usual one and fixes the final accuracy.
 #include <cmath>
 #include "ns_device.cuh"
@@ -59,7 +61,7 @@ constexpr int kJ32Threads = kJ32B * 32;        // one warp per pair of a round
 constexpr int kJ32Steps = kJ32Blocks - 1;      // outer steps per sweep
 constexpr int kJ32MaxSweeps = 8;
 constexpr float kJ32Tau = 1.0f / 131072.0f;    // 2^-17
-constexpr double kJ32Keep = 8.673617379884035e-19;  // 2^-60: kept columns have |x|^2 >= 2^-60 max |x|^2
+constexpr double kJ32Keep = 7.52316384526264e-37;   // 2^-120: kept columns have |x| >= 2^-60 max |x|
 constexpr size_t kJ32Smem = (size_t)4 * kJ32Slot * sizeof(float);
 
 // slot index in the per-CTA array of four block slots: parity p holds
@@ -93,7 +95,9 @@ __device__ __forceinline__ unsigned int j32_pair(float *a, float *b, float da, f
         be += __shfl_xor_sync(0xffffffffu, be, o);
         ga += __shfl_xor_sync(0xffffffffu, ga, o);
     }
-    if (!(ga != 0.0f && ga * ga > tau2 * (al * be))) return 0u;
+    // |gamma| > tau sqrt(alpha beta), as (gamma/alpha)(gamma/beta) > tau^2: the
+    // product alpha beta of two columns ~2^-60 of the largest would underflow
+    if (!(ga != 0.0f && al > 0.0f && be > 0.0f && __fdividef(ga, al) * __fdividef(ga, be) > tau2)) return 0u;
     // the rotation of the FP64 kernel: zeta = (beta - alpha) / (2 gamma),
     // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t;
     // a <- c a - s b, b <- s a + c b
@@ -136,12 +140,12 @@ __device__ __forceinline__ unsigned int j32_pair(float *a, float *b, float da, f
     return 1u;
 }
 
+// (not volatile, no memory clobber: the blocks it reads were completed before
+// the cluster barrier that precedes the exchange, so the compiler may issue all
+// of a thread's loads before its stores)
 __device__ __forceinline__ float4 ld_peer_f4(uint32_t addr) {
     float4 v;
-    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "r"(addr)
-                 : "memory");
+    asm("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
     return v;
 }
 
@@ -291,12 +295,19 @@ __global__ void __cluster_dims__(kJ32Cta, 1, 1) __launch_bounds__(kJ32Threads, 1
                 asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(src) : "memory");
                 s_d[2 * np + h][i] = v;
             }
-#pragma unroll 4
-            for (int v = tid; v < kJ32Slot / 4; v += kJ32Threads) {
-                const float4 x = ld_peer_f4(srcT + 16u * (uint32_t)v);
-                const float4 y = ld_peer_f4(srcB + 16u * (uint32_t)v);
-                ((float4 *)dT)[v] = x;
-                ((float4 *)dB)[v] = y;
+            {
+                constexpr int kPer = kJ32Slot / 4 / kJ32Threads;  // float4 per thread and block (4)
+                float4 x[kPer], y[kPer];
+#pragma unroll
+                for (int u = 0; u < kPer; ++u) {
+                    x[u] = ld_peer_f4(srcT + 16u * (uint32_t)(tid + u * kJ32Threads));
+                    y[u] = ld_peer_f4(srcB + 16u * (uint32_t)(tid + u * kJ32Threads));
+                }
+#pragma unroll
+                for (int u = 0; u < kPer; ++u) {
+                    ((float4 *)dT)[tid + u * kJ32Threads] = x[u];
+                    ((float4 *)dB)[tid + u * kJ32Threads] = y[u];
+                }
             }
             __syncthreads();
             par = np;

@@ -138,7 +138,7 @@ def test_dense_stage_near_repeated_column(api):
 def test_dense_stage_fp32_phase_guard(api):
     # 100 columns graded over 1 .. 1e-8 take part in the FP32 phase; 28 more,
     # graded from 1e-20 down to 1e-60 (not null: sigma of high relative accuracy),
-    # are left out of it (below 2^-30 of the largest norm).  Every singular
+    # are left out of it (below 2^-60 of the largest norm).  Every singular
     # value must keep one-sided Jacobi's relative accuracy.
     rng = np.random.default_rng(19)
     s, n, k = 512, 128, 2
