@@ -241,7 +241,7 @@ ns_status ns_backward(const ns_sketch_desc *desc, int64_t m, int64_t n, int32_t 
  * trailing right singular vector of the sketch.
  */
 typedef struct {
-    const void *A;   /* m x n, column-major, leading dimension lda >= m; FP64 */
+    const void *A;   /* m x n, column-major, leading dimension lda >= m; FP64 or FP32 (dtype) */
     int64_t m, n, lda;
     int64_t s;       /* SRHT sketch size: n <= s <= min(m', 16384) */
     int32_t k;       /* trailing vectors, 1 <= k <= n */
@@ -250,6 +250,10 @@ typedef struct {
     double *Vk;      /* n x k out (ordering and signs as ns_solve) */
     double *sigk;    /* k out */
     double *x;       /* n - 1 out when tls != 0, else unused */
+    int32_t dtype;   /* NS_F64: exact fixed-point sketch (NS_PREC_FP64); NS_F32:
+                        the FP32-stream sketch (NS_PREC_FP32_STREAM); QR and
+                        Jacobi run in FP64 either way */
+    int32_t reserved;  /* 0 */
 } ns_problem;
 
 /* Workspace bytes for ns_solve_batched; host_problems is a HOST copy of the
@@ -261,8 +265,9 @@ size_t ns_batched_workspace_size(const ns_sketch_desc *desc, int32_t batch, cons
  * vectors) on `batch` independent problems of arbitrary shapes in one
  * sequence of launches with no host round trip: a persistent sketch kernel
  * takes (problem, column) items from a device work counter, a persistent dense
- * kernel takes whole problems.  desc: kind NS_SRHT, prec NS_PREC_FP64 (its s and
- * seed are unused; each problem has its own).  host_problems and dev_problems
+ * kernel takes whole problems.  desc: kind NS_SRHT, prec NS_PREC_FP64 or
+ * NS_PREC_FP32_STREAM (its s and seed are unused; each problem has its own
+ * size, seed and dtype).  host_problems and dev_problems
  * hold the same array (host copy for validation and sizing, device copy for
  * the kernels).  dev_status: device int32[batch], per-problem status
  * (0, NS_ERR_NONFINITE, NS_ERR_NOCONV, NS_ERR_TLS_NOSOLUTION).
@@ -270,6 +275,20 @@ size_t ns_batched_workspace_size(const ns_sketch_desc *desc, int32_t batch, cons
 ns_status ns_solve_batched(const ns_sketch_desc *desc, int32_t batch, const ns_problem *host_problems,
                            const ns_problem *dev_problems, int32_t *dev_status, void *ws, size_t ws_bytes,
                            void *stream);
+
+/*
+ * ns_batched_tuning -- launch geometry of ns_solve_batched, chosen by the
+ * autotuner of the Python package (paper_2206_00975_gb300.autotune) and cached
+ * per (architecture, m' of the largest problem, column panel, dtype):
+ *   panel               columns per sketch work item (1..64; 0 = 1);
+ *   sketch_ctas_per_sm  persistent sketch CTAs per SM (0 = the occupancy limit);
+ *   dense_ctas_per_sm   persistent dense CTAs per SM (0 = the occupancy limit).
+ * None of them changes the arithmetic: the results are bit-identical for every
+ * setting.  The setting is process-wide and read when ns_solve_batched
+ * launches; calls that change it must not race with those launches.
+ * Errors: NS_ERR_INVALID_ARG for a value outside its range.
+ */
+ns_status ns_batched_tuning(int32_t panel, int32_t sketch_ctas_per_sm, int32_t dense_ctas_per_sm);
 
 /*
  * ns_aaa_real -- AAA rational approximation of f on real points x (Section

@@ -23,7 +23,7 @@ EXPORTS = [
     "ns_backward", "ns_residual", "ns_srht_meta", "ns_sparse_meta", "ns_sketch_static",
     "ns_batched_workspace_size", "ns_solve_batched", "ns_aaa_workspace_size", "ns_aaa_real",
     "ns_solve_sketched", "ns_solve_stats", "ns_sketched_stats", "ns_solve_eps", "ns_sketch_update",
-    "ns_test_bounded_wait",
+    "ns_test_bounded_wait", "ns_batched_tuning",
 ]
 
 
@@ -36,7 +36,8 @@ class Problem(ctypes.Structure):
     """ns_problem of include/ns.h (device pointers inside)."""
     _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("lda", ctypes.c_int64),
                 ("s", ctypes.c_int64), ("k", ctypes.c_int32), ("tls", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("Vk", ctypes.c_void_p), ("sigk", ctypes.c_void_p), ("x", ctypes.c_void_p)]
+                ("Vk", ctypes.c_void_p), ("sigk", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class NSError(RuntimeError):
@@ -81,6 +82,7 @@ def load():
         "ns_solve_eps": (ctypes.c_int, [D, P, i32, i64, i64, i64, ctypes.c_double, P, P, P, P, P, P, sz, P]),
         "ns_sketch_update": (ctypes.c_int, [D, i64, i32, i64, P, i64, P, P]),
         "ns_test_bounded_wait": (ctypes.c_int, [i32, i64, P, P, sz, P]),
+        "ns_batched_tuning": (ctypes.c_int, [i32, i32, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -208,13 +208,17 @@ def ns_sketch_static(d, A, SA=None, status=None, stream=None):
     return SA, status
 
 
-def ns_solve_batched(problems, stream=None, ws=None, device="cuda"):
+def ns_solve_batched(problems, stream=None, ws=None, device="cuda", tuning=None):
     """Batched Algorithm 1.  problems: list of dicts with A (column-major CUDA
-    tensor), s, k, seed and optionally tls=True.  Returns (list of (Vk, sigk, x),
-    status int32 tensor)."""
+    tensor, float64 or float32: the FP32-stream sketch), s, k, seed and
+    optionally tls=True.  tuning: None (keep the current launch geometry) or a
+    dict with panel, sketch_ctas_per_sm, dense_ctas_per_sm (see
+    paper_2206_00975_gb300.autotune; the results do not depend on it).
+    Returns (list of (Vk, sigk, x), status int32 tensor, keep-alive tuple)."""
     n_b = len(problems)
     arr = (Problem * n_b)()
     outs = []
+    any32 = False
     for i, p in enumerate(problems):
         A = p["A"]
         m, n = A.shape
@@ -223,14 +227,19 @@ def ns_solve_batched(problems, stream=None, ws=None, device="cuda"):
         sigk = torch.empty(k, dtype=torch.float64, device=A.device)
         x = torch.empty(max(n - 1, 1), dtype=torch.float64, device=A.device) if p.get("tls") else None
         outs.append((Vk, sigk, x))
+        dt = _dtype_code(A)
+        any32 = any32 or dt == NS_F32
         arr[i] = Problem(A.data_ptr(), m, n, _ld(A), int(p["s"]), k, 1 if p.get("tls") else 0,
                          int(p.get("seed", 0)) & ((1 << 64) - 1), Vk.data_ptr(), sigk.data_ptr(),
-                         x.data_ptr() if x is not None else 0)
+                         x.data_ptr() if x is not None else 0, dt, 0)
     raw = bytes(arr)
     dev_arr = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
     status = torch.zeros(n_b, dtype=torch.int32, device=device)
-    d = desc(NS_SRHT, s=1, seed=0)
+    d = desc(NS_SRHT, s=1, seed=0, prec=NS_PREC_FP32_STREAM if any32 else NS_PREC_FP64)
     lib = _lib.load()
+    if tuning is not None:
+        _lib.check(lib.ns_batched_tuning(int(tuning.get("panel", 0)), int(tuning.get("sketch_ctas_per_sm", 0)),
+                                         int(tuning.get("dense_ctas_per_sm", 0))), "ns_batched_tuning")
     nbytes = int(lib.ns_batched_workspace_size(ctypes.byref(d), n_b, ctypes.byref(arr)))
     if nbytes == 0:
         raise NSError(_lib.NS_ERR_INVALID_ARG, "ns_batched_workspace_size")
@@ -242,6 +251,11 @@ def ns_solve_batched(problems, stream=None, ws=None, device="cuda"):
     # keep the device copy of the descriptors alive until the work is done
     outs_ref = (outs, dev_arr, ws)
     return outs_ref[0], status, outs_ref
+
+
+def batched_supports_fp32():
+    """ns_problem carries a dtype: FP32 problems take the FP32-stream sketch."""
+    return True
 
 
 def ns_aaa_real(x, f, K, smax, seed=0, forced=None, want_sketch=False, ws=None, stream=None):

@@ -329,16 +329,21 @@ ns_status ns_backward(const ns_sketch_desc *d, int64_t m, int64_t n, int32_t k, 
 
 static bool problem_ok(const ns_problem &p) {
     if (!p.A || !p.Vk || !p.sigk) return false;
+    if (p.dtype != NS_F64 && p.dtype != NS_F32) return false;
     if (p.m < 1 || p.n < 1 || p.m < p.n || p.lda < p.m || p.n > kMaxN) return false;
     if (p.s < p.n || p.s > kMaxS || p.s > ((int64_t)1 << ceil_log2(p.m))) return false;
     if (p.k < 1 || p.k > p.n) return false;
     if (p.tls && (p.k != 1 || p.n < 2 || !p.x)) return false;
-    if ((((uintptr_t)p.A) & 7) != 0) return false;
+    if ((((uintptr_t)p.A) & (p.dtype == NS_F32 ? 3 : 7)) != 0) return false;
     return true;
 }
 
+static bool batch_desc_ok(const ns_sketch_desc *d) {
+    return d && d->kind == NS_SRHT && (d->prec == NS_PREC_FP64 || d->prec == NS_PREC_FP32_STREAM);
+}
+
 size_t ns_batched_workspace_size(const ns_sketch_desc *d, int32_t batch, const ns_problem *host) {
-    if (!d || d->kind != NS_SRHT || d->prec != NS_PREC_FP64 || batch < 1 || !host) return 0;
+    if (!batch_desc_ok(d) || batch < 1 || !host) return 0;
     for (int32_t i = 0; i < batch; ++i)
         if (!problem_ok(host[i])) return 0;
     return batched_work_bytes(batch, host);
@@ -346,7 +351,7 @@ size_t ns_batched_workspace_size(const ns_sketch_desc *d, int32_t batch, const n
 
 ns_status ns_solve_batched(const ns_sketch_desc *d, int32_t batch, const ns_problem *host, const ns_problem *dev,
                            int32_t *dev_status, void *ws, size_t ws_bytes, void *stream) {
-    if (!d || d->kind != NS_SRHT || d->prec != NS_PREC_FP64) return NS_ERR_INVALID_ARG;
+    if (!batch_desc_ok(d)) return NS_ERR_INVALID_ARG;
     if (batch < 1 || !host || !dev || !dev_status || !ws) return NS_ERR_INVALID_ARG;
     if ((((uintptr_t)ws) & 255) != 0) return NS_ERR_INVALID_ARG;
     for (int32_t i = 0; i < batch; ++i)
@@ -412,6 +417,10 @@ ns_status ns_srht_meta(const ns_sketch_desc *d, int64_t m, uint32_t *sign_words,
 ns_status ns_sparse_meta(const ns_sketch_desc *d, int64_t m, int32_t *rows, int8_t *signs, void *stream) {
     if (!desc_ok(d) || d->kind != NS_SPARSE_SIGN || m < 1 || !rows || !signs) return NS_ERR_INVALID_ARG;
     return cuda_status(launch_sparse_meta(d->seed, d->s, d->zeta, m, rows, signs, (cudaStream_t)stream));
+}
+
+ns_status ns_batched_tuning(int32_t panel, int32_t sketch_ctas_per_sm, int32_t dense_ctas_per_sm) {
+    return set_batch_tuning(panel, sketch_ctas_per_sm, dense_ctas_per_sm) ? NS_OK : NS_ERR_INVALID_ARG;
 }
 
 ns_status ns_test_bounded_wait(int32_t which, int64_t limit, int32_t *dev_status, void *ws, size_t ws_bytes,

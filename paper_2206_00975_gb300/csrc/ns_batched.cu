@@ -6,9 +6,10 @@
 //   setup   one CTA: per-problem workspace offsets and work-item ranges
 //           (prefix sums over the device problem array);
 //   meta    one CTA per problem: SRHT signs and sample rows from its seed;
-//   sketch  persistent CTAs take (problem, column) items from an atomic
-//           counter (uneven problems balance dynamically) and run the exact
-//           fixed-point SRHT pipeline over the column's blocks;
+//   sketch  persistent CTAs take (problem, panel of columns) items from an
+//           atomic counter (uneven problems balance dynamically) and run, per
+//           column, the exact fixed-point SRHT pipeline over its blocks (FP64
+//           problems) or the FP32-stream pipeline (FP32 problems);
 //   dense   persistent CTAs take whole problems from a second counter: pivoted
 //           Householder QR, QR of R^T, one-sided Jacobi on R2^T with one warp
 //           per pair, V = P Q2 Vx, extraction, TLS.
@@ -24,9 +25,27 @@ namespace ns {
 
 constexpr int kBatchThreads = 256;
 
+// Tuning of the batched launches (process-wide, set by ns_batched_tuning; 0 =
+// the default).  None of them changes the arithmetic: a column is sketched and
+// a problem solved the same way whatever the panel width or the grid sizes.
+struct BatchTuning {
+    int panel = 1;              // columns per sketch work item
+    int sketch_ctas_per_sm = 0; // persistent sketch CTAs per SM (0: occupancy limit)
+    int dense_ctas_per_sm = 0;  // persistent dense CTAs per SM (0: occupancy limit)
+};
+static BatchTuning g_batch_tuning;
+
+bool set_batch_tuning(int panel, int sketch_cps, int dense_cps) {
+    if (panel < 0 || panel > 64 || sketch_cps < 0 || sketch_cps > 64 || dense_cps < 0 || dense_cps > 64) return false;
+    g_batch_tuning.panel = panel > 0 ? panel : 1;
+    g_batch_tuning.sketch_ctas_per_sm = sketch_cps;
+    g_batch_tuning.dense_ctas_per_sm = dense_cps;
+    return true;
+}
+
 struct BatchSlot {
     int64_t off;       // byte offset of the problem's workspace
-    int64_t item0;     // first sketch work item (one per column)
+    int64_t item0;     // first sketch work item (one per panel of columns)
     int32_t nblk;      // 4096-row blocks of its padded length
     int32_t lg;        // m' = 2^lg
 };
@@ -74,7 +93,7 @@ size_t batched_head_bytes(int32_t batch) { return align256(sizeof(BatchSlot) * (
 // ------------------------------------------------------------------ setup ----
 __global__ void __launch_bounds__(1024) batched_setup_kernel(const ns_problem *__restrict__ P, int32_t batch,
                                                              BatchSlot *slots, unsigned long long *counters,
-                                                             int64_t head) {
+                                                             int64_t head, int panel) {
     __shared__ int64_t part_b[1024], part_i[1024];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t per = (batch + nt - 1) / nt;
@@ -82,7 +101,7 @@ __global__ void __launch_bounds__(1024) batched_setup_kernel(const ns_problem *_
     int64_t sb = 0, si = 0;
     for (int64_t i = i0; i < i1; ++i) {
         sb += problem_bytes(P[i].m, P[i].n, P[i].s);
-        si += P[i].n;
+        si += (P[i].n + panel - 1) / panel;
     }
     part_b[tid] = sb;
     part_i[tid] = si;
@@ -110,7 +129,7 @@ __global__ void __launch_bounds__(1024) batched_setup_kernel(const ns_problem *_
         slots[i].nblk = (int32_t)(mp > kBlock ? mp / kBlock : 1);
         slots[i].lg = lg;
         ob += problem_bytes(P[i].m, P[i].n, P[i].s);
-        oi += P[i].n;
+        oi += (P[i].n + panel - 1) / panel;
     }
 }
 
@@ -134,7 +153,7 @@ __global__ void batched_meta_kernel(const ns_problem *__restrict__ P, const Batc
 __global__ void __launch_bounds__(64) batched_sketch_kernel(const ns_problem *__restrict__ P, int32_t batch,
                                                             const BatchSlot *__restrict__ slots, char *ws,
                                                             unsigned long long *counters, int64_t smax,
-                                                            int32_t *status) {
+                                                            int32_t *status, int panel) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     long long *Zs = (long long *)smem_raw;
     long long *acc = Zs + kBlock;                                   // smax
@@ -160,24 +179,40 @@ __global__ void __launch_bounds__(64) batched_sketch_kernel(const ns_problem *__
         }
         const ns_problem pr = P[lo];
         const BatchSlot sl = slots[lo];
-        const int64_t c = item - sl.item0;
+        const int64_t c0 = (item - sl.item0) * panel;
+        const int64_t c1 = (c0 + panel < pr.n) ? c0 + panel : pr.n;
         ProblemView v = problem_view(ws + sl.off, pr.m, pr.n, pr.s);
         const int64_t s = pr.s;
-        for (int64_t i = t; i < s; i += 64) {
-            rows_s[i] = srht_pack_row(v.rows[i]);
-            acc[i] = 0;
+        for (int64_t i = t; i < s; i += 64) rows_s[i] = srht_pack_row(v.rows[i]);
+        int nonfinite = 0;
+        for (int64_t c = c0; c < c1; ++c) {
+            double *out = v.SA + c * s;
+            if (pr.dtype == NS_F32) {  // FP32-stream: FP32 butterflies and accumulation
+                float *accf = (float *)acc;
+                for (int64_t i = t; i < s; i += 64) accf[i] = 0.0f;
+                __syncthreads();
+                const float *Acol = (const float *)pr.A + c * pr.lda;
+                const int vec_ok = ((((uintptr_t)pr.A) & 7) == 0 && (pr.lda & 1) == 0) ? 1 : 0;
+                for (int64_t b = 0; b < sl.nblk; ++b)
+                    srht_f32_block(Acol, pr.m, s, b, v.sign_words, rows_s, (float *)Zs, accf, sgn, vec_ok,
+                                   nonfinite);
+                const double scale = 1.0 / sqrt((double)s);
+                for (int64_t i = t; i < s; i += 64) out[i] = (double)accf[i] * scale;
+            } else {  // FP64: exact fixed point
+                for (int64_t i = t; i < s; i += 64) acc[i] = 0;
+                __syncthreads();
+                const double *Acol = (const double *)pr.A + c * pr.lda;
+                const int vec_ok = ((((uintptr_t)pr.A) & 15) == 0 && (pr.lda & 1) == 0) ? 1 : 0;
+                const int P_bits = 63 - kBlockLog - clog2(sl.nblk) - 1;
+                int Erun = 0;
+                for (int64_t b = 0; b < sl.nblk; ++b)
+                    srht_f64_block(Acol, pr.m, s, b, P_bits, v.sign_words, rows_s, Zs, acc, sgn, red, vec_ok, Erun,
+                                   nonfinite, b + 1 < sl.nblk);
+                const double scale = ldexp(1.0, Erun - 1022 - P_bits) / sqrt((double)s);
+                for (int64_t i = t; i < s; i += 64) out[i] = (double)acc[i] * scale;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        const double *Acol = (const double *)pr.A + c * pr.lda;
-        const int vec_ok = ((((uintptr_t)pr.A) & 15) == 0 && (pr.lda & 1) == 0) ? 1 : 0;
-        const int P_bits = 63 - kBlockLog - clog2(sl.nblk) - 1;
-        int Erun = 0, nonfinite = 0;
-        for (int64_t b = 0; b < sl.nblk; ++b)
-            srht_f64_block(Acol, pr.m, s, b, P_bits, v.sign_words, rows_s, Zs, acc, sgn, red, vec_ok, Erun,
-                           nonfinite, b + 1 < sl.nblk);
-        const double scale = ldexp(1.0, Erun - 1022 - P_bits) / sqrt((double)s);
-        double *out = v.SA + c * s;
-        for (int64_t i = t; i < s; i += 64) out[i] = (double)acc[i] * scale;
         if (nonfinite) atomicMax(status + lo, (int32_t)NS_ERR_NONFINITE);
         __syncthreads();
     }
@@ -244,7 +279,8 @@ cudaError_t launch_batched(int32_t batch, const ns_problem *host, const ns_probl
     const int64_t head = (int64_t)batched_head_bytes(batch);
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t) * (size_t)batch, st);
     if (e != cudaSuccess) return e;
-    batched_setup_kernel<<<1, 1024, 0, st>>>(dev, batch, slots, counters, head);
+    const BatchTuning tu = g_batch_tuning;
+    batched_setup_kernel<<<1, 1024, 0, st>>>(dev, batch, slots, counters, head, tu.panel);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     batched_meta_kernel<<<(unsigned)batch, 256, 0, st>>>(dev, slots, base);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -253,15 +289,19 @@ cudaError_t launch_batched(int32_t batch, const ns_problem *host, const ns_probl
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_sketch_kernel, 64, smem);
-    const int grid1 = sm_count_b() * (per_sm > 0 ? per_sm : 1);
-    batched_sketch_kernel<<<grid1, 64, smem, st>>>(dev, batch, slots, base, counters, smax, status);
+    if (per_sm < 1) per_sm = 1;
+    if (tu.sketch_ctas_per_sm > 0 && tu.sketch_ctas_per_sm < per_sm) per_sm = tu.sketch_ctas_per_sm;
+    const int grid1 = sm_count_b() * per_sm;
+    batched_sketch_kernel<<<grid1, 64, smem, st>>>(dev, batch, slots, base, counters, smax, status, tu.panel);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t dsmem = sizeof(double) * (size_t)(smax + 2 * nmax);
     e = cudaFuncSetAttribute(batched_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
     if (e != cudaSuccess) return e;
     int per_sm2 = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, batched_dense_kernel, kBatchThreads, dsmem);
-    int64_t grid2 = (int64_t)sm_count_b() * (per_sm2 > 0 ? per_sm2 : 1);
+    if (per_sm2 < 1) per_sm2 = 1;
+    if (tu.dense_ctas_per_sm > 0 && tu.dense_ctas_per_sm < per_sm2) per_sm2 = tu.dense_ctas_per_sm;
+    int64_t grid2 = (int64_t)sm_count_b() * per_sm2;
     if (grid2 > batch) grid2 = batch;
     batched_dense_kernel<<<(unsigned)grid2, kBatchThreads, dsmem, st>>>(dev, batch, slots, base, counters, status);
     return cudaGetLastError();

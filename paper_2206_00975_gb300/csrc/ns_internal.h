@@ -134,6 +134,7 @@ cudaError_t launch_backward(uint64_t seed, int64_t m, int64_t n, int32_t k, int6
                             cudaStream_t st);
 
 size_t batched_work_bytes(int32_t batch, const ns_problem *host);
+bool set_batch_tuning(int panel, int sketch_cps, int dense_cps);
 cudaError_t launch_batched(int32_t batch, const ns_problem *host, const ns_problem *dev, int32_t *status, void *ws,
                            cudaStream_t st);
 

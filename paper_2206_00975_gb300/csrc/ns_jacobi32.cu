@@ -14,7 +14,8 @@
 //      sweeps of their own among themselves.
 //   2. One-sided Jacobi sweeps on Y in FP32, the rotations accumulated in W
 //      (FP32, from I), with the rotation threshold |y_a . y_b| > tau |y_a||y_b|,
-//      tau = 2^-17, until a sweep rotates nothing or 8 sweeps.  W is held
+//      tau = 2^-17, until a sweep rotates fewer than half of the pairs (the
+//      iteration has left its linear phase) or 8 sweeps.  W is held
 //      graded, W~[i, j] = W[i, j] d_i / d_j with d the column norms of X0 (a
 //      rotation (c, s) of columns a, b then uses s d_b/d_a and s d_a/d_b, see
 //      j32_pair): one-sided Jacobi keeps W[i, j] ~ d_j/d_i between columns of
@@ -140,6 +141,108 @@ __device__ __forceinline__ unsigned int j32_pair(float *a, float *b, float da, f
     return 1u;
 }
 
+// The 16 rounds of cross pairs of one outer step (all warps of the CTA): warp w
+// keeps top column T[w] (y and w~, 8 + 8 values per lane) and its squared norm
+// in registers; in round r it pairs with bottom column B[(w + r) mod 16], read
+// from and written back to shared memory with its squared norm in bn[].  Only
+// the inner product needs a warp reduction: a rotation that zeroes gamma maps
+// the squared norms to alpha - t gamma and beta + t gamma exactly (the
+// one-sided Jacobi identity), and both are recomputed from the columns at the
+// start of every outer step, so rounding does not accumulate.  Returns the
+// warp's rotations.
+__device__ __forceinline__ unsigned int j32_cross_rounds(float *T, float *B, float dt, const float *dB, float *bn,
+                                                         float tau2) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float *tc = T + w * kJ32Col;
+    float4 ty0 = *(const float4 *)(tc + 4 * lane), ty1 = *(const float4 *)(tc + 128 + 4 * lane);
+    float4 tw0 = *(const float4 *)(tc + kJ32Rows + 4 * lane), tw1 = *(const float4 *)(tc + kJ32Rows + 128 + 4 * lane);
+    float al, be;
+    {   // exact squared norms: this warp's top column, and bottom column w into bn[w]
+        const float *bc = B + w * kJ32Col;
+        const float4 b0 = *(const float4 *)(bc + 4 * lane), b1 = *(const float4 *)(bc + 128 + 4 * lane);
+        al = ty0.x * ty0.x; be = b0.x * b0.x;
+        al = fmaf(ty0.y, ty0.y, al); be = fmaf(b0.y, b0.y, be);
+        al = fmaf(ty0.z, ty0.z, al); be = fmaf(b0.z, b0.z, be);
+        al = fmaf(ty0.w, ty0.w, al); be = fmaf(b0.w, b0.w, be);
+        al = fmaf(ty1.x, ty1.x, al); be = fmaf(b1.x, b1.x, be);
+        al = fmaf(ty1.y, ty1.y, al); be = fmaf(b1.y, b1.y, be);
+        al = fmaf(ty1.z, ty1.z, al); be = fmaf(b1.z, b1.z, be);
+        al = fmaf(ty1.w, ty1.w, al); be = fmaf(b1.w, b1.w, be);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            al += __shfl_xor_sync(0xffffffffu, al, o);
+            be += __shfl_xor_sync(0xffffffffu, be, o);
+        }
+        if (lane == 0) bn[w] = be;
+    }
+    const float inv_dt = __fdividef(1.0f, dt);
+    __syncthreads();
+    unsigned int rots = 0;
+    for (int r = 0; r < kJ32B; ++r) {
+        const int bq = (w + r) & (kJ32B - 1);
+        float *bc = B + bq * kJ32Col;
+        float4 by0 = *(const float4 *)(bc + 4 * lane), by1 = *(const float4 *)(bc + 128 + 4 * lane);
+        const float4 bw0 = *(const float4 *)(bc + kJ32Rows + 4 * lane);
+        const float4 bw1 = *(const float4 *)(bc + kJ32Rows + 128 + 4 * lane);
+        const float bb = bn[bq], db = dB[bq];
+        float ga = ty0.x * by0.x;
+        ga = fmaf(ty0.y, by0.y, ga);
+        ga = fmaf(ty0.z, by0.z, ga);
+        ga = fmaf(ty0.w, by0.w, ga);
+        ga = fmaf(ty1.x, by1.x, ga);
+        ga = fmaf(ty1.y, by1.y, ga);
+        ga = fmaf(ty1.z, by1.z, ga);
+        ga = fmaf(ty1.w, by1.w, ga);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        const bool rot = ga != 0.0f && al > 0.0f && bb > 0.0f && __fdividef(ga, al) * __fdividef(ga, bb) > tau2;
+        if (rot) {  // warp-uniform: every lane holds the same sums
+            const float z = __fdividef(bb - al, 2.0f * ga), az = fabsf(z);
+            const float w1 = fmaf(z, z, 1.0f);
+            const float t = (az > 1e18f) ? __fdividef(0.5f, z) : copysignf(__fdividef(1.0f, az + w1 * rsqrtf(w1)), z);
+            const float cs = rsqrtf(fmaf(t, t, 1.0f)), sn = cs * t;
+            const float sab = sn * db * inv_dt, sba = sn * dt * __fdividef(1.0f, db);
+            float4 na0, na1;
+            na0.x = cs * ty0.x - sn * by0.x; by0.x = sn * ty0.x + cs * by0.x;
+            na0.y = cs * ty0.y - sn * by0.y; by0.y = sn * ty0.y + cs * by0.y;
+            na0.z = cs * ty0.z - sn * by0.z; by0.z = sn * ty0.z + cs * by0.z;
+            na0.w = cs * ty0.w - sn * by0.w; by0.w = sn * ty0.w + cs * by0.w;
+            na1.x = cs * ty1.x - sn * by1.x; by1.x = sn * ty1.x + cs * by1.x;
+            na1.y = cs * ty1.y - sn * by1.y; by1.y = sn * ty1.y + cs * by1.y;
+            na1.z = cs * ty1.z - sn * by1.z; by1.z = sn * ty1.z + cs * by1.z;
+            na1.w = cs * ty1.w - sn * by1.w; by1.w = sn * ty1.w + cs * by1.w;
+            ty0 = na0;
+            ty1 = na1;
+            float4 nb0, nb1;
+            na0.x = cs * tw0.x - sab * bw0.x; nb0.x = sba * tw0.x + cs * bw0.x;
+            na0.y = cs * tw0.y - sab * bw0.y; nb0.y = sba * tw0.y + cs * bw0.y;
+            na0.z = cs * tw0.z - sab * bw0.z; nb0.z = sba * tw0.z + cs * bw0.z;
+            na0.w = cs * tw0.w - sab * bw0.w; nb0.w = sba * tw0.w + cs * bw0.w;
+            na1.x = cs * tw1.x - sab * bw1.x; nb1.x = sba * tw1.x + cs * bw1.x;
+            na1.y = cs * tw1.y - sab * bw1.y; nb1.y = sba * tw1.y + cs * bw1.y;
+            na1.z = cs * tw1.z - sab * bw1.z; nb1.z = sba * tw1.z + cs * bw1.z;
+            na1.w = cs * tw1.w - sab * bw1.w; nb1.w = sba * tw1.w + cs * bw1.w;
+            tw0 = na0;
+            tw1 = na1;
+            *(float4 *)(bc + 4 * lane) = by0;
+            *(float4 *)(bc + 128 + 4 * lane) = by1;
+            *(float4 *)(bc + kJ32Rows + 4 * lane) = nb0;
+            *(float4 *)(bc + kJ32Rows + 128 + 4 * lane) = nb1;
+            const float tg = t * ga;
+            al -= tg;
+            if (lane == 0) bn[bq] = bb + tg;
+            ++rots;
+        }
+        __syncthreads();
+    }
+    *(float4 *)(tc + 4 * lane) = ty0;
+    *(float4 *)(tc + 128 + 4 * lane) = ty1;
+    *(float4 *)(tc + kJ32Rows + 4 * lane) = tw0;
+    *(float4 *)(tc + kJ32Rows + 128 + 4 * lane) = tw1;
+    __syncthreads();
+    return rots;
+}
+
 // (not volatile, no memory clobber: the blocks it reads were completed before
 // the cluster barrier that precedes the exchange, so the compiler may issue all
 // of a thread's loads before its stores)
@@ -172,6 +275,7 @@ __global__ void __cluster_dims__(kJ32Cta, 1, 1) __launch_bounds__(kJ32Threads, 1
     __shared__ unsigned int s_local;
     __shared__ float s_d[4][kJ32B];  // column scales d of the four block slots (moved with the blocks)
     __shared__ float d_all[kJ32N];   // column scales d of every column (rows of W)
+    __shared__ float s_bn[kJ32B];    // squared norms of the bottom block's columns during the cross rounds
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int c = (int)cluster_rank();
     const int btop = c, bbot = kJ32Blocks - 1 - c;  // blocks held at the start of every sweep
@@ -260,12 +364,10 @@ __global__ void __cluster_dims__(kJ32Cta, 1, 1) __launch_bounds__(kJ32Threads, 1
                     __syncthreads();
                 }
             }
-            const float *dT0 = s_d[2 * par], *dB0 = s_d[2 * par + 1];
-            for (int r = 0; r < kJ32B; ++r) {  // the 256 pairs between the two blocks
-                const int bq = (w + r) & (kJ32B - 1);
-                mine += j32_pair(T + w * kJ32Col, B + bq * kJ32Col, dT0[w], dB0[bq], tau2);
-                __syncthreads();
-            }
+            // the 256 pairs between the two blocks: warp w holds top column w in
+            // registers for all 16 rounds; bottom column (w + r) mod 16 visits it
+            // through shared memory with its squared norm
+            mine += j32_cross_rounds(T, B, s_d[2 * par][w], s_d[2 * par + 1], s_bn, tau2);
             if (step == kJ32Steps - 1) {  // publish this CTA's rotation count of the sweep
                 if (lane == 0) atomicAdd(&s_local, mine);
                 __syncthreads();
@@ -316,7 +418,9 @@ __global__ void __cluster_dims__(kJ32Cta, 1, 1) __launch_bounds__(kJ32Threads, 1
         unsigned int tot = 0;
         for (int r = 0; r < kJ32Cta; ++r) tot += s_rot[r];
         rot_total += tot;
-        if (tot == 0u) break;
+        // a sweep that rotated fewer than half of the pairs has left the linear
+        // phase: the FP64 iteration converges quadratically from here
+        if (2ull * tot < (unsigned long long)kept * (kept - 1) / 2) break;
     }
     // ---- blocks are back where they started: W = D^-1 W~ D -> V0 (FP64); the
     // scale of row r (column r of X0) is read from the slot that holds it

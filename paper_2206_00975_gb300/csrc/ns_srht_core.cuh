@@ -280,6 +280,84 @@ __device__ __forceinline__ void srht_f64_block128(const double *__restrict__ Aco
     __syncthreads();
 }
 
+// in-register Walsh-Hadamard transform of 64 FP32 values (Sylvester order on
+// the register index)
+__device__ __forceinline__ void fwht64_f32(float (&z)[64]) {
+#pragma unroll
+    for (int h = 1; h < 64; h <<= 1) {
+#pragma unroll
+        for (int k = 0; k < 64; ++k) {
+            if ((k & h) == 0) {
+                const float a = z[k], b = z[k + h];
+                z[k] = a + b;
+                z[k + h] = a - b;
+            }
+        }
+    }
+}
+
+// One 4096-row block b of an FP32 column with 64 threads (the FP32-stream
+// precision mode): load, exact sign flip by D, H_4096 in FP32 in two register
+// phases around the swizzled transpose (the layouts of srht_f64_block), and the
+// signed gather of the sampled rows (rows_s packed by srht_pack_row) into the
+// FP32 accumulator acc[0..s).  Zs holds 4096 floats.  Ends with __syncthreads().
+__device__ __forceinline__ void srht_f32_block(const float *__restrict__ Acol, int64_t m, int64_t s, int64_t b,
+                                               const uint32_t *__restrict__ sign_words, const int32_t *rows_s,
+                                               float *Zs, float *acc, uint32_t *sgn, int vec_ok, int &nonfinite) {
+    const int t = threadIdx.x;
+    const int64_t base = b * kBlock;
+    sgn[t] = sign_words[(base >> 5) + t];
+    sgn[t + 64] = sign_words[(base >> 5) + 64 + t];
+    float z[64];
+    if (vec_ok && base + kBlock <= m) {
+#pragma unroll
+        for (int kk = 0; kk < 32; ++kk) {
+            const float2 v = __ldcs((const float2 *)(Acol + base + 2 * t + 128 * kk));
+            z[2 * kk] = v.x;
+            z[2 * kk + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int kk = 0; kk < 32; ++kk) {
+            const int64_t i0 = base + 2 * t + 128 * kk;
+            z[2 * kk] = (i0 < m) ? __ldcs(Acol + i0) : 0.0f;
+            z[2 * kk + 1] = (i0 + 1 < m) ? __ldcs(Acol + i0 + 1) : 0.0f;
+        }
+    }
+    __syncthreads();  // publishes sgn[]
+#pragma unroll
+    for (int kk = 0; kk < 32; ++kk) {
+        const uint32_t sw = sgn[4 * kk + (t >> 4)] >> (2 * (t & 15));
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t bits = __float_as_uint(z[2 * kk + h]);
+            if ((bits & 0x7F800000u) == 0x7F800000u) nonfinite = 1;
+            bits ^= ((sw >> h) & 1u) << 31;
+            z[2 * kk + h] = __uint_as_float(bits);
+        }
+    }
+    fwht64_f32(z);
+#pragma unroll
+    for (int kk = 0; kk < 32; ++kk) {
+        const int i = 2 * t + 128 * kk;
+        *(float2 *)(Zs + swz(i)) = make_float2(z[2 * kk], z[2 * kk + 1]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 64; ++k) z[k] = Zs[swz(l2_elem(t, k))];
+    __syncthreads();
+    fwht64_f32(z);
+#pragma unroll
+    for (int k = 0; k < 64; ++k) Zs[swz(l2_elem(t, k))] = z[k];
+    __syncthreads();
+    for (int64_t i = t; i < s; i += 64) {
+        const uint32_t pr = (uint32_t)rows_s[i];
+        const float v = Zs[pr & (kBlock - 1)];
+        acc[i] += (__popc(pr >> kBlockLog & (uint32_t)b) & 1) ? -v : v;
+    }
+    __syncthreads();
+}
+
 // sample row r as the gather uses it: (hi(r) << 12) | swz(lo(r)) (r < 2^31)
 __device__ __forceinline__ int32_t srht_pack_row(int32_t r) {
     return (int32_t)(((uint32_t)r >> kBlockLog << kBlockLog) | (uint32_t)swz(r & (kBlock - 1)));

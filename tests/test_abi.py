@@ -169,7 +169,8 @@ def test_backward_rejections(lib):
 
 
 def _problem(**kw):
-    base = dict(A=0x100000, m=1000, n=8, lda=1000, s=32, k=1, tls=0, seed=1, Vk=0x100000, sigk=0x100000, x=0)
+    base = dict(A=0x100000, m=1000, n=8, lda=1000, s=32, k=1, tls=0, seed=1, Vk=0x100000, sigk=0x100000, x=0,
+                dtype=_lib.NS_F64, reserved=0)
     base.update(kw)
     return _lib.Problem(**base)
 
@@ -179,7 +180,8 @@ def test_batched_rejections(lib):
     ok = (_lib.Problem * 1)(_problem())
     assert lib.ns_batched_workspace_size(ctypes.byref(d), 1, ok) > 0
     for bad in (dict(s=4), dict(s=2048), dict(m=4), dict(lda=999), dict(k=0), dict(k=9), dict(tls=1),
-                dict(tls=1, k=1, x=0), dict(A=0x100004), dict(A=0), dict(Vk=0)):
+                dict(tls=1, k=1, x=0), dict(A=0x100004), dict(A=0), dict(Vk=0), dict(dtype=2),
+                dict(dtype=_lib.NS_F32, A=0x100002)):
         arr = (_lib.Problem * 2)(_problem(), _problem(**bad))
         assert lib.ns_batched_workspace_size(ctypes.byref(d), 2, arr) == 0, bad
         assert lib.ns_solve_batched(ctypes.byref(d), 2, arr, FAKE, FAKE, FAKE, 1 << 30, None) == INV, bad
@@ -257,3 +259,15 @@ def test_sweep_limit_range(lib):
         assert st == INV
     d = _lib.SketchDesc(_lib.NS_SRHT, 8, 64, 1, _lib.NS_PREC_FP64, 1)
     assert lib.ns_workspace_size(ctypes.byref(d), 100, 4, 1) > 0
+
+
+def test_batched_fp32_problems_and_tuning(lib):
+    d32 = _lib.SketchDesc(_lib.NS_SRHT, 8, 32, 0, _lib.NS_PREC_FP32_STREAM, 0)
+    ok32 = (_lib.Problem * 1)(_problem(dtype=_lib.NS_F32, A=0x100004))  # 4-byte alignment suffices for FP32
+    assert lib.ns_batched_workspace_size(ctypes.byref(d32), 1, ok32) > 0
+    dg = _lib.SketchDesc(_lib.NS_GAUSSIAN, 8, 32, 0, _lib.NS_PREC_BF16X3, 0)
+    assert lib.ns_batched_workspace_size(ctypes.byref(dg), 1, ok32) == 0
+    assert lib.ns_batched_tuning(2, 4, 1) == 0
+    assert lib.ns_batched_tuning(0, 0, 0) == 0   # back to the defaults
+    for bad in ((-1, 0, 0), (65, 0, 0), (1, -2, 0), (1, 0, 99)):
+        assert lib.ns_batched_tuning(*bad) == INV

@@ -78,6 +78,78 @@ def test_batched_tls_benchmark_shapes(api):
         assert r_gpu <= (1 + 1e-10) * r_or + 10 * U53 * np.sqrt(Xb.shape[1]) * np.linalg.norm(Xb)
 
 
+def test_batched_fp32_stream_matches_oracle(api):
+    # FP32-stored [X b] through the FP32-stream sketch (FP32 butterflies and
+    # accumulation; QR and Jacobi in FP64), against the oracle's FP64 solve of
+    # the same FP32 data: the sketch noise (~2^-24 ||A|| per entry) is far below
+    # the TLS noise level (1e-3), so the residual matches the oracle's and x
+    # agrees to ~1e-4 relative
+    ms, ns = workloads.tls_batch_shapes(seed=7, batch=12, m_lo=2048, m_hi=40000, n_lo=8, n_hi=100)
+    rng = np.random.default_rng(17)
+    probs, host = [], []
+    for i, (m, n) in enumerate(zip(ms, ns)):
+        Xb, _ = workloads.tls_problem(rng, int(m), int(n))
+        Xb32 = Xb.astype(np.float32)
+        s = 2 * (int(n) + 1)
+        host.append((Xb32.astype(np.float64), s, 300 + i))
+        probs.append({"A": api.colmajor(Xb32, device="cuda"), "s": s, "k": 1, "seed": 300 + i, "tls": True})
+    outs, status, keep = api.ns_solve_batched(probs)
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    for (Xb, s, seed), (Vk, sk, x) in zip(host, outs):
+        x_or, v_or, st = O.tls(seed, s, Xb)
+        assert st == O.OK
+        v = Vk.cpu().numpy()
+        r_gpu, r_or = O.residual(Xb, v), O.residual(Xb, v_or[:, None])
+        assert r_gpu <= r_or * (1 + 1e-3)
+        assert np.linalg.norm(x.cpu().numpy() - x_or) <= 1e-4 * np.linalg.norm(x_or)
+
+
+def test_batched_tuning_keeps_the_bits(api):
+    # the launch knobs (panel width, persistent grid sizes) change the work
+    # distribution only: every setting gives the default's results bit for bit
+    ms, ns = workloads.tls_batch_shapes(seed=9, batch=40, m_lo=2048, m_hi=30000, n_lo=8, n_hi=90)
+    rng = np.random.default_rng(3)
+    probs = []
+    for i, (m, n) in enumerate(zip(ms, ns)):
+        Xb, _ = workloads.tls_problem(rng, int(m), int(n))
+        A = api.colmajor(Xb if i % 2 else Xb.astype(np.float32), device="cuda")   # FP64 and FP32 problems mixed
+        probs.append({"A": A, "s": 2 * (int(n) + 1), "k": 1, "seed": i, "tls": True})
+    ref, st0, _ = api.ns_solve_batched(probs, tuning={})
+    torch.cuda.synchronize()
+    ref = [[t.clone() for t in o] for o in ref]
+    for setting in ({"panel": 2}, {"panel": 4, "sketch_ctas_per_sm": 2}, {"panel": 3, "dense_ctas_per_sm": 1},
+                    {"panel": 1, "sketch_ctas_per_sm": 1, "dense_ctas_per_sm": 2}):
+        outs, st, _ = api.ns_solve_batched(probs, tuning=setting)
+        torch.cuda.synchronize()
+        assert torch.equal(st, st0)
+        for o, r in zip(outs, ref):
+            for a, b in zip(o, r):
+                assert torch.equal(a, b), setting
+    api.ns_solve_batched(probs[:1], tuning={})   # back to the defaults
+
+
+def test_autotuner_caches_a_setting_with_the_same_bits(api, tmp_path):
+    from paper_2206_00975_gb300 import autotune
+    ms, ns = workloads.tls_batch_shapes(seed=4, batch=48, m_lo=2048, m_hi=20000, n_lo=8, n_hi=64)
+    rng = np.random.default_rng(8)
+    probs = []
+    for i, (m, n) in enumerate(zip(ms, ns)):
+        Xb, _ = workloads.tls_problem(rng, int(m), int(n))
+        probs.append({"A": api.colmajor(Xb, device="cuda"), "s": 2 * (int(n) + 1), "k": 1, "seed": i, "tls": True})
+    path = str(tmp_path / "tuning.json")
+    ref, _, _ = api.ns_solve_batched(probs, tuning={})
+    torch.cuda.synchronize()
+    ref = [[t.clone() for t in o] for o in ref]
+    (outs, st, keep), setting = autotune.solve_batched_tuned(probs, cache_path=path)
+    torch.cuda.synchronize()
+    assert autotune.lookup(probs, cache_path=path) == setting
+    for o, r in zip(outs, ref):
+        for a, b in zip(o, r):
+            assert torch.equal(a, b)
+    api.ns_solve_batched(probs[:1], tuning={})
+
+
 def test_batched_general_problems(api):
     rng = np.random.default_rng(9)
     shapes = [(5000, 24, 96, 2), (300, 3, 8, 1), (4096, 32, 128, 4), (9000, 17, 40, 17), (70000, 40, 200, 3)]
