@@ -128,6 +128,35 @@ ns_status ns_sketch(const ns_sketch_desc *desc, const void *A, int32_t dtype, in
                     int64_t lda, double *SA, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * ns_sketch_rows -- the share of one row block of A in its sketch, for A split
+ * by rows across devices or streamed in row blocks (Section 1: A need only be
+ * read once, in any order; Section 5: a sketch is a sum over the rows of A):
+ * SA_p = S[:, o:o+m_p] A[o:o+m_p, :], with S the sketch of the whole m_total x n
+ * matrix.  The sum of the SA_p of blocks that cover rows 0..m_total-1 is
+ * ns_sketch's SA up to the rounding of the sum (exactly, for integer data).
+ * For the SRHT, H_{m'} = H_{m'/4096} (x) H_4096: the block is transformed in its
+ * 4096-row blocks with their global indices (rows of a block outside
+ * [o, o + m_p) count as zero); for the sparse sign, column j of S belongs to
+ * global row j.
+ *   desc      NS_SRHT (NS_PREC_FP64) or NS_SPARSE_SIGN (NS_PREC_FP64).
+ *   A_p       device, m_p x n FP64, column-major, leading dimension lda >= m_p:
+ *             rows o .. o + m_p - 1 of A (o = row_offset).
+ *   m_total   rows of the whole A (sets m' and the sketch's columns).
+ *   SA_p      device, s x n FP64 output, leading dimension s.
+ *   dev_status  device int32 or NULL: 0, or NS_ERR_NONFINITE.
+ *   ws        ns_sketch_rows_workspace_size(desc, m_total, row_offset, m_p, n)
+ *             bytes, 256-byte aligned.
+ * Errors: NS_ERR_INVALID_ARG for another kind or precision, row_offset < 0,
+ * m_p < 1, row_offset + m_p > m_total, n < 1, lda < m_p, SRHT s > m', or a
+ * NULL pointer; NS_ERR_WORKSPACE for a short workspace.
+ */
+size_t ns_sketch_rows_workspace_size(const ns_sketch_desc *desc, int64_t m_total, int64_t row_offset, int64_t m_p,
+                                     int64_t n);
+ns_status ns_sketch_rows(const ns_sketch_desc *desc, const void *A_p, int32_t dtype, int64_t m_total,
+                         int64_t row_offset, int64_t m_p, int64_t n, int64_t lda, double *SA_p, int32_t *dev_status,
+                         void *ws, size_t ws_bytes, void *stream);
+
+/*
  * ns_solve -- Algorithm 1 end to end: sketch, QR of SA, one-sided Jacobi SVD
  * of R, and W = V(:, n-k+1:n) (line 4).
  *   Vk    device, n x k FP64 output: the k trailing right singular vectors of

@@ -23,7 +23,7 @@ EXPORTS = [
     "ns_backward", "ns_residual", "ns_srht_meta", "ns_sparse_meta", "ns_sketch_static",
     "ns_batched_workspace_size", "ns_solve_batched", "ns_aaa_workspace_size", "ns_aaa_real",
     "ns_solve_sketched", "ns_solve_stats", "ns_sketched_stats", "ns_solve_eps", "ns_sketch_update",
-    "ns_test_bounded_wait", "ns_batched_tuning",
+    "ns_test_bounded_wait", "ns_batched_tuning", "ns_sketch_rows", "ns_sketch_rows_workspace_size",
 ]
 
 
@@ -83,6 +83,8 @@ def load():
         "ns_sketch_update": (ctypes.c_int, [D, i64, i32, i64, P, i64, P, P]),
         "ns_test_bounded_wait": (ctypes.c_int, [i32, i64, P, P, sz, P]),
         "ns_batched_tuning": (ctypes.c_int, [i32, i32, i32]),
+        "ns_sketch_rows_workspace_size": (sz, [D, i64, i64, i64, i64]),
+        "ns_sketch_rows": (ctypes.c_int, [D, P, i32, i64, i64, i64, i64, i64, P, P, P, sz, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

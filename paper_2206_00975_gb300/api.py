@@ -85,6 +85,27 @@ def ns_sketch(d, A, SA=None, ws=None, stream=None):
     return SA
 
 
+def ns_sketch_rows(d, A_p, row_offset, m_total, SA=None, status=None, ws=None, stream=None):
+    """The share S[:, o:o+m_p] A_p of the row block A_p = A[o:o+m_p, :] in the
+    sketch of the whole m_total-row A (s x n FP64, column-major); the shares of
+    blocks covering every row sum to ns_sketch's SA."""
+    m_p, n = A_p.shape
+    if SA is None:
+        SA = _empty_cm(d.s, n, A_p.device)
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=A_p.device)
+    lib = _lib.load()
+    if ws is None:
+        nbytes = int(lib.ns_sketch_rows_workspace_size(ctypes.byref(d), int(m_total), int(row_offset), m_p, n))
+        if nbytes == 0:
+            raise NSError(_lib.NS_ERR_INVALID_ARG, "ns_sketch_rows_workspace_size")
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=A_p.device)
+    st = lib.ns_sketch_rows(ctypes.byref(d), _p(A_p), _dtype_code(A_p), int(m_total), int(row_offset), m_p, n,
+                            _ld(A_p), _p(SA), _p(status), _p(ws), ws.numel(), _stream(stream))
+    _lib.check(st, "ns_sketch_rows")
+    return SA
+
+
 def ns_solve(d, A, k, save=True, status=None, ws=None, stream=None):
     """Algorithm 1: returns (Vk n x k, sigk k, save or None, status int32 tensor)."""
     m, n = A.shape

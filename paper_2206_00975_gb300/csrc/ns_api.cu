@@ -220,6 +220,53 @@ ns_status ns_sketch(const ns_sketch_desc *d, const void *A, int32_t dtype, int64
     return run_sketch(d, A, m, n, lda, SA, L, L.status_word, st);
 }
 
+static bool rows_ok(const ns_sketch_desc *d, int32_t dtype, int64_t m_total, int64_t o, int64_t m_p, int64_t n) {
+    if (!desc_ok(d) || d->prec != NS_PREC_FP64 || dtype != NS_F64) return false;
+    if (d->kind != NS_SRHT && d->kind != NS_SPARSE_SIGN) return false;
+    if (m_total < 1 || o < 0 || m_p < 1 || o + m_p > m_total || n < 1) return false;
+    if (d->kind == NS_SRHT && d->s > ((int64_t)1 << ceil_log2(m_total))) return false;
+    return true;
+}
+
+static size_t rows_layout(void *ws, const ns_sketch_desc *d, int64_t m_total, int64_t o, int64_t m_p, int64_t n,
+                          int32_t **status_word, SrhtWork *sw, SparseWork *pw) {
+    Carver c(ws);
+    *status_word = c.take<int32_t>(1);
+    if (d->kind == NS_SRHT) *sw = srht_rows_carve(c, m_total, o, o + m_p, n, d->s);
+    else *pw = sparse_carve(c, m_p, n, d->s, d->zeta);
+    return c.used;
+}
+
+size_t ns_sketch_rows_workspace_size(const ns_sketch_desc *d, int64_t m_total, int64_t o, int64_t m_p, int64_t n) {
+    if (!d || !rows_ok(d, NS_F64, m_total, o, m_p, n)) return 0;
+    int32_t *sw_;
+    SrhtWork a;
+    SparseWork b;
+    return rows_layout(nullptr, d, m_total, o, m_p, n, &sw_, &a, &b);
+}
+
+ns_status ns_sketch_rows(const ns_sketch_desc *d, const void *A_p, int32_t dtype, int64_t m_total, int64_t o,
+                         int64_t m_p, int64_t n, int64_t lda, double *SA_p, int32_t *dev_status, void *ws,
+                         size_t ws_bytes, void *stream) {
+    if (!d || !A_p || !SA_p || !ws || !rows_ok(d, dtype, m_total, o, m_p, n) || lda < m_p) return NS_ERR_INVALID_ARG;
+    if ((((uintptr_t)ws) & 255) != 0 || (((uintptr_t)A_p) & 7) != 0) return NS_ERR_INVALID_ARG;
+    int32_t *status_word;
+    SrhtWork sw{nullptr, nullptr, nullptr};
+    SparseWork pw{nullptr, nullptr, nullptr};
+    if (rows_layout(ws, d, m_total, o, m_p, n, &status_word, &sw, &pw) > ws_bytes) return NS_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *status = dev_status ? dev_status : status_word;
+    if (cudaMemsetAsync(status, 0, sizeof(int32_t), st) != cudaSuccess) return NS_ERR_CUDA;
+    if (d->kind == NS_SPARSE_SIGN)
+        return cuda_status(
+            launch_sparse_f64(d->seed, (const double *)A_p, m_p, n, lda, d->s, d->zeta, pw, SA_p, status, st, o));
+    const SrhtRowsGeom g = srht_rows_geom(m_total, o, o + m_p, n);
+    if (launch_srht_meta(d->seed, g.lg, g.sign_words, d->s, sw.sign_words, sw.rows, st) != cudaSuccess)
+        return NS_ERR_CUDA;
+    return cuda_status(launch_srht_f64_rows((const double *)A_p, m_total, o, o + m_p, n, lda, d->s, sw, SA_p, status,
+                                            st));
+}
+
 ns_status ns_solve(const ns_sketch_desc *d, const void *A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
                    int32_t k, double *Vk, double *sigk, double *save, int32_t *dev_status, void *ws, size_t ws_bytes,
                    void *stream) {

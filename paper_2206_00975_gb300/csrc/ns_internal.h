@@ -59,6 +59,19 @@ struct SrhtWork {
 size_t srht_work_bytes(int64_t m, int64_t n, int64_t s);
 SrhtWork srht_carve(Carver &c, int64_t m, int64_t n, int64_t s);
 
+// SRHT of a row window [lo, hi) of A (the partial sketch of a row block):
+// global blocks b0 .. b_end - 1 in nchunk chunks of `chunk` blocks
+struct SrhtRowsGeom {
+    int lg;
+    int64_t b0, b_end;
+    int chunk;
+    int64_t nchunk;
+    int fx_bits;
+    int64_t sign_words;
+};
+SrhtRowsGeom srht_rows_geom(int64_t m_total, int64_t lo, int64_t hi, int64_t n);
+SrhtWork srht_rows_carve(Carver &c, int64_t m_total, int64_t lo, int64_t hi, int64_t n, int64_t s);
+
 // launches (return cudaGetLastError())
 cudaError_t launch_srht_meta(uint64_t seed, int lg, int64_t nsign_words, int64_t s, uint32_t *sign_words,
                              int32_t *rows, cudaStream_t st);
@@ -67,6 +80,8 @@ cudaError_t launch_srht_f64(const double *A, int64_t m, int64_t n, int64_t lda, 
 cudaError_t launch_srht_f32(const float *A, int64_t m, int64_t n, int64_t lda, int64_t s, const SrhtWork &w,
                             double *SA, int32_t *status, cudaStream_t st);
 // SA[t, c] = scale * sum over nchunk partials (chunk-major, s x n each), in chunk order
+cudaError_t launch_srht_f64_rows(const double *A_p, int64_t m_total, int64_t lo, int64_t hi, int64_t n, int64_t lda,
+                                 int64_t s, const SrhtWork &w, double *SA_p, int32_t *status, cudaStream_t st);
 cudaError_t launch_srht_reduce(const double *partial, int64_t n, int64_t s, int64_t nchunk, double scale, double *SA,
                                cudaStream_t st);
 
@@ -115,8 +130,10 @@ SparseGeom sparse_geom(int64_t m, int64_t n, int64_t s, int zeta);
 SparseWork sparse_carve(Carver &c, int64_t m, int64_t n, int64_t s, int zeta);
 cudaError_t launch_sparse_meta(uint64_t seed, int64_t s, int zeta, int64_t m, int32_t *rows, int8_t *signs,
                                cudaStream_t st);
+// j0: global index of row 0 of A (the columns of S follow the global row index;
+// a row block [j0, j0 + m) gives its partial sketch)
 cudaError_t launch_sparse_f64(uint64_t seed, const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, int zeta,
-                              const SparseWork &w, double *SA, int32_t *status, cudaStream_t st);
+                              const SparseWork &w, double *SA, int32_t *status, cudaStream_t st, int64_t j0 = 0);
 
 struct BackwardWork {
     uint32_t *sign_words;

@@ -84,7 +84,7 @@ __global__ void sparse_meta_kernel(uint64_t seed, int64_t s, int zeta, int64_t m
 // first entry of bucket b, offsets[tile][nbucket] = nent
 __global__ void __launch_bounds__(256) sparse_bucket_kernel(uint64_t seed, int64_t s, int zeta, int64_t m,
                                                             int64_t nent, int64_t nbucket, uint32_t *entries,
-                                                            int32_t *offsets) {
+                                                            int32_t *offsets, int64_t j0) {
     extern __shared__ int32_t cnt[];  // nbucket + 1
     __shared__ uint32_t keys[kSpTile * 64];
     const int64_t tile = blockIdx.x;
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) sparse_bucket_kernel(uint64_t seed, int64
         if (j >= m) continue;
         int32_t r[64];
         int8_t g[64];
-        sparse_column(seed, s, zeta, j, r, g);
+        sparse_column(seed, s, zeta, j0 + j, r, g);  // column j0 + j of S (global row index)
         for (int i = 0; i < zeta; ++i) {
             const uint32_t key = ((uint32_t)r[i] << 8) | ((uint32_t)jl << 1) | (g[i] < 0 ? 1u : 0u);
             keys[jl * zeta + i] = key;
@@ -280,11 +280,11 @@ cudaError_t launch_sparse_meta(uint64_t seed, int64_t s, int zeta, int64_t m, in
 }
 
 cudaError_t launch_sparse_f64(uint64_t seed, const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, int zeta,
-                              const SparseWork &w, double *SA, int32_t *status, cudaStream_t st) {
+                              const SparseWork &w, double *SA, int32_t *status, cudaStream_t st, int64_t j0) {
     const SparseGeom g = sparse_geom(m, n, s, zeta);
     const size_t bsmem = sizeof(int32_t) * (size_t)(g.nbucket + 1);
     sparse_bucket_kernel<<<(unsigned)g.ntile, 256, bsmem, st>>>(seed, s, zeta, m, g.nent, g.nbucket, w.entries,
-                                                                w.offsets);
+                                                                w.offsets, j0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = sizeof(long long) * (size_t)(kSpGroup * kSpCols + kSpCols * kSpTileStride) +

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(128, 4) srht_f64_chunk128_kernel(const double 
                                                             int P, const uint32_t *__restrict__ sign_words,
                                                             const int32_t *__restrict__ rows,
                                                             double *__restrict__ partial, int32_t *status,
-                                                            int vec_ok) {
+                                                            int vec_ok, int64_t lo, int64_t b0, int64_t b_end) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     long long *Zs = (long long *)smem_raw;                       // 4096
     long long *acc = Zs + kBlock;                                // s
@@ -108,9 +108,13 @@ __global__ void __launch_bounds__(128, 4) srht_f64_chunk128_kernel(const double 
 
     int Erun = 0;  // running biased exponent of the chunk (0: none yet)
     int nonfinite = 0;
-    for (int bl = 0; bl < chunk; ++bl)
-        srht_f64_block128(Acol, m, s, ch * chunk + bl, P, sign_words, rows_s, Zs, acc, sgn, red, vec_ok, Erun,
-                       nonfinite, bl + 1 < chunk);
+    // blocks b0 + ch * chunk + bl of the column (global block indices), up to b_end
+    for (int bl = 0; bl < chunk; ++bl) {
+        const int64_t b = b0 + ch * chunk + bl;
+        if (b >= b_end) break;
+        srht_f64_block128(Acol, m, s, b, P, sign_words, rows_s, Zs, acc, sgn, red, vec_ok, Erun, nonfinite,
+                          bl + 1 < chunk && b + 1 < b_end, lo);
+    }
     // chunk partial in FP64: value = acc * 2^(E - 1022 - P)
     const double scale = ldexp(1.0, Erun - 1022 - P);
     double *out = partial + (ch * n + c) * s;
@@ -403,13 +407,68 @@ cudaError_t launch_srht_f64(const double *A, int64_t m, int64_t n, int64_t lda, 
     const int vec_ok = ((((uintptr_t)A) & 15) == 0 && (lda & 1) == 0) ? 1 : 0;
     const int64_t items = n * g.nchunk;
     srht_f64_chunk128_kernel<<<(unsigned)items, 128, smem, st>>>(A, m, n, lda, s, g.chunk, g.nchunk, g.fx_bits,
-                                                                 w.sign_words, w.rows, w.partial, status, vec_ok);
+                                                                 w.sign_words, w.rows, w.partial, status, vec_ok,
+                                                                 0, 0, g.nblk);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int threads = 256;
     const int64_t blocks = (n * s + threads - 1) / threads;
     srht_reduce_kernel<<<(unsigned)blocks, threads, 0, st>>>(w.partial, n, s, g.nchunk, 1.0 / std::sqrt((double)s),
                                                             SA);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- row window ----
+// The partial sketch of rows [lo, hi) of A (A_p points at row lo): the blocks
+// that overlap the window, with global block indices (so the signs of D and
+// the row parities of H are the whole sketch's), grouped into chunks as for a
+// whole column; rows outside the window count as zero.  Summing the partials of
+// windows that cover [0, m) gives the whole sketch up to the FP64 rounding of
+// the chunk sums (exactly, on integer data).
+SrhtRowsGeom srht_rows_geom(int64_t m_total, int64_t lo, int64_t hi, int64_t n) {
+    SrhtRowsGeom g;
+    g.lg = ceil_log2(m_total);
+    const int64_t mp = (int64_t)1 << g.lg;
+    g.b0 = lo / kBlock;
+    g.b_end = mp > kBlock ? (hi + kBlock - 1) / kBlock : 1;
+    const int64_t nb = g.b_end - g.b0;
+    int64_t want = (nb * n) / 2048;
+    int chunk = 1;
+    while (chunk * 2 <= want && chunk * 2 <= kMaxChunkBlocks) chunk *= 2;
+    while (chunk > 1 && chunk > nb) chunk /= 2;
+    g.chunk = chunk;
+    g.nchunk = (nb + chunk - 1) / chunk;
+    g.fx_bits = 63 - kBlockLog - ceil_log2(chunk) - 1;
+    g.sign_words = (mp > kBlock ? mp : kBlock) / 32;
+    return g;
+}
+
+SrhtWork srht_rows_carve(Carver &c, int64_t m_total, int64_t lo, int64_t hi, int64_t n, int64_t s) {
+    const SrhtRowsGeom g = srht_rows_geom(m_total, lo, hi, n);
+    SrhtWork w;
+    w.sign_words = c.take<uint32_t>((size_t)g.sign_words);
+    w.rows = c.take<int32_t>((size_t)s);
+    w.partial = c.take<double>((size_t)(g.nchunk * n * s));
+    return w;
+}
+
+cudaError_t launch_srht_f64_rows(const double *A_p, int64_t m_total, int64_t lo, int64_t hi, int64_t n, int64_t lda,
+                                 int64_t s, const SrhtWork &w, double *SA_p, int32_t *status, cudaStream_t st) {
+    const SrhtRowsGeom g = srht_rows_geom(m_total, lo, hi, n);
+    const size_t smem = srht_f64_smem(s);
+    cudaError_t e = cudaFuncSetAttribute(srht_f64_chunk128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    // whole blocks are loaded with 16-byte loads when global row lo sits on a
+    // 16-byte boundary of the row block's storage
+    const int vec_ok = ((((uintptr_t)A_p) & 15) == 0 && (lda & 1) == 0 && (lo & 1) == 0) ? 1 : 0;
+    const int64_t items = n * g.nchunk;
+    srht_f64_chunk128_kernel<<<(unsigned)items, 128, smem, st>>>(A_p, hi, n, lda, s, g.chunk, g.nchunk, g.fx_bits,
+                                                                 w.sign_words, w.rows, w.partial, status, vec_ok, lo,
+                                                                 g.b0, g.b_end);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    srht_reduce_kernel<<<(unsigned)((n * s + 255) / 256), 256, 0, st>>>(w.partial, n, s, g.nchunk,
+                                                                        1.0 / std::sqrt((double)s), SA_p);
     return cudaGetLastError();
 }
 

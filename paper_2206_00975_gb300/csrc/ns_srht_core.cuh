@@ -162,23 +162,30 @@ __device__ __forceinline__ void fwht32(long long (&z)[32]) {
 // srht_block128_core runs the load, the quantisation at Erun (rescaling
 // acc[0..s) when Erun grows) and all 12 levels, and returns Z_b in registers
 // in layout C; the shared-memory reads are complete on return.
+//
+// Row window: the column holds global rows [lo, m) of the padded column and
+// Acol points at global row lo (lo = 0 for a whole column); rows outside the
+// window read as zero, and b is the global block index (the signs of D and
+// the row parities of H follow it).  A row block of A sketched this way gives
+// its partial sum S[:, lo:m] A[lo:m, :] of the whole sketch.
 __device__ __forceinline__ int layout_c(int t, int k) { return (t & 63) | (k << 6) | ((t >> 6) << 11); }
 
 __device__ __forceinline__ void srht_block128_core(const double *__restrict__ Acol, int64_t m, int64_t s, int64_t b,
                                                    int P, const uint32_t *__restrict__ sign_words, long long *Zs,
                                                    long long *acc, uint32_t *sgn, int *red, int vec_ok, int &Erun,
-                                                   int &nonfinite, bool prefetch_next, long long (&z)[32]) {
+                                                   int &nonfinite, bool prefetch_next, long long (&z)[32],
+                                                   int64_t lo = 0) {
     const int t = threadIdx.x, lane = t & 31;
     const int64_t base = b * kBlock;
+    const double *Ab = Acol + (base - lo);  // global row base (not dereferenced below lo)
     sgn[t] = sign_words[(base >> 5) + t];
-    if (t == 0 && prefetch_next && vec_ok && base + 2 * kBlock <= m)  // the next block, into L2
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(Acol + base + kBlock),
-                     "r"((uint32_t)(kBlock * 8))
+    if (t == 0 && prefetch_next && vec_ok && base >= lo && base + 2 * kBlock <= m)  // the next block, into L2
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(Ab + kBlock), "r"((uint32_t)(kBlock * 8))
                      : "memory");
-    if (vec_ok && base + kBlock <= m) {
+    if (vec_ok && base >= lo && base + kBlock <= m) {
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
-            const double2 v = __ldcs((const double2 *)(Acol + base + 2 * t + 256 * kk));
+            const double2 v = __ldcs((const double2 *)(Ab + 2 * t + 256 * kk));
             z[2 * kk] = __double_as_longlong(v.x);
             z[2 * kk + 1] = __double_as_longlong(v.y);
         }
@@ -186,8 +193,8 @@ __device__ __forceinline__ void srht_block128_core(const double *__restrict__ Ac
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
             const int64_t i0 = base + 2 * t + 256 * kk;
-            z[2 * kk] = (i0 < m) ? __double_as_longlong(__ldcs(Acol + i0)) : 0;
-            z[2 * kk + 1] = (i0 + 1 < m) ? __double_as_longlong(__ldcs(Acol + i0 + 1)) : 0;
+            z[2 * kk] = (i0 >= lo && i0 < m) ? __double_as_longlong(__ldcs(Acol + (i0 - lo))) : 0;
+            z[2 * kk + 1] = (i0 + 1 >= lo && i0 + 1 < m) ? __double_as_longlong(__ldcs(Acol + (i0 + 1 - lo))) : 0;
         }
     }
     unsigned int hmax = 0x00100000u;  // biased exponent 1
@@ -264,10 +271,11 @@ __device__ __forceinline__ void srht_f64_block128(const double *__restrict__ Aco
                                                   int P, const uint32_t *__restrict__ sign_words,
                                                   const int32_t *rows_s, long long *Zs, long long *acc,
                                                   uint32_t *sgn, int *red, int vec_ok, int &Erun, int &nonfinite,
-                                                  bool prefetch_next) {
+                                                  bool prefetch_next, int64_t lo = 0) {
     const int t = threadIdx.x;
     long long z[32];
-    srht_block128_core(Acol, m, s, b, P, sign_words, Zs, acc, sgn, red, vec_ok, Erun, nonfinite, prefetch_next, z);
+    srht_block128_core(Acol, m, s, b, P, sign_words, Zs, acc, sgn, red, vec_ok, Erun, nonfinite, prefetch_next, z,
+                       lo);
 #pragma unroll
     for (int k = 0; k < 32; ++k) Zs[swz(layout_c(t, k))] = z[k];
     __syncthreads();

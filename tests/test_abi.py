@@ -271,3 +271,18 @@ def test_batched_fp32_problems_and_tuning(lib):
     assert lib.ns_batched_tuning(0, 0, 0) == 0   # back to the defaults
     for bad in ((-1, 0, 0), (65, 0, 0), (1, -2, 0), (1, 0, 99)):
         assert lib.ns_batched_tuning(*bad) == INV
+
+
+def test_sketch_rows_rejections(lib):
+    rows = lambda dd, m_total=1000, o=0, m_p=100, lda=100, A=FAKE, nb=1 << 30: lib.ns_sketch_rows(  # noqa: E731
+        ctypes.byref(dd), A, _lib.NS_F64, m_total, o, m_p, 4, lda, FAKE, None, FAKE, nb, None)
+    d = _desc(s=64)
+    assert lib.ns_sketch_rows_workspace_size(ctypes.byref(d), 1000, 0, 100, 4) > 0
+    assert rows(d, o=950) == INV                      # beyond m_total
+    assert rows(d, o=-1) == INV
+    assert rows(d, m_p=0) == INV
+    assert rows(d, lda=99) == INV
+    assert rows(_desc(s=64, kind=_lib.NS_HRHT)) == INV
+    assert rows(_desc(s=64, kind=_lib.NS_GAUSSIAN, prec=_lib.NS_PREC_BF16X3)) == INV
+    assert rows(_desc(s=2048)) == INV                 # SRHT s > m' = 1024
+    assert rows(d, nb=16) == WSP

@@ -97,3 +97,67 @@ def test_reference_arm_runs_on_rank_zero_only():
 
     # a rank other than 0 returns at once: no workload, no oracle
     assert bench.run_reference(Args(), 1, 2) is None
+
+
+
+class _Desc:
+    def __init__(self, kind, s, seed, zeta=8):
+        self.kind, self.s, self.seed, self.zeta = kind, s, seed, zeta
+
+
+def _sharded_rank(rank, world, port, kind, out):
+    """One gloo rank of the row-sharded sketch: its rows' share computed by the
+    oracle (the sketch of A with every row outside the rank's block zeroed),
+    then the host driver's sum all-reduce."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import oracle
+    from paper_2206_00975_gb300 import sharded
+    m, n, s, seed = 3 * 4096 + 777, 5, 96, 11
+    A = np.random.default_rng(4).integers(-9, 10, size=(m, n)).astype(np.float64)
+    o, rows = sharded.row_partition(m, world)[rank]
+
+    def share(d, A_loc, off, m_total, SA):
+        Az = np.zeros((m_total, A_loc.shape[1]))
+        Az[off:off + A_loc.shape[0]] = A_loc.numpy()
+        part = oracle.sketch(d.kind, d.seed, d.s, Az, zeta=d.zeta)
+        SA.copy_(torch.from_numpy(part))
+        return SA
+    d = _Desc(kind, s, seed)
+    SA = sharded.sharded_sketch(d, torch.from_numpy(np.asfortranarray(A[o:o + rows])), o, m, sketch_rows=share)
+    full = oracle.sketch(kind, seed, s, A)
+    out.put((rank, o, rows, float(np.max(np.abs(SA.numpy() - full))), float(np.max(np.abs(full)))))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("kind", [0, 1])   # SRHT, sparse sign
+def test_row_sharded_sketch_over_gloo(kind):
+    # two ranks, each with its block of rows (block-aligned boundary), one sum
+    # all-reduce of the s x n shares: every rank ends with the whole sketch
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sharded_rank, args=(r, 2, port, kind, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(out.get(timeout=180) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [g[:3] for g in got] == [(0, 0, 2 * 4096), (1, 2 * 4096, 4096 + 777)]
+    for g in got:   # integer data: the shares add up to the sketch up to the scale's rounding
+        assert g[3] <= 1e-13 * g[4]
+
+
+def test_row_partition_covers_the_rows_on_block_boundaries():
+    sys.path.insert(0, ROOT)
+    from paper_2206_00975_gb300 import sharded
+    for m, world in ((1 << 20, 4), (3 * 4096 + 5, 2), (1000, 3), (5 * 4096, 8)):
+        parts = sharded.row_partition(m, world)
+        assert len(parts) == world
+        assert parts[0][0] == 0 and sum(r for _, r in parts) == m
+        for (o, r), (o2, _) in zip(parts, parts[1:]):
+            assert o + r == o2 and o2 % 4096 == 0 or o2 == m
