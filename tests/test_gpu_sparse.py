@@ -39,8 +39,13 @@ def test_sparse_meta_bitexact(api, m, s, zeta, seed):
     assert np.array_equal(signs.cpu().numpy(), g_or)
 
 
+# s <= 1024 with zeta <= 8 takes the gather form (target-sorted 512-row chunks,
+# register accumulators, 16 columns per CTA); larger s or zeta the scatter form.
+# The gather cases include ragged row and column counts, several chunk ranges
+# per column group, and the three register-tile sizes (s <= 256, 512, 1024).
 SHAPES = [(1, 1, 1, 1), (100, 3, 16, 4), (1000, 33, 300, 8), (5000, 64, 256, 8), (9999, 17, 1000, 8),
-          ((1 << 16) + 3, 40, 512, 8), ((1 << 18), 2, 2048, 8), (3000, 5, 70, 13)]
+          ((1 << 16) + 3, 40, 512, 8), ((1 << 18), 2, 2048, 8), (3000, 5, 70, 13),
+          ((1 << 17) + 333, 17, 1024, 8), (70001, 33, 513, 8), (40000, 5, 257, 4), (511, 16, 64, 8)]
 
 
 @pytest.mark.parametrize("m,n,s,zeta", SHAPES)
@@ -53,7 +58,19 @@ def test_sparse_sketch_parity(api, m, n, s, zeta):
     assert np.max(np.abs(SA - ref)) <= 1e-12 * np.linalg.norm(A)
 
 
-@pytest.mark.parametrize("m,n,s", [(3000, 7, 128), ((1 << 15) + 11, 3, 1024)])
+def test_sparse_odd_leading_dimension(api):
+    # lda odd: the staged copies fall back from 16-byte to 8-byte pieces
+    rng = np.random.default_rng(41)
+    m, n, s, ld = 20001, 19, 512, 20003
+    A = rng.standard_normal((m, n))
+    buf = torch.zeros((n, ld), dtype=torch.float64, device="cuda")
+    buf[:, :m] = torch.as_tensor(A.T.copy(), device="cuda")
+    d = api.desc(api.NS_SPARSE_SIGN, s=s, seed=6, zeta=8)
+    SA = api.ns_sketch(d, buf.t()[:m, :]).cpu().numpy()
+    assert np.max(np.abs(SA - O.sparse_sign(6, s, 8, A))) <= 1e-12 * np.linalg.norm(A)
+
+
+@pytest.mark.parametrize("m,n,s", [(3000, 7, 128), ((1 << 15) + 11, 3, 1024), (50000, 21, 600)])
 def test_sparse_integer_inputs_bitexact(api, m, n, s):
     rng = np.random.default_rng(m)
     A = rng.integers(-1000, 1001, size=(m, n)).astype(np.float64)
