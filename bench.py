@@ -441,6 +441,37 @@ def batched_leg(torch, api, dev, timer):
     return res
 
 
+def row_sharded_leg(torch, api, dev, dist, rank, world, args):
+    """One A (the headline workload, the same seed on every rank) split by rows
+    across the ranks: each rank forms its block's share of the SRHT sketch
+    (ns_sketch_rows), one NCCL sum all-reduce of the s x n shares gives every
+    rank the whole sketch, and every rank runs the dense stage.  One solve per
+    step for the whole job (strong scaling of the sketch)."""
+    from paper_2206_00975_gb300 import sharded
+    w = make_workload(SEED)
+    o, rows = sharded.row_partition(M, world)[rank]
+    A_blk = torch.from_numpy(np.ascontiguousarray(w["A"][o:o + rows].T)).to(dev).t()
+    del w
+    d = api.desc(api.NS_SRHT, s=S, seed=SEED)
+    ws_r = api.sketch_rows_workspace(d, M, o, max(rows, 1), N, dev)
+    ws_d = api.workspace(d, M, N, K_NULL, dev)
+    SA = api._empty_cm(S, N, dev)
+
+    def step():
+        sharded.sharded_sketch(d, A_blk, o, M, SA=SA, ws=ws_r)
+        return api.ns_solve_sketched(d, SA, K_NULL, ws=ws_d)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    timer = Timer(torch, torch.cuda.current_stream(), dist, dev)
+    ms = timer(step, args.steps)
+    Vk, sk, _, st = step()
+    torch.cuda.synchronize()
+    return {"solves_per_s": args.steps / (ms / 1e3), "ms_per_solve": ms / args.steps, "rows_per_rank": rows,
+            "scaling": "strong", "collective": "one NCCL all-reduce (sum) of the s x n FP64 shares per solve",
+            "status": int(st.item()), "sigma_k": [float(x) for x in sk.cpu()]}
+
+
 def hrht_moved_bytes(m, n, s):
     """DRAM bytes the two-pass H-RHT moves per sketch: A read once, the
     transformed blocks (int64, m' x n) written by pass 1 and read by pass 2,
@@ -730,6 +761,8 @@ def main():
         "gpu_launches": launches_per_solve(stats) * args.steps,
         "clocks": clocks,
     }
+    if world > 1:
+        line["row_sharded"] = row_sharded_leg(torch, api, dev, dist, rank, world, args)
     if rank == 0 and n_ranks == 1 and not args.no_configs:
         line["configs"] = config_legs(torch, api, dev, Timer(torch, stream, None, dev), hbm_peak, bf16_peak,
                                       fp64_peak)

@@ -85,6 +85,15 @@ def ns_sketch(d, A, SA=None, ws=None, stream=None):
     return SA
 
 
+def sketch_rows_workspace(d, m_total, row_offset, m_p, n, device="cuda"):
+    """Workspace tensor for ns_sketch_rows of rows [row_offset, row_offset + m_p)."""
+    nbytes = int(_lib.load().ns_sketch_rows_workspace_size(ctypes.byref(d), int(m_total), int(row_offset),
+                                                           int(m_p), int(n)))
+    if nbytes == 0:
+        raise NSError(_lib.NS_ERR_INVALID_ARG, "ns_sketch_rows_workspace_size")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
 def ns_sketch_rows(d, A_p, row_offset, m_total, SA=None, status=None, ws=None, stream=None):
     """The share S[:, o:o+m_p] A_p of the row block A_p = A[o:o+m_p, :] in the
     sketch of the whole m_total-row A (s x n FP64, column-major); the shares of
@@ -96,10 +105,7 @@ def ns_sketch_rows(d, A_p, row_offset, m_total, SA=None, status=None, ws=None, s
         status = torch.zeros(1, dtype=torch.int32, device=A_p.device)
     lib = _lib.load()
     if ws is None:
-        nbytes = int(lib.ns_sketch_rows_workspace_size(ctypes.byref(d), int(m_total), int(row_offset), m_p, n))
-        if nbytes == 0:
-            raise NSError(_lib.NS_ERR_INVALID_ARG, "ns_sketch_rows_workspace_size")
-        ws = torch.empty(nbytes, dtype=torch.uint8, device=A_p.device)
+        ws = sketch_rows_workspace(d, m_total, row_offset, m_p, n, A_p.device)
     st = lib.ns_sketch_rows(ctypes.byref(d), _p(A_p), _dtype_code(A_p), int(m_total), int(row_offset), m_p, n,
                             _ld(A_p), _p(SA), _p(status), _p(ws), ws.numel(), _stream(stream))
     _lib.check(st, "ns_sketch_rows")

@@ -127,19 +127,6 @@ struct SparseWork {
     double *partial;
 };
 SparseGeom sparse_geom(int64_t m, int64_t n, int64_t s, int zeta);
-// gather form of the sparse-sign sketch (s <= 1024, zeta <= 8): 512-row chunks
-// with target-sorted records, CTAs over (16-column group, range of chunks)
-struct SparseGatherGeom {
-    int64_t nchunk;     // 512-row chunks
-    int64_t rec_words;  // uint32 words per chunk record
-    int64_t ncolgrp;    // 16-column groups
-    int64_t nrange;     // chunk ranges (one FP64 partial each)
-    int64_t cpr;        // chunks per range
-    int fx_bits;        // fixed-point magnitude bits P
-    int rt;             // targets per thread (s <= 32 rt)
-};
-bool sparse_gather_applies(int64_t s, int zeta);
-SparseGatherGeom sparse_gather_geom(int64_t m, int64_t n, int64_t s, int zeta);
 SparseWork sparse_carve(Carver &c, int64_t m, int64_t n, int64_t s, int zeta);
 cudaError_t launch_sparse_meta(uint64_t seed, int64_t s, int zeta, int64_t m, int32_t *rows, int8_t *signs,
                                cudaStream_t st);

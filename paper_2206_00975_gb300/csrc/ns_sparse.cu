@@ -22,18 +22,6 @@
 //   3. one FP64 partial per chunk is summed over chunks in a fixed order.
 // Integer addition is exact and associative, so the result does not depend on
 // the order of the updates.
-//
-// Gather form (s <= 1024, zeta <= 8: the benchmark's shapes).  The scatter
-// above reads and writes a shared-memory accumulator for every (entry, column)
-// pair.  The gather form sorts each 512-row chunk's entries by target row and
-// sign once (sparse_chunk_meta_kernel), and keeps the accumulators in
-// registers: a CTA of 16 warps owns 16 columns and a range of chunks; half
-// warp h of warp w owns the targets 2w + h + 32 q (lane = column), and for
-// each target adds its chunk entries' quantised values, read from a swizzled
-// row-major tile in shared memory (one conflict-free 128-byte row per half
-// warp and entry).  The FP64 tiles of the next chunk are in flight (cp.async,
-// double-buffered) while the current chunk is gathered.  Shared-memory traffic
-// is one 8-byte read per (entry, column) pair instead of a read-modify-write.
 #include <cmath>
 #include "ns_device.cuh"
 #include "ns_internal.h"
@@ -48,8 +36,6 @@ constexpr int kSpGroup = 1024;    // target rows per accumulator
 constexpr int kSpThreads = kSpWarps * 32;
 constexpr int kSpTileStride = 2 * kSpTile + 1;  // per column: +v, -v of each row, padded (conflict-free reads)
 constexpr int kSpMaxEntPerThread = kSpTile * 64 / kSpThreads;  // zeta <= 64
-
-bool sparse_gather_applies(int64_t s, int zeta);
 
 SparseGeom sparse_geom(int64_t m, int64_t n, int64_t s, int zeta) {
     SparseGeom g;
@@ -72,15 +58,8 @@ SparseGeom sparse_geom(int64_t m, int64_t n, int64_t s, int zeta) {
 }
 
 SparseWork sparse_carve(Carver &c, int64_t m, int64_t n, int64_t s, int zeta) {
-    SparseWork w;
-    if (sparse_gather_applies(s, zeta)) {  // gather form: sorted chunk records, one partial per range
-        const SparseGatherGeom g = sparse_gather_geom(m, n, s, zeta);
-        w.entries = c.take<uint32_t>((size_t)(g.nchunk * g.rec_words));
-        w.offsets = nullptr;
-        w.partial = c.take<double>((size_t)(g.nrange * n * s));
-        return w;
-    }
     SparseGeom g = sparse_geom(m, n, s, zeta);
+    SparseWork w;
     w.entries = c.take<uint32_t>((size_t)(g.ntile * g.nent));
     w.offsets = c.take<int32_t>((size_t)(g.ntile * (g.nbucket + 1)));
     w.partial = c.take<double>((size_t)(g.nchunk * n * s));
@@ -294,262 +273,6 @@ __global__ void chunk_reduce_kernel(const double *__restrict__ partial, int64_t 
     SA[t + c * s] = a * scale;
 }
 
-// ------------------------------------------------------------ gather form ----
-constexpr int kGT = 512;          // rows of A per chunk
-constexpr int kGC = 16;           // columns per CTA (lane % 16)
-constexpr int kGThreads = 512;    // 16 warps: 32 half warps own the targets
-constexpr int kGMaxS = 1024;
-constexpr int kGMaxZeta = 8;      // entries per chunk <= 4096 (12-bit start)
-constexpr int kGRawStride = kGT + 2;  // doubles per staged column (16-byte padding against bank conflicts)
-
-bool sparse_gather_applies(int64_t s, int zeta) { return s >= 1 && s <= kGMaxS && zeta >= 1 && zeta <= kGMaxZeta; }
-
-SparseGatherGeom sparse_gather_geom(int64_t m, int64_t n, int64_t s, int zeta) {
-    SparseGatherGeom g;
-    g.nchunk = (m + kGT - 1) / kGT;
-    const int64_t rec_bytes = ((4 * s + 2 * (int64_t)kGT * zeta) + 15) / 16 * 16;
-    g.rec_words = rec_bytes / 4;
-    g.ncolgrp = (n + kGC - 1) / kGC;
-    int64_t want = (2 * (int64_t)device_sm_count() + g.ncolgrp - 1) / g.ncolgrp;  // about two CTAs per SM
-    if (want < 1) want = 1;
-    if (want > g.nchunk) want = g.nchunk;
-    g.cpr = (g.nchunk + want - 1) / want;
-    g.nrange = (g.nchunk + g.cpr - 1) / g.cpr;
-    g.fx_bits = 62 - ceil_log2(g.cpr * kGT);  // each target takes at most one entry per row
-    if (g.fx_bits > 52) g.fx_bits = 52;
-    g.rt = s <= 256 ? 8 : s <= 512 ? 16 : 32;
-    return g;
-}
-
-// One CTA per 512-row chunk: the chunk's (target, row, sign) entries sorted by
-// target and, within a target, positive signs first.  Record layout: s words
-// (start << 20 | positives << 10 | negatives), then the entries' local rows as
-// 16-bit words.  (The order inside a (target, sign) group is irrelevant: the
-// gather adds integers.)
-__global__ void __launch_bounds__(kGT) sparse_chunk_meta_kernel(uint64_t seed, int64_t s, int zeta, int64_t m,
-                                                                int64_t rec_words, uint32_t *recs, int64_t j0) {
-    __shared__ uint32_t cnt[2 * kGMaxS];
-    __shared__ uint32_t pos[2 * kGMaxS];
-    __shared__ uint32_t wsum[kGT / 32];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int64_t chunk = blockIdx.x, j = chunk * kGT + tid;
-    for (int i = tid; i < 2 * s; i += kGT) cnt[i] = 0;
-    __syncthreads();
-    int32_t r[kGMaxZeta];
-    int8_t g[kGMaxZeta];
-    const bool live = j < m;
-    if (live) {
-        int32_t rr[64];
-        int8_t gg[64];
-        sparse_column(seed, s, zeta, j0 + j, rr, gg);  // column j0 + j of S (global row index)
-        for (int i = 0; i < zeta; ++i) {
-            r[i] = rr[i];
-            g[i] = gg[i];
-            atomicAdd(&cnt[2 * r[i] + (g[i] < 0 ? 1 : 0)], 1u);
-        }
-    }
-    __syncthreads();
-    // exclusive prefix over targets of (positives + negatives): each thread
-    // sums two targets, then a block scan
-    uint32_t t2[2] = {0u, 0u};
-    for (int q = 0; q < 2; ++q) {
-        const int64_t tg = 2 * tid + q;
-        if (tg < s) t2[q] = cnt[2 * tg] + cnt[2 * tg + 1];
-    }
-    uint32_t v = t2[0] + t2[1], incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += x;
-    }
-    if (lane == 31) wsum[wid] = incl;
-    __syncthreads();
-    uint32_t before = 0;
-    for (int w2 = 0; w2 < wid; ++w2) before += wsum[w2];
-    uint32_t start = before + incl - v;
-    uint32_t *rec = recs + chunk * rec_words;
-    for (int q = 0; q < 2; ++q) {
-        const int64_t tg = 2 * tid + q;
-        if (tg < s) {
-            const uint32_t np = cnt[2 * tg], nn = cnt[2 * tg + 1];
-            rec[tg] = (start << 20) | (np << 10) | nn;
-            pos[2 * tg] = start;
-            pos[2 * tg + 1] = start + np;
-            start += np + nn;
-        }
-    }
-    __syncthreads();
-    uint16_t *ent = (uint16_t *)(rec + s);
-    if (live)
-        for (int i = 0; i < zeta; ++i) {
-            const uint32_t p = atomicAdd(&pos[2 * r[i] + (g[i] < 0 ? 1 : 0)], 1u);
-            ent[p] = (uint16_t)tid;
-        }
-}
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(shared_addr(dst)), "l"(src), "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *dst, const void *src, uint32_t src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(shared_addr(dst)), "l"(src), "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// quantised value of row j, column c in the swizzled row-major tile
-__device__ __forceinline__ int sg_q(int j, int c) { return (j << 4) | (c ^ (j & 15)); }
-
-template <int RT>
-__global__ void __launch_bounds__(kGThreads, 1) sparse_gather_kernel(
-    const double *__restrict__ A, int64_t m, int64_t n, int64_t lda, int64_t s, int64_t nchunk, int64_t cpr,
-    int64_t rec_words, int P, int vec16, const uint32_t *__restrict__ recs, double *__restrict__ partial,
-    int32_t *status) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *raw = (double *)smem_raw;                                   // [2][kGC][kGRawStride]
-    long long *tq = (long long *)(raw + 2 * kGC * kGRawStride);         // kGT x kGC, swizzled
-    uint32_t *recb = (uint32_t *)(tq + kGT * kGC);                       // [2][rec_words]
-    __shared__ int s_emax[kGC];
-    __shared__ int Ecol[kGC];
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int c = lane & (kGC - 1), hw = (w << 1) | (lane >> 4);
-    const int64_t cg = blockIdx.x, rg = blockIdx.y;
-    const int64_t c0 = rg * cpr, c1 = (c0 + cpr < nchunk) ? c0 + cpr : nchunk;
-    if (tid < kGC) Ecol[tid] = 0;
-    long long acc[RT];
-#pragma unroll
-    for (int q = 0; q < RT; ++q) acc[q] = 0;
-    int nonfinite = 0;
-    // stage chunk ch into buffer b: the 16 columns' rows (zero beyond m or n) and the chunk's record
-    auto issue = [&](int64_t ch, int b) {
-        if (ch < c1) {
-            const int64_t row0 = ch * kGT;
-            double *dst = raw + b * kGC * kGRawStride;
-            if (vec16) {
-                for (int k = tid; k < kGC * (kGT / 2); k += kGThreads) {
-                    const int cc = k / (kGT / 2), p = k % (kGT / 2);
-                    const int64_t col = cg * kGC + cc, row = row0 + 2 * p;
-                    const int64_t left = (col < n) ? m - row : 0;
-                    const uint32_t bytes = left >= 2 ? 16u : (left == 1 ? 8u : 0u);
-                    const double *src = bytes ? A + col * lda + row : A;
-                    cp_async16(dst + cc * kGRawStride + 2 * p, src, bytes);
-                }
-            } else {
-                for (int k = tid; k < kGC * kGT; k += kGThreads) {
-                    const int cc = k / kGT, p = k % kGT;
-                    const int64_t col = cg * kGC + cc, row = row0 + p;
-                    const uint32_t bytes = (col < n && row < m) ? 8u : 0u;
-                    const double *src = bytes ? A + col * lda + row : A;
-                    cp_async8(dst + cc * kGRawStride + p, src, bytes);
-                }
-            }
-            const uint32_t *src = recs + ch * rec_words;
-            uint32_t *rdst = recb + b * rec_words;
-            for (int64_t k = tid; k < rec_words / 4; k += kGThreads) cp_async16(rdst + 4 * k, src + 4 * k, 16u);
-        }
-        cp_async_commit();
-    };
-    issue(c0, 0);
-    issue(c0 + 1, 1);
-    for (int64_t ch = c0; ch < c1; ++ch) {
-        const int b = (int)((ch - c0) & 1);
-        cp_async_wait<1>();
-        __syncthreads();
-        const double *rb = raw + b * kGC * kGRawStride;
-        // largest biased exponent of each column of the chunk (warp w: column w)
-        {
-            unsigned int hmax = 0x00100000u;
-            for (int j = lane; j < kGT; j += 32)
-                hmax = max(hmax, (unsigned int)((unsigned long long)__double_as_longlong(rb[w * kGRawStride + j]) >>
-                                                32) &
-                                     0x7FF00000u);
-            hmax = warp_max(hmax);
-            if (lane == 0) s_emax[w] = (int)(hmax >> 20);
-        }
-        __syncthreads();
-        // running exponent of this thread's column; rescale its accumulators when it grows
-        {
-            const int eo = Ecol[c], en = s_emax[c];
-            const int e = en == 0x7FF ? eo : max(eo, en);
-            nonfinite |= (en == 0x7FF);
-            if (e > eo && eo > 0) {
-                const int d = e - eo;
-#pragma unroll
-                for (int q = 0; q < RT; ++q) acc[q] = (d >= 63) ? (acc[q] >> 63) : (acc[q] >> d);
-            }
-        }
-        __syncthreads();  // every thread has read the old Ecol
-        if (lane == 0) {
-            const int eo = Ecol[w], en = s_emax[w];
-            Ecol[w] = en == 0x7FF ? eo : max(eo, en);
-        }
-        __syncwarp();
-        // quantise column w at 2^(E - 1022 - P), magnitude rounded to nearest, into the swizzled tile
-        {
-            const int E = max(Ecol[w], 1);
-            const int sh1b = E + 52 - P;
-            for (int j = lane; j < kGT; j += 32) {
-                const unsigned long long bits = (unsigned long long)__double_as_longlong(rb[w * kGRawStride + j]);
-                const uint32_t hi = (uint32_t)(bits >> 32);
-                const int e = (int)((hi >> 20) & 0x7FF), e1b = max(e, 1);
-                const uint32_t sh1 = (uint32_t)(sh1b - e1b);
-                const unsigned long long mant =
-                    (bits & 0x000FFFFFFFFFFFFFull) | ((unsigned long long)(1 - (e1b - e)) << 52);
-                unsigned long long q1;
-                asm("shr.b64 %0, %1, %2;" : "=l"(q1) : "l"(mant), "r"(sh1));
-                unsigned long long qv = (q1 + 1ull) >> 1;
-                if (e == 0x7FF) qv = 0ull;
-                const long long msk = (long long)(int)(hi & 0x80000000u) >> 31;
-                tq[sg_q(j, w)] = ((long long)qv ^ msk) - msk;
-            }
-        }
-        __syncthreads();  // tile and record in place
-        // gather: half warp hw owns targets hw + 32 q; lane = column
-        {
-            const uint32_t *off = recb + b * rec_words;
-            const uint16_t *ent = (const uint16_t *)(off + s);
-#pragma unroll
-            for (int q = 0; q < RT; ++q) {
-                const int r = hw + 32 * q;
-                const uint32_t oc = (r < s) ? off[r] : 0u;
-                const int st = (int)(oc >> 20), np = (int)((oc >> 10) & 1023u), nn = (int)(oc & 1023u);
-                long long a = 0;
-                for (int e = 0; e < np; ++e) {
-                    const int j = ent[st + e];
-                    a += tq[sg_q(j, c)];
-                }
-                for (int e = 0; e < nn; ++e) {
-                    const int j = ent[st + np + e];
-                    a -= tq[sg_q(j, c)];
-                }
-                acc[q] += a;
-            }
-        }
-        __syncthreads();  // tile and record consumed
-        issue(ch + 2, b);
-    }
-    cp_async_wait<0>();
-    // range partial in FP64: value = acc * 2^(E - 1022 - P)
-    const int64_t col = cg * kGC + c;
-    if (col < n) {
-        const int E = Ecol[c];
-        const double scale = E > 0 ? ldexp(1.0, E - 1022 - P) : 0.0;
-        double *out = partial + (rg * n + col) * s;
-#pragma unroll
-        for (int q = 0; q < RT; ++q) {
-            const int r = hw + 32 * q;
-            if (r < s) out[r] = (double)acc[q] * scale;
-        }
-    }
-    if (nonfinite) set_status(status, NS_ERR_NONFINITE);
-}
-
-size_t sparse_gather_smem(int64_t rec_words) {
-    return sizeof(double) * 2 * kGC * kGRawStride + sizeof(long long) * kGT * kGC + sizeof(uint32_t) * 2 * rec_words;
-}
-
 cudaError_t launch_sparse_meta(uint64_t seed, int64_t s, int zeta, int64_t m, int32_t *rows, int8_t *signs,
                                cudaStream_t st) {
     sparse_meta_kernel<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(seed, s, zeta, m, rows, signs);
@@ -558,26 +281,6 @@ cudaError_t launch_sparse_meta(uint64_t seed, int64_t s, int zeta, int64_t m, in
 
 cudaError_t launch_sparse_f64(uint64_t seed, const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, int zeta,
                               const SparseWork &w, double *SA, int32_t *status, cudaStream_t st, int64_t j0) {
-    if (sparse_gather_applies(s, zeta)) {
-        const SparseGatherGeom gg = sparse_gather_geom(m, n, s, zeta);
-        sparse_chunk_meta_kernel<<<(unsigned)gg.nchunk, kGT, 0, st>>>(seed, s, zeta, m, gg.rec_words, w.entries,
-                                                                      j0);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        const size_t smem = sparse_gather_smem(gg.rec_words);
-        const int vec16 = ((((uintptr_t)A) & 15) == 0 && (lda & 1) == 0) ? 1 : 0;
-        auto kern = gg.rt == 8 ? sparse_gather_kernel<8> : gg.rt == 16 ? sparse_gather_kernel<16>
-                                                                        : sparse_gather_kernel<32>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        dim3 grid((unsigned)gg.ncolgrp, (unsigned)gg.nrange);
-        kern<<<grid, kGThreads, smem, st>>>(A, m, n, lda, s, gg.nchunk, gg.cpr, gg.rec_words, gg.fx_bits, vec16,
-                                            w.entries, w.partial, status);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        chunk_reduce_kernel<<<(unsigned)((n * s + 255) / 256), 256, 0, st>>>(w.partial, n, s, gg.nrange,
-                                                                              1.0 / std::sqrt((double)zeta), SA);
-        return cudaGetLastError();
-    }
     const SparseGeom g = sparse_geom(m, n, s, zeta);
     const size_t bsmem = sizeof(int32_t) * (size_t)(g.nbucket + 1);
     sparse_bucket_kernel<<<(unsigned)g.ntile, 256, bsmem, st>>>(seed, s, zeta, m, g.nent, g.nbucket, w.entries,
