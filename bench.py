@@ -124,24 +124,30 @@ def dense_flops(s, n, k, stats):
     """Algorithmic FP64 flops of lines 3-4 of Algorithm 1 as the GPU runs them:
     Householder QR of s x n, Householder QR of n x n, one-sided Jacobi (dot
     products 6n per visited pair, rotation of two columns of X and of V 12n),
-    the five n^3 products that make the FP32 phase's V0 orthogonal and apply
-    it (when it ran), and the k trailing columns of V (4 n^2 k).  The FP32
-    phase's own arithmetic is FP32 and not counted."""
+    the n^3 products after the FP32 phase (when it ran): V0 made orthogonal
+    (two symmetric products, n^3 each, and one 2n^3) and applied to X0 and Q2
+    (2n^3 each), then two first-order completions (G = X^T X and K^2, n^3
+    each, K^4 and K^6 when formed, n^3 each, and X Q, V Q, 2n^3 each), and
+    the k trailing columns of V (4 n^2 k).  The FP32 phase's own arithmetic is
+    FP32 and not counted."""
     sweeps, rots, checks = stats[:3]
     pairs = n * (n - 1) / 2
     qr1 = 2.0 * n * n * (s - n / 3.0)
     qr2 = 4.0 / 3.0 * n ** 3
     jac = (sweeps + checks) * pairs * 6.0 * n + rots * 12.0 * n
-    prod = 5 * 2.0 * n ** 3 if len(stats) > 4 and stats[4] > 0 else 0.0
+    prod = 0.0
+    if len(stats) > 4 and stats[4] > 0:
+        prod = 8.0 * n ** 3 + 2 * 6.0 * n ** 3 + (stats[6] if len(stats) > 6 else 0) * 2.0 * n ** 3
     return qr1 + qr2 + jac + prod + 4.0 * n * n * k
 
 
 def launches_per_solve(stats):
     """Library kernels one ns_solve launches: the sketch (meta, chunk, reduce),
     the column order (3), the first QR, [R^T | I] (2), the second QR, X and V
-    (2), the FP32 phase with its products and copies (8, when it runs), the
-    ring Jacobi, V = P Q2 V0 Vx, the extraction and the two save copies."""
-    return 17 + (8 if len(stats) > 4 and stats[4] > 0 else 0)
+    (2), the FP32 phase with its products, two completions of 7 launches and
+    two copies (21, when it runs), the ring Jacobi, V = P Q2 V0 Vx, the
+    extraction and the two save copies."""
+    return 17 + (21 if len(stats) > 4 and stats[4] > 0 else 0)
 
 
 def cpu_baseline(A):
@@ -731,6 +737,7 @@ def main():
                   "peak_source": "derived: %d SMs x 4 FP64 flop/clk x sampled SM clock" % n_sm,
                   "algorithmic_flops": dflops, "jacobi_sweeps_rotations_checks": stats[:3],
                   "fp32_phase_sweeps_rotations": stats[4:6],
+                  "completions_with_k4_and_check_first": stats[6:8],
                   "jacobi_kernel": ("cluster ring, %d CTAs per cluster" % stats[3]) if stats[3] else "barrier-separated"}
     dominant = dense_roof if t_dense > t_sketch else sketch_roof
     line = {

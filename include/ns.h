@@ -233,12 +233,14 @@ ns_status ns_solve_sketched(const ns_sketch_desc *desc, const double *SA, int64_
 /*
  * ns_solve_stats / ns_sketched_stats -- statistics of the Jacobi iteration of
  * the last ns_solve (ns_solve_sketched) that ran in workspace ws with the same
- * desc and shape: dev_out (device int64[6]) receives the number of full FP64
+ * desc and shape: dev_out (device int64[8]) receives the number of full FP64
  * sweeps, the number of FP64 rotations, the number of barrier-free check
  * passes, the kernel that ran (the cluster size, 8 or 16, of the cluster-ring
- * Jacobi, or 0: the barrier-separated one), and the sweeps and rotations of
- * the FP32 linear phase that precedes the FP64 iteration for 64 <= n <= 256
- * (0 and 0 when it did not run).
+ * Jacobi, or 0: the barrier-separated one), the sweeps and rotations of the
+ * FP32 linear phase that precedes the FP64 iteration for 64 <= n <= 256 (0
+ * and 0 when it did not run), how many of the two first-order completions
+ * that follow the phase formed their K^4 and K^6 terms, and 1 if the FP64
+ * iteration started with its convergence check (else 0).
  * Enqueued on stream after that call.
  */
 ns_status ns_solve_stats(const ns_sketch_desc *desc, int64_t m, int64_t n, const void *ws, int64_t *dev_out,

@@ -331,8 +331,9 @@ def ns_solve_sketched(d, SA, k, save=False, status=None, ws=None, stream=None):
 
 def jacobi_stats(d, m, n, ws, sketched=False, stream=None):
     """(FP64 full sweeps, FP64 rotations, check passes, ring cluster size or 0, FP32-phase sweeps,
-    FP32-phase rotations) of the last solve in workspace ws."""
-    out = torch.zeros(6, dtype=torch.int64, device=ws.device)
+    FP32-phase rotations, completions with K^4 and K^6 terms, 1 if the FP64 iteration started with
+    its check) of the last solve in workspace ws."""
+    out = torch.zeros(8, dtype=torch.int64, device=ws.device)
     lib = _lib.load()
     if sketched:
         st = lib.ns_sketched_stats(ctypes.byref(d), int(n), _p(ws), _p(out), _stream(stream))

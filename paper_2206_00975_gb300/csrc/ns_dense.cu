@@ -44,9 +44,13 @@ namespace ns {
 constexpr int kDenseThreads = 256;
 constexpr int kMaxSweeps = 30;
 constexpr int kCheckBelow = 4096;        // run the barrier-free check after a sweep with fewer rotations
-constexpr int kBarWords = 64 + 2 * 64 + 16;  // barrier word (padded), rotation counts, check flags, stats,
-                                             // FP32-phase control (bar[196..198])
-constexpr int kJ32Ctl = 196;                 // word of bar: 1 if the FP32 phase ran, then its sweeps, rotations
+constexpr int kBarWords = 64 + 2 * 64 + 32;  // barrier word (padded), rotation counts, check flags, stats,
+                                             // FP32-phase control (bar[196..211])
+// words of bar from kJ32Ctl: 1 if the FP32 phase ran, its sweeps, its rotations,
+// the completions' verdict (2: start the FP64 iteration with the convergence
+// check), then 6 words per completion (see ns_jacobi32.cu)
+constexpr int kJ32Ctl = 196;
+static_assert(kJ32Ctl + 16 <= kBarWords, "FP32-phase control words");
 
 size_t dense_work_bytes(int64_t s, int64_t n) {
     Carver c(nullptr);
@@ -803,6 +807,27 @@ __device__ __forceinline__ int64_t rr_player(int64_t pos, int64_t step, int64_t 
     return pos == 0 ? 0 : 1 + (pos - 1 + step) % (n2 - 1);
 }
 
+// The FP32 images of a pair's sums (a, b the squared norms, g the inner
+// product, all scaled alike) cannot resolve the angle when the norms agree to
+// about their rounding and the inner product is small as well: there
+// tan(2 theta) = 2 g / (a - b) is decided by a difference the images lost, an
+// angle taken from them leaves the inner product at the images' noise level,
+// and the pair would stall (clustered singular values).  Those pairs take the
+// angle from FP64 sums.
+__device__ __forceinline__ bool ring_unresolved(float a, float b, float g) {
+    const float mx = fmaxf(a, b);
+    return fabsf(b - a) <= 0x1p-12f * mx && fabsf(g) <= 0x1p-10f * mx;
+}
+
+// tan(theta) = sign(z) / (|z| + (1 + z^2)^(1/2)), z = num / den, in FP64;
+// `fallback` when z is not a finite number
+__device__ __forceinline__ double exact_tan(double num, double den, double fallback) {
+    const double z = num / den;
+    if (!isfinite(z)) return fallback;
+    const double az = fabs(z);
+    return (az > 1e150) ? 0.5 / z : copysign(1.0, z) / (az + sqrt(fma(z, z, 1.0)));
+}
+
 // Rotation for (alpha, beta, gamma): returns false if the pair is already
 // orthogonal to the tolerance.  One thread.
 __device__ __forceinline__ bool rotation(double alpha, double beta, double gamma, double tol2, double *c_out,
@@ -818,7 +843,11 @@ __device__ __forceinline__ bool rotation(double alpha, double beta, double gamma
     const double sc = __longlong_as_double((long long)se << 52);
     const float a32 = (float)(alpha * sc), b32 = (float)(beta * sc), g32 = (float)(gamma * sc);
     double t;
-    if (fabsf(g32) >= 1e-30f) {
+    if (ring_unresolved(a32, b32, g32)) {
+        // nearly equal norms and a small inner product: the FP32 images cannot
+        // resolve beta - alpha, which then decides the angle
+        t = exact_tan(beta - alpha, 2.0 * gamma, 1.0);
+    } else if (fabsf(g32) >= 1e-30f) {
         const float z = (b32 - a32) / (2.0f * g32);
         t = (double)((fabsf(z) > 1e18f) ? 0.5f / z : copysignf(1.0f, z) / (fabsf(z) + sqrtf(1.0f + z * z)));
     } else {
@@ -1166,7 +1195,7 @@ __device__ __forceinline__ bool ring_above(const RingSums &r, double tol2) {
 // orthogonal whatever t is), so it comes from FP32 images of the scaled sums;
 // it is evaluated unconditionally, beside the threshold test.
 __device__ __forceinline__ bool ring_angle(const RingSums &r, double tol2, float dp2, float dq2, float dpq, double dp,
-                                           double dq, double *t_out) {
+                                           double dq, double *t_out, bool *exact) {
     const bool above = ring_above(r, tol2);
     const int la = ring_lexp(r.fa, r.Ea), lb = ring_lexp(r.fb, r.Eb), shift = max(la, lb);
     const float a32 = r.fa * pow2f(2 * (r.Ea - 1023) - shift) * dp2;
@@ -1175,6 +1204,7 @@ __device__ __forceinline__ bool ring_angle(const RingSums &r, double tol2, float
     const float z = __fdividef(b32 - a32, 2.0f * g32), az = fabsf(z);
     const float w = fmaf(z, z, 1.0f);
     const float tb = (az > 1e18f) ? __fdividef(0.5f, z) : copysignf(__fdividef(1.0f, az + w * rsqrtf(w)), z);
+    *exact = above && ring_unresolved(a32, b32, g32);
     if (!above) return false;
     if (fabsf(g32) >= 1e-30f) {
         *t_out = f64_of(tb);
@@ -1289,6 +1319,7 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
     __shared__ double rg[4];          // per X row warp: x~_p . x~_q
     __shared__ float2 rab[4];         // per X row warp: FP32 images of |x~_p|^2, |x~_q|^2
     __shared__ uint32_t rexp[4];      // per X row warp: (E_p << 16) | E_q, the images' exponents
+    __shared__ double2 rn[4];         // per X row warp: FP64 |x~_p|^2, |x~_q|^2 (unresolved pairs only)
     __shared__ double par[kRingC][3];
     __shared__ double s_fin[2];
     __shared__ volatile int s_abort;
@@ -1343,10 +1374,13 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
     unsigned int prev_rot = 0xFFFFFFFFu;
     int full_sweeps = 0, check_passes = 0;
     uint32_t ostep = 0;  // outer steps so far: phase parity of the slot mbarriers
-    // After the FP32 phase the columns start nearly orthogonal (cosines ~2^-17):
-    // two sweeps reach FP64 convergence, so the barrier-free check runs from
-    // the third sweep on whatever the rotation count was.
-    const int check_from = (fp32_ran && *(volatile const unsigned int *)fp32_ran != 0u) ? 2 : max_sweeps + 1;
+    // After the FP32 phase and its first-order completions the columns start
+    // nearly orthogonal: the barrier-free check runs from the third sweep on
+    // whatever the rotation count was, and before the first sweep when the
+    // last completion left no pair out and only tiny rotations (verdict 2).
+    const unsigned int ran = fp32_ran ? *(volatile const unsigned int *)fp32_ran : 0u;
+    const int check_from =
+        ran ? ((*(volatile const unsigned int *)(fp32_ran + 3) == 2u) ? 0 : 2) : max_sweeps + 1;
     for (int sweep = 0; sweep < max_sweeps && !converged && ok; ++sweep) {
         if (prev_rot < (unsigned int)kCheckBelow || sweep >= check_from) {
             ++check_passes;
@@ -1469,7 +1503,17 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
                         rs.Eb = __shfl_sync(0xffffffffu, Eb, 0);
                     }
                     double tn = 0.0;
-                    const bool rot = ring_angle(rs, tol2, fP * fP, fQ * fQ, fP * fQ, dP, dQ, &tn);
+                    bool exact = false;
+                    const bool rot = ring_angle(rs, tol2, fP * fP, fQ * fQ, fP * fQ, dP, dQ, &tn, &exact);
+                    if (exact) {  // (rare; uniform over the warp) the angle from FP64 norms
+                        if (lane == 0) par[j][0] = 2.0;  // the request to the X row warps
+                        __syncwarp();
+                        xbar();  // the request is visible
+                        xbar();  // their FP64 squared norms are in rn
+                        const double at = (rn[0].x + rn[1].x) + (rn[2].x + rn[3].x);
+                        const double bt = (rn[0].y + rn[1].y) + (rn[2].y + rn[3].y);
+                        tn = exact_tan((dQ * dQ) * bt - (dP * dP) * at, 2.0 * (dP * dQ) * rs.g, tn);
+                    }
                     const double mn = tn * rr;  // lane 0: mu (x~_p -= mu x~_q), lane 1: nu (x~_q += nu x~_p)
                     if (lane < 2) par[j][1 + lane] = rot ? mn : 0.0;
                     if (lane == 0) par[j][0] = rot ? 1.0 : 0.0;
@@ -1550,7 +1594,18 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
                             rexp[t >> 5] = e2;
                         }
                         xbar();  // sums to the scalar warp
-                        xbar();  // par[j] from the scalar warp
+                        xbar();  // par[j] from the scalar warp, or its request for FP64 norms
+                        if (par[j][0] == 2.0) {
+                            double a2 = fma(p1, p1, p0 * p0), b2 = fma(q1, q1, q0 * q0);
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) {
+                                a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+                                b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+                            }
+                            if ((t & 31) == 0) rn[t >> 5] = make_double2(a2, b2);
+                            xbar();  // norms to the scalar warp
+                            xbar();  // the final par[j]
+                        }
                     } else {
                         if (!s_abort && !ring_wait_cta(shared_addr(&mbr[j]), parity)) {
                             s_abort = 1;
@@ -1968,6 +2023,9 @@ __global__ void dense_stats_kernel(const unsigned int *bar, int64_t *out) {
         out[3] = bar[64 + 131];
         out[4] = bar[kJ32Ctl] ? bar[kJ32Ctl + 1] : 0;  // FP32-phase sweeps (0: the phase did not run)
         out[5] = bar[kJ32Ctl] ? bar[kJ32Ctl + 2] : 0;  // FP32-phase rotations
+        // completions that formed the K^4 and K^6 terms; FP64 iteration started with its check
+        out[6] = bar[kJ32Ctl] ? (int64_t)bar[kJ32Ctl + 5] + (int64_t)bar[kJ32Ctl + 11] : 0;
+        out[7] = (bar[kJ32Ctl] && bar[kJ32Ctl + 3] == 2u) ? 1 : 0;
     }
 }
 

@@ -25,9 +25,14 @@
 //   3. V0 = W made orthogonal in FP64: E = I - W^T W (about 1e-6), and
 //      V0 = W (I + E/2 + 3 E^2 / 8), the series of (W^T W)^(-1/2) to second
 //      order (the remainder is of order E^3).
-//   4. X1 = X0 V0 and V = Q2 V0 in FP64; the FP64 ring Jacobi then starts from
-//      nearly orthogonal columns (cosines ~ tau) and needs two sweeps and a
-//      check instead of seven sweeps and a check.
+//   4. X1 = X0 V0 and V = Q2 V0 in FP64: nearly orthogonal columns (cosines
+//      ~ tau), where the rotations still to come are small.
+//   5. Two first-order completions (see completion below): the rotation that
+//      diagonalises G = X^T X to first order, made exactly orthogonal to
+//      working accuracy, applied to X and V as one FP64 product each.  On the
+//      benchmark's spectrum the FP64 ring then only runs its convergence check
+//      (seven sweeps and a check without steps 1-5, two sweeps and a check
+//      without step 5).
 //
 // Step 2 runs on one cluster of 8 CTAs (n <= 256): the 256 columns of Y and W
 // are 16 blocks of 16 columns, two blocks per CTA in shared memory.  A sweep is
@@ -446,46 +451,124 @@ __global__ void __cluster_dims__(kJ32Cta, 1, 1) __launch_bounds__(kJ32Threads, 1
 }
 
 // ----------------------------------------------------- small FP64 GEMMs ----
-// C (M x N) = op(A) B with op(A) = A (M x K) or A^T (A: K x M); column-major,
-// leading dimensions lda, ldb, ldc.  Epilogues: 0: C = AB; 1: C = I - A^T B;
-// 2: C = I + E/2 + (3/8) A B (E: M x N, ld ldc).  One 16 x 16 tile per CTA,
-// one output per thread, K in chunks of 16 through shared memory.  Skipped
-// when *ctl == 0 (the FP32 phase did not run).
+// C (M x N, column-major, leading dimension ldc) = op(A) B with op(A) = A
+// (M x K) or A^T (A: K x M), B (K x N).  One 16 x 16 tile per CTA, one output
+// per thread, K in chunks of 16 through shared memory.  Skipped when
+// *ctl == 0 (the FP32 phase did not run).
+//   EPI 0: C = AB;  1: C = I - AB;  2: C = I + E/2 + (3/8) AB;
+//   EPI 3: C = Q = I + t K + t^2 K2/2 - t^4 K4/8 + t^6 AB/16, the
+//          completion's rotation (K's diagonal slots hold other data and
+//          count as 0; t and the skip of the last two terms follow from the
+//          bound b, see completion).
+//   EPI 4: C = AB unless the completion's bound b says the K^4 term is
+//          negligible (then nothing runs).
+//   DZ: the diagonal entries of A and B count as 0 (K held in place of G).
+//   SYM: the product is symmetric.  Only the tiles on and above the diagonal
+//        run (a triangular grid); each writes its mirror image, with K's sign
+//        flipped for EPI 3, and on a diagonal tile the upper entry defines
+//        both, so the result is exactly symmetric (apart from K).
+//   blockIdx.z picks one of two (A, C) pairs: X Q and V Q in one launch.
 constexpr int kG64T = 16;
 
-template <bool TA, int EPI>
-__global__ void __launch_bounds__(kG64T * kG64T) gemm64_kernel(const double *__restrict__ A, int64_t lda,
-                                                              const double *__restrict__ B, int64_t ldb,
-                                                              double *__restrict__ C, int64_t ldc,
-                                                              const double *__restrict__ E, int64_t M, int64_t N,
-                                                              int64_t K, const unsigned int *ctl) {
-    if (ctl && *(volatile const unsigned int *)ctl == 0u) return;
+struct G64Args {
+    const double *A[2];
+    int64_t lda;
+    const double *B;
+    int64_t ldb;
+    double *C[2];
+    int64_t ldc;
+    const double *E;      // EPI 2: E (M x N, ld ldc)
+    const double *Km;     // EPI 3: K off the diagonal (ld ldc)
+    const double *K2;     // EPI 3: K^2 (ld ldc)
+    const double *K4;     // EPI 3: K^4 (ld ldc)
+    const unsigned long long *bnd;  // EPI 3, 4: the completion's bound b (bits of a double)
+    unsigned int *verdict;          // EPI 3: where the last completion writes its verdict, else null
+    unsigned int *ran;              // EPI 4: set to 1 when the product ran
+    const unsigned int *cnt;        // EPI 3: pairs left out, then max |K| (bits) at cnt + 2
+    int64_t M, N, K;
+    const unsigned int *ctl;
+};
+
+// Entries of |K| above this are left to the FP64 sweeps (pairs whose squared
+// norms are too close for the first-order rotation to be small).
+constexpr double kCorrKappa = 0.00390625;      // 2^-8
+constexpr double kCorrBmax = 1.220703125e-4;   // 2^-13: largest b taken with t = 1
+constexpr double kCorrSmall = 1.862645149230957e-9;  // 2^-29: below, the K^4, K^6 terms are < 2^-60
+constexpr double kCorrDone = 9.5367431640625e-7;     // 2^-20
+
+__device__ __forceinline__ double corr_bound(const unsigned long long *bnd) {
+    return __longlong_as_double((long long)*(volatile const unsigned long long *)bnd);
+}
+
+template <bool TA, int EPI, bool SYM, bool DZ>
+__global__ void __launch_bounds__(kG64T * kG64T) gemm64_kernel(const G64Args g) {
+    if (g.ctl && *(volatile const unsigned int *)g.ctl == 0u) return;
+    bool skip_k = false;  // EPI 3, 4: the K^4 and K^6 terms are negligible
+    if (EPI == 3 || EPI == 4) skip_k = corr_bound(g.bnd) <= kCorrSmall;
+    if (EPI == 4 && skip_k) return;
+    if (EPI == 4 && blockIdx.x == 0 && threadIdx.x == 0) *g.ran = 1u;
     __shared__ double As[kG64T][kG64T + 1];  // As[k][i] = op(A)[i, k]
     __shared__ double Bs[kG64T][kG64T + 1];  // Bs[k][j] = B[k, j]
+    int64_t bx = blockIdx.x, by = blockIdx.y;
+    if (SYM) {  // triangular index -> tile (bx, by), bx <= by
+        int64_t t = blockIdx.x;
+        by = 0;
+        while (t > by) {
+            t -= by + 1;
+            ++by;
+        }
+        bx = t;
+    }
+    const double *A = g.A[blockIdx.z];
+    double *C = g.C[blockIdx.z];
     const int tx = threadIdx.x % kG64T, ty = threadIdx.x / kG64T;
-    const int64_t i = (int64_t)blockIdx.x * kG64T + tx, j = (int64_t)blockIdx.y * kG64T + ty;
+    const int64_t i = bx * kG64T + tx, j = by * kG64T + ty;
+    const int64_t M = g.M, N = g.N, K = skip_k ? 0 : g.K;
     double acc = 0.0;
     for (int64_t k0 = 0; k0 < K; k0 += kG64T) {
-        {   // thread (tx, ty) loads op(A)[blockIdx.x*16 + ?, k0 + ?] and B[k0 + ?, blockIdx.y*16 + ?]
-            const int64_t ai = (int64_t)blockIdx.x * kG64T + (TA ? ty : tx), ak = k0 + (TA ? tx : ty);
+        {   // thread (tx, ty) loads op(A)[bx*16 + ?, k0 + ?] and B[k0 + ?, by*16 + ?]
+            const int64_t ai = bx * kG64T + (TA ? ty : tx), ak = k0 + (TA ? tx : ty);
             double av = 0.0;
-            if (ai < M && ak < K) av = TA ? A[ak + ai * lda] : A[ai + ak * lda];
+            if (ai < M && ak < K && !(DZ && ai == ak)) av = TA ? A[ak + ai * g.lda] : A[ai + ak * g.lda];
             if (TA) As[tx][ty] = av;
             else As[ty][tx] = av;
-            const int64_t bk = k0 + tx, bj = (int64_t)blockIdx.y * kG64T + ty;
-            Bs[tx][ty] = (bk < K && bj < N) ? B[bk + bj * ldb] : 0.0;
+            const int64_t bk = k0 + tx, bj = by * kG64T + ty;
+            Bs[tx][ty] = (bk < K && bj < N && !(DZ && bk == bj)) ? g.B[bk + bj * g.ldb] : 0.0;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < kG64T; ++kk) acc = fma(As[kk][tx], Bs[kk][ty], acc);
         __syncthreads();
     }
-    if (i < M && j < N) {
-        double v = acc;
-        if (EPI == 1) v = (i == j ? 1.0 : 0.0) - acc;
-        if (EPI == 2) v = (i == j ? 1.0 : 0.0) + 0.5 * E[i + j * ldc] + 0.375 * acc;
-        C[i + j * ldc] = v;
+    if (EPI == 3 && g.verdict && blockIdx.x == 0 && threadIdx.x == 0) {
+        // verdict for the FP64 iteration: 2 (start with the convergence check)
+        // when the full step was taken, no pair was left out and every
+        // rotation was tiny
+        const double b = corr_bound(g.bnd);
+        const double mk = __longlong_as_double((long long)*(volatile const unsigned long long *)(g.cnt + 2));
+        *g.verdict = (b <= kCorrBmax && g.cnt[0] == 0u && mk <= kCorrDone) ? 2u : 0u;
     }
+    if (i >= M || j >= N) return;
+    if (SYM && bx == by && i > j) return;  // the upper entry writes both
+    const double id = (i == j) ? 1.0 : 0.0;
+    const int64_t ld = g.ldc;
+    double v = acc, vm = acc;  // C[i, j] and its mirror C[j, i]
+    if (EPI == 1) v = vm = id - acc;
+    if (EPI == 2) v = vm = id + 0.5 * g.E[i + j * ld] + 0.375 * acc;
+    if (EPI == 3) {
+        const double b = corr_bound(g.bnd);
+        const double t = (b > kCorrBmax) ? sqrt(kCorrBmax / b) : 1.0, t2 = t * t;
+        const double kij = (i == j) ? 0.0 : t * g.Km[i + j * ld];
+        double sym = 0.5 * t2 * g.K2[i + j * ld];
+        if (!skip_k) {
+            const double t4 = t2 * t2;
+            sym += -0.125 * t4 * g.K4[i + j * ld] + 0.0625 * (t4 * t2) * acc;
+        }
+        v = (id + kij) + sym;
+        vm = (id - kij) + sym;
+    }
+    C[i + j * ld] = v;
+    if (SYM && i != j) C[j + i * ld] = vm;
 }
 
 __global__ void copy_if_kernel(const double *__restrict__ a, int64_t len, double *__restrict__ b,
@@ -495,13 +578,130 @@ __global__ void copy_if_kernel(const double *__restrict__ a, int64_t len, double
         b[i] = a[i];
 }
 
-template <bool TA, int EPI>
-static cudaError_t gemm64(const double *A, int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc,
-                          const double *E, int64_t M, int64_t N, int64_t K, const unsigned int *ctl,
-                          cudaStream_t st) {
-    dim3 grid((unsigned)((M + kG64T - 1) / kG64T), (unsigned)((N + kG64T - 1) / kG64T));
-    gemm64_kernel<TA, EPI><<<grid, kG64T * kG64T, 0, st>>>(A, lda, B, ldb, C, ldc, E, M, N, K, ctl);
+template <bool TA, int EPI, bool SYM, bool DZ = false>
+static cudaError_t gemm64(const G64Args &g, bool dual, cudaStream_t st) {
+    const int64_t mt = (g.M + kG64T - 1) / kG64T, nt = (g.N + kG64T - 1) / kG64T;
+    const dim3 grid = SYM ? dim3((unsigned)(mt * (mt + 1) / 2), 1, dual ? 2 : 1)
+                          : dim3((unsigned)mt, (unsigned)nt, dual ? 2 : 1);
+    gemm64_kernel<TA, EPI, SYM, DZ><<<grid, kG64T * kG64T, 0, st>>>(g);
     return cudaGetLastError();
+}
+
+static G64Args g64(const double *A, int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc, int64_t n,
+                   const unsigned int *ctl) {
+    G64Args g = {};
+    g.A[0] = g.A[1] = A;
+    g.lda = lda;
+    g.B = B;
+    g.ldb = ldb;
+    g.C[0] = g.C[1] = C;
+    g.ldc = ldc;
+    g.M = g.N = g.K = n;
+    g.ctl = ctl;
+    return g;
+}
+
+// -------------------------------------------- first-order completion ----
+// After the FP32 phase the columns of X are orthogonal to ~1e-5 relative to
+// their sizes, so G = X^T X is diagonal up to small off-diagonal entries.  For
+// such a nearly diagonal symmetric matrix the rotation that diagonalises it is,
+// to first order, exp(K) with K skew, K[p, q] = G[p, q] / (G[q, q] - G[p, p])
+// (the first-order completion of a nearly diagonal eigenproblem, Davies and
+// Modi, Linear Algebra Appl. 77 (1986)).  It is applied as the orthogonal
+//   Q = K + (I + K^2)^(1/2),
+// (Q^T Q = (A - K)(A + K) = A^2 - K^2 = I for A = (I + K^2)^(1/2), which
+// commutes with K), the square root by its binomial series to K^6:
+// A = I + K^2/2 - K^4/8 + K^6/16, so that Q^T Q = I + O(5 K^8 / 64).  The
+// step is scaled, K -> t K, so that this remainder stays below 2^-55:
+// b = max_j sum_i |K^2[i, j]| bounds ||K||_2^2 and t = min(1, sqrt(bmax / b)).
+// Pairs whose |K| exceeds kCorrKappa (close squared norms) keep K = 0 and are
+// left to the FP64 sweeps.  After two completions the cosines on the
+// benchmark's spectrum fall from ~1e-5 to ~1e-9 and ~1e-16.
+//
+// Control words of one completion (from cw, zeroed with the barrier words):
+// cw[0] pairs left out, cw[1] 1 if the K^4 and K^6 terms were formed,
+// cw[2..3] max |K| kept, cw[4..5] the bound b (doubles as bits: non-negative doubles order like their bit patterns, so integer
+// atomic max gives a deterministic result).
+
+// K in place of G off the diagonal (the diagonal keeps G's), with the count of
+// pairs left out and the largest |K| kept.
+__global__ void __launch_bounds__(256) corr_k_kernel(double *GK, int64_t n, unsigned int *cw,
+                                                     const unsigned int *ctl) {
+    if (*(volatile const unsigned int *)ctl == 0u) return;
+    unsigned int out = 0;
+    double mk = 0.0;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n * n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx % n, j = idx / n;
+        if (i == j) continue;
+        const double g = GK[idx];
+        double k = 0.0;
+        if (g != 0.0) {
+            const double den = GK[j + j * n] - GK[i + i * n];
+            if (fabs(g) <= kCorrKappa * fabs(den)) {
+                k = g / den;
+                mk = fmax(mk, fabs(k));
+            } else if (i < j) {
+                ++out;  // also Inf and NaN
+            }
+        }
+        GK[idx] = k;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        out += __shfl_xor_sync(0xffffffffu, out, o);
+        mk = fmax(mk, __shfl_xor_sync(0xffffffffu, mk, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (out) atomicAdd(cw, out);
+        atomicMax((unsigned long long *)(cw + 2), (unsigned long long)__double_as_longlong(mk));
+    }
+}
+
+// b = max_j sum_i |K2[i, j]|, one warp per column
+__global__ void __launch_bounds__(256) corr_bound_kernel(const double *K2, int64_t n, unsigned int *cw,
+                                                         const unsigned int *ctl) {
+    if (*(volatile const unsigned int *)ctl == 0u) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= n) return;
+    double sum = 0.0;
+    for (int64_t i = lane; i < n; i += 32) sum += fabs(K2[i + j * n]);
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) atomicMax((unsigned long long *)(cw + 4), (unsigned long long)__double_as_longlong(sum));
+}
+
+// (Xo, Vo) = (Xi, Vi) Q for one completion; scratch: G (then K) and K^2
+// (n x n each, in R2), K^4 (n x n), Q (n x n); cw: this completion's control
+// words; verdict: where the last completion writes its verdict, else null.
+static cudaError_t completion(const double *Xi, const double *Vi, double *Xo, double *Vo, int64_t n, double *GKm,
+                              double *K2m, double *K4m, double *Qm, unsigned int *cw, unsigned int *verdict,
+                              const unsigned int *ctl, cudaStream_t st) {
+    cudaError_t e;
+    const unsigned long long *bnd = reinterpret_cast<const unsigned long long *>(cw + 4);
+    G64Args g = g64(Xi, n, Xi, n, GKm, n, n, ctl);  // G = X^T X
+    if ((e = gemm64<true, 0, true>(g, false, st)) != cudaSuccess) return e;
+    corr_k_kernel<<<64, 256, 0, st>>>(GKm, n, cw, ctl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    g = g64(GKm, n, GKm, n, K2m, n, n, ctl);  // K^2 (K's diagonal slots read as 0)
+    if ((e = gemm64<false, 0, true, true>(g, false, st)) != cudaSuccess) return e;
+    corr_bound_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(K2m, n, cw, ctl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    g = g64(K2m, n, K2m, n, K4m, n, n, ctl);  // K^4 (skipped when negligible)
+    g.bnd = bnd;
+    g.ran = cw + 1;
+    if ((e = gemm64<false, 4, true>(g, false, st)) != cudaSuccess) return e;
+    g = g64(K2m, n, K4m, n, Qm, n, n, ctl);  // Q from K, K^2, K^4 and K^6 = K^2 K^4
+    g.Km = GKm;
+    g.K2 = K2m;
+    g.K4 = K4m;
+    g.bnd = bnd;
+    g.verdict = verdict;
+    g.cnt = cw;
+    if ((e = gemm64<false, 3, true>(g, false, st)) != cudaSuccess) return e;
+    g = g64(Xi, n, Qm, n, Xo, n, n, ctl);  // X Q and V Q
+    g.A[1] = Vi;
+    g.C[1] = Vo;
+    return gemm64<false, 0, false>(g, true, st);
 }
 
 bool jacobi32_applicable(int64_t n) { return n >= 64 && n <= kJ32N; }
@@ -537,13 +737,25 @@ cudaError_t launch_jacobi32_precondition(const DenseWork &w, int64_t n, unsigned
     double *V0 = w.L, *Em = w.L + n * n, *Mm = w.U, *V0p = w.W, *X1 = w.U, *V1 = w.L;
     jacobi32_phase_kernel<<<kJ32Cta, kJ32Threads, kJ32Smem, st>>>(w.X, n, V0, ctl);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // E = I - V0^T V0;  M = I + E/2 + (3/8) E^2;  V0' = V0 M
-    if ((e = gemm64<true, 1>(V0, n, V0, n, Em, n, nullptr, n, n, n, ctl, st)) != cudaSuccess) return e;
-    if ((e = gemm64<false, 2>(Em, n, Em, n, Mm, n, Em, n, n, n, ctl, st)) != cudaSuccess) return e;
-    if ((e = gemm64<false, 0>(V0, n, Mm, n, V0p, n, nullptr, n, n, n, ctl, st)) != cudaSuccess) return e;
-    // X1 = X0 V0' (into U, then X);  V = Q2 V0' (into L, then V)
-    if ((e = gemm64<false, 0>(w.X, n, V0p, n, X1, n, nullptr, n, n, n, ctl, st)) != cudaSuccess) return e;
-    if ((e = gemm64<false, 0>(w.V, n, V0p, n, V1, n, nullptr, n, n, n, ctl, st)) != cudaSuccess) return e;
+    // E = I - V0^T V0;  M = I + E/2 + (3/8) E^2 (both symmetric);  V0' = V0 M
+    G64Args g = g64(V0, n, V0, n, Em, n, n, ctl);
+    if ((e = gemm64<true, 1, true>(g, false, st)) != cudaSuccess) return e;
+    g = g64(Em, n, Em, n, Mm, n, n, ctl);
+    g.E = Em;
+    if ((e = gemm64<false, 2, true>(g, false, st)) != cudaSuccess) return e;
+    g = g64(V0, n, Mm, n, V0p, n, n, ctl);
+    if ((e = gemm64<false, 0, false>(g, false, st)) != cudaSuccess) return e;
+    // X1 = X0 V0' (into U), V1 = Q2 V0' (into L)
+    g = g64(w.X, n, V0p, n, X1, n, n, ctl);
+    g.A[1] = w.V;
+    g.C[1] = V1;
+    if ((e = gemm64<false, 0, false>(g, true, st)) != cudaSuccess) return e;
+    // two first-order completions: (U, L) -> (X, V) -> (U, L); scratch G (then
+    // K) and K^2 in R2, K^4 in the second half of L, Q in W
+    double *GKm = w.R2, *K2m = w.R2 + n * n, *K4m = w.L + n * n, *Qm = w.W;
+    unsigned int *cw0 = ctl + 4, *cw1 = ctl + 10, *verdict = ctl + 3;
+    if ((e = completion(X1, V1, w.X, w.V, n, GKm, K2m, K4m, Qm, cw0, nullptr, ctl, st)) != cudaSuccess) return e;
+    if ((e = completion(w.X, w.V, X1, V1, n, GKm, K2m, K4m, Qm, cw1, verdict, ctl, st)) != cudaSuccess) return e;
     copy_if_kernel<<<64, 256, 0, st>>>(X1, n * n, w.X, ctl);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     copy_if_kernel<<<64, 256, 0, st>>>(V1, n * n, w.V, ctl);

@@ -181,6 +181,9 @@ def test_dense_stage_benchmark_spectrum(api):
     stats = api.jacobi_stats(d, s, n, ws, sketched=True)
     print("benchmark spectrum: FP64 sweeps %d rotations %d checks %d; FP32 sweeps %d rotations %d" %
           (stats[0], stats[1], stats[2], stats[4], stats[5]))
+    # after the FP32 phase and two first-order completions the FP64 iteration
+    # needs at most its convergence check and one sweep
+    assert stats[4] >= 1 and stats[0] <= 1, stats
     Vk_or, sk_or, _, sig_or, _, st = O.solve_sketched(SA, k)
     _, V, sigma = api.unpack_save(sv, s, n)
     V = V.cpu().numpy()
@@ -192,3 +195,42 @@ def test_dense_stage_benchmark_spectrum(api):
     assert np.max(np.abs(got[big] - ref[big]) / ref[big]) <= 1e-9
     assert sine(Vk_or, Vk.cpu().numpy()) < 1e-8
     assert sine(Vt[:, -k:], Vk.cpu().numpy()) < 1e-8
+
+
+@pytest.mark.parametrize("kind", ["clustered", "half_null"])
+def test_dense_stage_completion_guard(api, kind):
+    # The first-order completion after the FP32 phase, on spectra where it must
+    # hold back: pairs of singular values 1e-10 apart (their rotations are far
+    # from small, so those pairs are left to the FP64 sweeps), and a
+    # 128-dimensional null space (the FP32 phase stops after one sweep, the
+    # cosines are still large and the step is scaled down).  V stays
+    # orthonormal, sigma accurate, and the computed null vectors annihilate SA.
+    rng = np.random.default_rng(31)
+    s, n, k = 1024, 256, 4
+    Q = workloads.orthonormal(rng, s, n)
+    Vt = workloads.orthonormal(rng, n, n)
+    if kind == "clustered":
+        base = np.logspace(0, -5, (n - k) // 2)
+        sig = np.concatenate([np.sort(np.concatenate([base, base * (1 + 1e-10)]))[::-1], np.zeros(k)])
+    else:
+        sig = np.concatenate([np.logspace(0, -3, n // 2), np.zeros(n // 2)])
+    SA = np.asfortranarray(workloads.from_svd(Q, sig, Vt))
+    d = api.desc(api.NS_SRHT, s=s, seed=0)
+    ws = api.workspace(d, s, n, k, "cuda")
+    Vk, sk, sv, status = api.ns_solve_sketched(d, api.colmajor(SA, device="cuda"), k, save=True, ws=ws)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    stats = api.jacobi_stats(d, s, n, ws, sketched=True)
+    assert stats[4] >= 1, stats
+    _, V, sigma = api.unpack_save(sv, s, n)
+    V = V.cpu().numpy()
+    assert np.linalg.norm(V.T @ V - np.eye(n)) < 1e-13 * n
+    _, _, _, sig_or, _, st = O.solve_sketched(SA, k)
+    assert st == 0
+    ref = np.sort(sig_or)[::-1]
+    got = np.sort(sigma.cpu().numpy())[::-1]
+    assert np.max(np.abs(got - ref)) <= 1e-12 * ref[0]
+    Vkn = Vk.cpu().numpy()
+    assert np.linalg.norm(SA @ Vkn) <= 1e-13 * n * ref[0]
+    if kind == "clustered":
+        assert sine(Vt[:, -k:], Vkn) < 1e-8
