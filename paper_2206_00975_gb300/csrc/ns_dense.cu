@@ -573,10 +573,18 @@ __device__ double pipe_apply_form(double *U, int64_t rows, int64_t j, const doub
     return s_beta;
 }
 
-__global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(const double *W, double *U, int64_t rows,
-                                                               int64_t cols, int64_t nown_max, double *u0, double *cf,
-                                                               unsigned long long *flag, double *Rout,
-                                                               int32_t *status) {
+__device__ __forceinline__ void red_release_add(unsigned int *p, unsigned int v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// One CTA's part of the pipelined QR: CTA `me` of a group of G CTAs.  With Lg
+// non-null (the fused two-QR kernel) it also publishes each finished entry of
+// R as an entry of L = R^T (Lg, column-major, leading dimension ldl: column j
+// of L is row j of R) and adds the number it published for row j to rowcnt[j]
+// (release): row j is complete when rowcnt[j] = cols - j.
+__device__ void pipe_qr_cta(const double *W, double *U, int64_t rows, int64_t cols, int64_t nown_max, double *u0,
+                            double *cf, unsigned long long *flag, double *Rout, int32_t *status, int me, int G,
+                            double *Lg, int64_t ldl, unsigned int *rowcnt) {
     extern __shared__ double sm[];
     double *own = sm;                          // nown_max * rows: owned columns
     double *ubuf = sm + nown_max * rows;       // 2 * rows: reflectors j (even/odd)
@@ -585,7 +593,6 @@ __global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(const double *W,
     __shared__ double s_coef[2], s_unrm[2];  // coefficient and tail norm^2 of reflectors j (by parity)
     __shared__ int s_ok;
     const int tid = threadIdx.x;
-    const int G = (int)gridDim.x, me = (int)blockIdx.x;
     const int64_t nown = (cols - me + G - 1) / G;
     const int64_t steps = rows < cols ? rows : cols;
     for (int64_t o = 0; o < nown; ++o)
@@ -595,6 +602,10 @@ __global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(const double *W,
     if (me == 0 && steps > 0) {
         const double b0 = pipe_form(U, rows, 0, own, ubuf, u0, cf, flag, red, &s_coef[0], &s_unrm[0]);
         if (tid == 0) beta[0] = b0;
+        if (Lg && tid == 0) {
+            Lg[0] = b0;  // R[0, 0]
+            red_release_add(rowcnt, 1u);
+        }
         __syncthreads();
     }
     int jm = 0;                                // j mod G: the CTA that formed reflector j
@@ -668,16 +679,32 @@ __global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(const double *W,
                                &s_unrm[(j + 1) & 1]);
             }
             if (tid == 0) beta[o_first] = bj;
+            if (Lg && tid == 0) {
+                Lg[(j + 1) + (j + 1) * ldl] = bj;  // R[j + 1, j + 1]
+                red_release_add(rowcnt + j + 1, 1u);
+            }
         }
         if (coef != 0.0)
             for (int64_t o = o_first + (mine ? 1 : 0); o < nown; ++o) pipe_apply(rows, j, ush, coef, own + o * rows, red);
         if (jn_owner == me) ++o_first;
         __syncthreads();
+        if (Lg && tid == 0) {  // row j of R is final in every owned column past j
+            unsigned int cnt = 0;
+            for (int64_t o = 0; o < nown; ++o) {
+                const int64_t c = me + o * G;
+                if (c > j) {
+                    Lg[c + j * ldl] = own[o * rows + j];
+                    ++cnt;
+                }
+            }
+            if (cnt) red_release_add(rowcnt + j, cnt);
+        }
         if (++jm == G) jm = 0;
     }
     // R: rows 0..steps-1 of every column (column order as stored in W),
     // leading dimension steps; for cols > rows the columns past the last
     // reflector come out as Q^T times their input
+    if (!Rout) return;
     for (int64_t o = 0; o < nown; ++o) {
         const int64_t c = me + o * G;
         for (int64_t i = tid; i < steps; i += kPipeThreads) {
@@ -687,6 +714,293 @@ __global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(const double *W,
             Rout[i + c * steps] = r;
         }
     }
+}
+
+__global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(const double *W, double *U, int64_t rows,
+                                                               int64_t cols, int64_t nown_max, double *u0, double *cf,
+                                                               unsigned long long *flag, double *Rout,
+                                                               int32_t *status) {
+    pipe_qr_cta(W, U, rows, cols, nown_max, u0, cf, flag, Rout, status, (int)blockIdx.x, (int)gridDim.x, nullptr, 0,
+                nullptr);
+}
+
+// ------------------------------------------------- fused two-QR pipeline ----
+// The second QR (of L = [R^T | I], n x 2n) needs column c of L, row c of R,
+// which is final once the first QR has applied reflector c to every column.
+// In one cooperative launch CTAs [0, G1) run the first QR's pipeline and
+// publish each row of R as it becomes final (pipe_qr_cta with Lg); CTAs
+// [G1, G) run the second QR's pipeline on L.  They hold the identity columns
+// from the start and load each column of R^T when its row of R is complete,
+// then bring it up to date with the second QR's reflectors published so far
+// (one warp per column, the reflectors read from U through registers).  The
+// second QR then trails the first by the catch-up of its newest column
+// instead of starting after it.  The arithmetic of each reflector and of its
+// application is that of pipe_form / pipe_apply_form / pipe_apply, so R2 and
+// Q2 equal those of the two separate launches up to the order of the sums in
+// the catch-up and in the warp-level applications.
+constexpr int kQ2MaxOwn = 32;  // owned columns per second-QR CTA
+constexpr int kQ2Lane = 8;     // rows per lane in a warp-level application (n <= 256 = 4 blocks of 64)
+
+// y <- H_{to-1} ... H_from y with the published reflectors (u_i = U[i + k rows]
+// for i >= k, u_k = U[k, k]; coefficient cf[k]).  Warps 0-3 of the CTA, one
+// per SM sub-partition (FP64 issue is scarce per sub-partition): warp w holds
+// rows 64 w + l and 64 w + 32 + l in lane l; each warp's sum goes through
+// shared memory (two slots by parity) and a named barrier of the four warps,
+// and every warp adds the four in the same order.  The next reflector is
+// loaded while the current one is applied.
+__device__ void q2_catch_up4(double *y, int64_t rows, int64_t from, int64_t to, const double *U, const double *cf,
+                             double (*red4)[4]) {
+    if (from >= to) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i0 = 64 * w + lane, i1 = i0 + 32;
+    auto ld = [&](int64_t k, double &a, double &b, double &c) {
+        a = (i0 >= k && i0 < rows) ? __ldcg(U + i0 + k * rows) : 0.0;
+        b = (i1 >= k && i1 < rows) ? __ldcg(U + i1 + k * rows) : 0.0;
+        c = __ldcg(cf + k);
+    };
+    double u0, u1, c;
+    ld(from, u0, u1, c);
+    for (int64_t k = from; k < to; ++k) {
+        double v0 = 0.0, v1 = 0.0, cn = 0.0;
+        if (k + 1 < to) ld(k + 1, v0, v1, cn);
+        const bool a0 = i0 >= k && i0 < rows, a1 = i1 >= k && i1 < rows;
+        const double y0 = a0 ? y[i0] : 0.0, y1 = a1 ? y[i1] : 0.0;
+        const double d = warp_sum(fma(u1, y1, u0 * y0));
+        if (lane == 0) red4[k & 1][w] = d;
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        const double f = c * ((red4[k & 1][0] + red4[k & 1][1]) + (red4[k & 1][2] + red4[k & 1][3]));
+        if (a0) y[i0] = fma(-f, u0, y0);
+        if (a1) y[i1] = fma(-f, u1, y1);
+        u0 = v0;
+        u1 = v1;
+        c = cn;
+    }
+}
+
+// Column o of this CTA (column c of L, c < n) from Lg once row c of R is
+// complete: blocking (bounded wait) or a single probe.  Returns false if the
+// probe found the row incomplete or the wait timed out (then status is set).
+__device__ bool q2_load(const double *Lg, int64_t ldl, const unsigned int *rowcnt, int64_t n, int64_t c, double *y,
+                        bool block, int32_t *status, int *s_flag) {
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        const unsigned int want = (unsigned int)(n - c);
+        int ok = ld_acquire_u32(rowcnt + c) >= want ? 1 : 0;
+        if (!ok && block) {
+            const long long t0 = clock64();
+            while (!ok) {
+                ok = ld_acquire_u32(rowcnt + c) >= want ? 1 : 0;
+                if (!ok && clock64() - t0 > (1ll << 32)) {  // ~2 s; rows arrive microseconds apart
+                    set_status(status, NS_ERR_TIMEOUT);
+                    ok = -1;
+                }
+            }
+        }
+        *s_flag = ok;
+    }
+    __syncthreads();
+    const int ok = *s_flag;
+    if (ok != 1) return false;
+    for (int64_t i = tid; i < n; i += kPipeThreads) y[i] = (i < c) ? 0.0 : __ldcg(Lg + i + c * ldl);
+    __syncthreads();
+    return true;
+}
+
+// One CTA of the second QR in the fused kernel: CTA me of G, columns me,
+// me + G, ... of L = [R^T | I] (n x 2n).
+__device__ void pipe_qr2_cta(const double *Lg, int64_t ldl, const unsigned int *rowcnt, double *U, int64_t n,
+                             int64_t nown_max, double *u0, double *cf, unsigned long long *flag, double *Rout,
+                             int32_t *status, int me, int G) {
+    extern __shared__ double sm[];
+    const int64_t rows = n, cols = 2 * n, steps = n;
+    double *own = sm;                     // nown_max * rows: owned columns
+    double *ubuf = sm + nown_max * rows;  // 2 * rows: reflectors j (even/odd)
+    double *beta = ubuf + 2 * rows;       // nown_max: R2's diagonal of owned columns
+    __shared__ double red[2 * (kPipeThreads / 32) + 1];
+    __shared__ double s_coef[2], s_unrm[2];
+    __shared__ int s_ok, s_flag;
+    __shared__ int s_app[kQ2MaxOwn];  // reflectors applied to owned column o; -1: not loaded yet
+    __shared__ double red4[2][4];     // catch-up: the four warps' sums by parity
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t nown = (cols - me + G - 1) / G;
+    for (int64_t o = 0; o < nown; ++o) {
+        const int64_t c = me + o * G;
+        if (c >= n)
+            for (int64_t i = tid; i < rows; i += kPipeThreads) own[o * rows + i] = (i == c - n) ? 1.0 : 0.0;
+        if (tid == 0) s_app[o] = (c >= n) ? 0 : -1;
+    }
+    if (tid == 0) s_ok = 1;
+    __syncthreads();
+    if (me == 0) {  // column 0 of L: row 0 of R, then reflector 0
+        if (!q2_load(Lg, ldl, rowcnt, n, 0, own, true, status, &s_flag)) return;
+        const double b0 = pipe_form(U, rows, 0, own, ubuf, u0, cf, flag, red, &s_coef[0], &s_unrm[0]);
+        if (tid == 0) {
+            beta[0] = b0;
+            s_app[0] = 1;
+        }
+        __syncthreads();
+    }
+    int jm = 0;                          // j mod G: the CTA that formed reflector j
+    int64_t o_first = (me > 0) ? 0 : 1;  // first owned column after column j
+    for (int64_t j = 0; j < steps; ++j) {
+        double *ush = ubuf + (j & 1) * rows;
+        const int jn_owner = (jm + 1 == G) ? 0 : jm + 1;
+        const bool mine = (j + 1 < steps) && jn_owner == me;  // this CTA forms reflector j + 1
+        if (mine) {  // column j + 1 loaded and brought up to reflector j - 1
+            double *y = own + o_first * rows;
+            if (s_app[o_first] < 0) {
+                if (!q2_load(Lg, ldl, rowcnt, n, j + 1, y, true, status, &s_flag)) return;
+                if (tid == 0) s_app[o_first] = 0;
+                __syncthreads();
+            }
+            if (s_app[o_first] < j) {
+                if (warp < 4) q2_catch_up4(y, rows, s_app[o_first], j, U, cf, red4);
+                __syncthreads();
+                if (tid == 0) s_app[o_first] = (int)j;
+                __syncthreads();
+            }
+        }
+        if (jm != me) {  // reflector j from its owner (as in pipe_qr_cta)
+            const long long t0 = clock64();
+            if (mine) {
+                bool late = false;
+                for (int64_t i = j + tid; i < rows && !late; i += kPipeThreads) {
+                    unsigned long long b;
+                    while ((b = ld_relaxed_u64(U + i + j * rows)) == kPipeEmpty)
+                        if (clock64() - t0 > (1ll << 32)) {
+                            late = true;
+                            break;
+                        }
+                    ush[i] = __longlong_as_double((long long)b);
+                }
+                if (tid == 0 && !late) {
+                    unsigned long long fw, nw = 0;
+                    while ((fw = ld_acquire_flag(flag + j)) == kPipeEmpty)
+                        if (clock64() - t0 > (1ll << 32)) {
+                            late = true;
+                            break;
+                        }
+                    while (!late && j >= 1 && (nw = ld_relaxed_u64(U + j - 1 + j * rows)) == kPipeEmpty)
+                        if (clock64() - t0 > (1ll << 32)) late = true;
+                    s_coef[j & 1] = __longlong_as_double((long long)fw);
+                    s_unrm[j & 1] = __longlong_as_double((long long)nw);
+                }
+                if (late) {
+                    set_status(status, NS_ERR_TIMEOUT);
+                    s_ok = 0;
+                }
+                __syncthreads();
+                if (!s_ok) return;
+            } else {
+                if (tid == 0) {
+                    unsigned long long fw;
+                    while ((fw = ld_acquire_flag(flag + j)) == kPipeEmpty) {
+                        if (clock64() - t0 > (1ll << 32)) {
+                            set_status(status, NS_ERR_TIMEOUT);
+                            s_ok = 0;
+                            break;
+                        }
+                    }
+                    s_coef[j & 1] = __longlong_as_double((long long)fw);
+                }
+                __syncthreads();
+                if (!s_ok) return;
+                for (int64_t i = j + tid; i < rows; i += kPipeThreads) ush[i] = __ldcg(U + i + j * rows);
+                __syncthreads();
+            }
+        }
+        const double coef = s_coef[j & 1];
+        if (mine) {  // look-ahead: column j + 1 first, then reflector j + 1
+            double *y = own + o_first * rows;
+            double *ushn = ubuf + ((j + 1) & 1) * rows;
+            double bj;
+            if (j >= 1) {
+                bj = pipe_apply_form(U, rows, j, ush, coef, s_unrm[j & 1], y, ushn, u0, cf, flag, red,
+                                     &s_coef[(j + 1) & 1], &s_unrm[(j + 1) & 1]);
+            } else {
+                if (coef != 0.0) pipe_apply(rows, j, ush, coef, y, red);
+                bj = pipe_form(U, rows, j + 1, y, ushn, u0, cf, flag, red, &s_coef[(j + 1) & 1],
+                               &s_unrm[(j + 1) & 1]);
+            }
+            if (tid == 0) {
+                beta[o_first] = bj;
+                s_app[o_first] = (int)(j + 2);  // reflectors 0..j applied, j + 1 formed from it
+            }
+        }
+        // reflector j to the other loaded columns past j, one warp per column
+        {
+            int rank = 0;
+            for (int64_t o = o_first + (mine ? 1 : 0); o < nown; ++o) {
+                if (s_app[o] != (int)j) continue;
+                if ((rank & 7) == warp) {
+                    if (coef != 0.0) {
+                        // the sums in the order of q2_catch_up4 (blocks of 64
+                        // rows, then (S0 + S1) + (S2 + S3)), so that a column
+                        // gets the same bits whichever path applies a reflector
+                        double *y = own + o * rows;
+                        const int lane = tid & 31;
+                        double sb[4];
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const int64_t i0 = 64 * b + lane, i1 = i0 + 32;
+                            const bool a0 = i0 >= j && i0 < rows, a1 = i1 >= j && i1 < rows;
+                            const double u0 = a0 ? ush[i0] : 0.0, u1 = a1 ? ush[i1] : 0.0;
+                            const double y0 = a0 ? y[i0] : 0.0, y1 = a1 ? y[i1] : 0.0;
+                            sb[b] = warp_sum(fma(u1, y1, u0 * y0));
+                        }
+                        const double f = coef * ((sb[0] + sb[1]) + (sb[2] + sb[3]));
+#pragma unroll
+                        for (int m = 0; m < kQ2Lane; ++m) {
+                            const int64_t i = lane + 32 * m;
+                            if (i >= j && i < rows) y[i] = fma(-f, ush[i], y[i]);
+                        }
+                    }
+                }
+                ++rank;
+            }
+        }
+        __syncthreads();
+        if (tid == 0)
+            for (int64_t o = o_first + (mine ? 1 : 0); o < nown; ++o)
+                if (s_app[o] == (int)j) s_app[o] = (int)(j + 1);
+        if (jn_owner == me) ++o_first;
+        __syncthreads();
+        // the next own column (the one this CTA forms a reflector from next):
+        // once its row of R is complete, load it and bring it up to reflector
+        // j, off the critical path when the row completed early enough
+        // (columns further on wait: their catch-up would delay this CTA's
+        // next turn on the critical path)
+        if (o_first < nown && me + o_first * G < n && s_app[o_first] < 0 &&
+            q2_load(Lg, ldl, rowcnt, n, me + o_first * G, own + o_first * rows, false, status, &s_flag)) {
+            if (warp < 4) q2_catch_up4(own + o_first * rows, rows, 0, j + 1, U, cf, red4);
+            __syncthreads();
+            if (tid == 0) s_app[o_first] = (int)(j + 1);
+            __syncthreads();
+        }
+        if (++jm == G) jm = 0;
+    }
+    for (int64_t o = 0; o < nown; ++o) {  // [R2 | Q2^T], leading dimension n
+        const int64_t c = me + o * G;
+        for (int64_t i = tid; i < steps; i += kPipeThreads) {
+            double r = 0.0;
+            if (i < c) r = own[o * rows + i];
+            else if (i == c) r = beta[o];
+            Rout[i + c * steps] = r;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kPipeThreads) hqr_fused_kernel(const double *W, double *U1, int64_t s, int64_t n,
+                                                                int64_t nown1, double *u0a, double *cfa,
+                                                                unsigned long long *flag1, double *Lg,
+                                                                unsigned int *rowcnt, double *U2, int64_t nown2,
+                                                                double *u0b, double *cfb, unsigned long long *flag2,
+                                                                double *Rout2, int G1, int32_t *status) {
+    if ((int)blockIdx.x < G1)
+        pipe_qr_cta(W, U1, s, n, nown1, u0a, cfa, flag1, nullptr, status, (int)blockIdx.x, G1, Lg, n, rowcnt);
+    else
+        pipe_qr2_cta(Lg, n, rowcnt, U2, n, nown2, u0b, cfb, flag2, Rout2, status, (int)blockIdx.x - G1,
+                     (int)gridDim.x - G1);
 }
 
 // ------------------------------------------------- static column order ----
@@ -1999,6 +2313,57 @@ static bool launch_hqr_pipe(const double *W, double *U, int64_t rows, int64_t co
     return true;
 }
 
+// The fused two-QR launch (hqr_fused_kernel): both QRs on the pipelined path,
+// n <= 256 (the warp-level applications hold 8 rows per lane).  The CTAs are
+// split in proportion to the two QRs' work per reflector (s n against 2 n^2).
+struct FusedGeom {
+    int G1, G2;
+    int64_t nown1, nown2;
+    size_t smem;
+};
+static bool fused_geom(int64_t s, int64_t n, FusedGeom *g) {
+    if (n < 2 || n > 32 * kQ2Lane || s < n || !pipe_fits(s, n) || !pipe_fits(n, 2 * n)) return false;
+    const int64_t G = sm_count();
+    int64_t G1 = (G * s + (s + 2 * n) / 2) / (s + 2 * n);
+    const int64_t g2min = (2 * n + kQ2MaxOwn - 1) / kQ2MaxOwn;
+    if (G1 > n) G1 = n;
+    if (G1 > G - g2min) G1 = G - g2min;
+    if (G1 < 1) return false;
+    int64_t G2 = G - G1;
+    if (G2 > 2 * n) G2 = 2 * n;
+    g->G1 = (int)G1;
+    g->G2 = (int)G2;
+    g->nown1 = (n + G1 - 1) / G1;
+    g->nown2 = (2 * n + G2 - 1) / G2;
+    if (g->nown2 > kQ2MaxOwn) return false;
+    const int64_t d1 = g->nown1 * s + 2 * s + g->nown1, d2 = g->nown2 * n + 2 * n + g->nown2;
+    g->smem = sizeof(double) * (size_t)(d1 > d2 ? d1 : d2);
+    return g->smem <= 200 * 1024;
+}
+
+// Both QRs of the dense stage in one launch: W (s x n, ordered) -> R2 and Q2^T
+// in Rout2 = [R2 | Q2^T] (n x 2n).  Scratch: U1 (s x n), flag1 (n), Lg (n x n),
+// rowcnt (n words), U2 (n x n), flag2 (n).
+static cudaError_t launch_hqr_fused(const FusedGeom &g, const double *W, double *U1, int64_t s, int64_t n,
+                                    double *u0a, double *cfa, unsigned long long *flag1, double *Lg,
+                                    unsigned int *rowcnt, double *U2, double *u0b, double *cfb,
+                                    unsigned long long *flag2, double *Rout2, int32_t *status, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(flag1, 0xFF, sizeof(unsigned long long) * (size_t)n, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(U1, 0xFF, sizeof(double) * (size_t)(s * n), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(flag2, 0xFF, sizeof(unsigned long long) * (size_t)n, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(U2, 0xFF, sizeof(double) * (size_t)(n * n), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(rowcnt, 0, sizeof(unsigned int) * (size_t)n, st)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(hqr_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem)) !=
+        cudaSuccess)
+        return e;
+    int64_t s_ = s, n_ = n, nown1 = g.nown1, nown2 = g.nown2;
+    int G1 = g.G1;
+    void *args[] = {&W,  &U1,     &s_, &n_,    &nown1, &u0a, &cfa,   &flag1, &Lg,    &rowcnt,
+                    &U2, &nown2,  &u0b, &cfb,  &flag2, &Rout2, &G1, &status};
+    return cudaLaunchCooperativeKernel((const void *)hqr_fused_kernel, g.G1 + g.G2, kPipeThreads, args, g.smem, st);
+}
+
 static cudaError_t launch_hqr(double *W, int64_t rows, int64_t cols, int pivot, double *u0, double *cf,
                               int32_t *perm, unsigned long long *pivslot, double *Rout, GridBarrier bar,
                               cudaStream_t st) {
@@ -2045,6 +2410,7 @@ cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k
     // of the columns by decreasing norm when it fits, else barrier-separated
     // with column pivoting.
     unsigned long long *flags = w.pivslot;  // n + 1 words >= n flags
+    bool fused = false;
     if (pipe_fits(s, n)) {
         double *key = w.X;  // n doubles; X is free until the QR writes R
         colnorm_kernel<<<(unsigned)(n < 1024 ? n : 1024), 256, 0, st>>>(SA, s, n, key);
@@ -2059,7 +2425,17 @@ cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k
         dim3 grid((unsigned)((s + 255) / 256 < 8 ? (s + 255) / 256 : 8), (unsigned)(n < 1024 ? n : 1024));
         permute_cols_kernel<<<grid, 256, 0, st>>>(SA, s, n, w.perm, w.W);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        launch_hqr_pipe(w.W, w.U, s, n, u0a, cfa, flags, w.X, status, st, &e);
+        FusedGeom fg;
+        if (fused_geom(s, n, &fg)) {
+            // both QRs in one launch: [R2 | Q2^T] lands in R2 (Lg in L, U2 in X,
+            // the second QR's flags in sigma, row counts in colver)
+            e = launch_hqr_fused(fg, w.W, w.U, s, n, u0a, cfa, flags, w.L, w.colver, w.X, u0b, cfb,
+                                 reinterpret_cast<unsigned long long *>(w.sigma), w.R2, status, st);
+            fused = (e == cudaSuccess);
+            if (e != cudaSuccess) return e;
+        } else {
+            launch_hqr_pipe(w.W, w.U, s, n, u0a, cfa, flags, w.X, status, st, &e);
+        }
     } else {
         e = cudaMemcpyAsync(w.W, SA, sizeof(double) * (size_t)(s * n), cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
@@ -2073,15 +2449,19 @@ cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k
     // applied to Vx afterwards.
     const dim3 ttb(32, 8), tgrid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
     const unsigned nn_blocks = (unsigned)((n * n + 255) / 256);
-    transpose_kernel<<<tgrid, ttb, 0, st>>>(w.X, n, w.L);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const bool q2_in_v = pipe_fits(n, 2 * n);
+    if (!fused) {
+        transpose_kernel<<<tgrid, ttb, 0, st>>>(w.X, n, w.L);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const bool q2_in_v = fused || pipe_fits(n, 2 * n);
     const double *Lq = w.L;  // reflectors of the second QR (barrier-separated path)
     if (q2_in_v) {
-        identity_kernel<<<nn_blocks, 256, 0, st>>>(w.L + n * n, n);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        launch_hqr_pipe(w.L, w.U, n, 2 * n, u0b, cfb, flags, w.R2, status, st, &e);
-        if (e != cudaSuccess) return e;
+        if (!fused) {
+            identity_kernel<<<nn_blocks, 256, 0, st>>>(w.L + n * n, n);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            launch_hqr_pipe(w.L, w.U, n, 2 * n, u0b, cfb, flags, w.R2, status, st, &e);
+            if (e != cudaSuccess) return e;
+        }
         // 3. X = R2^T, V = (Q2^T)^T
         r2t_kernel<<<nn_blocks, 256, 0, st>>>(w.R2, n, w.X);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
