@@ -741,15 +741,28 @@ __global__ void __launch_bounds__(kPipeThreads) hqr_pipe_kernel(const double *W,
 constexpr int kQ2MaxOwn = 32;  // owned columns per second-QR CTA
 constexpr int kQ2Lane = 8;     // rows per lane in a warp-level application (n <= 256 = 4 blocks of 64)
 
+// The inner product u . y of a second-QR reflector with a column (n <= 256)
+// in one fixed order, whichever path applies it: lane l forms
+// q_b = u[64b+32+l] y[64b+32+l] + u[64b+l] y[64b+l] (one FMA after a product)
+// for the four blocks b, adds (q_0 + q_1) + (q_2 + q_3), and the warp sums the
+// lanes with the butterfly of warp_sum.  So a column gets the same bits
+// whether a reflector reaches it in the step loop or in a catch-up.
+__device__ __forceinline__ double q2_block_term(const double *u, const double *y, int64_t rows, int64_t k, int b) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i0 = 64 * b + lane, i1 = i0 + 32;
+    const bool a0 = i0 >= k && i0 < rows, a1 = i1 >= k && i1 < rows;
+    return fma(a1 ? u[i1] : 0.0, a1 ? y[i1] : 0.0, (a0 ? u[i0] : 0.0) * (a0 ? y[i0] : 0.0));
+}
+
 // y <- H_{to-1} ... H_from y with the published reflectors (u_i = U[i + k rows]
 // for i >= k, u_k = U[k, k]; coefficient cf[k]).  Warps 0-3 of the CTA, one
-// per SM sub-partition (FP64 issue is scarce per sub-partition): warp w holds
-// rows 64 w + l and 64 w + 32 + l in lane l; each warp's sum goes through
-// shared memory (two slots by parity) and a named barrier of the four warps,
-// and every warp adds the four in the same order.  The next reflector is
-// loaded while the current one is applied.
+// per SM sub-partition (FP64 issue is scarce per sub-partition): warp w forms
+// q_w for every lane from its rows 64 w + l, 64 w + 32 + l; the four q's meet
+// in shared memory (two slots by parity, a named barrier of the four warps)
+// and every warp finishes the sum in the order above.  The next reflector
+// is loaded while the current one is applied.
 __device__ void q2_catch_up4(double *y, int64_t rows, int64_t from, int64_t to, const double *U, const double *cf,
-                             double (*red4)[4]) {
+                             double (*qbuf)[4][32]) {
     if (from >= to) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t i0 = 64 * w + lane, i1 = i0 + 32;
@@ -765,10 +778,10 @@ __device__ void q2_catch_up4(double *y, int64_t rows, int64_t from, int64_t to, 
         if (k + 1 < to) ld(k + 1, v0, v1, cn);
         const bool a0 = i0 >= k && i0 < rows, a1 = i1 >= k && i1 < rows;
         const double y0 = a0 ? y[i0] : 0.0, y1 = a1 ? y[i1] : 0.0;
-        const double d = warp_sum(fma(u1, y1, u0 * y0));
-        if (lane == 0) red4[k & 1][w] = d;
+        qbuf[k & 1][w][lane] = fma(u1, y1, u0 * y0);
         asm volatile("bar.sync 1, 128;" ::: "memory");
-        const double f = c * ((red4[k & 1][0] + red4[k & 1][1]) + (red4[k & 1][2] + red4[k & 1][3]));
+        const double p = (qbuf[k & 1][0][lane] + qbuf[k & 1][1][lane]) + (qbuf[k & 1][2][lane] + qbuf[k & 1][3][lane]);
+        const double f = c * warp_sum(p);
         if (a0) y[i0] = fma(-f, u0, y0);
         if (a1) y[i1] = fma(-f, u1, y1);
         u0 = v0;
@@ -820,7 +833,7 @@ __device__ void pipe_qr2_cta(const double *Lg, int64_t ldl, const unsigned int *
     __shared__ double s_coef[2], s_unrm[2];
     __shared__ int s_ok, s_flag;
     __shared__ int s_app[kQ2MaxOwn];  // reflectors applied to owned column o; -1: not loaded yet
-    __shared__ double red4[2][4];     // catch-up: the four warps' sums by parity
+    __shared__ double qbuf[2][4][32];  // catch-up: the four warps' lane terms by parity
     const int tid = threadIdx.x, warp = tid >> 5;
     const int64_t nown = (cols - me + G - 1) / G;
     for (int64_t o = 0; o < nown; ++o) {
@@ -854,7 +867,7 @@ __device__ void pipe_qr2_cta(const double *Lg, int64_t ldl, const unsigned int *
                 __syncthreads();
             }
             if (s_app[o_first] < j) {
-                if (warp < 4) q2_catch_up4(y, rows, s_app[o_first], j, U, cf, red4);
+                if (warp < 4) q2_catch_up4(y, rows, s_app[o_first], j, U, cf, qbuf);
                 __syncthreads();
                 if (tid == 0) s_app[o_first] = (int)j;
                 __syncthreads();
@@ -934,21 +947,11 @@ __device__ void pipe_qr2_cta(const double *Lg, int64_t ldl, const unsigned int *
                 if (s_app[o] != (int)j) continue;
                 if ((rank & 7) == warp) {
                     if (coef != 0.0) {
-                        // the sums in the order of q2_catch_up4 (blocks of 64
-                        // rows, then (S0 + S1) + (S2 + S3)), so that a column
-                        // gets the same bits whichever path applies a reflector
                         double *y = own + o * rows;
                         const int lane = tid & 31;
-                        double sb[4];
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            const int64_t i0 = 64 * b + lane, i1 = i0 + 32;
-                            const bool a0 = i0 >= j && i0 < rows, a1 = i1 >= j && i1 < rows;
-                            const double u0 = a0 ? ush[i0] : 0.0, u1 = a1 ? ush[i1] : 0.0;
-                            const double y0 = a0 ? y[i0] : 0.0, y1 = a1 ? y[i1] : 0.0;
-                            sb[b] = warp_sum(fma(u1, y1, u0 * y0));
-                        }
-                        const double f = coef * ((sb[0] + sb[1]) + (sb[2] + sb[3]));
+                        const double p = (q2_block_term(ush, y, rows, j, 0) + q2_block_term(ush, y, rows, j, 1)) +
+                                         (q2_block_term(ush, y, rows, j, 2) + q2_block_term(ush, y, rows, j, 3));
+                        const double f = coef * warp_sum(p);
 #pragma unroll
                         for (int m = 0; m < kQ2Lane; ++m) {
                             const int64_t i = lane + 32 * m;
@@ -972,7 +975,7 @@ __device__ void pipe_qr2_cta(const double *Lg, int64_t ldl, const unsigned int *
         // next turn on the critical path)
         if (o_first < nown && me + o_first * G < n && s_app[o_first] < 0 &&
             q2_load(Lg, ldl, rowcnt, n, me + o_first * G, own + o_first * rows, false, status, &s_flag)) {
-            if (warp < 4) q2_catch_up4(own + o_first * rows, rows, 0, j + 1, U, cf, red4);
+            if (warp < 4) q2_catch_up4(own + o_first * rows, rows, 0, j + 1, U, cf, qbuf);
             __syncthreads();
             if (tid == 0) s_app[o_first] = (int)(j + 1);
             __syncthreads();
@@ -2324,7 +2327,11 @@ struct FusedGeom {
 static bool fused_geom(int64_t s, int64_t n, FusedGeom *g) {
     if (n < 2 || n > 32 * kQ2Lane || s < n || !pipe_fits(s, n) || !pipe_fits(n, 2 * n)) return false;
     const int64_t G = sm_count();
-    int64_t G1 = (G * s + (s + 2 * n) / 2) / (s + 2 * n);
+    // columns per first-QR CTA for a split in proportion to the work per
+    // reflector (s n against 2 n^2), then the fewest CTAs with that many: the
+    // second QR, whose CTAs also catch columns up, gets the rest
+    const int64_t per1 = (n * (s + 2 * n) + G * s - 1) / (G * s);
+    int64_t G1 = (n + per1 - 1) / per1;
     const int64_t g2min = (2 * n + kQ2MaxOwn - 1) / kQ2MaxOwn;
     if (G1 > n) G1 = n;
     if (G1 > G - g2min) G1 = G - g2min;

@@ -106,4 +106,12 @@ def test_aaa_full_size_workload(api):
     assert g["status"][0] == 0
     sup, W, err, st, SAk = O.aaa(0, x, f, 100, 400, forced=g["support"], return_sketch=True)
     assert np.max(np.abs(g["SAk"] - SAk)) <= 1e-10 * np.max(np.abs(SAk))
-    assert g["errmax"][-1] < 1e-10 * np.abs(f).max()
+    # AAA converges (to ~1e-13 here, near iteration 25) and then keeps adding
+    # support points to an ever worse conditioned Loewner matrix: past that
+    # point the error is set by rounding, for the oracle replaying the same
+    # support points as much as for the GPU (both wander between 1e-11 and
+    # 1e-7).  So: the GPU converges, and its error after the last iteration is
+    # no worse than the oracle's on the same support points.
+    fmax = np.abs(f).max()
+    assert g["errmax"].min() < 1e-12 * fmax
+    assert g["errmax"][-1] <= max(1e-10 * fmax, 10.0 * err[-1])
