@@ -737,7 +737,7 @@ def main():
                   "peak_source": "derived: %d SMs x 4 FP64 flop/clk x sampled SM clock" % n_sm,
                   "algorithmic_flops": dflops, "jacobi_sweeps_rotations_checks": stats[:3],
                   "fp32_phase_sweeps_rotations": stats[4:6],
-                  "completions_with_k4_and_check_first": stats[6:8],
+                  "completions_with_k4_and_gram_check": stats[6:8],
                   "jacobi_kernel": ("cluster ring, %d CTAs per cluster" % stats[3]) if stats[3] else "barrier-separated"}
     dominant = dense_roof if t_dense > t_sketch else sketch_roof
     line = {

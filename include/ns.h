@@ -239,8 +239,10 @@ ns_status ns_solve_sketched(const ns_sketch_desc *desc, const double *SA, int64_
  * Jacobi, or 0: the barrier-separated one), the sweeps and rotations of the
  * FP32 linear phase that precedes the FP64 iteration for 64 <= n <= 256 (0
  * and 0 when it did not run), how many of the two first-order completions
- * that follow the phase formed their K^4 and K^6 terms, and 1 if the FP64
- * iteration started with its convergence check (else 0).
+ * that follow the phase formed their K^4 and K^6 terms, and 1 if the
+ * iteration's convergence test ran on the Gram matrix X^T X after the last
+ * completion (else 0; when it finds no pair above the tolerance the FP64
+ * iteration runs no sweep).
  * Enqueued on stream after that call.
  */
 ns_status ns_solve_stats(const ns_sketch_desc *desc, int64_t m, int64_t n, const void *ws, int64_t *dev_out,

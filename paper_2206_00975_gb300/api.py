@@ -331,8 +331,8 @@ def ns_solve_sketched(d, SA, k, save=False, status=None, ws=None, stream=None):
 
 def jacobi_stats(d, m, n, ws, sketched=False, stream=None):
     """(FP64 full sweeps, FP64 rotations, check passes, ring cluster size or 0, FP32-phase sweeps,
-    FP32-phase rotations, completions with K^4 and K^6 terms, 1 if the FP64 iteration started with
-    its check) of the last solve in workspace ws."""
+    FP32-phase rotations, completions with K^4 and K^6 terms, 1 if the convergence test ran on the
+    Gram matrix after the completions) of the last solve in workspace ws."""
     out = torch.zeros(8, dtype=torch.int64, device=ws.device)
     lib = _lib.load()
     if sketched:

@@ -45,12 +45,12 @@ constexpr int kDenseThreads = 256;
 constexpr int kMaxSweeps = 30;
 constexpr int kCheckBelow = 4096;        // run the barrier-free check after a sweep with fewer rotations
 constexpr int kBarWords = 64 + 2 * 64 + 32;  // barrier word (padded), rotation counts, check flags, stats,
-                                             // FP32-phase control (bar[196..211])
+                                             // FP32-phase control (bar[196..212])
 // words of bar from kJ32Ctl: 1 if the FP32 phase ran, its sweeps, its rotations,
 // the completions' verdict (2: start the FP64 iteration with the convergence
 // check), then 6 words per completion (see ns_jacobi32.cu)
 constexpr int kJ32Ctl = 196;
-static_assert(kJ32Ctl + 16 <= kBarWords, "FP32-phase control words");
+static_assert(kJ32Ctl + 17 <= kBarWords, "FP32-phase control words");
 
 size_t dense_work_bytes(int64_t s, int64_t n) {
     Carver c(nullptr);
@@ -1693,11 +1693,18 @@ __global__ void __cluster_dims__(kRingC, 1, 1) __launch_bounds__(kRingCta, 2)
     uint32_t ostep = 0;  // outer steps so far: phase parity of the slot mbarriers
     // After the FP32 phase and its first-order completions the columns start
     // nearly orthogonal: the barrier-free check runs from the third sweep on
-    // whatever the rotation count was, and before the first sweep when the
-    // last completion left no pair out and only tiny rotations (verdict 2).
+    // whatever the rotation count was.  When the last completion left no pair
+    // out and only tiny rotations (verdict 2), the convergence test has
+    // already run on the Gram matrix of X (the FP64 rule of the check pass,
+    // on G = X^T X), and with no pair above the tolerance (word 16 still 0)
+    // there is nothing left to do but the singular values.
     const unsigned int ran = fp32_ran ? *(volatile const unsigned int *)fp32_ran : 0u;
-    const int check_from =
-        ran ? ((*(volatile const unsigned int *)(fp32_ran + 3) == 2u) ? 0 : 2) : max_sweeps + 1;
+    const bool gram_checked = ran && *(volatile const unsigned int *)(fp32_ran + 3) == 2u;
+    if (gram_checked && *(volatile const unsigned int *)(fp32_ran + 16) == 0u) {
+        converged = true;
+        check_passes = 1;
+    }
+    const int check_from = ran ? 2 : max_sweeps + 1;
     for (int sweep = 0; sweep < max_sweeps && !converged && ok; ++sweep) {
         if (prev_rot < (unsigned int)kCheckBelow || sweep >= check_from) {
             ++check_passes;
@@ -2047,6 +2054,7 @@ __global__ void __launch_bounds__(kDenseThreads) apply_q2_kernel(const double *_
 // (lowest index on ties) is positive.  One CTA per returned column.
 __global__ void __launch_bounds__(kDenseThreads) extract_kernel(const double *V, const double *sigma, int64_t n,
                                                                int32_t k, double *Vk, double *sigk) {
+    extern __shared__ long long skey[];  // n: sigma as ordered integer keys
     __shared__ int src_sh;
     __shared__ long long bestk[32];
     __shared__ int besti[32];
@@ -2054,12 +2062,15 @@ __global__ void __launch_bounds__(kDenseThreads) extract_kernel(const double *V,
     const int64_t col = blockIdx.x;  // output column
     const int64_t want = (n - k) + col;  // rank of the wanted singular value
     if (tid == 0) src_sh = -1;
+    // sigma >= 0 orders like its bit pattern (NaN above every number), so the
+    // ranks are integer compares
+    for (int64_t i = tid; i < n; i += blockDim.x) skey[i] = __double_as_longlong(sigma[i]);
     __syncthreads();
     for (int64_t i = tid; i < n; i += blockDim.x) {
-        const double si = sigma[i];
+        const long long si = skey[i];
         int64_t r = 0;
         for (int64_t j = 0; j < n; ++j) {
-            const double sj = sigma[j];
+            const long long sj = skey[j];
             r += (sj > si || (sj == si && j < i)) ? 1 : 0;
         }
         if (r == want) src_sh = (int)i;
@@ -2180,7 +2191,8 @@ cudaError_t launch_test_wait(int which, long long limit, int32_t *status, unsign
 cudaError_t launch_dense_select_eps(const DenseWork &w, int64_t n, double eps, double *Vk, double *sigk,
                                     int32_t *dev_k, cudaStream_t st) {
     // all n columns in order into X (free after the iteration), their sigma into L
-    extract_kernel<<<(unsigned)n, kDenseThreads, 0, st>>>(w.W, w.sigma, n, (int32_t)n, w.X, w.L);
+    extract_kernel<<<(unsigned)n, kDenseThreads, sizeof(long long) * (size_t)n, st>>>(w.W, w.sigma, n, (int32_t)n, w.X,
+                                                                                      w.L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t blocks = n < sm_count() * 4 ? n : sm_count() * 4;
@@ -2395,7 +2407,7 @@ __global__ void dense_stats_kernel(const unsigned int *bar, int64_t *out) {
         out[3] = bar[64 + 131];
         out[4] = bar[kJ32Ctl] ? bar[kJ32Ctl + 1] : 0;  // FP32-phase sweeps (0: the phase did not run)
         out[5] = bar[kJ32Ctl] ? bar[kJ32Ctl + 2] : 0;  // FP32-phase rotations
-        // completions that formed the K^4 and K^6 terms; FP64 iteration started with its check
+        // completions that formed the K^4 and K^6 terms; convergence test ran on the Gram matrix
         out[6] = bar[kJ32Ctl] ? (int64_t)bar[kJ32Ctl + 5] + (int64_t)bar[kJ32Ctl + 11] : 0;
         out[7] = (bar[kJ32Ctl] && bar[kJ32Ctl + 3] == 2u) ? 1 : 0;
     }
@@ -2517,7 +2529,7 @@ cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k
     }
     // 5. extraction (k = 0: left to the caller, V in w.W and sigma in w.sigma)
     if (k > 0) {
-        extract_kernel<<<(unsigned)k, kDenseThreads, 0, st>>>(w.W, w.sigma, n, k, Vk, sigk);
+        extract_kernel<<<(unsigned)k, kDenseThreads, sizeof(long long) * (size_t)n, st>>>(w.W, w.sigma, n, k, Vk, sigk);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (save_V) {

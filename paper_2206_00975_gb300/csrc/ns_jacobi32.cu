@@ -452,9 +452,12 @@ __global__ void __cluster_dims__(kJ32Cta, 1, 1) __launch_bounds__(kJ32Threads, 1
 
 // ----------------------------------------------------- small FP64 GEMMs ----
 // C (M x N, column-major, leading dimension ldc) = op(A) B with op(A) = A
-// (M x K) or A^T (A: K x M), B (K x N).  One 16 x 16 tile per CTA, one output
-// per thread, K in chunks of 16 through shared memory.  Skipped when
-// *ctl == 0 (the FP32 phase did not run).
+// (M x K) or A^T (A: K x M), B (K x N).  One 8 x 8 tile per CTA of 128
+// threads: two threads per output, one summing the even chunks of 8 k, the
+// other the odd ones (each an FMA chain in increasing k), then their sum.
+// Small tiles and the split of K keep enough independent chains in flight on
+// each SM sub-partition's FP64 pipe even for a symmetric product of n = 256
+// (528 tiles).  Skipped when *ctl == 0 (the FP32 phase did not run).
 //   EPI 0: C = AB;  1: C = I - AB;  2: C = I + E/2 + (3/8) AB;
 //   EPI 3: C = Q = I + t K + t^2 K2/2 - t^4 K4/8 + t^6 AB/16, the
 //          completion's rotation (K's diagonal slots hold other data and
@@ -468,7 +471,7 @@ __global__ void __cluster_dims__(kJ32Cta, 1, 1) __launch_bounds__(kJ32Threads, 1
 //        flipped for EPI 3, and on a diagonal tile the upper entry defines
 //        both, so the result is exactly symmetric (apart from K).
 //   blockIdx.z picks one of two (A, C) pairs: X Q and V Q in one launch.
-constexpr int kG64T = 16;
+constexpr int kG64T = 8;
 
 struct G64Args {
     const double *A[2];
@@ -485,6 +488,7 @@ struct G64Args {
     unsigned int *verdict;          // EPI 3: where the last completion writes its verdict, else null
     unsigned int *ran;              // EPI 4: set to 1 when the product ran
     const unsigned int *cnt;        // EPI 3: pairs left out, then max |K| (bits) at cnt + 2
+    const unsigned int *gate;       // if set: the product runs only when *gate == 2
     int64_t M, N, K;
     const unsigned int *ctl;
 };
@@ -501,14 +505,16 @@ __device__ __forceinline__ double corr_bound(const unsigned long long *bnd) {
 }
 
 template <bool TA, int EPI, bool SYM, bool DZ>
-__global__ void __launch_bounds__(kG64T * kG64T) gemm64_kernel(const G64Args g) {
+__global__ void __launch_bounds__(2 * kG64T * kG64T) gemm64_kernel(const G64Args g) {
     if (g.ctl && *(volatile const unsigned int *)g.ctl == 0u) return;
+    if (g.gate && *(volatile const unsigned int *)g.gate != 2u) return;
     bool skip_k = false;  // EPI 3, 4: the K^4 and K^6 terms are negligible
     if (EPI == 3 || EPI == 4) skip_k = corr_bound(g.bnd) <= kCorrSmall;
     if (EPI == 4 && skip_k) return;
     if (EPI == 4 && blockIdx.x == 0 && threadIdx.x == 0) *g.ran = 1u;
-    __shared__ double As[kG64T][kG64T + 1];  // As[k][i] = op(A)[i, k]
-    __shared__ double Bs[kG64T][kG64T + 1];  // Bs[k][j] = B[k, j]
+    __shared__ double As[2][kG64T][kG64T + 1];  // As[h][k][i] = op(A)[i, k] of chunk h
+    __shared__ double Bs[2][kG64T][kG64T + 1];  // Bs[h][k][j] = B[k, j] of chunk h
+    __shared__ double part[kG64T * kG64T];      // the odd chunks' sums
     int64_t bx = blockIdx.x, by = blockIdx.y;
     if (SYM) {  // triangular index -> tile (bx, by), bx <= by
         int64_t t = blockIdx.x;
@@ -521,25 +527,31 @@ __global__ void __launch_bounds__(kG64T * kG64T) gemm64_kernel(const G64Args g) 
     }
     const double *A = g.A[blockIdx.z];
     double *C = g.C[blockIdx.z];
-    const int tx = threadIdx.x % kG64T, ty = threadIdx.x / kG64T;
+    const int h = threadIdx.x / (kG64T * kG64T), tl = threadIdx.x % (kG64T * kG64T);
+    const int tx = tl % kG64T, ty = tl / kG64T;
     const int64_t i = bx * kG64T + tx, j = by * kG64T + ty;
     const int64_t M = g.M, N = g.N, K = skip_k ? 0 : g.K;
     double acc = 0.0;
-    for (int64_t k0 = 0; k0 < K; k0 += kG64T) {
-        {   // thread (tx, ty) loads op(A)[bx*16 + ?, k0 + ?] and B[k0 + ?, by*16 + ?]
+    for (int64_t k00 = 0; k00 < K; k00 += 2 * kG64T) {
+        {   // half h loads chunk k00 + h*8: op(A)[bx*8 + ?, k + ?] and B[k + ?, by*8 + ?]
+            const int64_t k0 = k00 + h * kG64T;
             const int64_t ai = bx * kG64T + (TA ? ty : tx), ak = k0 + (TA ? tx : ty);
             double av = 0.0;
             if (ai < M && ak < K && !(DZ && ai == ak)) av = TA ? A[ak + ai * g.lda] : A[ai + ak * g.lda];
-            if (TA) As[tx][ty] = av;
-            else As[ty][tx] = av;
+            if (TA) As[h][tx][ty] = av;
+            else As[h][ty][tx] = av;
             const int64_t bk = k0 + tx, bj = by * kG64T + ty;
-            Bs[tx][ty] = (bk < K && bj < N && !(DZ && bk == bj)) ? g.B[bk + bj * g.ldb] : 0.0;
+            Bs[h][tx][ty] = (bk < K && bj < N && !(DZ && bk == bj)) ? g.B[bk + bj * g.ldb] : 0.0;
         }
         __syncthreads();
 #pragma unroll
-        for (int kk = 0; kk < kG64T; ++kk) acc = fma(As[kk][tx], Bs[kk][ty], acc);
+        for (int kk = 0; kk < kG64T; ++kk) acc = fma(As[h][kk][tx], Bs[h][kk][ty], acc);
         __syncthreads();
     }
+    if (h == 1) part[tl] = acc;
+    __syncthreads();
+    if (h == 1) return;
+    acc += part[tl];
     if (EPI == 3 && g.verdict && blockIdx.x == 0 && threadIdx.x == 0) {
         // verdict for the FP64 iteration: 2 (start with the convergence check)
         // when the full step was taken, no pair was left out and every
@@ -583,7 +595,7 @@ static cudaError_t gemm64(const G64Args &g, bool dual, cudaStream_t st) {
     const int64_t mt = (g.M + kG64T - 1) / kG64T, nt = (g.N + kG64T - 1) / kG64T;
     const dim3 grid = SYM ? dim3((unsigned)(mt * (mt + 1) / 2), 1, dual ? 2 : 1)
                           : dim3((unsigned)mt, (unsigned)nt, dual ? 2 : 1);
-    gemm64_kernel<TA, EPI, SYM, DZ><<<grid, kG64T * kG64T, 0, st>>>(g);
+    gemm64_kernel<TA, EPI, SYM, DZ><<<grid, 2 * kG64T * kG64T, 0, st>>>(g);
     return cudaGetLastError();
 }
 
@@ -668,6 +680,24 @@ __global__ void __launch_bounds__(256) corr_bound_kernel(const double *K2, int64
     for (int64_t i = lane; i < n; i += 32) sum += fabs(K2[i + j * n]);
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (lane == 0) atomicMax((unsigned long long *)(cw + 4), (unsigned long long)__double_as_longlong(sum));
+}
+
+// The FP64 iteration's convergence test on the Gram matrix of the final X
+// (G = X^T X, only when the last completion's verdict is 2): a pair needs a
+// rotation when G[p, q] != 0 and G[p, q]^2 > tol^2 G[p, p] G[q, q], the rule of
+// the iteration's own check pass; any such pair sets ctl[16].
+__global__ void __launch_bounds__(256) corr_check_kernel(const double *G, int64_t n, double tol2,
+                                                         unsigned int *ctl) {
+    if (*(volatile const unsigned int *)ctl == 0u || *(volatile const unsigned int *)(ctl + 3) != 2u) return;
+    int bad = 0;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n * n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = idx % n, q = idx / n;
+        if (p >= q) continue;
+        const double g = G[idx];
+        if (g != 0.0 && g * g > tol2 * G[p + p * n] * G[q + q * n]) bad = 1;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(ctl + 16, 1u);
 }
 
 // (Xo, Vo) = (Xi, Vi) Q for one completion; scratch: G (then K) and K^2
@@ -756,6 +786,14 @@ cudaError_t launch_jacobi32_precondition(const DenseWork &w, int64_t n, unsigned
     unsigned int *cw0 = ctl + 4, *cw1 = ctl + 10, *verdict = ctl + 3;
     if ((e = completion(X1, V1, w.X, w.V, n, GKm, K2m, K4m, Qm, cw0, nullptr, ctl, st)) != cudaSuccess) return e;
     if ((e = completion(w.X, w.V, X1, V1, n, GKm, K2m, K4m, Qm, cw1, verdict, ctl, st)) != cudaSuccess) return e;
+    // the FP64 iteration's convergence test, on G = X^T X of the final X when
+    // the last completion expects convergence (tolerance n 2^-53, as there)
+    g = g64(X1, n, X1, n, GKm, n, n, ctl);
+    g.gate = verdict;
+    if ((e = gemm64<true, 0, true>(g, false, st)) != cudaSuccess) return e;
+    const double tol = (double)n * std::ldexp(1.0, -53);
+    corr_check_kernel<<<64, 256, 0, st>>>(GKm, n, tol * tol, ctl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     copy_if_kernel<<<64, 256, 0, st>>>(X1, n * n, w.X, ctl);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     copy_if_kernel<<<64, 256, 0, st>>>(V1, n * n, w.V, ctl);
