@@ -175,6 +175,33 @@ ns_status ns_solve(const ns_sketch_desc *desc, const void *A, int32_t dtype, int
                    size_t ws_bytes, void *stream);
 
 /*
+ * ns_solve_pipelined -- Algorithm 1 (as ns_solve) for `count` independent
+ * problems of the same shape, dtype and lda, with the sketch of problem i + 1
+ * running while the dense stage of problem i is past its two QRs (which hold
+ * every SM): a throughput form for a stream of problems.  The library runs the
+ * sketches and the dense stages on two streams of its own (per device; dense
+ * stages at the higher priority), ordered after all work already enqueued on
+ * `stream`; every result is complete before work enqueued on `stream` later.
+ *   A      host array of `count` device pointers, problem i = A[i] (m x n,
+ *          column-major, leading dimension lda, dtype as ns_solve).
+ *   Vk     device, count * n * k FP64: problem i at Vk + i n k (n x k each,
+ *          ordered and signed as ns_solve).
+ *   sigk   device, count * k FP64: problem i at sigk + i k.
+ *   dev_status  device int32[count] (may be NULL): problem i's status.
+ *   ws     ns_solve_pipelined_workspace_size(desc, m, n) bytes, 256-byte
+ *          aligned (two sketch slots and one dense workspace).
+ * The results are those of ns_solve on each problem, bit for bit (the same
+ * kernels in the same order per problem).  Not re-entrant for one device
+ * from several host threads at once (the library's streams are shared).
+ * Errors: NS_ERR_INVALID_ARG as ns_solve, and for count < 1 or a null or
+ * misaligned A[i]; NS_ERR_WORKSPACE; NS_ERR_CUDA.
+ */
+size_t ns_solve_pipelined_workspace_size(const ns_sketch_desc *desc, int64_t m, int64_t n);
+ns_status ns_solve_pipelined(const ns_sketch_desc *desc, const void *const *A, int32_t count, int32_t dtype,
+                             int64_t m, int64_t n, int64_t lda, int32_t k, double *Vk, double *sigk,
+                             int32_t *dev_status, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * ns_solve_eps -- the tolerance version of Algorithm 1 (Section 2, the remark
  * after Algorithm 1): instead of k, W is every right singular vector of SA
  * whose singular value is below eps (eps = O(u) sigma_1 gives the numerical

@@ -24,6 +24,7 @@ EXPORTS = [
     "ns_batched_workspace_size", "ns_solve_batched", "ns_aaa_workspace_size", "ns_aaa_real",
     "ns_solve_sketched", "ns_solve_stats", "ns_sketched_stats", "ns_solve_eps", "ns_sketch_update",
     "ns_test_bounded_wait", "ns_batched_tuning", "ns_sketch_rows", "ns_sketch_rows_workspace_size",
+    "ns_solve_pipelined", "ns_solve_pipelined_workspace_size",
 ]
 
 
@@ -84,6 +85,8 @@ def load():
         "ns_test_bounded_wait": (ctypes.c_int, [i32, i64, P, P, sz, P]),
         "ns_batched_tuning": (ctypes.c_int, [i32, i32, i32]),
         "ns_sketch_rows_workspace_size": (sz, [D, i64, i64, i64, i64]),
+        "ns_solve_pipelined_workspace_size": (sz, [D, i64, i64]),
+        "ns_solve_pipelined": (ctypes.c_int, [D, P, i32, i32, i64, i64, i64, i32, P, P, P, P, sz, P]),
         "ns_sketch_rows": (ctypes.c_int, [D, P, i32, i64, i64, i64, i64, i64, P, P, P, sz, P]),
     }
     for name, (res, args) in sig.items():

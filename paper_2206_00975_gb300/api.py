@@ -133,6 +133,40 @@ def ns_solve(d, A, k, save=True, status=None, ws=None, stream=None):
     return Vk, sigk, sv, status
 
 
+def pipelined_workspace(d, m, n, device):
+    nbytes = _lib.load().ns_solve_pipelined_workspace_size(ctypes.byref(d), m, n)
+    if nbytes == 0:
+        raise ValueError("invalid pipelined solve shape")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def ns_solve_pipelined(d, As, k, status=None, ws=None, stream=None):
+    """Algorithm 1 for the problems As (column-major device tensors of one shape and dtype), the
+    sketch of problem i + 1 overlapping the dense stage of problem i: returns (Vk count x n x k as
+    a list of n x k column-major views, sigk count x k, status int32 per problem)."""
+    if not As:
+        raise ValueError("no problems")
+    m, n = As[0].shape
+    dev = As[0].device
+    for A in As:
+        if A.shape != As[0].shape or A.dtype != As[0].dtype or _ld(A) != _ld(As[0]):
+            raise ValueError("the problems must share shape, dtype and leading dimension")
+    count = len(As)
+    Vall = torch.empty(count * n * k, dtype=torch.float64, device=dev)
+    sig = torch.empty(count * k, dtype=torch.float64, device=dev)
+    if status is None:
+        status = torch.zeros(count, dtype=torch.int32, device=dev)
+    if ws is None:
+        ws = pipelined_workspace(d, m, n, dev)
+    ptrs = (ctypes.c_void_p * count)(*[_p(A) for A in As])
+    st = _lib.load().ns_solve_pipelined(ctypes.byref(d), ptrs, count, _dtype_code(As[0]), m, n, _ld(As[0]),
+                                        int(k), _p(Vall), _p(sig), _p(status), _p(ws), ws.numel(),
+                                        _stream(stream))
+    _lib.check(st, "ns_solve_pipelined")
+    Vks = [Vall[i * n * k:(i + 1) * n * k].view(k, n).t() for i in range(count)]
+    return Vks, sig.view(count, k), status
+
+
 def ns_solve_eps(d, A, eps, save=True, status=None, ws=None, stream=None):
     """Tolerance version of Algorithm 1: returns (Vk n x n, sigk n, k int32 tensor, save or None,
     status); columns 0..k-1 of Vk hold the right singular vectors with sigma < eps."""

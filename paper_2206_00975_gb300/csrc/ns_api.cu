@@ -5,6 +5,7 @@
 // allocated, freed or synchronised here.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include "ns_device.cuh"
 #include "ns_internal.h"
 
@@ -68,10 +69,8 @@ struct SolveLayout {
     size_t bytes;
 };
 
-static SolveLayout solve_layout(void *ws, const ns_sketch_desc *d, int64_t m, int64_t n, bool need_sa) {
-    Carver c(ws);
-    SolveLayout L;
-    L.status_word = c.take<int32_t>(1);
+// the sketch's scratch (and SA when need_sa) of one solve
+static void carve_sketch(Carver &c, const ns_sketch_desc *d, int64_t m, int64_t n, bool need_sa, SolveLayout &L) {
     L.srht = SrhtWork{nullptr, nullptr, nullptr};
     L.sparse = SparseWork{nullptr, nullptr, nullptr};
     if (d->kind == NS_SRHT) L.srht = srht_carve(c, m, n, d->s);
@@ -84,6 +83,32 @@ static SolveLayout solve_layout(void *ws, const ns_sketch_desc *d, int64_t m, in
         L.gauss_partial = c.take<float>((size_t)(g.nsplit * n * d->s));
     }
     L.SA = need_sa ? c.take<double>((size_t)(d->s * n)) : nullptr;
+}
+
+static SolveLayout solve_layout(void *ws, const ns_sketch_desc *d, int64_t m, int64_t n, bool need_sa) {
+    Carver c(ws);
+    SolveLayout L;
+    L.status_word = c.take<int32_t>(1);
+    carve_sketch(c, d, m, n, need_sa, L);
+    L.dense = dense_carve(c, d->s, n);
+    L.bytes = c.used;
+    return L;
+}
+
+// ns_solve_pipelined: a status word, two sketch slots (scratch and SA), one
+// dense workspace
+struct PipeLayout {
+    int32_t *status_word;
+    SolveLayout slot[2];
+    DenseWork dense;
+    size_t bytes;
+};
+
+static PipeLayout pipe_layout(void *ws, const ns_sketch_desc *d, int64_t m, int64_t n) {
+    Carver c(ws);
+    PipeLayout L;
+    L.status_word = c.take<int32_t>(1);
+    for (int i = 0; i < 2; ++i) carve_sketch(c, d, m, n, true, L.slot[i]);
     L.dense = dense_carve(c, d->s, n);
     L.bytes = c.used;
     return L;
@@ -286,6 +311,88 @@ ns_status ns_solve(const ns_sketch_desc *d, const void *A, int32_t dtype, int64_
     double *save_sigma = save ? save + d->s * n + n * n : nullptr;
     return cuda_status(
         launch_dense_solve(SA, d->s, n, k, L.dense, Vk, sigk, save_V, save_sigma, status, st, d->max_sweeps));
+}
+
+size_t ns_solve_pipelined_workspace_size(const ns_sketch_desc *d, int64_t m, int64_t n) {
+    if (!desc_ok(d) || m < 1 || n < 1 || n > kMaxN) return 0;
+    return pipe_layout(nullptr, d, m, n).bytes;
+}
+
+// Two streams of the library per device: the dense stages at the higher
+// priority, the sketches below it, and the events that order them.
+struct PipeRes {
+    cudaStream_t dense = nullptr, sketch = nullptr;
+    cudaEvent_t in = nullptr, out = nullptr, after_qr = nullptr, sk[2] = {nullptr, nullptr};
+};
+
+static PipeRes *pipe_resources() {
+    static std::mutex mu;
+    static PipeRes res[64];
+    static bool made[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!made[dev]) {
+        int lo = 0, hi = 0;
+        PipeRes r;
+        if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&r.dense, cudaStreamNonBlocking, hi) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&r.sketch, cudaStreamNonBlocking, lo) != cudaSuccess)
+            return nullptr;
+        cudaEvent_t *evs[] = {&r.in, &r.out, &r.after_qr, &r.sk[0], &r.sk[1]};
+        for (cudaEvent_t *e : evs)
+            if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        res[dev] = r;
+        made[dev] = true;
+    }
+    return &res[dev];
+}
+
+ns_status ns_solve_pipelined(const ns_sketch_desc *d, const void *const *A, int32_t count, int32_t dtype, int64_t m,
+                             int64_t n, int64_t lda, int32_t k, double *Vk, double *sigk, int32_t *dev_status,
+                             void *ws, size_t ws_bytes, void *stream) {
+    if (!desc_ok(d) || !A || count < 1 || !Vk || !sigk || !ws) return NS_ERR_INVALID_ARG;
+    if (!path_ok(d, dtype) || !shape_ok(d, m, n, lda)) return NS_ERR_INVALID_ARG;
+    if (m < n || n > d->s || n > kMaxN || k < 1 || k > n) return NS_ERR_INVALID_ARG;
+    if ((((uintptr_t)ws) & 255) != 0) return NS_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < count; ++i)
+        if (!A[i] || (((uintptr_t)A[i]) & (dtype == NS_F32 ? 3 : 7)) != 0) return NS_ERR_INVALID_ARG;
+    const PipeLayout L = pipe_layout(ws, d, m, n);
+    if (L.bytes > ws_bytes) return NS_ERR_WORKSPACE;
+    PipeRes *R = pipe_resources();
+    if (!R) return NS_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *status = dev_status ? dev_status : L.status_word;
+    const size_t nstat = dev_status ? (size_t)count : 1;
+    if (cudaMemsetAsync(status, 0, sizeof(int32_t) * nstat, st) != cudaSuccess) return NS_ERR_CUDA;
+    if (cudaEventRecord(R->in, st) != cudaSuccess || cudaStreamWaitEvent(R->dense, R->in, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(R->sketch, R->in, 0) != cudaSuccess)
+        return NS_ERR_CUDA;
+    auto stat = [&](int32_t i) { return dev_status ? dev_status + i : L.status_word; };
+    ns_status r = run_sketch(d, A[0], m, n, lda, L.slot[0].SA, L.slot[0], stat(0), R->sketch);
+    if (r != NS_OK) return r;
+    if (cudaEventRecord(R->sk[0], R->sketch) != cudaSuccess) return NS_ERR_CUDA;
+    for (int32_t i = 0; i < count; ++i) {
+        const int p = i & 1;
+        const bool more = i + 1 < count;
+        if (cudaStreamWaitEvent(R->dense, R->sk[p], 0) != cudaSuccess) return NS_ERR_CUDA;
+        const cudaError_t e = launch_dense_solve(L.slot[p].SA, d->s, n, k, L.dense, Vk + (int64_t)i * n * k,
+                                                 sigk + (int64_t)i * k, nullptr, nullptr, stat(i), R->dense,
+                                                 d->max_sweeps, true, more ? R->after_qr : nullptr);
+        if (e != cudaSuccess) return NS_ERR_CUDA;
+        if (more) {
+            // the next sketch once this dense stage is past its QRs (which hold
+            // every SM); its slot's SA was last read by dense stage i - 1,
+            // finished before this one began
+            if (cudaStreamWaitEvent(R->sketch, R->after_qr, 0) != cudaSuccess) return NS_ERR_CUDA;
+            r = run_sketch(d, A[i + 1], m, n, lda, L.slot[p ^ 1].SA, L.slot[p ^ 1], stat(i + 1), R->sketch);
+            if (r != NS_OK) return r;
+            if (cudaEventRecord(R->sk[p ^ 1], R->sketch) != cudaSuccess) return NS_ERR_CUDA;
+        }
+    }
+    if (cudaEventRecord(R->out, R->dense) != cudaSuccess || cudaStreamWaitEvent(st, R->out, 0) != cudaSuccess)
+        return NS_ERR_CUDA;
+    return NS_OK;
 }
 
 ns_status ns_solve_eps(const ns_sketch_desc *d, const void *A, int32_t dtype, int64_t m, int64_t n, int64_t lda,

@@ -2420,7 +2420,7 @@ cudaError_t launch_dense_stats(const DenseWork &w, int64_t *out, cudaStream_t st
 
 cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k, const DenseWork &w, double *Vk,
                                double *sigk, double *save_V, double *save_sigma, int32_t *status, cudaStream_t st,
-                               int max_sweeps, bool fp32_phase) {
+                               int max_sweeps, bool fp32_phase, cudaEvent_t after_qr) {
     cudaError_t e = cudaSuccess;
     if (max_sweeps <= 0 || max_sweeps > kMaxSweeps) max_sweeps = kMaxSweeps;
     GridBarrier bar{w.bar, status};
@@ -2498,6 +2498,7 @@ cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k
     e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * kBarWords, st);
     if (e != cudaSuccess) return e;
     const int vinit = q2_in_v ? 1 : 0;
+    if (after_qr && (e = cudaEventRecord(after_qr, st)) != cudaSuccess) return e;
     bool ring = false;
     unsigned int *fp32_ran = nullptr;
     if (q2_in_v && n <= kRingN && jacobi32_applicable(n) && fp32_phase) {

@@ -201,9 +201,11 @@ cudaError_t launch_dense_select_eps(const DenseWork &w, int64_t n, double eps, d
 // NS_ERR_NOCONV, with the partial result written, when the limit is reached
 // fp32_phase: run the linear phase of the Jacobi iteration in FP32 first
 // (ns_jacobi32.cu) where it applies (pipelined QRs, 64 <= n <= 256)
+// after_qr: if set, recorded on st once the QRs and X0 = R2^T, V = Q2 are in
+// place (from then on the stage no longer needs every SM at once)
 cudaError_t launch_dense_solve(const double *SA, int64_t s, int64_t n, int32_t k, const DenseWork &w, double *Vk,
                                double *sigk, double *save_V, double *save_sigma, int32_t *status, cudaStream_t st,
-                               int max_sweeps = 0, bool fp32_phase = true);
+                               int max_sweeps = 0, bool fp32_phase = true, cudaEvent_t after_qr = nullptr);
 // FP32 linear phase of the Jacobi iteration on X = w.X (n x n) with V = w.V
 // holding Q2: X <- X V0, V <- Q2 V0 (V0 orthogonal in FP64); ctl[0] = 1 if it
 // ran, ctl[1..2] its sweeps and rotations.  Scratch: w.L, w.U, w.W.

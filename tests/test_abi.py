@@ -286,3 +286,20 @@ def test_sketch_rows_rejections(lib):
     assert rows(_desc(s=64, kind=_lib.NS_GAUSSIAN, prec=_lib.NS_PREC_BF16X3)) == INV
     assert rows(_desc(s=2048)) == INV                 # SRHT s > m' = 1024
     assert rows(d, nb=16) == WSP
+
+
+def test_solve_pipelined_rejections(lib):
+    d = _desc(s=64)
+    ptrs = (ctypes.c_void_p * 2)(0x100000, 0x200000)
+    call = lambda dd=d, A=ptrs, count=2, m=100, n=4, lda=100, k=1, nb=1 << 30: lib.ns_solve_pipelined(  # noqa: E731
+        ctypes.byref(dd), A, count, _lib.NS_F64, m, n, lda, k, FAKE, FAKE, None, FAKE, nb, None)
+    assert lib.ns_solve_pipelined_workspace_size(ctypes.byref(d), 100, 4) > \
+        lib.ns_workspace_size(ctypes.byref(d), 100, 4, 1) // 2
+    assert call(count=0) == INV
+    assert call(A=None) == INV
+    assert call(A=(ctypes.c_void_p * 2)(0x100000, 0)) == INV         # a null problem
+    assert call(A=(ctypes.c_void_p * 2)(0x100000, 0x100004)) == INV  # a misaligned problem
+    assert call(k=0) == INV
+    assert call(k=5) == INV
+    assert call(lda=99) == INV
+    assert call(nb=16) == WSP
