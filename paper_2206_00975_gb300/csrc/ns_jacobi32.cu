@@ -455,6 +455,11 @@ __global__ void __cluster_dims__(kJ32Cta, 1, 1) __launch_bounds__(kJ32Threads, 1
 // (M x K) or A^T (A: K x M), B (K x N).  One 8 x 8 tile per CTA of 128
 // threads: two threads per output, one summing the even chunks of 8 k, the
 // other the odd ones (each an FMA chain in increasing k), then their sum.
+// The products run in T: double, or float where the FP32 error (2^-24 times
+// the sum of the |terms|) stays below 2^-53 once the series' coefficient is
+// applied: E^2 in the series for (W^T W)^(-1/2) (|E| ~ 3e-6, n <= 256: sums
+// below 2^-28) and K^4, K^6 of the completion (sums below b^2 <= 2^-26, t^4 b^2
+// once scaled).
 // Small tiles and the split of K keep enough independent chains in flight on
 // each SM sub-partition's FP64 pipe even for a symmetric product of n = 256
 // (528 tiles).  Skipped when *ctl == 0 (the FP32 phase did not run).
@@ -504,7 +509,7 @@ __device__ __forceinline__ double corr_bound(const unsigned long long *bnd) {
     return __longlong_as_double((long long)*(volatile const unsigned long long *)bnd);
 }
 
-template <bool TA, int EPI, bool SYM, bool DZ>
+template <typename T, bool TA, int EPI, bool SYM, bool DZ>
 __global__ void __launch_bounds__(2 * kG64T * kG64T) gemm64_kernel(const G64Args g) {
     if (g.ctl && *(volatile const unsigned int *)g.ctl == 0u) return;
     if (g.gate && *(volatile const unsigned int *)g.gate != 2u) return;
@@ -512,9 +517,9 @@ __global__ void __launch_bounds__(2 * kG64T * kG64T) gemm64_kernel(const G64Args
     if (EPI == 3 || EPI == 4) skip_k = corr_bound(g.bnd) <= kCorrSmall;
     if (EPI == 4 && skip_k) return;
     if (EPI == 4 && blockIdx.x == 0 && threadIdx.x == 0) *g.ran = 1u;
-    __shared__ double As[2][kG64T][kG64T + 1];  // As[h][k][i] = op(A)[i, k] of chunk h
-    __shared__ double Bs[2][kG64T][kG64T + 1];  // Bs[h][k][j] = B[k, j] of chunk h
-    __shared__ double part[kG64T * kG64T];      // the odd chunks' sums
+    __shared__ T As[2][kG64T][kG64T + 1];  // As[h][k][i] = op(A)[i, k] of chunk h
+    __shared__ T Bs[2][kG64T][kG64T + 1];  // Bs[h][k][j] = B[k, j] of chunk h
+    __shared__ T part[kG64T * kG64T];      // the odd chunks' sums
     int64_t bx = blockIdx.x, by = blockIdx.y;
     if (SYM) {  // triangular index -> tile (bx, by), bx <= by
         int64_t t = blockIdx.x;
@@ -531,17 +536,17 @@ __global__ void __launch_bounds__(2 * kG64T * kG64T) gemm64_kernel(const G64Args
     const int tx = tl % kG64T, ty = tl / kG64T;
     const int64_t i = bx * kG64T + tx, j = by * kG64T + ty;
     const int64_t M = g.M, N = g.N, K = skip_k ? 0 : g.K;
-    double acc = 0.0;
+    T acc = T(0);
     for (int64_t k00 = 0; k00 < K; k00 += 2 * kG64T) {
         {   // half h loads chunk k00 + h*8: op(A)[bx*8 + ?, k + ?] and B[k + ?, by*8 + ?]
             const int64_t k0 = k00 + h * kG64T;
             const int64_t ai = bx * kG64T + (TA ? ty : tx), ak = k0 + (TA ? tx : ty);
             double av = 0.0;
             if (ai < M && ak < K && !(DZ && ai == ak)) av = TA ? A[ak + ai * g.lda] : A[ai + ak * g.lda];
-            if (TA) As[h][tx][ty] = av;
-            else As[h][ty][tx] = av;
+            if (TA) As[h][tx][ty] = (T)av;
+            else As[h][ty][tx] = (T)av;
             const int64_t bk = k0 + tx, bj = by * kG64T + ty;
-            Bs[h][tx][ty] = (bk < K && bj < N && !(DZ && bk == bj)) ? g.B[bk + bj * g.ldb] : 0.0;
+            Bs[h][tx][ty] = (T)((bk < K && bj < N && !(DZ && bk == bj)) ? g.B[bk + bj * g.ldb] : 0.0);
         }
         __syncthreads();
 #pragma unroll
@@ -552,6 +557,7 @@ __global__ void __launch_bounds__(2 * kG64T * kG64T) gemm64_kernel(const G64Args
     __syncthreads();
     if (h == 1) return;
     acc += part[tl];
+    const double accd = (double)acc;
     if (EPI == 3 && g.verdict && blockIdx.x == 0 && threadIdx.x == 0) {
         // verdict for the FP64 iteration: 2 (start with the convergence check)
         // when the full step was taken, no pair was left out and every
@@ -564,9 +570,9 @@ __global__ void __launch_bounds__(2 * kG64T * kG64T) gemm64_kernel(const G64Args
     if (SYM && bx == by && i > j) return;  // the upper entry writes both
     const double id = (i == j) ? 1.0 : 0.0;
     const int64_t ld = g.ldc;
-    double v = acc, vm = acc;  // C[i, j] and its mirror C[j, i]
-    if (EPI == 1) v = vm = id - acc;
-    if (EPI == 2) v = vm = id + 0.5 * g.E[i + j * ld] + 0.375 * acc;
+    double v = accd, vm = accd;  // C[i, j] and its mirror C[j, i]
+    if (EPI == 1) v = vm = id - accd;
+    if (EPI == 2) v = vm = id + 0.5 * g.E[i + j * ld] + 0.375 * accd;
     if (EPI == 3) {
         const double b = corr_bound(g.bnd);
         const double t = (b > kCorrBmax) ? sqrt(kCorrBmax / b) : 1.0, t2 = t * t;
@@ -574,7 +580,7 @@ __global__ void __launch_bounds__(2 * kG64T * kG64T) gemm64_kernel(const G64Args
         double sym = 0.5 * t2 * g.K2[i + j * ld];
         if (!skip_k) {
             const double t4 = t2 * t2;
-            sym += -0.125 * t4 * g.K4[i + j * ld] + 0.0625 * (t4 * t2) * acc;
+            sym += -0.125 * t4 * g.K4[i + j * ld] + 0.0625 * (t4 * t2) * accd;
         }
         v = (id + kij) + sym;
         vm = (id - kij) + sym;
@@ -590,12 +596,12 @@ __global__ void copy_if_kernel(const double *__restrict__ a, int64_t len, double
         b[i] = a[i];
 }
 
-template <bool TA, int EPI, bool SYM, bool DZ = false>
+template <bool TA, int EPI, bool SYM, bool DZ = false, typename T = double>
 static cudaError_t gemm64(const G64Args &g, bool dual, cudaStream_t st) {
     const int64_t mt = (g.M + kG64T - 1) / kG64T, nt = (g.N + kG64T - 1) / kG64T;
     const dim3 grid = SYM ? dim3((unsigned)(mt * (mt + 1) / 2), 1, dual ? 2 : 1)
                           : dim3((unsigned)mt, (unsigned)nt, dual ? 2 : 1);
-    gemm64_kernel<TA, EPI, SYM, DZ><<<grid, 2 * kG64T * kG64T, 0, st>>>(g);
+    gemm64_kernel<T, TA, EPI, SYM, DZ><<<grid, 2 * kG64T * kG64T, 0, st>>>(g);
     return cudaGetLastError();
 }
 
@@ -719,7 +725,7 @@ static cudaError_t completion(const double *Xi, const double *Vi, double *Xo, do
     g = g64(K2m, n, K2m, n, K4m, n, n, ctl);  // K^4 (skipped when negligible)
     g.bnd = bnd;
     g.ran = cw + 1;
-    if ((e = gemm64<false, 4, true>(g, false, st)) != cudaSuccess) return e;
+    if ((e = gemm64<false, 4, true, false, float>(g, false, st)) != cudaSuccess) return e;
     g = g64(K2m, n, K4m, n, Qm, n, n, ctl);  // Q from K, K^2, K^4 and K^6 = K^2 K^4
     g.Km = GKm;
     g.K2 = K2m;
@@ -727,7 +733,7 @@ static cudaError_t completion(const double *Xi, const double *Vi, double *Xo, do
     g.bnd = bnd;
     g.verdict = verdict;
     g.cnt = cw;
-    if ((e = gemm64<false, 3, true>(g, false, st)) != cudaSuccess) return e;
+    if ((e = gemm64<false, 3, true, false, float>(g, false, st)) != cudaSuccess) return e;
     g = g64(Xi, n, Qm, n, Xo, n, n, ctl);  // X Q and V Q
     g.A[1] = Vi;
     g.C[1] = Vo;
@@ -772,7 +778,7 @@ cudaError_t launch_jacobi32_precondition(const DenseWork &w, int64_t n, unsigned
     if ((e = gemm64<true, 1, true>(g, false, st)) != cudaSuccess) return e;
     g = g64(Em, n, Em, n, Mm, n, n, ctl);
     g.E = Em;
-    if ((e = gemm64<false, 2, true>(g, false, st)) != cudaSuccess) return e;
+    if ((e = gemm64<false, 2, true, false, float>(g, false, st)) != cudaSuccess) return e;
     g = g64(V0, n, Mm, n, V0p, n, n, ctl);
     if ((e = gemm64<false, 0, false>(g, false, st)) != cudaSuccess) return e;
     // X1 = X0 V0' (into U), V1 = Q2 V0' (into L)
