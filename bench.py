@@ -612,8 +612,8 @@ def main():
     if int(status.item()) != 0:
         raise SystemExit("solve status %d" % int(status.item()))
 
-    # the headline: a stream of solves through ns_solve_pipelined, the sketch
-    # of problem i + 1 overlapping the dense stage of problem i past its QRs
+    # the headline: a stream of solves through ns_solve_pipelined, three in
+    # flight, each lane's next sketch overlapping its dense stage past the QRs
     # (every step the same resident A; each problem is sketched and solved)
     ws_pipe = api.pipelined_workspace(d, M, N, dev)
     st_pipe = torch.zeros(args.steps, dtype=torch.int32, device=dev)
@@ -759,8 +759,9 @@ def main():
     line = {
         "metric": METRIC, "value": n_ranks * args.steps / (ms_pipe / 1e3), "unit": "solves/s", "n_gpus": n_ranks,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_pipe / args.steps, "higher_is_better": True,
-        "mode": "ns_solve_pipelined: each step sketches and solves one problem; the sketch of step i+1 "
-                "overlaps the dense stage of step i past its QRs (two library streams)",
+        "mode": "ns_solve_pipelined: each step sketches and solves one problem; steps go round-robin to "
+                "three lanes (three solves in flight), and within a lane the next sketch overlaps the dense "
+                "stage past its QRs",
         "sequential": {"solves_per_s": n_ranks * args.steps / (ms_solve / 1e3), "ms_per_solve": ms_solve / args.steps,
                        "api": "ns_solve, one problem after the other on one stream"},
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

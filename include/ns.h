@@ -176,12 +176,14 @@ ns_status ns_solve(const ns_sketch_desc *desc, const void *A, int32_t dtype, int
 
 /*
  * ns_solve_pipelined -- Algorithm 1 (as ns_solve) for `count` independent
- * problems of the same shape, dtype and lda, with the sketch of problem i + 1
- * running while the dense stage of problem i is past its two QRs (which hold
- * every SM): a throughput form for a stream of problems.  The library runs the
- * sketches and the dense stages on two streams of its own (per device; dense
- * stages at the higher priority), ordered after all work already enqueued on
- * `stream`; every result is complete before work enqueued on `stream` later.
+ * problems of the same shape, dtype and lda: a throughput form for a stream
+ * of problems.  Problems go round-robin to three lanes, so several solves are
+ * in flight (the dense stage is bound by FP64 latency chains, and a few of
+ * them share the SMs well); within a lane the sketch of its next problem runs
+ * while the current dense stage is past its two QRs.  The library runs the
+ * lanes on streams of its own (per device; dense stages at the higher
+ * priority), ordered after all work already enqueued on `stream`; every
+ * result is complete before work enqueued on `stream` later.
  *   A      host array of `count` device pointers, problem i = A[i] (m x n,
  *          column-major, leading dimension lda, dtype as ns_solve).
  *   Vk     device, count * n * k FP64: problem i at Vk + i n k (n x k each,
@@ -189,7 +191,7 @@ ns_status ns_solve(const ns_sketch_desc *desc, const void *A, int32_t dtype, int
  *   sigk   device, count * k FP64: problem i at sigk + i k.
  *   dev_status  device int32[count] (may be NULL): problem i's status.
  *   ws     ns_solve_pipelined_workspace_size(desc, m, n) bytes, 256-byte
- *          aligned (two sketch slots and one dense workspace).
+ *          aligned (per lane two sketch slots and a dense workspace).
  * The results are those of ns_solve on each problem, bit for bit (the same
  * kernels in the same order per problem).  Not re-entrant for one device
  * from several host threads at once (the library's streams are shared).

@@ -95,12 +95,13 @@ static SolveLayout solve_layout(void *ws, const ns_sketch_desc *d, int64_t m, in
     return L;
 }
 
-// ns_solve_pipelined: a status word, two sketch slots (scratch and SA), one
-// dense workspace
+// ns_solve_pipelined: kPipeLanes lanes, each with two sketch slots (scratch
+// and SA) and a dense workspace, after one status word
+constexpr int kPipeLanes = 3;
 struct PipeLayout {
     int32_t *status_word;
-    SolveLayout slot[2];
-    DenseWork dense;
+    SolveLayout slot[kPipeLanes][2];
+    DenseWork dense[kPipeLanes];
     size_t bytes;
 };
 
@@ -108,8 +109,10 @@ static PipeLayout pipe_layout(void *ws, const ns_sketch_desc *d, int64_t m, int6
     Carver c(ws);
     PipeLayout L;
     L.status_word = c.take<int32_t>(1);
-    for (int i = 0; i < 2; ++i) carve_sketch(c, d, m, n, true, L.slot[i]);
-    L.dense = dense_carve(c, d->s, n);
+    for (int l = 0; l < kPipeLanes; ++l) {
+        for (int i = 0; i < 2; ++i) carve_sketch(c, d, m, n, true, L.slot[l][i]);
+        L.dense[l] = dense_carve(c, d->s, n);
+    }
     L.bytes = c.used;
     return L;
 }
@@ -318,11 +321,11 @@ size_t ns_solve_pipelined_workspace_size(const ns_sketch_desc *d, int64_t m, int
     return pipe_layout(nullptr, d, m, n).bytes;
 }
 
-// Two streams of the library per device: the dense stages at the higher
-// priority, the sketches below it, and the events that order them.
+// The library's streams per device: for each lane a dense stream (higher
+// priority) and a sketch stream, and the events that order them.
 struct PipeRes {
-    cudaStream_t dense = nullptr, sketch = nullptr;
-    cudaEvent_t in = nullptr, out = nullptr, after_qr = nullptr, sk[2] = {nullptr, nullptr};
+    cudaStream_t dense[kPipeLanes] = {}, sketch[kPipeLanes] = {};
+    cudaEvent_t in = nullptr, out[kPipeLanes] = {}, after_qr[kPipeLanes] = {}, sk[kPipeLanes][2] = {};
 };
 
 static PipeRes *pipe_resources() {
@@ -335,19 +338,27 @@ static PipeRes *pipe_resources() {
     if (!made[dev]) {
         int lo = 0, hi = 0;
         PipeRes r;
-        if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
-            cudaStreamCreateWithPriority(&r.dense, cudaStreamNonBlocking, hi) != cudaSuccess ||
-            cudaStreamCreateWithPriority(&r.sketch, cudaStreamNonBlocking, lo) != cudaSuccess)
-            return nullptr;
-        cudaEvent_t *evs[] = {&r.in, &r.out, &r.after_qr, &r.sk[0], &r.sk[1]};
-        for (cudaEvent_t *e : evs)
-            if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) return nullptr;
+        if (cudaEventCreateWithFlags(&r.in, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        for (int l = 0; l < kPipeLanes; ++l) {
+            if (cudaStreamCreateWithPriority(&r.dense[l], cudaStreamNonBlocking, hi) != cudaSuccess ||
+                cudaStreamCreateWithPriority(&r.sketch[l], cudaStreamNonBlocking, lo) != cudaSuccess)
+                return nullptr;
+            cudaEvent_t *evs[] = {&r.out[l], &r.after_qr[l], &r.sk[l][0], &r.sk[l][1]};
+            for (cudaEvent_t *e : evs)
+                if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        }
         res[dev] = r;
         made[dev] = true;
     }
     return &res[dev];
 }
 
+// Problems i = l, l + kPipeLanes, ... go to lane l, so several dense stages
+// are in flight (the dense stage is bound by FP64 latency chains, and a few
+// of them share the SMs well).  Within a lane, the sketch of the lane's next
+// problem waits for the event the dense launcher records once the QRs are
+// done, and runs at the lower priority beside the rest of that dense stage.
 ns_status ns_solve_pipelined(const ns_sketch_desc *d, const void *const *A, int32_t count, int32_t dtype, int64_t m,
                              int64_t n, int64_t lda, int32_t k, double *Vk, double *sigk, int32_t *dev_status,
                              void *ws, size_t ws_bytes, void *stream) {
@@ -365,33 +376,42 @@ ns_status ns_solve_pipelined(const ns_sketch_desc *d, const void *const *A, int3
     int32_t *status = dev_status ? dev_status : L.status_word;
     const size_t nstat = dev_status ? (size_t)count : 1;
     if (cudaMemsetAsync(status, 0, sizeof(int32_t) * nstat, st) != cudaSuccess) return NS_ERR_CUDA;
-    if (cudaEventRecord(R->in, st) != cudaSuccess || cudaStreamWaitEvent(R->dense, R->in, 0) != cudaSuccess ||
-        cudaStreamWaitEvent(R->sketch, R->in, 0) != cudaSuccess)
-        return NS_ERR_CUDA;
+    if (cudaEventRecord(R->in, st) != cudaSuccess) return NS_ERR_CUDA;
+    for (int l = 0; l < kPipeLanes; ++l)
+        if (cudaStreamWaitEvent(R->dense[l], R->in, 0) != cudaSuccess ||
+            cudaStreamWaitEvent(R->sketch[l], R->in, 0) != cudaSuccess)
+            return NS_ERR_CUDA;
     auto stat = [&](int32_t i) { return dev_status ? dev_status + i : L.status_word; };
-    ns_status r = run_sketch(d, A[0], m, n, lda, L.slot[0].SA, L.slot[0], stat(0), R->sketch);
-    if (r != NS_OK) return r;
-    if (cudaEventRecord(R->sk[0], R->sketch) != cudaSuccess) return NS_ERR_CUDA;
+    const int lanes = count < kPipeLanes ? count : kPipeLanes;
+    for (int l = 0; l < lanes; ++l) {  // each lane's first sketch
+        const ns_status r = run_sketch(d, A[l], m, n, lda, L.slot[l][0].SA, L.slot[l][0], stat(l), R->sketch[l]);
+        if (r != NS_OK) return r;
+        if (cudaEventRecord(R->sk[l][0], R->sketch[l]) != cudaSuccess) return NS_ERR_CUDA;
+    }
     for (int32_t i = 0; i < count; ++i) {
-        const int p = i & 1;
-        const bool more = i + 1 < count;
-        if (cudaStreamWaitEvent(R->dense, R->sk[p], 0) != cudaSuccess) return NS_ERR_CUDA;
-        const cudaError_t e = launch_dense_solve(L.slot[p].SA, d->s, n, k, L.dense, Vk + (int64_t)i * n * k,
-                                                 sigk + (int64_t)i * k, nullptr, nullptr, stat(i), R->dense,
-                                                 d->max_sweeps, true, more ? R->after_qr : nullptr);
+        const int l = i % kPipeLanes, p = (i / kPipeLanes) & 1;
+        const int32_t next = i + kPipeLanes;  // the lane's next problem
+        const bool more = next < count;
+        if (cudaStreamWaitEvent(R->dense[l], R->sk[l][p], 0) != cudaSuccess) return NS_ERR_CUDA;
+        const cudaError_t e = launch_dense_solve(L.slot[l][p].SA, d->s, n, k, L.dense[l], Vk + (int64_t)i * n * k,
+                                                 sigk + (int64_t)i * k, nullptr, nullptr, stat(i), R->dense[l],
+                                                 d->max_sweeps, true, more ? R->after_qr[l] : nullptr);
         if (e != cudaSuccess) return NS_ERR_CUDA;
         if (more) {
-            // the next sketch once this dense stage is past its QRs (which hold
-            // every SM); its slot's SA was last read by dense stage i - 1,
+            // the lane's next sketch once this dense stage is past its QRs; its
+            // slot's SA was last read by the lane's previous dense stage,
             // finished before this one began
-            if (cudaStreamWaitEvent(R->sketch, R->after_qr, 0) != cudaSuccess) return NS_ERR_CUDA;
-            r = run_sketch(d, A[i + 1], m, n, lda, L.slot[p ^ 1].SA, L.slot[p ^ 1], stat(i + 1), R->sketch);
+            if (cudaStreamWaitEvent(R->sketch[l], R->after_qr[l], 0) != cudaSuccess) return NS_ERR_CUDA;
+            const ns_status r = run_sketch(d, A[next], m, n, lda, L.slot[l][p ^ 1].SA, L.slot[l][p ^ 1], stat(next),
+                                           R->sketch[l]);
             if (r != NS_OK) return r;
-            if (cudaEventRecord(R->sk[p ^ 1], R->sketch) != cudaSuccess) return NS_ERR_CUDA;
+            if (cudaEventRecord(R->sk[l][p ^ 1], R->sketch[l]) != cudaSuccess) return NS_ERR_CUDA;
         }
     }
-    if (cudaEventRecord(R->out, R->dense) != cudaSuccess || cudaStreamWaitEvent(st, R->out, 0) != cudaSuccess)
-        return NS_ERR_CUDA;
+    for (int l = 0; l < kPipeLanes; ++l)
+        if (cudaEventRecord(R->out[l], R->dense[l]) != cudaSuccess ||
+            cudaStreamWaitEvent(st, R->out[l], 0) != cudaSuccess)
+            return NS_ERR_CUDA;
     return NS_OK;
 }
 
