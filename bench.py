@@ -142,12 +142,13 @@ def dense_flops(s, n, k, stats):
 
 
 def launches_per_solve(stats):
-    """Library kernels one ns_solve launches: the sketch (meta, chunk, reduce),
-    the column order (3), the first QR, [R^T | I] (2), the second QR, X and V
-    (2), the FP32 phase with its products, two completions of 7 launches and
-    two copies (21, when it runs), the ring Jacobi, V = P Q2 V0 Vx, the
-    extraction and the two save copies."""
-    return 17 + (21 if len(stats) > 4 and stats[4] > 0 else 0)
+    """Library kernels one solve of the headline launches (ns_solve_pipelined,
+    nothing saved): the sketch (meta, chunk, reduce), the column order (3),
+    both QRs (1, fused), X0 = R2^T and V = Q2 (2), the ring Jacobi, V = P Q2 V0 Vx
+    and the extraction; when the FP32 phase runs (23 more): the phase, four
+    products making V0 orthogonal and applying it, two completions of seven
+    launches, the Gram-matrix check (2) and two copies."""
+    return 12 + (23 if len(stats) > 4 and stats[4] > 0 else 0)
 
 
 def cpu_baseline(A):
