@@ -75,7 +75,9 @@ constexpr size_t kJ32Smem = (size_t)4 * kJ32Slot * sizeof(float);
 __device__ __forceinline__ float *j32_slot(float *base, int idx) { return base + (size_t)idx * kJ32Slot; }
 
 // player of tournament position `pos` at step `step` (16 players, player 0 fixed)
-__device__ __forceinline__ int j32_rr(int pos, int step) { return pos == 0 ? 0 : 1 + (pos - 1 + step) % 15; }
+__device__ __forceinline__ int j32_rr(int pos, int step) {
+    return pos == 0 ? 0 : 1 + (pos - 1 + step) % (kJ32B - 1);
+}
 
 // One pair (columns a, b: pointers to their y rows; w~ follows at +kJ32Rows;
 // da, db their scales d), one warp; returns 1 (in every lane) if the pair was
@@ -359,10 +361,11 @@ __global__ void __cluster_dims__(kJ32Cta, 1, 1) __launch_bounds__(kJ32Threads, 1
         unsigned int mine = 0;  // rotations of this warp (lane values agree)
         for (int step = 0; step < kJ32Steps; ++step) {
             float *T = j32_slot(j32_smem, 2 * par), *B = j32_slot(j32_smem, 2 * par + 1);
-            if (step == 0) {  // pairs inside each block: warps 0-7 the top block, 8-15 the bottom
-                float *M = w < 8 ? T : B;
-                const float *dM = s_d[w < 8 ? 2 * par : 2 * par + 1];
-                const int q = w & 7;
+            if (step == 0) {  // pairs inside each block: the first half of the warps the top block
+                constexpr int kHalf = kJ32B / 2;
+                float *M = w < kHalf ? T : B;
+                const float *dM = s_d[w < kHalf ? 2 * par : 2 * par + 1];
+                const int q = w & (kHalf - 1);
                 for (int r = 0; r < kJ32B - 1; ++r) {
                     const int pa = j32_rr(q, r), pb = j32_rr(kJ32B - 1 - q, r);
                     mine += j32_pair(M + pa * kJ32Col, M + pb * kJ32Col, dM[pa], dM[pb], tau2);
@@ -752,7 +755,9 @@ cudaError_t launch_jacobi32_precondition(const DenseWork &w, int64_t n, unsigned
     cudaError_t e = cudaSuccess;
     if (state[dev] == 0) {
         if (cudaFuncSetAttribute(jacobi32_phase_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kJ32Smem) != cudaSuccess) {
+                                 (int)kJ32Smem) != cudaSuccess ||
+            (kJ32Cta > 8 && cudaFuncSetAttribute(jacobi32_phase_kernel,
+                                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
             cudaGetLastError();
             state[dev] = -1;
             return cudaSuccess;

@@ -25,16 +25,24 @@ def rank_deficient(rng, m, n, k):
 
 
 @pytest.mark.parametrize("kind,m,n,s,k,count", [
-    ("srht", 1 << 15, 256, 1024, 4, 3),    # both QRs fused, FP32 phase, completions
+    ("srht", 1 << 15, 256, 1024, 4, 7),    # both QRs fused, FP32 phase, completions; every lane twice
     ("srht", 20000, 96, 384, 3, 4),        # ragged m, n < 128
     ("sparse", 1 << 14, 64, 256, 2, 3),
     ("srht", 5000, 40, 160, 1, 2),         # no FP32 phase (n < 64)
+    ("hrht", 1 << 14, 64, 256, 2, 4),
+    ("gauss", 8192, 64, 256, 2, 4),        # FP32-stored A, BF16x3 tensor-core sketch
+    ("srht", 4096, 32, 128, 1, 1),         # a single problem
 ])
 def test_pipelined_matches_ns_solve(api, kind, m, n, s, k, count):
     rng = np.random.default_rng(m + n + count)
-    As = [api.colmajor(rank_deficient(rng, m, n, k), device="cuda") for _ in range(count)]
+    dtype = torch.float32 if kind == "gauss" else torch.float64
+    As = [api.colmajor(rank_deficient(rng, m, n, k), dtype=dtype, device="cuda") for _ in range(count)]
     if kind == "srht":
         d = api.desc(api.NS_SRHT, s=s, seed=3)
+    elif kind == "hrht":
+        d = api.desc(api.NS_HRHT, s=s, seed=3)
+    elif kind == "gauss":
+        d = api.desc(api.NS_GAUSSIAN, s=s, seed=3, prec=api.NS_PREC_BF16X3)
     else:
         d = api.desc(api.NS_SPARSE_SIGN, s=s, seed=3, zeta=8)
     Vks, sig, status = api.ns_solve_pipelined(d, As, k)
