@@ -505,29 +505,59 @@ __device__ __forceinline__ void pipe_apply(int64_t rows, int64_t j, const double
 // the magnitudes it was formed from (the rounding of the cancellations is
 // bounded by u times those) or the norm would need rescaling, the norm is
 // recomputed from the updated column (pipe_form).
-__device__ double pipe_apply_form(double *U, int64_t rows, int64_t j, const double *ush, double coef, double unrm2,
-                                  double *y, double *ushn, double *u0, double *cf, unsigned long long *flag,
-                                  double *red, double *coef_sh, double *unrm_sh) {
+//
+// Reflector j's head u_j and its scalars come out of its producer's scalar
+// chain, after the tail rows u[j+1:] are already published.  So the sums
+// run over the tail first (u . y without its head term, S_yy), and only then
+// does thread 0 wait for flag j (acquire; the coefficient), read u_j and the
+// tail-norm slot U[j-1, j], and add u_j y_j: the CTA reduction overlaps the
+// producer's chain instead of following it.  ush[j] and *coef_now receive
+// u_j and the coefficient for the caller.  A wait that runs out sets status
+// and *ok_sh = 0 (every thread returns 0.0 then).
+__device__ double pipe_apply_form(double *U, int64_t rows, int64_t j, double *ush, double *y, double *ushn,
+                                  double *u0, double *cf, unsigned long long *flag, double *red, double *coef_sh,
+                                  double *unrm_sh, double *coef_now, int *ok_sh, int32_t *status) {
     __shared__ double s_f, s_beta;
     __shared__ int s_redo;
     const int tid = threadIdx.x;
     const int64_t jn = j + 1;
     double d = 0.0, syy = 0.0;
-    for (int64_t i = j + tid; i < rows; i += kPipeThreads) {
+    for (int64_t i = jn + tid; i < rows; i += kPipeThreads) {
         const double yi = y[i];
         d = fma(ush[i], yi, d);
         if (i > jn) syy = fma(yi, yi, syy);
     }
-    double yj = 0.0, yn = 0.0, uj = 0.0, un = 0.0;  // head entries, read before the update
+    double yj = 0.0, yn = 0.0, uj = 0.0, un = 0.0, coef = 0.0, unrm2 = 0.0;  // head entries, before the update
     if (tid == 0) {
         yj = y[j];
-        uj = ush[j];
         yn = y[jn];
         un = ush[jn];
     }
     pipe_sum2_t0(d, syy, red);
-    if (tid == 0) s_f = coef * d;
+    if (tid == 0) {
+        const long long t0 = clock64();
+        unsigned long long fw;
+        bool late = false;
+        while ((fw = ld_acquire_flag(flag + j)) == kPipeEmpty)
+            if (clock64() - t0 > (1ll << 32)) {  // ~2 s; a healthy pipeline waits microseconds
+                late = true;
+                break;
+            }
+        if (late) {
+            set_status(status, NS_ERR_TIMEOUT);
+            *ok_sh = 0;
+        } else {
+            coef = __longlong_as_double((long long)fw);
+            uj = __longlong_as_double((long long)ld_relaxed_u64(U + j + j * rows));  // written before the flag
+            unrm2 = __longlong_as_double((long long)ld_relaxed_u64(U + j - 1 + j * rows));
+            ush[j] = uj;
+            *coef_now = coef;
+            d = fma(uj, yj, d);
+        }
+        s_f = coef * d;
+    }
     __syncthreads();
+    if (!*ok_sh) return 0.0;
     const double f = s_f;
     for (int64_t i = j + tid; i < rows; i += kPipeThreads) {
         const double v = fma(-f, ush[i], y[i]);
@@ -618,7 +648,9 @@ __device__ void pipe_qr_cta(const double *W, double *U, int64_t rows, int64_t co
             const long long t0 = clock64();
             if (mine) {  // poll this thread's rows of U[:, j] (and the scalars) directly
                 bool late = false;
-                for (int64_t i = j + tid; i < rows && !late; i += kPipeThreads) {
+                // from j = 1 on only the tail: pipe_apply_form takes the head and
+                // the scalars once its sums over the tail are done
+                for (int64_t i = (j >= 1 ? j + 1 : j) + tid; i < rows && !late; i += kPipeThreads) {
                     unsigned long long b;
                     while ((b = ld_relaxed_u64(U + i + j * rows)) == kPipeEmpty)
                         if (clock64() - t0 > (1ll << 32)) {  // ~2 s; a healthy pipeline waits microseconds
@@ -627,7 +659,7 @@ __device__ void pipe_qr_cta(const double *W, double *U, int64_t rows, int64_t co
                         }
                     ush[i] = __longlong_as_double((long long)b);
                 }
-                if (tid == 0 && !late) {
+                if (tid == 0 && !late && j == 0) {
                     unsigned long long fw, nw = 0;
                     while ((fw = ld_acquire_flag(flag + j)) == kPipeEmpty)
                         if (clock64() - t0 > (1ll << 32)) {
@@ -663,7 +695,7 @@ __device__ void pipe_qr_cta(const double *W, double *U, int64_t rows, int64_t co
                 __syncthreads();
             }
         }
-        const double coef = s_coef[j & 1];
+        double coef = s_coef[j & 1];  // (the owner of column j + 1 learns it in pipe_apply_form)
         // the owner of column j + 1 takes it first and forms reflector j + 1
         // right away (look-ahead), then applies reflector j to its other columns
         if (mine) {
@@ -671,8 +703,9 @@ __device__ void pipe_qr_cta(const double *W, double *U, int64_t rows, int64_t co
             double *ushn = ubuf + ((j + 1) & 1) * rows;
             double bj;
             if (j >= 1) {
-                bj = pipe_apply_form(U, rows, j, ush, coef, s_unrm[j & 1], y, ushn, u0, cf, flag, red,
-                                     &s_coef[(j + 1) & 1], &s_unrm[(j + 1) & 1]);
+                bj = pipe_apply_form(U, rows, j, ush, y, ushn, u0, cf, flag, red, &s_coef[(j + 1) & 1],
+                                     &s_unrm[(j + 1) & 1], &s_coef[j & 1], &s_ok, status);
+                if (!s_ok) return;
             } else {
                 if (coef != 0.0) pipe_apply(rows, j, ush, coef, y, red);
                 bj = pipe_form(U, rows, j + 1, y, ushn, u0, cf, flag, red, &s_coef[(j + 1) & 1],
@@ -684,6 +717,7 @@ __device__ void pipe_qr_cta(const double *W, double *U, int64_t rows, int64_t co
                 red_release_add(rowcnt + j + 1, 1u);
             }
         }
+        coef = s_coef[j & 1];
         if (coef != 0.0)
             for (int64_t o = o_first + (mine ? 1 : 0); o < nown; ++o) pipe_apply(rows, j, ush, coef, own + o * rows, red);
         if (jn_owner == me) ++o_first;
@@ -875,9 +909,9 @@ __device__ void pipe_qr2_cta(const double *Lg, int64_t ldl, const unsigned int *
         }
         if (jm != me) {  // reflector j from its owner (as in pipe_qr_cta)
             const long long t0 = clock64();
-            if (mine) {
+            if (mine) {  // as in pipe_qr_cta: from j = 1 on only the tail
                 bool late = false;
-                for (int64_t i = j + tid; i < rows && !late; i += kPipeThreads) {
+                for (int64_t i = (j >= 1 ? j + 1 : j) + tid; i < rows && !late; i += kPipeThreads) {
                     unsigned long long b;
                     while ((b = ld_relaxed_u64(U + i + j * rows)) == kPipeEmpty)
                         if (clock64() - t0 > (1ll << 32)) {
@@ -886,7 +920,7 @@ __device__ void pipe_qr2_cta(const double *Lg, int64_t ldl, const unsigned int *
                         }
                     ush[i] = __longlong_as_double((long long)b);
                 }
-                if (tid == 0 && !late) {
+                if (tid == 0 && !late && j == 0) {
                     unsigned long long fw, nw = 0;
                     while ((fw = ld_acquire_flag(flag + j)) == kPipeEmpty)
                         if (clock64() - t0 > (1ll << 32)) {
@@ -922,14 +956,15 @@ __device__ void pipe_qr2_cta(const double *Lg, int64_t ldl, const unsigned int *
                 __syncthreads();
             }
         }
-        const double coef = s_coef[j & 1];
+        double coef = s_coef[j & 1];  // (the owner of column j + 1 learns it in pipe_apply_form)
         if (mine) {  // look-ahead: column j + 1 first, then reflector j + 1
             double *y = own + o_first * rows;
             double *ushn = ubuf + ((j + 1) & 1) * rows;
             double bj;
             if (j >= 1) {
-                bj = pipe_apply_form(U, rows, j, ush, coef, s_unrm[j & 1], y, ushn, u0, cf, flag, red,
-                                     &s_coef[(j + 1) & 1], &s_unrm[(j + 1) & 1]);
+                bj = pipe_apply_form(U, rows, j, ush, y, ushn, u0, cf, flag, red, &s_coef[(j + 1) & 1],
+                                     &s_unrm[(j + 1) & 1], &s_coef[j & 1], &s_ok, status);
+                if (!s_ok) return;
             } else {
                 if (coef != 0.0) pipe_apply(rows, j, ush, coef, y, red);
                 bj = pipe_form(U, rows, j + 1, y, ushn, u0, cf, flag, red, &s_coef[(j + 1) & 1],
@@ -940,6 +975,7 @@ __device__ void pipe_qr2_cta(const double *Lg, int64_t ldl, const unsigned int *
                 s_app[o_first] = (int)(j + 2);  // reflectors 0..j applied, j + 1 formed from it
             }
         }
+        coef = s_coef[j & 1];
         // reflector j to the other loaded columns past j, one warp per column
         {
             int rank = 0;
