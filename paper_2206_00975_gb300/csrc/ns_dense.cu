@@ -485,6 +485,32 @@ __device__ double pipe_form(double *U, int64_t rows, int64_t j, const double *x,
     return s_par[0];
 }
 
+// The owner of the next column polls its rows i0, i0 + kPipeThreads, ... of a
+// published reflector (Ucol = U[:, j]) into ush: four loads in flight at a
+// time, then the ones still empty polled again (one L2 round trip per group
+// of four instead of one per row).  Returns true if a wait ran out.
+__device__ __forceinline__ bool pipe_poll_rows(const double *Ucol, int64_t i0, int64_t rows, double *ush, long long t0) {
+    for (int64_t base = i0; base < rows; base += 4 * kPipeThreads) {
+        unsigned long long b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t i = base + q * kPipeThreads;
+            b[q] = i < rows ? ld_relaxed_u64(Ucol + i) : 0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t i = base + q * kPipeThreads;
+            if (i >= rows) continue;
+            while (b[q] == kPipeEmpty) {
+                if (clock64() - t0 > (1ll << 32)) return true;  // ~2 s; a healthy pipeline waits microseconds
+                b[q] = ld_relaxed_u64(Ucol + i);
+            }
+            ush[i] = __longlong_as_double((long long)b[q]);
+        }
+    }
+    return false;
+}
+
 // y <- H_j y on rows j.. (u in ush, coefficient coef)
 __device__ __forceinline__ void pipe_apply(int64_t rows, int64_t j, const double *ush, double coef, double *y,
                                            double *red) {
@@ -650,15 +676,7 @@ __device__ void pipe_qr_cta(const double *W, double *U, int64_t rows, int64_t co
                 bool late = false;
                 // from j = 1 on only the tail: pipe_apply_form takes the head and
                 // the scalars once its sums over the tail are done
-                for (int64_t i = (j >= 1 ? j + 1 : j) + tid; i < rows && !late; i += kPipeThreads) {
-                    unsigned long long b;
-                    while ((b = ld_relaxed_u64(U + i + j * rows)) == kPipeEmpty)
-                        if (clock64() - t0 > (1ll << 32)) {  // ~2 s; a healthy pipeline waits microseconds
-                            late = true;
-                            break;
-                        }
-                    ush[i] = __longlong_as_double((long long)b);
-                }
+                late = pipe_poll_rows(U + j * rows, (j >= 1 ? j + 1 : j) + tid, rows, ush, t0);
                 if (tid == 0 && !late && j == 0) {
                     unsigned long long fw, nw = 0;
                     while ((fw = ld_acquire_flag(flag + j)) == kPipeEmpty)
@@ -911,15 +929,7 @@ __device__ void pipe_qr2_cta(const double *Lg, int64_t ldl, const unsigned int *
             const long long t0 = clock64();
             if (mine) {  // as in pipe_qr_cta: from j = 1 on only the tail
                 bool late = false;
-                for (int64_t i = (j >= 1 ? j + 1 : j) + tid; i < rows && !late; i += kPipeThreads) {
-                    unsigned long long b;
-                    while ((b = ld_relaxed_u64(U + i + j * rows)) == kPipeEmpty)
-                        if (clock64() - t0 > (1ll << 32)) {
-                            late = true;
-                            break;
-                        }
-                    ush[i] = __longlong_as_double((long long)b);
-                }
+                late = pipe_poll_rows(U + j * rows, (j >= 1 ? j + 1 : j) + tid, rows, ush, t0);
                 if (tid == 0 && !late && j == 0) {
                     unsigned long long fw, nw = 0;
                     while ((fw = ld_acquire_flag(flag + j)) == kPipeEmpty)
