@@ -33,10 +33,10 @@ sys.path.insert(0, ROOT)
 
 M, N, S, K_NULL, SEED = 1 << 20, 256, 1024, 4, 0
 E2E_PARTS = 4   # concurrent host-to-device copies per step in the end-to-end leg
-# DRAM bytes of one srht_f64_chunk128_kernel launch at full size: dram__bytes_read.sum
-# + dram__bytes_write.sum of the ncu capture at m = 2^19, n = 64 (268.58 MB read +
-# 3.03 MB written), scaled by the 8x the full launch processes
-SRHT_TRAFFIC = (268.58e6 + 3.03e6) * 8
+# DRAM bytes of one srht_f64_chunk256_kernel launch at full size: dram__bytes_read.sum
+# + dram__bytes_write.sum of the ncu capture at m = 2^19, n = 64 (268.64 MB read +
+# 3.12 MB written), scaled by the 8x the full launch processes
+SRHT_TRAFFIC = (268.64e6 + 3.12e6) * 8
 SRHT_TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum at m=2^19 n=64, scaled x8"
 METRIC = "null-space solves/s and sketch HBM GB/s (% of peak) at stated ||AV||_F accuracy"
 WORKLOAD = "at_scale: m=2^20 n=256 FP64 column-major, sigma log-spaced 1..1e-6 + 4 exact zeros, SRHT s=1024, k=4"
@@ -745,7 +745,7 @@ def main():
     dense_tf = dflops / t_dense / 1e12
     sketch_roof = {"bound": "hbm", "achieved": sketch_gbs, "peak": hbm_peak, "unit": "GB/s",
                    "frac": sketch_gbs / hbm_peak, "traffic": SRHT_TRAFFIC, "traffic_source": SRHT_TRAFFIC_SOURCE,
-                   "kernel": "srht_f64_chunk128_kernel (ns_sketch)",
+                   "kernel": "srht_f64_chunk256_kernel (ns_sketch)",
                    "peak_source": peak_kind, "algorithmic_bytes": sketch_bytes}
     dense_roof = {"bound": "alu", "achieved": dense_tf, "peak": fp64_peak, "unit": "TFLOP/s",
                   "frac": dense_tf / fp64_peak, "traffic": None,

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(64) batched_sketch_kernel(const ns_problem *__
                 __syncthreads();
                 const double *Acol = (const double *)pr.A + c * pr.lda;
                 const int vec_ok = ((((uintptr_t)pr.A) & 15) == 0 && (pr.lda & 1) == 0) ? 1 : 0;
-                const int P_bits = 63 - kBlockLog - clog2(sl.nblk) - 1;
+                const int P_bits = 63 - kBlockLog - clog2(sl.nblk);
                 int Erun = 0;
                 for (int64_t b = 0; b < sl.nblk; ++b)
                     srht_f64_block(Acol, pr.m, s, b, P_bits, v.sign_words, rows_s, Zs, acc, sgn, red, vec_ok, Erun,

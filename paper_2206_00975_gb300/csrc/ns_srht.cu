@@ -4,22 +4,28 @@
 // Arithmetic.  FP64 throughput on this part is ~1/64 of INT32, so the
 // streaming pass never touches the FP64 pipe.  Each 4096-row block of a column
 // is mapped exactly onto 64-bit fixed point (integer bit manipulation of the
-// IEEE words, round to nearest on the magnitude), at a scale set by the largest
-// exponent seen so far in the chunk, with P = 63 - 12 - log2(chunk) - 1
-// magnitude bits.  The +-1 butterflies of H are then exact integer adds, so the
-// transform and the pruned sum over blocks carry no rounding at all; the only
-// rounding is the input quantisation (relative 2^-P of the chunk's largest
-// entry) and one conversion per output.
+// IEEE words, the magnitude truncated toward zero: srht_quant2), at a scale set
+// by the largest exponent seen so far in the chunk, with P = 63 - 12 -
+// log2(chunk) magnitude bits: a truncated magnitude stays below 2^P, so the
+// 2^(12 + log2 chunk) terms of a chunk sum to less than 2^63.  The signs of D
+// make the truncation error zero-mean in every output, and, uniform on one
+// quantum, it has the spread of rounding to nearest at P - 1 bits.  The +-1
+// butterflies of H are exact integer adds, so the transform and the pruned sum
+// over blocks carry no rounding at all; the only rounding is the input
+// quantisation (relative 2^-P of the chunk's largest entry) and one conversion
+// per output.
 //
 // Structure (Kronecker split H_{m'} = H_{m'/4096} (x) H_{4096}):
 //   y[r] = sum_b (-1)^popcount(hi(r) & b) Z_b[lo(r)],   Z_b = H_4096 (D a)_b,
-// with hi(r) = r >> 12, lo(r) = r & 4095.  A CTA of 128 threads holds a block
-// in registers (32 values per thread), takes the 12 butterfly levels in three
-// register phases around two swizzled shared-memory transposes
-// (srht_block128_core in ns_srht_core.cuh), and adds the s sampled values
-// Z_b[lo(r_t)] into its accumulator.  For m' <= 4096 the column is one
-// zero-padded block: H's entries depend only on popcount(i & j), so padding to
-// 4096 leaves the sampled rows unchanged.
+// with hi(r) = r >> 12, lo(r) = r & 4095.  A CTA holds a block in registers,
+// takes the 12 butterfly levels in three register phases around two swizzled
+// shared-memory transposes, and adds the s sampled values Z_b[lo(r_t)] into its
+// accumulator: 256 threads of 16 values for whole columns
+// (srht_f64_chunk256_kernel), 128 threads of 32 values for row windows
+// (srht_f64_chunk128_kernel over srht_block128_core in ns_srht_core.cuh).  The
+// two forms agree bit for bit on the same chunks.  For m' <= 4096 the column is
+// one zero-padded block: H's entries depend only on popcount(i & j), so padding
+// to 4096 leaves the sampled rows unchanged.
 #include <cmath>
 #include "ns_device.cuh"
 #include "ns_internal.h"
@@ -39,7 +45,7 @@ SrhtGeom srht_geom(int64_t m, int64_t n) {
     while (chunk > g.nblk) chunk /= 2;
     g.chunk = chunk;
     g.nchunk = g.nblk / chunk;
-    g.fx_bits = 63 - kBlockLog - ceil_log2(chunk) - 1;
+    g.fx_bits = 63 - kBlockLog - ceil_log2(chunk);
     g.sign_words = (mp > kBlock ? mp : kBlock) / 32;
     return g;
 }
@@ -395,20 +401,166 @@ cudaError_t launch_srht_f32(const float *A, int64_t m, int64_t n, int64_t lda, i
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------ 256-thread form ----
+// The block pipeline with 256 threads of 16 values: four CTAs of eight warps
+// share an SM (twice the warps of the 128-thread form, for the same shared
+// memory), which hides the shared-memory and dependent-add latencies that bind
+// the 128-thread form.  H runs in three register phases of four levels around
+// two transposes:
+//   layout A: register k holds element (k & 1) | (t << 1) | ((k >> 1) << 9)  (index bits 0, 9..11)
+//   layout B: (t & 1) | (k << 1) | ((t >> 1) << 5)                           (bits 1..4)
+//   layout C: (t & 31) | (k << 5) | ((t >> 5) << 9)                          (bits 5..8)
+// Entry i sits at swz5(i) = i ^ (((i >> 5) & 15) << 1) in shared memory.  The
+// 16-byte stores of layout A cover 256 consecutive bytes per half warp; the
+// lanes reading one register of layout B differ in index bits 0 and 5..8,
+// which swz5 spreads over all banks; a register of layout C is 32 consecutive
+// entries.  Each thread's addresses are one base XOR a constant per register.
+// A thread stores each layout back to the entries it read it from, so only
+// the A -> B and B -> C hand-overs and the publication need barriers.  The
+// quantisation and the adds are the 128-thread form's, so the result is that
+// form's, bit for bit.
+__device__ __forceinline__ int swz5(int i) { return i ^ (((i >> 5) & 15) << 1); }
+
+__device__ __forceinline__ void fwht16(long long (&z)[16]) {
+#pragma unroll
+    for (int h = 1; h < 16; h <<= 1) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if ((k & h) == 0) {
+                const long long a = z[k], c = z[k + h];
+                z[k] = a + c;
+                z[k + h] = a - c;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 4) srht_f64_chunk256_kernel(const double *__restrict__ A, int64_t m,
+                                                                    int64_t n, int64_t lda, int64_t s, int chunk,
+                                                                    int64_t nchunk, int P,
+                                                                    const uint32_t *__restrict__ sign_words,
+                                                                    const int32_t *__restrict__ rows,
+                                                                    double *__restrict__ partial, int32_t *status,
+                                                                    int vec_ok) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    long long *Zs = (long long *)smem_raw;   // 4096
+    long long *acc = Zs + kBlock;            // s
+    uint32_t *sgn = (uint32_t *)(acc + s);   // 128
+    int *red = (int *)(sgn + 128);           // 8
+    int32_t *rows_s = (int32_t *)(red + 8);  // s
+
+    const int t = threadIdx.x;
+    const int64_t item = blockIdx.x;
+    const int64_t c = item / nchunk, ch = item - c * nchunk;
+    const double *Acol = A + c * lda;
+    for (int64_t i = t; i < s; i += 256) {
+        const uint32_t r = (uint32_t)rows[i];
+        rows_s[i] = (int32_t)((r >> kBlockLog << kBlockLog) | (uint32_t)swz5((int)(r & (kBlock - 1))));
+        acc[i] = 0;
+    }
+    // byte offsets: layout A stores (plus 4096 kk), layout B (XOR 16 k), layout C (XOR 272 k)
+    const uint32_t zs = (uint32_t)__cvta_generic_to_shared(Zs);
+    const uint32_t offA = 8u * (uint32_t)swz5(2 * t);
+    const uint32_t offB = 8u * (uint32_t)swz5((t & 1) | ((t >> 1) << 5));
+    const uint32_t offC = 8u * (uint32_t)((t & 31) | ((t >> 5) << 9));
+    __syncthreads();
+
+    int Erun = 0, nonfinite = 0;
+    for (int bl = 0; bl < chunk; ++bl) {
+        const int64_t b = ch * chunk + bl;
+        const int64_t base = b * kBlock;
+        if (t < 128) sgn[t] = sign_words[(base >> 5) + t];
+        if (t == 0 && bl + 1 < chunk && vec_ok && base + 2 * kBlock <= m)  // the next block, into L2
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(Acol + base + kBlock),
+                         "r"((uint32_t)(kBlock * 8))
+                         : "memory");
+        long long z[16];
+        if (vec_ok && base + kBlock <= m) {
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const double2 v = __ldcs((const double2 *)(Acol + base + 2 * t + 512 * kk));
+                z[2 * kk] = __double_as_longlong(v.x);
+                z[2 * kk + 1] = __double_as_longlong(v.y);
+            }
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const int64_t i0 = base + 2 * t + 512 * kk;
+                z[2 * kk] = (i0 < m) ? __double_as_longlong(__ldcs(Acol + i0)) : 0;
+                z[2 * kk + 1] = (i0 + 1 < m) ? __double_as_longlong(__ldcs(Acol + i0 + 1)) : 0;
+            }
+        }
+        unsigned int hmax = 0x00100000u;  // biased exponent 1
+#pragma unroll
+        for (int k = 0; k < 16; ++k) hmax = max(hmax, (unsigned int)((unsigned long long)z[k] >> 32) & 0x7FF00000u);
+        hmax = warp_max(hmax);
+        if ((t & 31) == 0) red[t >> 5] = (int)(hmax >> 20);
+        __syncthreads();  // also publishes sgn[]; the previous block's gather is complete
+        int emax = red[0];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) emax = max(emax, red[q]);
+        if (emax == 0x7FF) nonfinite = 1;
+        if (emax > Erun) {
+            if (Erun > 0) {
+                const int d = emax - Erun;
+                for (int64_t i = t; i < s; i += 256) acc[i] = (d >= 63) ? (acc[i] >> 63) : (acc[i] >> d);
+            }
+            Erun = emax;
+        }
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            const uint32_t sw = sgn[16 * kk + (t >> 4)] >> (2 * (t & 15));
+            srht_quant2(z[2 * kk], z[2 * kk + 1], sw, Erun, P);
+        }
+        fwht16(z);  // index bits 0, 9..11
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk)
+            asm volatile("st.shared.v2.s64 [%0], {%1, %2};" ::"r"(zs + offA + 4096u * kk), "l"(z[2 * kk]),
+                         "l"(z[2 * kk + 1])
+                         : "memory");
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) asm volatile("ld.shared.s64 %0, [%1];" : "=l"(z[k]) : "r"(zs + (offB ^ (16u * k))) : "memory");
+        fwht16(z);  // index bits 1..4, stored back in place (no other thread reads these entries now)
+#pragma unroll
+        for (int k = 0; k < 16; ++k) asm volatile("st.shared.s64 [%0], %1;" ::"r"(zs + (offB ^ (16u * k))), "l"(z[k]) : "memory");
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) asm volatile("ld.shared.s64 %0, [%1];" : "=l"(z[k]) : "r"(zs + (offC ^ (272u * k))) : "memory");
+        fwht16(z);  // index bits 5..8, published in place
+#pragma unroll
+        for (int k = 0; k < 16; ++k) asm volatile("st.shared.s64 [%0], %1;" ::"r"(zs + (offC ^ (272u * k))), "l"(z[k]) : "memory");
+        __syncthreads();
+        for (int64_t i = t; i < s; i += 256) {
+            const uint32_t pr = (uint32_t)rows_s[i];  // (hi(r) << 12) | swz5(lo(r))
+            const long long v = Zs[pr & (kBlock - 1)];
+            const long long msk = -(long long)(__popc(pr >> kBlockLog & (uint32_t)b) & 1);
+            acc[i] += (v ^ msk) - msk;
+        }
+        // the next block's first barrier orders this gather before Zs is reused
+    }
+    __syncthreads();
+    const double scale = ldexp(1.0, Erun - 1022 - P);
+    double *out = partial + (ch * n + c) * s;
+    for (int64_t i = t; i < s; i += 256) out[i] = (double)acc[i] * scale;
+    if (nonfinite) set_status(status, NS_ERR_NONFINITE);
+}
+
+static size_t srht_f64_smem256(int64_t s) { return (size_t)kBlock * 8 + (size_t)s * 8 + 128 * 4 + 8 * 4 + (size_t)s * 4; }
+
 size_t srht_f64_smem(int64_t s) { return (size_t)kBlock * 8 + (size_t)s * 8 + 64 * 8 + 128 * 4 + 16 + (size_t)s * 4; }
 
 cudaError_t launch_srht_f64(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, const SrhtWork &w,
                             double *SA, int32_t *status, cudaStream_t st) {
     const SrhtGeom g = srht_geom(m, n);
-    const size_t smem = srht_f64_smem(s);
-    cudaError_t e = cudaFuncSetAttribute(srht_f64_chunk128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = srht_f64_smem256(s);
+    cudaError_t e = cudaFuncSetAttribute(srht_f64_chunk256_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const int vec_ok = ((((uintptr_t)A) & 15) == 0 && (lda & 1) == 0) ? 1 : 0;
     const int64_t items = n * g.nchunk;
-    srht_f64_chunk128_kernel<<<(unsigned)items, 128, smem, st>>>(A, m, n, lda, s, g.chunk, g.nchunk, g.fx_bits,
-                                                                 w.sign_words, w.rows, w.partial, status, vec_ok,
-                                                                 0, 0, g.nblk);
+    srht_f64_chunk256_kernel<<<(unsigned)items, 256, smem, st>>>(A, m, n, lda, s, g.chunk, g.nchunk, g.fx_bits,
+                                                                 w.sign_words, w.rows, w.partial, status, vec_ok);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int threads = 256;
@@ -438,7 +590,7 @@ SrhtRowsGeom srht_rows_geom(int64_t m_total, int64_t lo, int64_t hi, int64_t n) 
     while (chunk > 1 && chunk > nb) chunk /= 2;
     g.chunk = chunk;
     g.nchunk = (nb + chunk - 1) / chunk;
-    g.fx_bits = 63 - kBlockLog - ceil_log2(chunk) - 1;
+    g.fx_bits = 63 - kBlockLog - ceil_log2(chunk);
     g.sign_words = (mp > kBlock ? mp : kBlock) / 32;
     return g;
 }

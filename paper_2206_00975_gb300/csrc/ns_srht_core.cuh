@@ -1,7 +1,8 @@
-// ns_srht_core.cuh -- the per-block pipelines of the FP64 SRHT (see ns_srht.cu):
-// the 64-thread form (srht_f64_block, used by the batched kernel) and the
-// 128-thread form (srht_block128_core + srht_f64_block128, used by the
-// single-problem chunk kernel and by pass 1 of the H-RHT).
+// ns_srht_core.cuh -- the per-block pipelines of the FP64 SRHT (see ns_srht.cu)
+// and their shared quantiser (srht_quant2): the 64-thread form (srht_f64_block,
+// used by the batched kernel) and the 128-thread form (srht_block128_core +
+// srht_f64_block128, used by the row-window chunk kernel and by pass 1 of the
+// H-RHT).  The 256-thread whole-column kernel lives in ns_srht.cu.
 #pragma once
 #include "ns_device.cuh"
 #include "ns_internal.h"
@@ -25,6 +26,51 @@ __device__ __forceinline__ void fwht64(long long (&z)[64]) {
                 z[k] = a + b;
                 z[k + h] = a - b;
             }
+        }
+    }
+}
+
+// Quantisation of two entries of a block (the raw IEEE words in a, b, the
+// signs of D in bits 0 and 1 of sw) onto the block's fixed-point grid
+// 2^(Erun - 1022 - P): the magnitude truncated toward zero, then the sign of
+// the entry times d_i in two's complement.  A magnitude stays below 2^P.
+// While Erun >= P no subnormal can reach the grid, so every entry takes the
+// hidden bit and the 64-bit shift runs on 32-bit words (an entry 64 or more
+// binades below the grid shifts to 0); below that, subnormals are handled
+// exactly (exponent 1, no hidden bit).  Erun and P are uniform over the block,
+// so the branch is too.
+__device__ __forceinline__ void srht_quant2(long long &a, long long &b, uint32_t sw, int Erun, int P) {
+    if (Erun >= P) {
+        const int C = Erun + 53 - P;  // shift = C - e
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const unsigned long long raw = (unsigned long long)(h ? b : a);
+            const uint32_t whi = (uint32_t)(raw >> 32), wlo = (uint32_t)raw;
+            const uint32_t sh = (uint32_t)(C - (int)((whi >> 20) & 0x7FFu));
+            const uint32_t mhi = (whi & 0x000FFFFFu) | 0x00100000u;
+            uint32_t qhi, qmid, qlo;
+            asm("shr.b32 %0, %1, %2;" : "=r"(qhi) : "r"(mhi), "r"(sh));  // 0 for sh >= 32
+            asm("shf.r.clamp.b32 %0, %1, %2, %3;" : "=r"(qmid) : "r"(wlo), "r"(mhi), "r"(sh));
+            const uint32_t sh2 = (uint32_t)max((int)sh - 32, 0);
+            asm("shr.b32 %0, %1, %2;" : "=r"(qlo) : "r"(qmid), "r"(sh2));
+            const long long msk = (long long)((int)(whi ^ (sw << (31 - h))) >> 31);
+            const long long q = (long long)(((unsigned long long)qhi << 32) | qlo);
+            (h ? b : a) = (q ^ msk) - msk;
+        }
+    } else {
+        const int sh1b = Erun + 53 - P;  // shift = sh1b - max(e, 1)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const unsigned long long raw = (unsigned long long)(h ? b : a);
+            const uint32_t hi = (uint32_t)(raw >> 32);
+            const int e = (int)((hi >> 20) & 0x7FF), e1 = max(e, 1);
+            const uint32_t sh = (uint32_t)(sh1b - e1);
+            const uint32_t mhi = (hi & 0x000FFFFFu) | ((uint32_t)(1 - (e1 - e)) << 20);
+            const unsigned long long mant = ((unsigned long long)mhi << 32) | (uint32_t)raw;
+            unsigned long long q;
+            asm("shr.b64 %0, %1, %2;" : "=l"(q) : "l"(mant), "r"(sh));  // clamps shifts >= 64 to 0
+            const long long msk = (long long)((int)(hi ^ (sw << (31 - h))) >> 31);
+            (h ? b : a) = ((long long)q ^ msk) - msk;
         }
     }
 }
@@ -83,27 +129,10 @@ __device__ __forceinline__ void srht_f64_block(const double *__restrict__ Acol, 
         }
         Erun = emax;
     }
-    // quantise: magnitude rounded to nearest at 2^(Erun - 1022 - P), sign of the
-    // entry times d_i, two's complement (subnormals exact: exponent 1, no
-    // hidden bit; shifts of 64 or more give 0)
-    const int sh1b = Erun + 52 - P;  // shift - 1 = sh1b - max(e, 1)
 #pragma unroll
     for (int kk = 0; kk < 32; ++kk) {
         const uint32_t sw = sgn[4 * kk + (t >> 4)] >> (2 * (t & 15));
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const unsigned long long raw = (unsigned long long)z[2 * kk + h];
-            const uint32_t hi = (uint32_t)(raw >> 32);
-            const int e = (int)((hi >> 20) & 0x7FF), e1 = max(e, 1);
-            const uint32_t sh1 = (uint32_t)(sh1b - e1);
-            const uint32_t mhi = (hi & 0x000FFFFFu) | ((uint32_t)(1 - (e1 - e)) << 20);
-            const unsigned long long mant = ((unsigned long long)mhi << 32) | (uint32_t)raw;
-            unsigned long long q1;
-            asm("shr.b64 %0, %1, %2;" : "=l"(q1) : "l"(mant), "r"(sh1));  // clamps shifts >= 64 to 0
-            const unsigned long long q = (q1 + 1ull) >> 1;
-            const long long msk = (long long)(int)((hi ^ (sw << (31 - h))) & 0x80000000u) >> 31;
-            z[2 * kk + h] = ((long long)q ^ msk) - msk;
-        }
+        srht_quant2(z[2 * kk], z[2 * kk + 1], sw, Erun, P);
     }
     fwht64(z);
 #pragma unroll
@@ -117,10 +146,9 @@ __device__ __forceinline__ void srht_f64_block(const double *__restrict__ Acol, 
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < 64; ++k) z[k] = Zs[swz(l2_elem(t, k))];
-    __syncthreads();
     fwht64(z);
 #pragma unroll
-    for (int k = 0; k < 64; ++k) Zs[swz(l2_elem(t, k))] = z[k];  // all of them: cheaper than testing
+    for (int k = 0; k < 64; ++k) Zs[swz(l2_elem(t, k))] = z[k];  // in place; all of them: cheaper than testing
     __syncthreads();
     for (int64_t i = t; i < s; i += 64) {
         const uint32_t pr = (uint32_t)rows_s[i];  // srht_pack_row: (hi(r) << 12) | swz(lo(r))
@@ -156,12 +184,16 @@ __device__ __forceinline__ void fwht32(long long (&z)[32]) {
 //   layout C: (t & 63) | (k << 6) | ((t >> 6) << 11)  (bits 6, 7: the first
 //     two register bits only; bits 8..10 are done).
 // The lanes of a warp reading one register of layout B (C) differ in index
-// bits 0, 6..9 (0..4), which swz spreads over all banks.  Exact integer adds:
-// the result is the 64-thread form's, bit for bit.
+// bits 0, 6..9 (0..4), which swz spreads over all banks.  The quantisation
+// is the 64-thread form's (srht_quant2) and the adds are exact integer adds:
+// for the same blocks and exponent the result is that form's, bit for bit.
 //
 // srht_block128_core runs the load, the quantisation at Erun (rescaling
 // acc[0..s) when Erun grows) and all 12 levels, and returns Z_b in registers
-// in layout C; the shared-memory reads are complete on return.
+// in layout C.  Each thread reads a layout-B or layout-C register set from
+// entries that only it rewrites (the transposes are in place), so no barrier
+// separates a thread's reads of a layout from its stores back to it; a caller
+// that stores Z_b elsewhere must synchronise before reusing Zs.
 //
 // Row window: the column holds global rows [lo, m) of the padded column and
 // Acol points at global row lo (lo = 0 for a whole column); rows outside the
@@ -212,24 +244,10 @@ __device__ __forceinline__ void srht_block128_core(const double *__restrict__ Ac
         }
         Erun = emax;
     }
-    const int sh1b = Erun + 52 - P;
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
         const uint32_t sw = sgn[8 * kk + (t >> 4)] >> (2 * (t & 15));
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const unsigned long long raw = (unsigned long long)z[2 * kk + h];
-            const uint32_t hi = (uint32_t)(raw >> 32);
-            const int e = (int)((hi >> 20) & 0x7FF), e1 = max(e, 1);
-            const uint32_t sh1 = (uint32_t)(sh1b - e1);
-            const uint32_t mhi = (hi & 0x000FFFFFu) | ((uint32_t)(1 - (e1 - e)) << 20);
-            const unsigned long long mant = ((unsigned long long)mhi << 32) | (uint32_t)raw;
-            unsigned long long q1;
-            asm("shr.b64 %0, %1, %2;" : "=l"(q1) : "l"(mant), "r"(sh1));
-            const unsigned long long q = (q1 + 1ull) >> 1;
-            const long long msk = (long long)(int)((hi ^ (sw << (31 - h))) & 0x80000000u) >> 31;
-            z[2 * kk + h] = ((long long)q ^ msk) - msk;
-        }
+        srht_quant2(z[2 * kk], z[2 * kk + 1], sw, Erun, P);
     }
     fwht32(z);  // index bits 0, 8..11
 #pragma unroll
@@ -243,14 +261,12 @@ __device__ __forceinline__ void srht_block128_core(const double *__restrict__ Ac
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < 32; ++k) z[k] = Zs[swz((t & 1) | (k << 1) | ((t >> 1) << 6))];
-    __syncthreads();
-    fwht32(z);  // index bits 1..5
+    fwht32(z);  // index bits 1..5 (stored back in place: each thread rewrites the entries it read)
 #pragma unroll
     for (int k = 0; k < 32; ++k) Zs[swz((t & 1) | (k << 1) | ((t >> 1) << 6))] = z[k];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < 32; ++k) z[k] = Zs[swz((t & 63) | (k << 6) | ((t >> 6) << 11))];
-    __syncthreads();
 #pragma unroll
     for (int h = 1; h <= 2; h <<= 1) {  // index bits 6, 7
 #pragma unroll

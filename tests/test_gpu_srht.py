@@ -81,6 +81,41 @@ def test_srht_integer_inputs_bitexact(api, m, n, s):
     assert np.array_equal(SA, O.srht(11, s, A))
 
 
+@pytest.mark.parametrize("m,n,s", [((1 << 20) - 3, 128, 1000), (1 << 20, 130, 1024), ((1 << 19) + 4097, 64, 1025),
+                                   ((1 << 18) + 1, 40, 100)])
+def test_srht_sketch_sampled_columns(api, m, n, s):
+    # chunked geometries (up to 16 blocks per fixed-point accumulator, ragged
+    # last block, s on both sides of the pruned kernel's 1024) compared with the
+    # oracle on a few columns; the sketch acts on each column alone
+    g = torch.Generator(device="cuda")
+    g.manual_seed(m + n + s)
+    A = torch.randn((n, m), dtype=torch.float64, device="cuda", generator=g).t()
+    A = A * torch.exp(torch.linspace(-3.0, 3.0, n, dtype=torch.float64, device="cuda"))[None, :]
+    d = api.desc(api.NS_SRHT, s=s, seed=8)
+    SA = api.ns_sketch(d, A).cpu().numpy()
+    cols = [0, n // 2, n - 1]
+    Ah = A[:, cols].cpu().numpy()
+    ref = O.srht(8, s, Ah)
+    assert np.max(np.abs(SA[:, cols] - ref)) <= 1e-12 * np.linalg.norm(Ah)
+
+
+@pytest.mark.parametrize("m,n,s", [(1 << 12, 3, 64), (1 << 16, 5, 1000), (1 << 18, 9, 1024), (1 << 19, 4, 3000),
+                                   (1 << 20, 256, 1024)])
+def test_srht_block_forms_agree_bitwise(api, m, n, s):
+    # ns_sketch (256-thread block pipeline) and the whole-window share of
+    # ns_sketch_rows (128-thread block pipeline) quantise the same chunks the
+    # same way and add exactly, so for m a power of two (the same chunking)
+    # they agree bit for bit, up to the benchmark's size
+    g = torch.Generator(device="cuda")
+    g.manual_seed(m + s)
+    A = torch.randn((n, m), dtype=torch.float64, device="cuda", generator=g).t()
+    A = A * torch.exp(torch.linspace(-20.0, 20.0, n, dtype=torch.float64, device="cuda"))[None, :]
+    d = api.desc(api.NS_SRHT, s=s, seed=4)
+    a = api.ns_sketch(d, A)
+    b = api.ns_sketch_rows(d, A, 0, m)
+    assert torch.equal(a, b)
+
+
 def test_srht_wide_dynamic_range(api):
     # entries spanning 1e-200..1e+200 in one column: error bound is relative to ||A||_F
     rng = np.random.default_rng(3)
