@@ -1039,7 +1039,11 @@ __device__ void pipe_qr2_cta(const double *Lg, int64_t ldl, const unsigned int *
     }
 }
 
-__global__ void __launch_bounds__(kPipeThreads) hqr_fused_kernel(const double *W, double *U1, int64_t s, int64_t n,
+// At most 80 registers a thread (no spills), so three CTAs fit on an SM: the
+// fused QRs of solves in flight on other streams, and a QR beside the FP32
+// Jacobi phase's cluster, can then be resident together (two per SM made
+// concurrent solves wait for one another's QR or FP32 phase to drain).
+__global__ void __launch_bounds__(kPipeThreads, 3) hqr_fused_kernel(const double *W, double *U1, int64_t s, int64_t n,
                                                                 int64_t nown1, double *u0a, double *cfa,
                                                                 unsigned long long *flag1, double *Lg,
                                                                 unsigned int *rowcnt, double *U2, int64_t nown2,

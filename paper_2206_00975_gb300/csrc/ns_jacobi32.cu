@@ -272,7 +272,10 @@ __device__ __forceinline__ void st_peer_f64(uint32_t addr, double v) {
 // X (n x n FP64, column-major) -> V0 (n x n FP64: the accumulated FP32
 // rotations W, exactly), ctl[0] = 1 if the phase ran (0: it was skipped and V0
 // is not written), ctl[1] = sweeps, ctl[2] = rotations.
-__global__ void __cluster_dims__(kJ32Cta, 1, 1) __launch_bounds__(kJ32Threads, 1)
+// At most 64 registers a thread (no spills): a CTA of the phase then leaves
+// half of its SM's registers, room for a fused-QR CTA of another solve in
+// flight beside it.
+__global__ void __cluster_dims__(kJ32Cta, 1, 1) __maxnreg__(64)
     jacobi32_phase_kernel(const double *__restrict__ X, int64_t n, double *__restrict__ V0, unsigned int *ctl) {
     extern __shared__ __align__(16) float j32_smem[];
     __shared__ double s_nrm[2 * kJ32B];
