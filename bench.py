@@ -749,8 +749,9 @@ def main():
                    "peak_source": peak_kind, "algorithmic_bytes": sketch_bytes}
     dense_roof = {"bound": "alu", "achieved": dense_tf, "peak": fp64_peak, "unit": "TFLOP/s",
                   "frac": dense_tf / fp64_peak, "traffic": None,
-                  "kernel": "dense stage (column order, hqr_pipe x2 with Q2 formed in the second, FP32 Jacobi phase "
-                            "+ FP64 products, jacobi_ring from V = Q2 V0, extract) via ns_solve_sketched",
+                  "kernel": "dense stage (column order, both Householder QRs in one fused launch with Q2 formed in "
+                            "the second, FP32 Jacobi phase + FP64 products and two first-order completions, "
+                            "Gram-matrix check, jacobi_ring from V = Q2 V0, extract) via ns_solve_sketched",
                   "peak_source": "derived: %d SMs x 4 FP64 flop/clk x sampled SM clock" % n_sm,
                   "algorithmic_flops": dflops, "jacobi_sweeps_rotations_checks": stats[:3],
                   "fp32_phase_sweeps_rotations": stats[4:6],
