@@ -82,11 +82,12 @@ def test_srht_integer_inputs_bitexact(api, m, n, s):
 
 
 @pytest.mark.parametrize("m,n,s", [((1 << 20) - 3, 128, 1000), (1 << 20, 130, 1024), ((1 << 19) + 4097, 64, 1025),
-                                   ((1 << 18) + 1, 40, 100)])
+                                   ((1 << 18) + 1, 40, 100), (20000, 3, 16384)])
 def test_srht_sketch_sampled_columns(api, m, n, s):
     # chunked geometries (up to 16 blocks per fixed-point accumulator, ragged
-    # last block, s on both sides of the pruned kernel's 1024) compared with the
-    # oracle on a few columns; the sketch acts on each column alone
+    # last block) and the largest s the library takes (its sampled sums fill
+    # most of a CTA's shared memory) compared with the oracle on a few columns;
+    # the sketch acts on each column alone
     g = torch.Generator(device="cuda")
     g.manual_seed(m + n + s)
     A = torch.randn((n, m), dtype=torch.float64, device="cuda", generator=g).t()
