@@ -99,38 +99,40 @@ __global__ void __launch_bounds__(256) hrht_meta_kernel(uint64_t seed, int64_t s
 }
 
 // ----------------------------------------------------------------- pass 1 ----
-// One (column, block) per CTA of 128 threads: Z_b in int64 at quantum
-// 2^(E_b - 1022 - P1), E_b the block's largest biased exponent.  blk gets
-// (quantum exponent, exponent above the largest |Z|; INT_MIN for Z_b = 0).
-__global__ void __launch_bounds__(128, 4) hrht_block_kernel(const double *__restrict__ A, int64_t m, int64_t lda,
+// One (column, block) per CTA of 256 threads (srht_block256_core): Z_b in int64
+// at quantum 2^(E_b - 1022 - P1), E_b the block's largest biased exponent.  blk
+// gets (quantum exponent, exponent above the largest |Z|; INT_MIN for Z_b = 0).
+__global__ void __launch_bounds__(256, 4) hrht_block_kernel(const double *__restrict__ A, int64_t m, int64_t lda,
                                                             int64_t B, const uint32_t *__restrict__ sign_words,
                                                             long long *__restrict__ Z, int2 *__restrict__ blk,
                                                             int32_t *status, int vec_ok) {
     __shared__ __align__(16) long long Zs[kBlock];
     __shared__ uint32_t sgn[128];
-    __shared__ int red[4];
+    __shared__ int red[8];
     const int t = threadIdx.x;
     const int64_t item = blockIdx.x;
     const int64_t c = item / B, b = item - c * B;
     int Erun = 0, nonfinite = 0;
-    long long z[32];
-    srht_block128_core(A + c * lda, m, 0, b, kHrhtP1, sign_words, Zs, nullptr, sgn, red, vec_ok, Erun, nonfinite,
+    long long z[16];
+    srht_block256_core(A + c * lda, m, 0, b, kHrhtP1, sign_words, Zs, nullptr, sgn, red, vec_ok, Erun, nonfinite,
                        false, z);
     unsigned long long mx = 0;
 #pragma unroll
-    for (int k = 0; k < 32; ++k) {
+    for (int k = 0; k < 16; ++k) {
         const unsigned long long a = (unsigned long long)(z[k] < 0 ? -z[k] : z[k]);
         mx = mx > a ? mx : a;
     }
     int bl = mx ? 64 - __clzll((long long)mx) : 0;
     bl = warp_max(bl);
-    if ((t & 31) == 0) red[t >> 5] = bl;
+    if ((t & 31) == 0) red[t >> 5] = bl;  // the core's later barriers ordered every read of the exponents
     long long *out = Z + (item << kBlockLog);
 #pragma unroll
-    for (int k = 0; k < 32; ++k) out[layout_c(t, k)] = z[k];
+    for (int k = 0; k < 16; ++k) out[(t & 31) | (k << 5) | ((t >> 5) << 9)] = z[k];  // layout C
     __syncthreads();
     if (t == 0) {
-        const int bmax = max(max(red[0], red[1]), max(red[2], red[3]));
+        int bmax = red[0];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) bmax = max(bmax, red[q]);
         const int qx = Erun - 1022 - kHrhtP1;
         blk[item] = make_int2(qx, bmax ? qx + bmax : INT_MIN);
     }
@@ -379,7 +381,7 @@ cudaError_t launch_hrht_f64(uint64_t seed, const double *A, int64_t m, int64_t n
                                                            w.cmax);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int vec_ok = ((((uintptr_t)A) & 15) == 0 && (lda & 1) == 0) ? 1 : 0;
-    hrht_block_kernel<<<(unsigned)(n * g.B), 128, 0, st>>>(A, m, lda, g.B, w.sign_words, w.Z, w.blk, status, vec_ok);
+    hrht_block_kernel<<<(unsigned)(n * g.B), 256, 0, st>>>(A, m, lda, g.B, w.sign_words, w.Z, w.blk, status, vec_ok);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // two stages where shared memory allows (s up to ~9000 with B = 4096)
     const size_t cap = (size_t)200 * 1024;

@@ -1,8 +1,9 @@
 // ns_srht_core.cuh -- the per-block pipelines of the FP64 SRHT (see ns_srht.cu)
 // and their shared quantiser (srht_quant2): the 64-thread form (srht_f64_block,
-// used by the batched kernel) and the 128-thread form (srht_block128_core +
-// srht_f64_block128, used by the row-window chunk kernel and by pass 1 of the
-// H-RHT).  The 256-thread whole-column kernel lives in ns_srht.cu.
+// used by the batched kernel), the 128-thread form (srht_block128_core +
+// srht_f64_block128, used by the row-window chunk kernel) and the 256-thread
+// form (srht_block256_core, used by the whole-column chunk kernel and by pass 1
+// of the H-RHT).  All three give the same bits for the same blocks.
 #pragma once
 #include "ns_device.cuh"
 #include "ns_internal.h"
@@ -302,6 +303,117 @@ __device__ __forceinline__ void srht_f64_block128(const double *__restrict__ Aco
         acc[i] += (v ^ msk) - msk;
     }
     __syncthreads();
+}
+
+// The block pipeline with 256 threads of 16 values: four CTAs of eight warps
+// share an SM (twice the warps of the 128-thread form, for the same shared
+// memory), which hides the shared-memory and dependent-add latencies that bind
+// the 128-thread form.  H runs in three register phases of four levels around
+// two transposes:
+//   layout A: register k holds element (k & 1) | (t << 1) | ((k >> 1) << 9)  (index bits 0, 9..11)
+//   layout B: (t & 1) | (k << 1) | ((t >> 1) << 5)                           (bits 1..4)
+//   layout C: (t & 31) | (k << 5) | ((t >> 5) << 9)                          (bits 5..8)
+// Entry i sits at swz5(i) = i ^ (((i >> 5) & 15) << 1) in shared memory.  The
+// 16-byte stores of layout A cover 256 consecutive bytes per half warp; the
+// lanes reading one register of layout B differ in index bits 0 and 5..8,
+// which swz5 spreads over all banks; a register of layout C is 32 consecutive
+// entries.  Each thread's addresses are one base XOR a constant per register.
+// A thread writes each layout back to the entries it read it from, so only
+// the A -> B and B -> C hand-overs need barriers.  The quantisation
+// (srht_quant2) and the adds are the 128-thread form's, so the result is that
+// form's, bit for bit.
+__device__ __forceinline__ int swz5(int i) { return i ^ (((i >> 5) & 15) << 1); }
+
+__device__ __forceinline__ void fwht16(long long (&z)[16]) {
+#pragma unroll
+    for (int h = 1; h < 16; h <<= 1) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if ((k & h) == 0) {
+                const long long a = z[k], c = z[k + h];
+                z[k] = a + c;
+                z[k + h] = a - c;
+            }
+        }
+    }
+}
+
+// srht_block256_core: block b of the column Acol (rows >= m read as zero):
+// the load (and, with prefetch_next, a bulk L2 prefetch of block b + 1), the
+// largest exponent (a barrier that also publishes the sign words and orders
+// the caller's previous use of Zs), the quantisation at Erun (rescaling
+// acc[0..s) when Erun grows), all 12 levels; Z_b is returned in registers in
+// layout C, read from entries of Zs that only this thread rewrites.  Zs holds
+// 4096 int64, sgn 128 words, red 8 ints.
+__device__ __forceinline__ void srht_block256_core(const double *__restrict__ Acol, int64_t m, int64_t s, int64_t b,
+                                                   int P, const uint32_t *__restrict__ sign_words, long long *Zs,
+                                                   long long *acc, uint32_t *sgn, int *red, int vec_ok, int &Erun,
+                                                   int &nonfinite, bool prefetch_next, long long (&z)[16]) {
+    const int t = threadIdx.x;
+    const int64_t base = b * kBlock;
+    // shared addresses: layout A stores (plus 4096 kk), layout B (XOR 16 k), layout C (XOR 272 k)
+    const uint32_t zs = (uint32_t)__cvta_generic_to_shared(Zs);
+    const uint32_t offA = 8u * (uint32_t)swz5(2 * t);
+    const uint32_t offB = 8u * (uint32_t)swz5((t & 1) | ((t >> 1) << 5));
+    const uint32_t offC = 8u * (uint32_t)((t & 31) | ((t >> 5) << 9));
+    if (t < 128) sgn[t] = sign_words[(base >> 5) + t];
+    if (t == 0 && prefetch_next && vec_ok && base + 2 * kBlock <= m)  // the next block, into L2
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(Acol + base + kBlock),
+                     "r"((uint32_t)(kBlock * 8))
+                     : "memory");
+    if (vec_ok && base + kBlock <= m) {
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            const double2 v = __ldcs((const double2 *)(Acol + base + 2 * t + 512 * kk));
+            z[2 * kk] = __double_as_longlong(v.x);
+            z[2 * kk + 1] = __double_as_longlong(v.y);
+        }
+    } else {
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            const int64_t i0 = base + 2 * t + 512 * kk;
+            z[2 * kk] = (i0 < m) ? __double_as_longlong(__ldcs(Acol + i0)) : 0;
+            z[2 * kk + 1] = (i0 + 1 < m) ? __double_as_longlong(__ldcs(Acol + i0 + 1)) : 0;
+        }
+    }
+    unsigned int hmax = 0x00100000u;  // biased exponent 1
+#pragma unroll
+    for (int k = 0; k < 16; ++k) hmax = max(hmax, (unsigned int)((unsigned long long)z[k] >> 32) & 0x7FF00000u);
+    hmax = warp_max(hmax);
+    if ((t & 31) == 0) red[t >> 5] = (int)(hmax >> 20);
+    __syncthreads();
+    int emax = red[0];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) emax = max(emax, red[q]);
+    if (emax == 0x7FF) nonfinite = 1;
+    if (emax > Erun) {
+        if (Erun > 0) {
+            const int d = emax - Erun;
+            for (int64_t i = t; i < s; i += 256) acc[i] = (d >= 63) ? (acc[i] >> 63) : (acc[i] >> d);
+        }
+        Erun = emax;
+    }
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+        const uint32_t sw = sgn[16 * kk + (t >> 4)] >> (2 * (t & 15));
+        srht_quant2(z[2 * kk], z[2 * kk + 1], sw, Erun, P);
+    }
+    fwht16(z);  // index bits 0, 9..11
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk)
+        asm volatile("st.shared.v2.s64 [%0], {%1, %2};" ::"r"(zs + offA + 4096u * kk), "l"(z[2 * kk]),
+                     "l"(z[2 * kk + 1])
+                     : "memory");
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) asm volatile("ld.shared.s64 %0, [%1];" : "=l"(z[k]) : "r"(zs + (offB ^ (16u * k))) : "memory");
+    fwht16(z);  // index bits 1..4, stored back in place
+#pragma unroll
+    for (int k = 0; k < 16; ++k) asm volatile("st.shared.s64 [%0], %1;" ::"r"(zs + (offB ^ (16u * k))), "l"(z[k]) : "memory");
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) asm volatile("ld.shared.s64 %0, [%1];" : "=l"(z[k]) : "r"(zs + (offC ^ (272u * k))) : "memory");
+    fwht16(z);  // index bits 5..8
 }
 
 // in-register Walsh-Hadamard transform of 64 FP32 values (Sylvester order on
