@@ -223,10 +223,8 @@ __global__ void __launch_bounds__(kBatchThreads) batched_dense_kernel(const ns_p
                                                                       unsigned long long *counters, int32_t *status) {
     extern __shared__ double dsh[];  // xs (smax), nrm, nref (nmax each)
     __shared__ long long prob_sh;
-    __shared__ int src_sh;
     __shared__ long long bk[32];
-    __shared__ int bi_sh[32];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x;
     while (true) {
         if (tid == 0) prob_sh = (long long)atomicAdd(counters + 1, 1ull);
         __syncthreads();
