@@ -128,6 +128,24 @@ def test_srht_wide_dynamic_range(api):
     assert np.max(np.abs(SA - ref)) <= 1e-12 * np.linalg.norm(A)
 
 
+def test_srht_tiny_and_subnormal_entries(api):
+    # columns whose largest entry lies below 2^(P - 1023) (about 1e-294) take
+    # the quantiser's exact-subnormal path; subnormal entries are mixed in.
+    # Norms are taken on scaled copies (squares of 1e-309 underflow).
+    rng = np.random.default_rng(12)
+    m, n, s = 20000, 3, 256
+    A = rng.standard_normal((m, n)) * 1e-300
+    A[::7, 1] = 5e-324 * rng.integers(-1000, 1001, size=A[::7, 1].shape)
+    A[:, 2] *= 1e-9
+    d = api.desc(api.NS_SRHT, s=s, seed=6)
+    SA = api.ns_sketch(d, to_dev(api, A)).cpu().numpy()
+    ref = O.srht(6, s, A)
+    for c in range(n):
+        nrm = np.linalg.norm(A[:, c] * 2.0 ** 1000) * 2.0 ** -1000
+        assert nrm > 0
+        assert np.max(np.abs(SA[:, c] - ref[:, c])) <= 1e-12 * nrm, c
+
+
 def test_srht_exact_null_vector_gpu(api):
     rng = np.random.default_rng(2)
     m, n = 6000, 6
