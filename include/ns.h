@@ -66,7 +66,11 @@ typedef enum {
 
 typedef enum { NS_F64 = 0, NS_F32 = 1 } ns_dtype;
 
-/* Arithmetic used to form SA.  QR and Jacobi always run in FP64. */
+/* Arithmetic used to form SA.  The dense stage does not depend on it: the QRs
+ * run in FP64, and the one-sided Jacobi takes its linear phase in FP32 (graded
+ * rotations accumulated exactly) and finishes in FP64 (first-order completions,
+ * a Gram-matrix convergence test and, where pairs remain, FP64 sweeps), so V
+ * and sigma carry FP64 accuracy. */
 typedef enum {
     NS_PREC_FP64 = 0,        /* exact +-1 transforms on a 64-bit fixed-point
                                 image of A; FP64 results */
