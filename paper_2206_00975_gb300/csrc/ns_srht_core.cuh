@@ -317,7 +317,9 @@ __device__ __forceinline__ void srht_f64_block128(const double *__restrict__ Aco
 // 16-byte stores of layout A cover 256 consecutive bytes per half warp; the
 // lanes reading one register of layout B differ in index bits 0 and 5..8,
 // which swz5 spreads over all banks; a register of layout C is 32 consecutive
-// entries.  Each thread's addresses are one base XOR a constant per register.
+// entries.  A thread's layout-A addresses are one base plus a constant per
+// register pair; its layout-B and layout-C addresses one base XOR a constant
+// per register.
 // A thread writes each layout back to the entries it read it from, so only
 // the A -> B and B -> C hand-overs need barriers.  The quantisation
 // (srht_quant2) and the adds are the 128-thread form's, so the result is that
